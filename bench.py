@@ -1,0 +1,295 @@
+"""Benchmark of the randomized-multiplier GENP solve (Pan, Qian, Yan, arXiv:1406.5802) on GB300.
+
+One step = the whole hot path on one system: draw the Gaussian multiplier G (Def. 4.1), form
+M = A G (Fact 4.1), factor M by blocked GENP (Sec. 3), solve and recover X = G Y, and refine to
+normwise backward error <= 1e-13 (Sec. 7.1), all through the librmge C ABI.
+
+Workload: n = 4096, A = U diag(sigma) V^T with U, V Haar-orthogonal and sigma log-spaced 1 .. 1e-6,
+B 4096 x 16 i.i.d. N(0,1), FP64 (the paper's orthogonal-factor test matrices, Sec. 7.1, at this size).
+Inputs are larger than L2 (A, G and M are 134 MB each).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  N > 1 runs as torchrun replicas: each rank solves its own system,
+no collective on the data path (weak scaling).  --impl reference times the CPU FP64 oracle on the
+host cores instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s & TFLOP/s of A·G GENP solve at backward err ≤1e-13, mixed vs FP64"
+N_SYS, K_RHS, SIGMA_MIN = 4096, 16, 1e-6
+SEED = 0x5EED0000 + 2
+BE_TOL, MAX_ITERS = 1e-13, 10
+# FP64 on GB300 runs on the DFMA pipe: 2 DFMA per clock per SM (measured 1.195 TFLOP/s with an
+# FMA-chain microbenchmark); the nominal peak at the 2070 MHz maximum SM clock is
+# 152 SMs x 2 DFMA x 2 flop x 2.070 GHz = 1.2586 TFLOP/s.
+FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def flops_per_solve(n, k, sweeps):
+    """Algorithmic flops: A G (2n^3 - n^2), GENP (2n^3/3 - n^2/2 - n/6), L, U solves + X = G Y
+    (4n^2 k), and per refinement sweep the residual (2n^2 k) plus the correction (4n^2 k)."""
+    return (2 * n**3 - n**2) + (2 * n**3 / 3 - n**2 / 2 - n / 6) + 4 * n**2 * k + sweeps * 6 * n**2 * k
+
+
+def sample_clocks(stop, out):
+    cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-i", os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]]
+    while not stop.is_set():
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=5)
+            if r.returncode == 0 and r.stdout.strip():
+                out.append([t.strip() for t in r.stdout.strip().splitlines()[0].split(",")])
+        except Exception:
+            pass
+        stop.wait(0.2)
+
+
+def clocks_summary(samples):
+    if not samples:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    sm = [float(s[0]) for s in samples if s[0].replace(".", "").isdigit()]
+    mx = [float(s[1]) for s in samples if s[1].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for s in samples for i in range(4) if len(s) > 3 + i and s[3 + i] == "Active"})
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(samples)}
+
+
+def cpu_oracle_solve(A, B, G, threads):
+    from oracle import oracle as orc
+    orc.set_threads(threads)
+    t0 = time.perf_counter()
+    out = orc.rmge_solve(orc.GAUSSIAN, A, G, B, max_iters=MAX_ITERS, be_tol=BE_TOL)
+    dt = time.perf_counter() - t0
+    return dt, out
+
+
+def host_inputs():
+    from paper_1406_5802_gb300 import workloads as W
+    import numpy as np
+    A, B = W.orthogonal_factor_system(N_SYS, K_RHS, SIGMA_MIN, seed=SEED)
+    return np.ascontiguousarray(A), np.ascontiguousarray(B)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as orc
+    cores = os.cpu_count() or 1
+    A, B = host_inputs()
+    G = orc.gaussian(N_SYS * N_SYS, SEED, 1).reshape(N_SYS, N_SYS)
+    times, sweeps = [], 0
+    for i in range(args.warmup + args.steps):
+        dt, out = cpu_oracle_solve(A, B, G, cores)
+        if i >= args.warmup:
+            times.append(dt)
+            sweeps = out["iters"]
+    t = sum(times) / len(times)
+    value = 1.0 / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "randomized GENP solve, n=4096, 16 RHS, FP64, Gaussian multiplier",
+                       "n": N_SYS, "nrhs": K_RHS, "sigma": "log-spaced 1..1e-6", "precision": "f64"},
+            "tflops": flops_per_solve(N_SYS, K_RHS, sweeps) * value / 1e12,
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full n=4096 oracle solves (plain C, OpenMP rows)"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rmge", choices=["rmge", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1406_5802_gb300 import rmge
+    from paper_1406_5802_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_1406_5802_gb300 import build as B
+    if rank == 0:
+        B.build()
+    barrier()
+    rmge.load_library()
+
+    n, k = N_SYS, K_RHS
+    A, Bm = W.orthogonal_factor_system_torch(n, k, SIGMA_MIN, seed=SEED + 7919 * rank, device="cuda")
+    kind, prec = "gaussian", "f64"
+    ws = rmge.workspace(n, k, kind, prec)
+    G = rmge.empty_multiplier(kind, n, prec)
+    M = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    X = torch.empty(n, k, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    ev_apply = []
+
+    def step(i, record=False):
+        rmge.make_multiplier(kind, n, SEED + i, 1, prec, G=G)
+        if record:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        rmge.apply_multiplier(kind, A, G, prec, M=M, ws=ws)
+        if record:
+            e1.record(stream)
+            ev_apply.append((e0, e1))
+        info, growth = rmge.factor(M, prec, ws=ws)
+        rmge.solve(kind, M, G, Bm, prec, X=X, ws=ws)
+        berr, iters = rmge.refine(kind, A, M, G, Bm, X, prec, MAX_ITERS, BE_TOL, ws=ws)
+        return info, berr, iters
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+
+    stop = threading.Event()
+    clk = []
+    th = threading.Thread(target=sample_clocks, args=(stop, clk), daemon=True)
+    th.start()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    results = []
+    launches0 = rmge.kernel_launches()
+    for i in range(args.steps):
+        results.append(step(args.warmup + i, record=True))
+    launches = rmge.kernel_launches() - launches0
+    t1.record(stream)
+    torch.cuda.synchronize()
+    stop.set()
+    th.join(timeout=2)
+    barrier()
+    ms = t0.elapsed_time(t1)
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+
+    # every timed solve must have met the accuracy target
+    infos = [int(r[0].item()) for r in results]
+    sweeps = [int(r[2].item()) for r in results]
+    bes = [float(r[1][s].item()) for r, s in zip(results, sweeps)]
+    ok = all(i == 0 for i in infos) and all(b <= BE_TOL for b in bes)
+    # independent check of the last solve by the oracle's compensated residual (rank 0)
+    be_oracle = None
+    if rank == 0:
+        from oracle import oracle as orc
+        orc.set_threads(os.cpu_count() or 1)
+        be_oracle = orc.backward_error(A.cpu().numpy(), X.cpu().numpy(), Bm.cpu().numpy())
+
+    solves = args.steps * world
+    value = solves / (ms_max / 1e3)
+    mean_sweeps = sum(sweeps) / len(sweeps)
+    flops = flops_per_solve(n, k, mean_sweeps)
+    apply_ms = sum(a.elapsed_time(b) for a, b in ev_apply) / len(ev_apply)
+    achieved = (2 * n**3 - n**2) / (apply_ms / 1e3) / 1e12
+
+    # end to end through the public API with host buffers: H2D of A and B, D2H of X and berr each step
+    A_h = A.cpu().pin_memory()
+    B_h = Bm.cpu().pin_memory()
+    X_h = torch.empty(n, k, dtype=torch.float64).pin_memory()
+    be_h = torch.empty(MAX_ITERS + 1, dtype=torch.float64).pin_memory()
+    A_d = torch.empty_like(A)
+    B_d = torch.empty_like(Bm)
+    barrier()
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for i in range(args.steps):
+        A_d.copy_(A_h, non_blocking=True)
+        B_d.copy_(B_h, non_blocking=True)
+        rmge.make_multiplier(kind, n, SEED + i, 1, prec, G=G)
+        rmge.apply_multiplier(kind, A_d, G, prec, M=M, ws=ws)
+        rmge.factor(M, prec, ws=ws)
+        rmge.solve(kind, M, G, B_d, prec, X=X, ws=ws)
+        berr, _ = rmge.refine(kind, A_d, M, G, B_d, X, prec, MAX_ITERS, BE_TOL, ws=ws)
+        X_h.copy_(X, non_blocking=True)
+        be_h.copy_(berr, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - te
+    e2e_t = torch.tensor([e2e_s], device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = solves / float(e2e_t.item())
+
+    if rank == 0:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        cpu = None
+        if not args.no_cpu_baseline:
+            cores = os.cpu_count() or 1
+            dt, _ = cpu_oracle_solve(A.cpu().numpy(), Bm.cpu().numpy(), G.cpu().numpy(), cores)
+            cpu = {"value": 1.0 / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                   "sample": "one full n=4096, 16-RHS oracle solve (plain C FP64, OpenMP over rows) with the "
+                             "same A, B and G as the last timed GPU step"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "randomized GENP solve, n=4096, 16 RHS, FP64, Gaussian multiplier",
+                       "n": n, "nrhs": k, "sigma": "log-spaced 1..1e-6", "precision": "f64",
+                       "l2": "inputs larger than L2 (A, G, M 134 MB each)", "replicas": world},
+            "tflops": flops * value / 1e12,
+            "accuracy": {"all_steps_be_le_1e-13": ok, "max_berr": max(bes), "mean_sweeps": mean_sweeps,
+                         "oracle_berr_last": be_oracle},
+            "roofline": {"kernel": "gemm_kernel (M = A G, FP64 DFMA)", "bound": "alu", "achieved": achieved,
+                         "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_ALU_PEAK_TFLOPS,
+                         "traffic": None,
+                         "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (FP64 is not in "
+                                        "MEASURED_PEAKS.json)",
+                         "apply_ms": apply_ms},
+            "e2e": {"value": e2e_value, "unit": "solves/s",
+                    "h2d_bytes_per_step": (A.numel() + Bm.numel()) * 8,
+                    "d2h_bytes_per_step": (X.numel() + MAX_ITERS + 1) * 8},
+            "gpu_launches": launches,
+            "clocks": clocks_summary(clk),
+            "cpu_baseline": cpu,
+            "hbm_gbs_measured_peak": peaks.get("hbm_gbs"),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * rmge.h -- C ABI of librmge, a single-GPU (GB300, sm_103a) implementation of the
+ * randomized-multiplier GENP solve of Pan, Qian and Yan, "Random multipliers numerically
+ * stabilize Gaussian and block Gaussian elimination" (arXiv:1406.5802).
+ *
+ * The method (Fact 4.1 with F = I, H = G): to solve A X = B, draw a random multiplier G
+ * (Def. 4.1 Gaussian, or a circulant of Sec. 5), form M = A G, factor M = L U by Gaussian
+ * elimination with no pivoting (GENP, eq. (3.1) applied recursively, Sec. 3), solve
+ * L U Y = B, and return X = G Y; refine X by residual correction (Sec. 1.2, Sec. 7.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are row-major with an explicit leading dimension (elements between rows),
+ *   ld >= number of columns.  Element (i, j) of a matrix P with leading dimension ldp is
+ *   P[i * ldp + j].
+ * - Unless a parameter says otherwise, every pointer is caller-owned DEVICE memory (or
+ *   host memory the device can address, e.g. pinned), must stay valid until the work
+ *   enqueued on `stream` has completed, and is never freed or retained by the library.
+ * - The library allocates no memory.  Scratch comes from a caller buffer `ws` of at least
+ *   rmge_workspace_size(...) bytes, 256-byte aligned.  Its contents need not be initialised
+ *   and are undefined after the call.  Two calls that run concurrently need two buffers.
+ * - Every call only validates its arguments and enqueues kernels on `stream` (a
+ *   cudaStream_t; NULL = legacy default stream).  It returns RMGE_OK when all launches were
+ *   accepted.  Numerical outcomes (breakdown step, growth, backward errors, sweep count)
+ *   are written by the kernels to caller memory and are valid once the stream has been
+ *   synchronised; none of them changes the return value.  rmge_refine is the one exception
+ *   to "enqueue only": see its comment.
+ * - No call prints, aborts, throws, or traps on the device.  Argument errors return
+ *   RMGE_ERR_INVALID_ARG and enqueue nothing; a failed launch returns RMGE_ERR_CUDA.
+ * - n >= 1, nrhs >= 1; n <= RMGE_MAX_N.
+ */
+#ifndef RMGE_H
+#define RMGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RMGE_MAX_N 65536
+
+/* Opaque CUDA stream (identical to cudaStream_t), so this header needs no CUDA headers. */
+typedef struct CUstream_st* rmge_stream_t;
+
+typedef enum {
+    RMGE_OK = 0,
+    RMGE_ERR_INVALID_ARG = 1,   /* bad size, leading dimension, pointer or enum; nothing enqueued */
+    RMGE_ERR_BREAKDOWN = 2,     /* a zero or non-finite pivot (Cor. 3.1); only from rmge_refine */
+    RMGE_ERR_GROWTH = 3,        /* reserved */
+    RMGE_ERR_NOT_CONVERGED = 4, /* rmge_refine stopped above be_tol */
+    RMGE_ERR_CUDA = 5,          /* a CUDA launch or copy failed */
+    RMGE_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up (see rmge_refine) */
+    RMGE_ERR_WORKSPACE = 7,     /* ws is NULL, too small or misaligned */
+    RMGE_ERR_UNSUPPORTED = 8    /* valid request this build does not implement (e.g. circulant n not 2^p) */
+} rmge_status;
+
+/* Random multiplier G (Sec. 4-5). */
+typedef enum {
+    RMGE_GAUSSIAN = 0,           /* dense n x n, i.i.d. N(0,1) entries (Def. 4.1) */
+    RMGE_CIRCULANT_GAUSSIAN = 1, /* circulant whose first column is i.i.d. N(0,1) (Sec. 5) */
+    RMGE_CIRCULANT_UNIFORM = 2   /* circulant whose first column is i.i.d. U[-1,1) (Ex. 5.1) */
+} rmge_mult_kind;
+
+/* Precision of the working matrix M and of its factorization. */
+typedef enum {
+    RMGE_F64 = 0,    /* FP64 everywhere */
+    RMGE_F32 = 1,    /* FP32 working matrix and FP32 SIMT trailing updates */
+    RMGE_BF16_TC = 2,/* FP32 working matrix; trailing updates on tcgen05 tensor cores, BF16 operands, FP32 accumulation */
+    RMGE_F16_TC = 3  /* as RMGE_BF16_TC with FP16 operands */
+} rmge_prec;
+
+/*
+ * Multiplier storage (what `G` points to in every call below):
+ * - RMGE_GAUSSIAN: n x n row-major, leading dimension n; FP64 for RMGE_F64, FP32 for the other
+ *   precisions.
+ * - circulant kinds: 3n FP64 values: the first column c[0..n-1], then its DFT u = Omega c
+ *   (Theorem 5.1; Omega = (w^{ij}), w = exp(2 pi sqrt(-1) / n)) stored as n interleaved
+ *   (re, im) pairs.  n must be a power of two, 2 <= n <= 8192.
+ * rmge_multiplier_bytes returns the size (0 for an invalid request).
+ */
+size_t rmge_multiplier_bytes(rmge_mult_kind kind, int64_t n, rmge_prec prec);
+
+/*
+ * Scratch bytes needed by any of the calls below for this (n, nrhs, kind, prec); one buffer of
+ * this size serves all of them.  0 for an invalid request.
+ */
+size_t rmge_workspace_size(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec);
+
+/*
+ * Draw the multiplier (Def. 4.1; Ex. 5.1; Theorem 5.1 for the spectrum).
+ * Entries come from the counter-based generator Philox4x32-10 (Salmon et al., SC'11) with
+ * key = seed and the 64-bit counter words (2,3) = subsequence; entry e of the stream uses
+ * counter words (0,1) = e / 2.  Gaussian entries use Box-Muller on two 53-bit uniforms;
+ * uniform entries are 2 m / 2^53 - 1 for a 53-bit integer m.  Identical (seed, subsequence)
+ * give identical multipliers on every call.  Writes rmge_multiplier_bytes(kind, n, prec)
+ * bytes at G.  The circulant spectrum is computed by an O(n log n) FFT.
+ */
+rmge_status rmge_make_multiplier(rmge_mult_kind kind, int64_t n, uint64_t seed, uint64_t subsequence,
+                                 rmge_prec prec, void* G, rmge_stream_t stream);
+
+/*
+ * M = A G (post-multiplication, Fact 4.1).  A: n x n FP64 (lda).  M: n x n (ldm), FP64 for
+ * RMGE_F64, FP32 otherwise.  Dense G: 2n^3 - n^2 flops (Sec. 5 cost statement).  Circulant G:
+ * each row of A G is the circular cross-correlation of the row of A with c, computed by FFT
+ * (Theorem 5.1), O(n^2 log n).  M must not overlap A.
+ */
+rmge_status rmge_apply_multiplier(rmge_mult_kind kind, int64_t n, const double* A, int64_t lda,
+                                  const void* G, void* M, int64_t ldm, rmge_prec prec,
+                                  void* ws, size_t ws_bytes, rmge_stream_t stream);
+
+/*
+ * In-place blocked GENP of M (eq. (3.1) with pivot blocks of nb columns; by Sec. 3 every
+ * blocking yields the same Schur complements, hence the same L and U as unblocked GENP).
+ * On exit M holds the unit lower factor L strictly below the diagonal and U on and above it.
+ * info (device int32): 0, or the 1-based step of the first zero or non-finite pivot (Cor. 3.1:
+ * a leading block of M is singular); after a breakdown the remaining steps are skipped and M is
+ * partially factored.  growth (device double, may be NULL): max|U_ij| / max|M_ij| over the input
+ * M (the pivot-growth quantity bounded by Thm 3.2 / Remark 3.2); +Inf/NaN if non-finite values
+ * appeared.  prec selects the trailing-update engine and M's type (FP64 or FP32).
+ */
+rmge_status rmge_factor(int64_t n, void* M, int64_t ldm, rmge_prec prec, int32_t* info, double* growth,
+                        void* ws, size_t ws_bytes, rmge_stream_t stream);
+
+/*
+ * X = G U^{-1} L^{-1} B (Fact 4.1: x = H y with (A H) y = b), nrhs right-hand sides.
+ * LU: packed factors from rmge_factor (FP64 for RMGE_F64, FP32 otherwise).  B, X: n x nrhs FP64;
+ * X must not overlap B.  For reduced precisions B is rounded to FP32 for the triangular solves
+ * and X = G Y is accumulated in FP32 then widened.
+ */
+rmge_status rmge_solve(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void* LU, int64_t ldlu,
+                       const void* G, const double* B, int64_t ldb, double* X, int64_t ldx, rmge_prec prec,
+                       void* ws, size_t ws_bytes, rmge_stream_t stream);
+
+/*
+ * Iterative refinement of X (Sec. 1.2 and Sec. 7.1: one or more sweeps of residual
+ * correction).  A sweep computes R = B - A X in FP64, D = G U^{-1} L^{-1} R (in the factor
+ * precision), X <- X + D.  Before each sweep and after the last one the normwise backward error
+ *   eta = max_c ||b_c - A x_c||_inf / (||A||_inf ||x_c||_inf + ||b_c||_inf)
+ * is computed in FP64 on the device; sweeping stops when eta <= be_tol, after max_iters sweeps,
+ * or when eta fails to halve over two sweeps (stagnation).
+ * berr (device double[max_iters + 1], may be NULL): eta before sweep 0, 1, ...; entries after
+ * the last evaluated one are set to -1.  iters (device int32, may be NULL): sweeps performed.
+ * The sweep loop runs on the device state only: every sweep's kernels are enqueued and skip
+ * their work once the stopping test has fired, so the call never synchronises the stream.
+ * Returns RMGE_OK once enqueued; whether eta <= be_tol is read from berr/iters afterwards.
+ */
+rmge_status rmge_refine(rmge_mult_kind kind, int64_t n, int64_t nrhs, const double* A, int64_t lda,
+                        const void* LU, int64_t ldlu, const void* G, const double* B, int64_t ldb,
+                        double* X, int64_t ldx, rmge_prec prec, int32_t max_iters, double be_tol,
+                        double* berr, int32_t* iters, void* ws, size_t ws_bytes, rmge_stream_t stream);
+
+/*
+ * Adjoint of X = A^{-1} B for a loss L with dX = dL/dX given (n x nrhs): reusing the factors of
+ * A G = L U, A^{-T} = L^{-T} U^{-T} G^T, so
+ *   dB = L^{-T} U^{-T} (G^T dX)   (n x nrhs, FP64 out)
+ *   dA = -dB X^T                   (n x n, FP64 out, ldda; may be NULL to skip)
+ * X: the solution (n x nrhs FP64).  dB must not overlap dX.  (The paper has no gradients; this is
+ * the adjoint of the linear solve its method computes.)
+ */
+rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void* LU, int64_t ldlu,
+                                const void* G, const double* X, int64_t ldx, const double* dX, int64_t lddx,
+                                double* dB, int64_t lddb, double* dA, int64_t ldda, rmge_prec prec,
+                                void* ws, size_t ws_bytes, rmge_stream_t stream);
+
+/* Number of kernel launches this process has enqueued through the library so far (host-side
+ * counter; lets a caller count the kernels of a timed region). */
+unsigned long long rmge_kernel_launches(void);
+
+/* Human-readable name of a status code (static string). */
+const char* rmge_status_string(rmge_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RMGE_H */

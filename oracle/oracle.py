@@ -36,6 +36,8 @@ def lib():
             "orc_philox4x32_10": (None, [_up, _up, _up]),
             "orc_gaussian": (None, [_i64, _u64, _u64, _dp]),
             "orc_uniform_pm1": (None, [_i64, _u64, _u64, _dp]),
+            "orc_gaussian_f32": (None, [_i64, _u64, _u64, np.ctypeslib.ndpointer(dtype=np.float32,
+                                                                               flags="C_CONTIGUOUS")]),
             "orc_matmul": (None, [_i64, _i64, _i64, _dp, _dp, _dp]),
             "orc_circulant_dense": (None, [_i64, _dp, _dp]),
             "orc_dft": (None, [_i64, _dp, _dp, _dp, _dp, C.c_int]),
@@ -92,6 +94,12 @@ def philox4x32_10(ctr, key):
 def gaussian(count, seed, subseq=0):
     out = np.empty(int(count), np.float64)
     lib().orc_gaussian(int(count), int(seed), int(subseq), out)
+    return out
+
+
+def gaussian_f32(count, seed, subseq=0):
+    out = np.empty(int(count), np.float32)
+    lib().orc_gaussian_f32(int(count), int(seed), int(subseq), out)
     return out
 
 

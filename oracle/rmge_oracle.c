@@ -100,6 +100,24 @@ void orc_gaussian(int64_t count, uint64_t seed, uint64_t subseq, double* out) {
 }
 
 /*
+ * FP32 Gaussian entries for the reduced-precision multipliers: the same Box-Muller pair in
+ * single precision from 24-bit uniforms u1 = ((x0 >> 8) + 1) / 2^24, u2 = (x2 >> 8) / 2^24 of
+ * Philox block e/2.
+ */
+void orc_gaussian_f32(int64_t count, uint64_t seed, uint64_t subseq, float* out) {
+    const float two_m24 = 1.0f / 16777216.0f;
+    for (int64_t e = 0; e < count; e += 2) {
+        uint32_t x[4];
+        draw_block((uint64_t)(e / 2), seed, subseq, x);
+        const float u1 = (float)((x[0] >> 8) + 1u) * two_m24;
+        const float u2 = (float)(x[2] >> 8) * two_m24;
+        const float r = sqrtf(-2.0f * logf(u1));
+        out[e] = r * cosf(2.0f * (float)ORC_PI * u2);
+        if (e + 1 < count) out[e + 1] = r * sinf(2.0f * (float)ORC_PI * u2);
+    }
+}
+
+/*
  * Uniform entries in [-1, 1) (Ex. 5.1 draws the first column of a real
  * circulant uniformly from [-1, 1]).  Entry e uses Philox block e/2; word
  * pair (x0,x1) feeds even entries, (x2,x3) odd ones; value 2m/2^53 - 1.

@@ -1,0 +1,308 @@
+// api.cu -- the extern "C" entry points of librmge (declared and documented in include/rmge.h).
+//
+// Each entry point validates its arguments, carves its scratch out of the caller's workspace,
+// and enqueues the kernels of one step of the method on the caller's stream.
+#include <climits>
+#include <cstring>
+
+#include "kernels.cuh"
+
+namespace rmge {
+
+std::atomic<unsigned long long> g_launches{0};
+
+namespace {
+
+bool valid_kind(rmge_mult_kind k) {
+    return k == RMGE_GAUSSIAN || k == RMGE_CIRCULANT_GAUSSIAN || k == RMGE_CIRCULANT_UNIFORM;
+}
+bool valid_prec(rmge_prec p) { return p == RMGE_F64 || p == RMGE_F32 || p == RMGE_BF16_TC || p == RMGE_F16_TC; }
+bool is_circ(rmge_mult_kind k) { return k != RMGE_GAUSSIAN; }
+bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+bool circ_ok(int64_t n) { return pow2(n) && n >= 2 && n <= 8192; }
+size_t elem(rmge_prec p) { return p == RMGE_F64 ? 8 : 4; }
+
+int64_t nflags_for(int64_t n, int64_t nrhs) {
+    return ((n + kTrsvRows - 1) / kTrsvRows) * ((nrhs + kTrsvCols - 1) / kTrsvCols);
+}
+
+struct Ws {
+    DevState* st;
+    int* flags;
+    void* inv;
+    double* colred;
+    double* R;
+    double* Y;
+    double* D;
+    double2* tw;
+};
+
+rmge_status carve(void* ws, size_t ws_bytes, int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec, Ws* out) {
+    if (ws == nullptr || ((uintptr_t)ws & 255) != 0) return RMGE_ERR_WORKSPACE;
+    const WsLayout L = ws_layout(n, nrhs, kind, prec);
+    if (ws_bytes < L.total) return RMGE_ERR_WORKSPACE;
+    char* b = static_cast<char*>(ws);
+    out->st = reinterpret_cast<DevState*>(b + L.state);
+    out->flags = reinterpret_cast<int*>(b + L.flags);
+    out->inv = b + L.inv;
+    out->colred = reinterpret_cast<double*>(b + L.colred);
+    out->R = reinterpret_cast<double*>(b + L.R);
+    out->Y = reinterpret_cast<double*>(b + L.Y);
+    out->D = reinterpret_cast<double*>(b + L.D);
+    out->tw = reinterpret_cast<double2*>(b + L.fft);
+    return RMGE_OK;
+}
+
+bool check_dims(int64_t n, int64_t nrhs) { return n >= 1 && n <= RMGE_MAX_N && nrhs >= 1 && nrhs <= RMGE_MAX_N; }
+
+// d = op(G) y for the multiplier of `kind`; y, d are n x k (FP64, or FP32 for reduced precisions
+// with a dense G).  accumulate: d += op(G) y.
+rmge_status apply_g_cols(rmge_mult_kind kind, rmge_prec prec, int64_t n, int64_t k, const void* G, bool transpose,
+                         const void* y, int64_t ldy, void* d, int64_t ldd, bool accumulate, const int* skip,
+                         const Ws& w, cudaStream_t s) {
+    if (is_circ(kind))
+        return circulant_apply_cols(n, k, static_cast<const double*>(G), w.tw, transpose,
+                                    static_cast<const double*>(y), ldy, static_cast<double*>(d), ldd, accumulate, skip,
+                                    s);
+    if (prec == RMGE_F64)
+        return gemm<double>(transpose, n, k, n, 1.0, static_cast<const double*>(G), n, static_cast<const double*>(y),
+                            ldy, accumulate ? 1.0 : 0.0, static_cast<double*>(d), ldd, skip, s);
+    return gemm<float>(transpose, n, k, n, 1.0f, static_cast<const float*>(G), n, static_cast<const float*>(y), ldy,
+                       accumulate ? 1.0f : 0.0f, static_cast<float*>(d), ldd, skip, s);
+}
+
+// In-place y <- U^{-1} L^{-1} y (transposed: L^{-T} U^{-T} y) with the factor type of prec.
+rmge_status lu_solve(rmge_prec prec, bool transposed, int64_t n, int64_t k, const void* LU, int64_t ldlu, void* y,
+                     int64_t ldy, const Ws& w, int ticket, int epoch, const int* skip, cudaStream_t s) {
+    const int k1 = transposed ? 2 : 0, k2 = transposed ? 3 : 1;
+    if (prec == RMGE_F64) {
+        RMGE_TRY(trsv<double>(k1, n, k, static_cast<const double*>(LU), ldlu, static_cast<double*>(y), ldy, w.st,
+                              w.flags, ticket, epoch, skip, s));
+        return trsv<double>(k2, n, k, static_cast<const double*>(LU), ldlu, static_cast<double*>(y), ldy, w.st,
+                            w.flags, ticket + 1, epoch + 1, skip, s);
+    }
+    RMGE_TRY(trsv<float>(k1, n, k, static_cast<const float*>(LU), ldlu, static_cast<float*>(y), ldy, w.st, w.flags,
+                         ticket, epoch, skip, s));
+    return trsv<float>(k2, n, k, static_cast<const float*>(LU), ldlu, static_cast<float*>(y), ldy, w.st, w.flags,
+                       ticket + 1, epoch + 1, skip, s);
+}
+
+// X (+)= G U^{-1} L^{-1} V for FP64 V (n x k, ldv), using w.Y (and w.D) as scratch.
+rmge_status correction(rmge_mult_kind kind, rmge_prec prec, int64_t n, int64_t k, const void* LU, int64_t ldlu,
+                       const void* G, const double* V, int64_t ldv, double* X, int64_t ldx, bool accumulate,
+                       const Ws& w, int ticket, int epoch, const int* skip, cudaStream_t s) {
+    const bool low = prec != RMGE_F64;
+    if (!low || is_circ(kind)) {
+        if (!low) {
+            RMGE_TRY(copy_matrix<double, double>(n, k, V, ldv, w.Y, k, skip, s));
+            RMGE_TRY(lu_solve(prec, false, n, k, LU, ldlu, w.Y, k, w, ticket, epoch, skip, s));
+            return apply_g_cols(kind, prec, n, k, G, false, w.Y, k, X, ldx, accumulate, skip, w, s);
+        }
+        // reduced-precision factors with a circulant G: solve in FP32, widen, apply C in FP64
+        float* yf = reinterpret_cast<float*>(w.Y);
+        RMGE_TRY(copy_matrix<double, float>(n, k, V, ldv, yf, k, skip, s));
+        RMGE_TRY(lu_solve(prec, false, n, k, LU, ldlu, yf, k, w, ticket, epoch, skip, s));
+        RMGE_TRY(copy_matrix<float, double>(n, k, yf, k, w.D, k, skip, s));
+        return apply_g_cols(kind, RMGE_F64, n, k, G, false, w.D, k, X, ldx, accumulate, skip, w, s);
+    }
+    float* yf = reinterpret_cast<float*>(w.Y);
+    float* df = reinterpret_cast<float*>(w.D);
+    RMGE_TRY(copy_matrix<double, float>(n, k, V, ldv, yf, k, skip, s));
+    RMGE_TRY(lu_solve(prec, false, n, k, LU, ldlu, yf, k, w, ticket, epoch, skip, s));
+    RMGE_TRY(apply_g_cols(kind, prec, n, k, G, false, yf, k, df, k, false, skip, w, s));
+    if (accumulate) return add_update<float>(n, k, df, k, X, ldx, skip, s);
+    return copy_matrix<float, double>(n, k, df, k, X, ldx, skip, s);
+}
+
+}  // namespace
+
+WsLayout ws_layout(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec) {
+    WsLayout L{};
+    size_t off = 0;
+    L.state = off;
+    off = align256(off + sizeof(DevState));
+    L.flags = off;
+    off = align256(off + sizeof(int) * (size_t)nflags_for(n, nrhs));
+    L.inv = off;
+    off = align256(off + 2 * (size_t)kNb * kNb * elem(prec));
+    L.rowsum = off;
+    L.colred = off;
+    off = align256(off + 3 * sizeof(double) * (size_t)nrhs);
+    L.R = off;
+    off = align256(off + sizeof(double) * (size_t)(n * nrhs));
+    L.Y = off;
+    off = align256(off + sizeof(double) * (size_t)(n * nrhs));
+    L.D = off;
+    off = align256(off + sizeof(double) * (size_t)(n * nrhs));
+    L.fft = off;
+    if (is_circ(kind)) off = align256(off + sizeof(double2) * (size_t)(n / 2 + 1));
+    L.total = off;
+    return L;
+}
+
+}  // namespace rmge
+
+using namespace rmge;
+
+extern "C" {
+
+unsigned long long rmge_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* rmge_status_string(rmge_status s) {
+    switch (s) {
+        case RMGE_OK: return "ok";
+        case RMGE_ERR_INVALID_ARG: return "invalid argument";
+        case RMGE_ERR_BREAKDOWN: return "GENP breakdown (zero or non-finite pivot)";
+        case RMGE_ERR_GROWTH: return "growth above threshold";
+        case RMGE_ERR_NOT_CONVERGED: return "refinement did not converge";
+        case RMGE_ERR_CUDA: return "CUDA launch or copy failed";
+        case RMGE_ERR_TIMEOUT: return "bounded device wait expired";
+        case RMGE_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+        case RMGE_ERR_UNSUPPORTED: return "unsupported in this build";
+    }
+    return "unknown status";
+}
+
+size_t rmge_multiplier_bytes(rmge_mult_kind kind, int64_t n, rmge_prec prec) {
+    if (!valid_kind(kind) || !valid_prec(prec) || n < 1 || n > RMGE_MAX_N) return 0;
+    if (is_circ(kind)) return circ_ok(n) ? 3 * sizeof(double) * (size_t)n : 0;
+    return (size_t)n * (size_t)n * elem(prec);
+}
+
+size_t rmge_workspace_size(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec) {
+    if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs)) return 0;
+    if (is_circ(kind) && !circ_ok(n)) return 0;
+    return ws_layout(n, nrhs, kind, prec).total;
+}
+
+rmge_status rmge_make_multiplier(rmge_mult_kind kind, int64_t n, uint64_t seed, uint64_t subsequence, rmge_prec prec,
+                                 void* G, rmge_stream_t stream) {
+    if (!valid_kind(kind) || !valid_prec(prec) || n < 1 || n > RMGE_MAX_N || G == nullptr)
+        return RMGE_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (kind == RMGE_GAUSSIAN) {
+        if (prec == RMGE_F64) return launch_gaussian(n * n, seed, subsequence, static_cast<double*>(G), s);
+        return launch_gaussian(n * n, seed, subsequence, static_cast<float*>(G), s);
+    }
+    if (!circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
+    if (((uintptr_t)G & 15) != 0) return RMGE_ERR_INVALID_ARG;
+    double* g = static_cast<double*>(G);
+    if (kind == RMGE_CIRCULANT_GAUSSIAN)
+        RMGE_TRY(launch_gaussian(n, seed, subsequence, g, s));
+    else
+        RMGE_TRY(launch_uniform_pm1(n, seed, subsequence, g, s));
+    // The spectrum's twiddle table lives in the third block of G until the FFT overwrites it:
+    // u occupies G[n .. 3n) as n double2 and the table needs n/2 double2 -- use the tail half.
+    // The FFT reads the table into shared memory before writing u, so the overlap is safe.
+    return circulant_spectrum(n, g, reinterpret_cast<double2*>(g + 2 * n), s);
+}
+
+rmge_status rmge_apply_multiplier(rmge_mult_kind kind, int64_t n, const double* A, int64_t lda, const void* G, void* M,
+                                  int64_t ldm, rmge_prec prec, void* ws, size_t ws_bytes, rmge_stream_t stream) {
+    if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, 1) || A == nullptr || G == nullptr || M == nullptr ||
+        lda < n || ldm < n)
+        return RMGE_ERR_INVALID_ARG;
+    if (is_circ(kind) && !circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Ws w{};
+    RMGE_TRY(carve(ws, ws_bytes, n, 1, kind, prec, &w));
+    if (is_circ(kind))
+        return circulant_apply_rows(n, A, lda, static_cast<const double*>(G), w.tw, M, ldm, prec != RMGE_F64, s);
+    if (prec == RMGE_F64)
+        return gemm<double>(false, n, n, n, 1.0, A, lda, static_cast<const double*>(G), n, 0.0,
+                            static_cast<double*>(M), ldm, nullptr, s);
+    return RMGE_ERR_UNSUPPORTED;  // reduced-precision dense apply: see the tensor-core path
+}
+
+rmge_status rmge_factor(int64_t n, void* M, int64_t ldm, rmge_prec prec, int32_t* info, double* growth, void* ws,
+                        size_t ws_bytes, rmge_stream_t stream) {
+    if (!valid_prec(prec) || !check_dims(n, 1) || M == nullptr || ldm < n) return RMGE_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Ws w{};
+    RMGE_TRY(carve(ws, ws_bytes, n, 1, RMGE_GAUSSIAN, prec, &w));
+    RMGE_TRY(state_init(w.st, w.flags, 0, w.colred, 0, nullptr, 0, s));
+    if (prec == RMGE_F64)
+        RMGE_TRY(genp_factor<double>(n, static_cast<double*>(M), ldm, w.st, static_cast<double*>(w.inv), s));
+    else if (prec == RMGE_F32)
+        RMGE_TRY(genp_factor<float>(n, static_cast<float*>(M), ldm, w.st, static_cast<float*>(w.inv), s));
+    else
+        return RMGE_ERR_UNSUPPORTED;
+    return genp_finish(w.st, info, growth, s);
+}
+
+rmge_status rmge_solve(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void* LU, int64_t ldlu, const void* G,
+                       const double* B, int64_t ldb, double* X, int64_t ldx, rmge_prec prec, void* ws, size_t ws_bytes,
+                       rmge_stream_t stream) {
+    if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs) || LU == nullptr || G == nullptr ||
+        B == nullptr || X == nullptr || ldlu < n || ldb < nrhs || ldx < nrhs)
+        return RMGE_ERR_INVALID_ARG;
+    if (is_circ(kind) && !circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Ws w{};
+    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w));
+    RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, 0, nullptr, 0, s));
+    return correction(kind, prec, n, nrhs, LU, ldlu, G, B, ldb, X, ldx, false, w, 0, 1, nullptr, s);
+}
+
+rmge_status rmge_refine(rmge_mult_kind kind, int64_t n, int64_t nrhs, const double* A, int64_t lda, const void* LU,
+                        int64_t ldlu, const void* G, const double* B, int64_t ldb, double* X, int64_t ldx,
+                        rmge_prec prec, int32_t max_iters, double be_tol, double* berr, int32_t* iters, void* ws,
+                        size_t ws_bytes, rmge_stream_t stream) {
+    if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs) || A == nullptr || LU == nullptr ||
+        G == nullptr || B == nullptr || X == nullptr || lda < n || ldlu < n || ldb < nrhs || ldx < nrhs ||
+        max_iters < 0 || max_iters > (kMaxSolvesPerCall / 2) - 1 || !(be_tol >= 0.0))
+        return RMGE_ERR_INVALID_ARG;
+    if (is_circ(kind) && !circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Ws w{};
+    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w));
+    RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, (int)(3 * nrhs), berr, max_iters + 1, s));
+    RMGE_TRY(row_abs_sums(n, A, lda, w.st, s));
+    const int* stop = &w.st->stop;
+    for (int it = 0; it <= max_iters; ++it) {
+        // R = B - A X in FP64, then the backward error and the stopping test
+        RMGE_TRY(copy_matrix<double, double>(n, nrhs, B, ldb, w.R, nrhs, stop, s));
+        RMGE_TRY(gemm<double>(false, n, nrhs, n, -1.0, A, lda, X, ldx, 1.0, w.R, nrhs, stop, s));
+        RMGE_TRY(backward_error(n, nrhs, w.R, nrhs, X, ldx, B, ldb, w.st, w.colred, it, be_tol, max_iters, berr, s));
+        if (it == max_iters) break;
+        // X <- X + G U^{-1} L^{-1} R
+        RMGE_TRY(correction(kind, prec, n, nrhs, LU, ldlu, G, w.R, nrhs, X, ldx, true, w, 2 * it, 2 * it + 1, stop, s));
+    }
+    return refine_finish(w.st, max_iters, berr, iters, s);
+}
+
+rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void* LU, int64_t ldlu,
+                                const void* G, const double* X, int64_t ldx, const double* dX, int64_t lddx, double* dB,
+                                int64_t lddb, double* dA, int64_t ldda, rmge_prec prec, void* ws, size_t ws_bytes,
+                                rmge_stream_t stream) {
+    if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs) || LU == nullptr || G == nullptr ||
+        dX == nullptr || dB == nullptr || ldlu < n || lddx < nrhs || lddb < nrhs || (dA != nullptr && (X == nullptr ||
+        ldda < n || ldx < nrhs)))
+        return RMGE_ERR_INVALID_ARG;
+    if (is_circ(kind) && !circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Ws w{};
+    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w));
+    RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, 0, nullptr, 0, s));
+    if (prec == RMGE_F64) {
+        // dB = L^{-T} U^{-T} (G^T dX)
+        RMGE_TRY(apply_g_cols(kind, prec, n, nrhs, G, true, dX, lddx, dB, lddb, false, nullptr, w, s));
+        RMGE_TRY(lu_solve(prec, true, n, nrhs, LU, ldlu, dB, lddb, w, 0, 1, nullptr, s));
+    } else {
+        float* zf = reinterpret_cast<float*>(w.Y);
+        if (is_circ(kind)) {
+            RMGE_TRY(apply_g_cols(kind, RMGE_F64, n, nrhs, G, true, dX, lddx, w.D, nrhs, false, nullptr, w, s));
+            RMGE_TRY(copy_matrix<double, float>(n, nrhs, w.D, nrhs, zf, nrhs, nullptr, s));
+        } else {
+            float* df = reinterpret_cast<float*>(w.D);
+            RMGE_TRY(copy_matrix<double, float>(n, nrhs, dX, lddx, df, nrhs, nullptr, s));
+            RMGE_TRY(apply_g_cols(kind, prec, n, nrhs, G, true, df, nrhs, zf, nrhs, false, nullptr, w, s));
+        }
+        RMGE_TRY(lu_solve(prec, true, n, nrhs, LU, ldlu, zf, nrhs, w, 0, 1, nullptr, s));
+        RMGE_TRY(copy_matrix<float, double>(n, nrhs, zf, nrhs, dB, lddb, nullptr, s));
+    }
+    if (dA != nullptr) return outer_neg(n, nrhs, dB, lddb, X, ldx, dA, ldda, s);
+    return RMGE_OK;
+}
+
+}  // extern "C"

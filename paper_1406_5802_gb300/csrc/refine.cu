@@ -1,0 +1,210 @@
+// refine.cu -- residual-correction support kernels (Sec. 1.2, Sec. 7.1) and small utilities:
+// control-block initialisation, ||A||_inf, column maxima and the normwise backward error with
+// the stopping test, the FP64 update X += D, and dA = -dB X^T for the adjoint.
+#include <climits>
+
+#include "kernels.cuh"
+
+namespace rmge {
+namespace {
+
+__global__ void state_init_kernel(DevState* st, int* flags, int64_t nflags, double* colred, int ncolred,
+                                  double* berr_out, int nberr) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (tid == 0) {
+        st->info = INT_MAX;
+        st->halt = 0;
+        st->stop = 0;
+        st->sweeps = 0;
+        st->error = 0;
+        st->maxabs_m = 0;
+        st->maxabs_u = 0;
+        st->norm_a = 0.0;
+        st->berr_prev = __longlong_as_double(0x7ff0000000000000LL);
+        st->berr_last = __longlong_as_double(0x7ff0000000000000LL);
+    }
+    for (int64_t i = tid; i < 64; i += stride) st->tickets[i] = 0u;
+    for (int64_t i = tid; i < nflags; i += stride) flags[i] = 0;
+    for (int64_t i = tid; i < ncolred; i += stride) colred[i] = 0.0;
+    for (int64_t i = tid; i < nberr; i += stride) berr_out[i] = -1.0;
+}
+
+// One warp per row: ||A||_inf = max_i sum_j |a_ij|.
+__global__ void row_abs_sums_kernel(int64_t n, const double* __restrict__ A, int64_t lda, DevState* st) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long best = 0;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        double s = 0.0;
+        for (int64_t j = lane; j < n; j += 32) s += fabs(A[i * lda + j]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const unsigned long long b = abs_bits(s);
+        best = b > best ? b : best;
+    }
+    if (lane == 0 && best != 0) atomicMax(reinterpret_cast<unsigned long long*>(&st->norm_a), best);
+}
+
+template <typename Tin, typename Tout>
+__global__ void copy_kernel(int64_t rows, int64_t cols, const Tin* __restrict__ src, int64_t lds, Tout* __restrict__ dst,
+                            int64_t ldd, const int* skip) {
+    if (skip != nullptr && *(volatile const int*)skip != 0) return;
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / cols, j = e % cols;
+        dst[i * ldd + j] = (Tout)src[i * lds + j];
+    }
+}
+
+template <typename T>
+__global__ void add_kernel(int64_t rows, int64_t cols, const T* __restrict__ D, int64_t ldd, double* __restrict__ X,
+                           int64_t ldx, const int* skip) {
+    if (skip != nullptr && *(volatile const int*)skip != 0) return;
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / cols, j = e % cols;
+        X[i * ldx + j] += (double)D[i * ldd + j];
+    }
+}
+
+// colred layout (as ull bits of non-negative doubles): [0,k) max|r|, [k,2k) max|x|, [2k,3k) max|b|.
+__global__ void colmax_kernel(int64_t n, int64_t k, const double* __restrict__ R, int64_t ldr,
+                              const double* __restrict__ X, int64_t ldx, const double* __restrict__ B, int64_t ldb,
+                              const DevState* st, unsigned long long* colred) {
+    if (*(volatile const int*)&st->stop != 0) return;
+    const int64_t total = n * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / k, j = e % k;
+        const unsigned long long r = abs_bits(R[i * ldr + j]);
+        const unsigned long long x = abs_bits(X[i * ldx + j]);
+        const unsigned long long b = abs_bits(B[i * ldb + j]);
+        // NaN bit patterns exceed +Inf's, so a NaN anywhere surfaces in the maxima
+        if (r) atomicMax(colred + j, r);
+        if (x) atomicMax(colred + k + j, x);
+        if (b) atomicMax(colred + 2 * k + j, b);
+    }
+}
+
+// eta = max_c max|r_c| / (||A||_inf max|x_c| + max|b_c|); stopping test; clears colred.
+__global__ void decide_kernel(int64_t k, DevState* st, unsigned long long* colred, int sweep, double tol,
+                              int max_iters, double* berr_out) {
+    if (st->stop != 0) return;
+    double eta = 0.0;
+    bool bad = false;
+    for (int64_t j = 0; j < k; ++j) {
+        const double rn = __longlong_as_double((long long)colred[j]);
+        const double xn = __longlong_as_double((long long)colred[k + j]);
+        const double bn = __longlong_as_double((long long)colred[2 * k + j]);
+        colred[j] = colred[k + j] = colred[2 * k + j] = 0ull;
+        if (!isfinite(rn) || !isfinite(xn)) { bad = true; continue; }
+        const double den = st->norm_a * xn + bn;
+        const double e = den > 0.0 ? rn / den : (rn > 0.0 ? __longlong_as_double(0x7ff0000000000000LL) : 0.0);
+        eta = e > eta ? e : eta;
+    }
+    if (bad || !isfinite(st->norm_a)) eta = __longlong_as_double(0x7ff0000000000000LL);
+    if (berr_out) berr_out[sweep] = eta;
+    st->sweeps = sweep;
+    const bool stagnated = sweep >= 2 && !(eta <= 0.5 * st->berr_prev);
+    if (eta <= tol || sweep >= max_iters || stagnated || !isfinite(eta)) st->stop = 1;
+    st->berr_prev = st->berr_last;
+    st->berr_last = eta;
+}
+
+__global__ void refine_finish_kernel(const DevState* st, int32_t* iters) {
+    if (iters) *iters = st->sweeps;
+}
+
+__global__ void outer_neg_kernel(int64_t n, int64_t k, const double* __restrict__ dB, int64_t lddb,
+                                 const double* __restrict__ X, int64_t ldx, double* __restrict__ dA, int64_t ldda) {
+    // one CTA per row of dA; the row's dB entries are broadcast from registers
+    const int64_t i = blockIdx.x;
+    double b[16];
+    const int kk = (int)(k < 16 ? k : 16);
+    for (int c = 0; c < kk; ++c) b[c] = dB[i * lddb + c];
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < kk; ++c) s = fma(b[c], X[j * ldx + c], s);
+        for (int64_t c = 16; c < k; ++c) s = fma(dB[i * lddb + c], X[j * ldx + c], s);
+        dA[i * ldda + j] = -s;
+    }
+}
+
+unsigned grid_for(int64_t work, int threads) {
+    int64_t g = (work + threads - 1) / threads;
+    if (g > 152 * 8) g = 152 * 8;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+rmge_status state_init(DevState* st, int* flags, int64_t nflags, double* colred, int ncolred, double* berr_out,
+                       int nberr, cudaStream_t s) {
+    int64_t work = nflags > ncolred ? nflags : ncolred;
+    if (work < 64) work = 64;
+    state_init_kernel<<<grid_for(work, 256), 256, 0, s>>>(st, flags, nflags, colred, ncolred, berr_out,
+                                                          berr_out ? nberr : 0);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
+rmge_status row_abs_sums(int64_t n, const double* A, int64_t lda, DevState* st, cudaStream_t s) {
+    row_abs_sums_kernel<<<grid_for(n * 32, 256), 256, 0, s>>>(n, A, lda, st);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
+template <typename Tin, typename Tout>
+rmge_status copy_matrix(int64_t rows, int64_t cols, const Tin* src, int64_t lds, Tout* dst, int64_t ldd,
+                        const int* skip, cudaStream_t s) {
+    copy_kernel<Tin, Tout><<<grid_for(rows * cols, 256), 256, 0, s>>>(rows, cols, src, lds, dst, ldd, skip);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
+template <typename T>
+rmge_status add_update(int64_t rows, int64_t cols, const T* D, int64_t ldd, double* X, int64_t ldx, const int* skip,
+                       cudaStream_t s) {
+    add_kernel<T><<<grid_for(rows * cols, 256), 256, 0, s>>>(rows, cols, D, ldd, X, ldx, skip);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
+rmge_status backward_error(int64_t n, int64_t k, const double* R, int64_t ldr, const double* X, int64_t ldx,
+                           const double* B, int64_t ldb, DevState* st, double* colred, int sweep, double be_tol,
+                           int max_iters, double* berr_out, cudaStream_t s) {
+    unsigned long long* cr = reinterpret_cast<unsigned long long*>(colred);
+    colmax_kernel<<<grid_for(n * k, 256), 256, 0, s>>>(n, k, R, ldr, X, ldx, B, ldb, st, cr);
+    RMGE_LAUNCH_CHECK();
+    decide_kernel<<<1, 1, 0, s>>>(k, st, cr, sweep, be_tol, max_iters, berr_out);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
+rmge_status refine_finish(DevState* st, int max_iters, double* berr_out, int32_t* iters, cudaStream_t s) {
+    (void)max_iters;
+    (void)berr_out;
+    refine_finish_kernel<<<1, 1, 0, s>>>(st, iters);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
+rmge_status outer_neg(int64_t n, int64_t k, const double* dB, int64_t lddb, const double* X, int64_t ldx, double* dA,
+                      int64_t ldda, cudaStream_t s) {
+    outer_neg_kernel<<<(unsigned)n, 256, 0, s>>>(n, k, dB, lddb, X, ldx, dA, ldda);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
+template rmge_status copy_matrix<double, double>(int64_t, int64_t, const double*, int64_t, double*, int64_t,
+                                                 const int*, cudaStream_t);
+template rmge_status copy_matrix<double, float>(int64_t, int64_t, const double*, int64_t, float*, int64_t, const int*,
+                                                cudaStream_t);
+template rmge_status copy_matrix<float, double>(int64_t, int64_t, const float*, int64_t, double*, int64_t, const int*,
+                                                cudaStream_t);
+template rmge_status add_update<double>(int64_t, int64_t, const double*, int64_t, double*, int64_t, const int*,
+                                        cudaStream_t);
+template rmge_status add_update<float>(int64_t, int64_t, const float*, int64_t, double*, int64_t, const int*,
+                                       cudaStream_t);
+
+}  // namespace rmge

@@ -1,0 +1,153 @@
+// trsv.cu -- triangular solves with the packed GENP factors, one launch per solve.
+//
+// The solves of Fact 4.1 (L z = b, U y = z) and of the adjoint (U^T p = g, L^T q = p) are
+// blocked into TB-row blocks and KC-column blocks of the right-hand sides.  Each CTA owns one
+// (row block, column block) and runs left-looking: it subtracts the contributions of the
+// already-solved row blocks as they complete, then solves its diagonal block in shared memory.
+// Completion is published per (row block, column block) with a release store of an epoch value;
+// consumers acquire it.  CTAs take a ticket from an atomic counter at start and derive their
+// block from it, so a CTA only ever waits for CTAs that took earlier tickets and are therefore
+// already running: no co-residency assumption, no deadlock.  Every wait is bounded
+// (kSpinLimit polls); on expiry the CTA records RMGE_ERR_TIMEOUT in DevState::error and all
+// waiting CTAs return without writing.
+//
+// The factor is read once from HBM per column block; FP64 runs on the DFMA pipe.
+#include "kernels.cuh"
+
+namespace rmge {
+namespace {
+
+constexpr int TB = kTrsvRows;
+constexpr int KC = kTrsvCols;
+constexpr int NT = TB * KC;  // one thread per (row, column) of the block
+
+// Coefficient (i, t) of the triangular matrix of `kind`, read from the packed factors.
+template <typename T>
+__device__ __forceinline__ T coef(int kind, const T* LU, int64_t ld, int64_t i, int64_t t) {
+    return (kind <= 1) ? LU[i * ld + t] : LU[t * ld + i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t nrhs, const T* __restrict__ LU,
+                                                  int64_t ld, T* B, int64_t ldb, DevState* st, int* flags,
+                                                  int ticket_slot, int epoch, const int* skip) {
+    __shared__ T cs[TB][TB + 1];  // off-diagonal coefficient tile
+    __shared__ T cd[TB][TB + 1];  // diagonal block
+    __shared__ T ys[TB][KC];
+    __shared__ int my_ticket;
+    __shared__ int failed;
+    if (skip != nullptr && *(volatile const int*)skip != 0) return;
+
+    const int tid = threadIdx.x;
+    const int r = tid / KC, c = tid % KC;
+    const int64_t nblk = (n + TB - 1) / TB;
+    const int64_t ncb = (nrhs + KC - 1) / KC;
+    if (tid == 0) {
+        my_ticket = (int)atomicAdd(&st->tickets[ticket_slot], 1u);
+        failed = 0;
+    }
+    __syncthreads();
+    const int64_t q = my_ticket / ncb, cb = my_ticket % ncb;
+    const bool forward = (kind == 0 || kind == 2);
+    const bool unit = (kind == 0 || kind == 3);
+    const int64_t rb = forward ? q : nblk - 1 - q;
+    const int64_t r0 = rb * TB, c0 = cb * KC;
+    const int64_t gr = r0 + r, gc = c0 + c;
+    const bool live = (gr < n) && (gc < nrhs);
+
+    T acc = live ? B[gr * ldb + gc] : T(0);
+
+    // The diagonal block's coefficients do not depend on other blocks: stage them first.
+    for (int e = tid; e < TB * TB; e += NT) {
+        int i, t;
+        if (kind <= 1) { i = e / TB; t = e % TB; }   // rows of LU: contiguous along t
+        else           { t = e / TB; i = e % TB; }   // transposed: contiguous along i
+        const int64_t gi = r0 + i, gt = r0 + t;
+        cd[i][t] = (gi < n && gt < n) ? coef(kind, LU, ld, gi, gt) : ((i == t) ? T(1) : T(0));
+    }
+
+    constexpr int CPT = TB * TB / NT;  // coefficients per thread per tile
+    for (int64_t qq = 0; qq < q; ++qq) {
+        const int64_t sb = forward ? qq : nblk - 1 - qq;
+        const int64_t s0 = sb * TB;
+        // coefficient tile (rows r0.., columns s0..): fetched before waiting, it is final already
+        T cr[CPT];
+#pragma unroll
+        for (int u = 0; u < CPT; ++u) {
+            const int e = tid + u * NT;
+            int i, t;
+            if (kind <= 1) { i = e / TB; t = e % TB; }
+            else           { t = e / TB; i = e % TB; }
+            const int64_t gi = r0 + i, gt = s0 + t;
+            cr[u] = (gi < n && gt < n) ? coef(kind, LU, ld, gi, gt) : T(0);
+        }
+        if (tid == 0) {
+            const int* f = flags + sb * ncb + cb;
+            long long spins = 0;
+            while (ld_acquire(f) != epoch) {
+                if (*(volatile int*)&st->error != 0) { failed = 1; break; }
+                if (++spins > kSpinLimit) {
+                    atomicExch(&st->error, (int)RMGE_ERR_TIMEOUT);
+                    failed = 1;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __syncthreads();
+        if (failed) return;
+#pragma unroll
+        for (int u = 0; u < CPT; ++u) {
+            const int e = tid + u * NT;
+            int i, t;
+            if (kind <= 1) { i = e / TB; t = e % TB; }
+            else           { t = e / TB; i = e % TB; }
+            cs[i][t] = cr[u];
+        }
+        {
+            const int64_t gt = s0 + r;
+            ys[r][c] = (gt < n && gc < nrhs) ? ldcg(B + gt * ldb + gc) : T(0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int t = 0; t < TB; ++t) acc = fma(-cs[r][t], ys[t][c], acc);
+        __syncthreads();
+    }
+
+    // diagonal block: column-oriented substitution inside the block
+    for (int step = 0; step < TB; ++step) {
+        const int p = forward ? step : TB - 1 - step;  // row finalised in this step
+        if (r == p) {
+            const T y = unit ? acc : acc / cd[p][p];
+            acc = y;
+            ys[p][c] = y;
+        }
+        __syncthreads();
+        if ((forward && r > p) || (!forward && r < p)) acc = fma(-cd[r][p], ys[p][c], acc);
+    }
+    if (live) B[gr * ldb + gc] = acc;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release(flags + rb * ncb + cb, epoch);
+}
+
+}  // namespace
+
+template <typename T>
+rmge_status trsv(int kind, int64_t n, int64_t nrhs, const T* LU, int64_t ldlu, T* B, int64_t ldb, DevState* st,
+                 int* flags, int ticket, int epoch, const int* skip, cudaStream_t s) {
+    if (ticket < 0 || ticket >= kMaxSolvesPerCall) return RMGE_ERR_INVALID_ARG;
+    const int64_t nblk = (n + TB - 1) / TB;
+    const int64_t ncb = (nrhs + KC - 1) / KC;
+    const int64_t grid = nblk * ncb;
+    trsv_kernel<T><<<(unsigned)grid, NT, 0, s>>>(kind, n, nrhs, LU, ldlu, B, ldb, st, flags, ticket, epoch, skip);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
+template rmge_status trsv<double>(int, int64_t, int64_t, const double*, int64_t, double*, int64_t, DevState*, int*,
+                                  int, int, const int*, cudaStream_t);
+template rmge_status trsv<float>(int, int64_t, int64_t, const float*, int64_t, float*, int64_t, DevState*, int*, int,
+                                 int, const int*, cudaStream_t);
+
+}  // namespace rmge

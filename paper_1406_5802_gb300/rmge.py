@@ -1,0 +1,237 @@
+"""Thin Python binding of librmge (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps (``include/rmge.h``) without the
+``rmge_`` prefix, takes torch tensors, passes their device pointers and the current CUDA stream
+to the library, and raises ``RmgeError`` on a non-OK status.  All arithmetic runs in the
+library's CUDA kernels; PyTorch only provides device memory and streams.  There is no fallback:
+if the library is not built or no CUDA device is present, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librmge.so")
+
+# enums (include/rmge.h)
+GAUSSIAN, CIRCULANT_GAUSSIAN, CIRCULANT_UNIFORM = 0, 1, 2
+F64, F32, BF16_TC, F16_TC = 0, 1, 2, 3
+KINDS = {"gaussian": GAUSSIAN, "circulant": CIRCULANT_GAUSSIAN, "circulant_uniform": CIRCULANT_UNIFORM}
+PRECS = {"f64": F64, "f32": F32, "bf16": BF16_TC, "f16": F16_TC}
+STATUS = {0: "RMGE_OK", 1: "RMGE_ERR_INVALID_ARG", 2: "RMGE_ERR_BREAKDOWN", 3: "RMGE_ERR_GROWTH",
+          4: "RMGE_ERR_NOT_CONVERGED", 5: "RMGE_ERR_CUDA", 6: "RMGE_ERR_TIMEOUT", 7: "RMGE_ERR_WORKSPACE",
+          8: "RMGE_ERR_UNSUPPORTED"}
+
+EXPORTED = ["rmge_multiplier_bytes", "rmge_workspace_size", "rmge_make_multiplier", "rmge_apply_multiplier",
+            "rmge_factor", "rmge_solve", "rmge_refine", "rmge_solve_backward", "rmge_status_string",
+            "rmge_kernel_launches"]
+
+
+class RmgeError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} returned {STATUS.get(code, code)}")
+        self.code = code
+
+
+_lib = None
+_i64, _u64, _vp, _sz = C.c_int64, C.c_uint64, C.c_void_p, C.c_size_t
+
+
+def load_library(path: str = LIB_PATH):
+    """Load librmge and declare its signatures (no CUDA call is made)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librmge is not built ({path} missing): run __graft_entry__.build()")
+    L = C.CDLL(path)
+    sig = {
+        "rmge_multiplier_bytes": (_sz, [C.c_int, _i64, C.c_int]),
+        "rmge_workspace_size": (_sz, [_i64, _i64, C.c_int, C.c_int]),
+        "rmge_make_multiplier": (C.c_int, [C.c_int, _i64, _u64, _u64, C.c_int, _vp, _vp]),
+        "rmge_apply_multiplier": (C.c_int, [C.c_int, _i64, _vp, _i64, _vp, _vp, _i64, C.c_int, _vp, _sz, _vp]),
+        "rmge_factor": (C.c_int, [_i64, _vp, _i64, C.c_int, _vp, _vp, _vp, _sz, _vp]),
+        "rmge_solve": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, C.c_int, _vp, _sz, _vp]),
+        "rmge_refine": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, C.c_int,
+                                  C.c_int32, C.c_double, _vp, _vp, _vp, _sz, _vp]),
+        "rmge_solve_backward": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp,
+                                          _i64, C.c_int, _vp, _sz, _vp]),
+        "rmge_status_string": (C.c_char_p, [C.c_int]),
+        "rmge_kernel_launches": (C.c_ulonglong, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _cuda_lib():
+    if not torch.cuda.is_available():
+        raise RuntimeError("librmge needs a CUDA device; none is available")
+    return load_library()
+
+
+def _check(fn, code):
+    if code != 0:
+        raise RmgeError(fn, code)
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _ld(t):
+    return t.stride(0) if t.dim() == 2 else 1
+
+
+def _kind(k):
+    return KINDS[k] if isinstance(k, str) else int(k)
+
+
+def _prec(p):
+    return PRECS[p] if isinstance(p, str) else int(p)
+
+
+def _need(t, dtype, name):
+    if t.device.type != "cuda":
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.dim() == 2 and t.stride(1) != 1:
+        raise ValueError(f"{name} must be row-major with unit column stride")
+
+
+def kernel_launches() -> int:
+    """Kernel launches enqueued through the library by this process so far."""
+    return int(load_library().rmge_kernel_launches())
+
+
+def factor_dtype(prec) -> torch.dtype:
+    return torch.float64 if _prec(prec) == F64 else torch.float32
+
+
+def multiplier_bytes(kind, n, prec) -> int:
+    return int(load_library().rmge_multiplier_bytes(_kind(kind), int(n), _prec(prec)))
+
+
+def workspace_size(n, nrhs, kind, prec) -> int:
+    return int(load_library().rmge_workspace_size(int(n), int(nrhs), _kind(kind), _prec(prec)))
+
+
+def workspace(n, nrhs, kind, prec, device="cuda") -> torch.Tensor:
+    """A scratch buffer of rmge_workspace_size bytes (torch allocations are 256-byte aligned)."""
+    nb = workspace_size(n, nrhs, kind, prec)
+    if nb == 0:
+        raise ValueError("invalid workspace request")
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def empty_multiplier(kind, n, prec, device="cuda") -> torch.Tensor:
+    kind, prec = _kind(kind), _prec(prec)
+    if kind == GAUSSIAN:
+        return torch.empty(n, n, dtype=factor_dtype(prec), device=device)
+    return torch.empty(3 * n, dtype=torch.float64, device=device)
+
+
+def make_multiplier(kind, n, seed, subsequence=1, prec="f64", G=None) -> torch.Tensor:
+    L = _cuda_lib()
+    if G is None:
+        G = empty_multiplier(kind, n, prec)
+    if G.numel() * G.element_size() < multiplier_bytes(kind, n, prec):
+        raise ValueError("G too small")
+    _check("rmge_make_multiplier", L.rmge_make_multiplier(_kind(kind), int(n), int(seed), int(subsequence),
+                                                          _prec(prec), _p(G), _stream()))
+    return G
+
+
+def apply_multiplier(kind, A, G, prec="f64", M=None, ws=None) -> torch.Tensor:
+    L = _cuda_lib()
+    _need(A, torch.float64, "A")
+    n = A.shape[0]
+    if M is None:
+        M = torch.empty(n, n, dtype=factor_dtype(prec), device=A.device)
+    _need(M, factor_dtype(prec), "M")
+    if ws is None:
+        ws = workspace(n, 1, kind, prec)
+    _check("rmge_apply_multiplier", L.rmge_apply_multiplier(_kind(kind), n, _p(A), _ld(A), _p(G), _p(M), _ld(M),
+                                                            _prec(prec), _p(ws), ws.numel(), _stream()))
+    return M
+
+
+def factor(M, prec="f64", ws=None):
+    """In-place GENP of M; returns (info, growth) device tensors (int32, float64)."""
+    L = _cuda_lib()
+    _need(M, factor_dtype(prec), "M")
+    n = M.shape[0]
+    info = torch.empty(1, dtype=torch.int32, device=M.device)
+    growth = torch.empty(1, dtype=torch.float64, device=M.device)
+    if ws is None:
+        ws = workspace(n, 1, GAUSSIAN, prec)
+    _check("rmge_factor", L.rmge_factor(n, _p(M), _ld(M), _prec(prec), _p(info), _p(growth), _p(ws), ws.numel(),
+                                        _stream()))
+    return info, growth
+
+
+def solve(kind, LU, G, B, prec="f64", X=None, ws=None) -> torch.Tensor:
+    L = _cuda_lib()
+    _need(B, torch.float64, "B")
+    n, k = B.shape
+    if X is None:
+        X = torch.empty(n, k, dtype=torch.float64, device=B.device)
+    _need(X, torch.float64, "X")
+    if ws is None:
+        ws = workspace(n, k, kind, prec)
+    _check("rmge_solve", L.rmge_solve(_kind(kind), n, k, _p(LU), _ld(LU), _p(G), _p(B), _ld(B), _p(X), _ld(X),
+                                      _prec(prec), _p(ws), ws.numel(), _stream()))
+    return X
+
+
+def refine(kind, A, LU, G, B, X, prec="f64", max_iters=10, be_tol=1e-13, ws=None):
+    """In-place refinement of X; returns (berr[max_iters+1], iters) device tensors."""
+    L = _cuda_lib()
+    n, k = B.shape
+    berr = torch.empty(max_iters + 1, dtype=torch.float64, device=B.device)
+    iters = torch.empty(1, dtype=torch.int32, device=B.device)
+    if ws is None:
+        ws = workspace(n, k, kind, prec)
+    _check("rmge_refine", L.rmge_refine(_kind(kind), n, k, _p(A), _ld(A), _p(LU), _ld(LU), _p(G), _p(B), _ld(B),
+                                        _p(X), _ld(X), _prec(prec), int(max_iters), float(be_tol), _p(berr),
+                                        _p(iters), _p(ws), ws.numel(), _stream()))
+    return berr, iters
+
+
+def solve_backward(kind, LU, G, X, dX, prec="f64", want_dA=True, ws=None):
+    """(dB, dA) for X = A^{-1} B given dX; dA is None when want_dA is False."""
+    L = _cuda_lib()
+    n, k = dX.shape
+    dB = torch.empty(n, k, dtype=torch.float64, device=dX.device)
+    dA = torch.empty(n, n, dtype=torch.float64, device=dX.device) if want_dA else None
+    if ws is None:
+        ws = workspace(n, k, kind, prec)
+    _check("rmge_solve_backward", L.rmge_solve_backward(_kind(kind), n, k, _p(LU), _ld(LU), _p(G), _p(X),
+                                                        _ld(X) if X is not None else 0, _p(dX), _ld(dX), _p(dB),
+                                                        _ld(dB), _p(dA), _ld(dA) if dA is not None else 0, _prec(prec),
+                                                        _p(ws), ws.numel(), _stream()))
+    return dB, dA
+
+
+def gesv(kind, A, B, seed, prec="f64", max_iters=10, be_tol=1e-13, subsequence=1):
+    """The whole method on device tensors: G, M = A G, GENP, X = G Y, refinement.
+    Returns dict(X, LU, G, info, growth, berr, iters) (device tensors)."""
+    n, k = B.shape
+    ws = workspace(n, k, kind, prec)
+    G = make_multiplier(kind, n, seed, subsequence, prec)
+    M = apply_multiplier(kind, A, G, prec, ws=ws)
+    info, growth = factor(M, prec, ws=ws)
+    X = solve(kind, M, G, B, prec, ws=ws)
+    berr, iters = refine(kind, A, M, G, B, X, prec, max_iters, be_tol, ws=ws)
+    return {"X": X, "LU": M, "G": G, "info": info, "growth": growth, "berr": berr, "iters": iters}

@@ -1,0 +1,65 @@
+"""Host-side checks of the C ABI: the library loads, exports every entry point include/rmge.h declares,
+sizes its buffers, and rejects bad arguments before touching the GPU (no CUDA call is made here)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1406_5802_gb300 import build as B
+from paper_1406_5802_gb300 import rmge
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return rmge.load_library()
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(rmge_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert declared, "no declarations found"
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(rmge.EXPORTED) <= declared
+
+
+def test_workspace_and_multiplier_sizes(lib):
+    assert rmge.workspace_size(4096, 16, "gaussian", "f64") > 3 * 4096 * 16 * 8
+    assert rmge.workspace_size(4096, 16, "circulant", "f64") > rmge.workspace_size(4096, 16, "gaussian", "f64")
+    assert rmge.workspace_size(0, 1, "gaussian", "f64") == 0
+    assert rmge.workspace_size(100, 1, "circulant", "f64") == 0  # circulant needs n = 2^p
+    assert rmge.multiplier_bytes("gaussian", 256, "f64") == 256 * 256 * 8
+    assert rmge.multiplier_bytes("gaussian", 256, "f32") == 256 * 256 * 4
+    assert rmge.multiplier_bytes("circulant", 256, "f64") == 3 * 256 * 8
+    assert rmge.multiplier_bytes("circulant", 16384, "f64") == 0
+
+
+def test_bad_arguments_are_rejected_without_gpu_work(lib):
+    INVALID, WORKSPACE = 1, 7
+    # n = 0, NULL matrix, ld < n
+    assert lib.rmge_factor(0, None, 1, 0, None, None, None, 0, None) == INVALID
+    assert lib.rmge_factor(8, None, 8, 0, None, None, None, 0, None) == INVALID
+    assert lib.rmge_factor(8, C.c_void_p(256), 4, 0, None, None, None, 0, None) == INVALID
+    # valid shape, missing / misaligned / short workspace
+    assert lib.rmge_factor(8, C.c_void_p(256), 8, 0, None, None, None, 0, None) == WORKSPACE
+    assert lib.rmge_factor(8, C.c_void_p(256), 8, 0, None, None, C.c_void_p(256 + 8), 1 << 20, None) == WORKSPACE
+    assert lib.rmge_factor(8, C.c_void_p(256), 8, 0, None, None, C.c_void_p(512), 16, None) == WORKSPACE
+    # unknown enum values and too many refinement sweeps
+    assert lib.rmge_make_multiplier(7, 8, 1, 1, 0, C.c_void_p(256), None) == INVALID
+    p = C.c_void_p(256)
+    assert lib.rmge_refine(0, 8, 1, p, 8, p, 8, p, p, 1, p, 1, 0, 99, 1e-13, None, None, p, 1 << 20, None) == INVALID
+    assert lib.rmge_refine(0, 8, 1, p, 8, p, 8, p, p, 1, p, 1, 0, 3, -1.0, None, None, p, 1 << 20, None) == INVALID
+    assert lib.rmge_status_string(6) == b"bounded device wait expired"

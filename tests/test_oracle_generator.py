@@ -79,3 +79,16 @@ def test_gaussian_matrix_norm_and_condition_bounds(orc):
     assert np.mean(norms) <= 2 * math.sqrt(n)
     assert max(norms) <= 2 * math.sqrt(n) + 4.0  # t = 4: probability <= e^-8 per draw
     assert np.mean(logk) <= math.log(n) + 2.258
+
+
+def test_gaussian_f32_stream(orc):
+    z = orc.gaussian_f32(200_000, seed=4321, subseq=1).astype(np.float64)
+    assert abs(z.mean()) < 5 / math.sqrt(z.size)
+    assert abs(z.var() - 1.0) < 0.015
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    # the 24-bit uniforms are the top bits of the same Philox words as the FP64 stream's
+    x = orc.philox4x32_10([0, 0, 1, 0], [4321, 0])
+    u1 = ((int(x[0]) >> 8) + 1) / 2.0**24
+    u2 = (int(x[2]) >> 8) / 2.0**24
+    r = math.sqrt(-2.0 * math.log(u1))
+    assert z[0] == pytest.approx(r * math.cos(2 * math.pi * u2), rel=1e-5, abs=1e-5)
