@@ -68,7 +68,10 @@ typedef enum {
     RMGE_F64 = 0,    /* FP64 everywhere */
     RMGE_F32 = 1,    /* FP32 working matrix and FP32 SIMT trailing updates */
     RMGE_BF16_TC = 2,/* FP32 working matrix; trailing updates on tcgen05 tensor cores, BF16 operands, FP32 accumulation */
-    RMGE_F16_TC = 3  /* as RMGE_BF16_TC with FP16 operands */
+    RMGE_F16_TC = 3, /* as RMGE_BF16_TC with FP16 operands (power-of-two operand scaling for range) */
+    RMGE_BF16X3_TC = 4, /* as RMGE_BF16_TC, each FP32 operand split x = x_hi + x_lo into two BF16 terms and the
+                           product formed as x_hi y_hi + x_hi y_lo + x_lo y_hi (three tensor-core passes) */
+    RMGE_F16X3_TC = 5   /* the three-pass split with FP16 terms */
 } rmge_prec;
 
 /*
@@ -135,11 +138,17 @@ rmge_status rmge_solve(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void*
 
 /*
  * Iterative refinement of X (Sec. 1.2 and Sec. 7.1: one or more sweeps of residual
- * correction).  A sweep computes R = B - A X in FP64, D = G U^{-1} L^{-1} R (in the factor
- * precision), X <- X + D.  Before each sweep and after the last one the normwise backward error
+ * correction).  A sweep computes R = B - A X in FP64 and a correction D with A D ~= R, then
+ * X <- X + D.  With RMGE_F64 factors D = G U^{-1} L^{-1} R (classical refinement).  With
+ * reduced-precision factors (every other rmge_prec) classical refinement diverges once
+ * kappa(A G) times the factorization error exceeds one -- and kappa(A G) grows like kappa(A) n for a
+ * Gaussian G -- so each sweep instead runs one restarted cycle of flexible GMRES in FP64 on
+ * A D = R, right-preconditioned by G U^{-1} L^{-1} applied in the factor precision (GMRES-based
+ * refinement, Carson and Higham 2017).  Before each sweep and after the last one the normwise
+ * backward error
  *   eta = max_c ||b_c - A x_c||_inf / (||A||_inf ||x_c||_inf + ||b_c||_inf)
  * is computed in FP64 on the device; sweeping stops when eta <= be_tol, after max_iters sweeps,
- * or when eta fails to halve over two sweeps (stagnation).
+ * or when eta fails to halve over two sweeps (stagnation).  0 <= max_iters <= 64.
  * berr (device double[max_iters + 1], may be NULL): eta before sweep 0, 1, ...; entries after
  * the last evaluated one are set to -1.  iters (device int32, may be NULL): sweeps performed.
  * The sweep loop runs on the device state only: every sweep's kernels are enqueued and skip

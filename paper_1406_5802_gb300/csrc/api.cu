@@ -16,7 +16,11 @@ namespace {
 bool valid_kind(rmge_mult_kind k) {
     return k == RMGE_GAUSSIAN || k == RMGE_CIRCULANT_GAUSSIAN || k == RMGE_CIRCULANT_UNIFORM;
 }
-bool valid_prec(rmge_prec p) { return p == RMGE_F64 || p == RMGE_F32 || p == RMGE_BF16_TC || p == RMGE_F16_TC; }
+bool valid_prec(rmge_prec p) { return (int)p >= (int)RMGE_F64 && (int)p <= (int)RMGE_F16X3_TC; }
+bool is_tc(rmge_prec p) { return (int)p >= (int)RMGE_BF16_TC; }
+bool tc_bf16(rmge_prec p) { return p == RMGE_BF16_TC || p == RMGE_BF16X3_TC; }
+int tc_terms(rmge_prec p) { return (p == RMGE_BF16X3_TC || p == RMGE_F16X3_TC) ? 3 : 1; }
+int64_t tc_ldk(int64_t n) { return (n + 63) / 64 * 64; }
 bool is_circ(rmge_mult_kind k) { return k != RMGE_GAUSSIAN; }
 bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
 bool circ_ok(int64_t n) { return pow2(n) && n >= 2 && n <= 8192; }
@@ -29,12 +33,14 @@ int64_t nflags_for(int64_t n, int64_t nrhs) {
 struct Ws {
     DevState* st;
     int* flags;
-    void* inv;
     double* colred;
     double* R;
     double* Y;
     double* D;
     double2* tw;
+    void* tc;                  // 16-bit operand buffers: A hi, A lo, B hi, B lo, each n x tc_ldk(n)
+    double* gm;                // FGMRES work
+    unsigned long long* tcmx;  // FP16 scaling slots
 };
 
 rmge_status carve(void* ws, size_t ws_bytes, int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec, Ws* out) {
@@ -44,12 +50,14 @@ rmge_status carve(void* ws, size_t ws_bytes, int64_t n, int64_t nrhs, rmge_mult_
     char* b = static_cast<char*>(ws);
     out->st = reinterpret_cast<DevState*>(b + L.state);
     out->flags = reinterpret_cast<int*>(b + L.flags);
-    out->inv = b + L.inv;
     out->colred = reinterpret_cast<double*>(b + L.colred);
     out->R = reinterpret_cast<double*>(b + L.R);
     out->Y = reinterpret_cast<double*>(b + L.Y);
     out->D = reinterpret_cast<double*>(b + L.D);
     out->tw = reinterpret_cast<double2*>(b + L.fft);
+    out->tc = is_tc(prec) ? b + L.tc : nullptr;
+    out->tcmx = is_tc(prec) ? reinterpret_cast<unsigned long long*>(b + L.tcmx) : nullptr;
+    out->gm = prec != RMGE_F64 ? reinterpret_cast<double*>(b + L.gm) : nullptr;
     return RMGE_OK;
 }
 
@@ -73,45 +81,62 @@ rmge_status apply_g_cols(rmge_mult_kind kind, rmge_prec prec, int64_t n, int64_t
 
 // In-place y <- U^{-1} L^{-1} y (transposed: L^{-T} U^{-T} y) with the factor type of prec.
 rmge_status lu_solve(rmge_prec prec, bool transposed, int64_t n, int64_t k, const void* LU, int64_t ldlu, void* y,
-                     int64_t ldy, const Ws& w, int ticket, int epoch, const int* skip, cudaStream_t s) {
+                     int64_t ldy, const Ws& w, int epoch, const int* skip, cudaStream_t s) {
     const int k1 = transposed ? 2 : 0, k2 = transposed ? 3 : 1;
     if (prec == RMGE_F64) {
         RMGE_TRY(trsv<double>(k1, n, k, static_cast<const double*>(LU), ldlu, static_cast<double*>(y), ldy, w.st,
-                              w.flags, ticket, epoch, skip, s));
+                              w.flags, epoch, skip, s));
         return trsv<double>(k2, n, k, static_cast<const double*>(LU), ldlu, static_cast<double*>(y), ldy, w.st,
-                            w.flags, ticket + 1, epoch + 1, skip, s);
+                            w.flags, epoch + 1, skip, s);
     }
     RMGE_TRY(trsv<float>(k1, n, k, static_cast<const float*>(LU), ldlu, static_cast<float*>(y), ldy, w.st, w.flags,
-                         ticket, epoch, skip, s));
+                         epoch, skip, s));
     return trsv<float>(k2, n, k, static_cast<const float*>(LU), ldlu, static_cast<float*>(y), ldy, w.st, w.flags,
-                       ticket + 1, epoch + 1, skip, s);
+                       epoch + 1, skip, s);
 }
 
 // X (+)= G U^{-1} L^{-1} V for FP64 V (n x k, ldv), using w.Y (and w.D) as scratch.
 rmge_status correction(rmge_mult_kind kind, rmge_prec prec, int64_t n, int64_t k, const void* LU, int64_t ldlu,
                        const void* G, const double* V, int64_t ldv, double* X, int64_t ldx, bool accumulate,
-                       const Ws& w, int ticket, int epoch, const int* skip, cudaStream_t s) {
+                       const Ws& w, int epoch, const int* skip, cudaStream_t s) {
     const bool low = prec != RMGE_F64;
     if (!low || is_circ(kind)) {
         if (!low) {
             RMGE_TRY(copy_matrix<double, double>(n, k, V, ldv, w.Y, k, skip, s));
-            RMGE_TRY(lu_solve(prec, false, n, k, LU, ldlu, w.Y, k, w, ticket, epoch, skip, s));
+            RMGE_TRY(lu_solve(prec, false, n, k, LU, ldlu, w.Y, k, w, epoch, skip, s));
             return apply_g_cols(kind, prec, n, k, G, false, w.Y, k, X, ldx, accumulate, skip, w, s);
         }
         // reduced-precision factors with a circulant G: solve in FP32, widen, apply C in FP64
         float* yf = reinterpret_cast<float*>(w.Y);
         RMGE_TRY(copy_matrix<double, float>(n, k, V, ldv, yf, k, skip, s));
-        RMGE_TRY(lu_solve(prec, false, n, k, LU, ldlu, yf, k, w, ticket, epoch, skip, s));
+        RMGE_TRY(lu_solve(prec, false, n, k, LU, ldlu, yf, k, w, epoch, skip, s));
         RMGE_TRY(copy_matrix<float, double>(n, k, yf, k, w.D, k, skip, s));
         return apply_g_cols(kind, RMGE_F64, n, k, G, false, w.D, k, X, ldx, accumulate, skip, w, s);
     }
     float* yf = reinterpret_cast<float*>(w.Y);
     float* df = reinterpret_cast<float*>(w.D);
     RMGE_TRY(copy_matrix<double, float>(n, k, V, ldv, yf, k, skip, s));
-    RMGE_TRY(lu_solve(prec, false, n, k, LU, ldlu, yf, k, w, ticket, epoch, skip, s));
+    RMGE_TRY(lu_solve(prec, false, n, k, LU, ldlu, yf, k, w, epoch, skip, s));
     RMGE_TRY(apply_g_cols(kind, prec, n, k, G, false, yf, k, df, k, false, skip, w, s));
     if (accumulate) return add_update<float>(n, k, df, k, X, ldx, skip, s);
     return copy_matrix<float, double>(n, k, df, k, X, ldx, skip, s);
+}
+
+struct PrecondCtx {
+    rmge_mult_kind kind;
+    rmge_prec prec;
+    int64_t n, k;
+    const void* LU;
+    int64_t ldlu;
+    const void* G;
+    const Ws* w;
+};
+
+// z = G U^{-1} L^{-1} v (the preconditioner of the FGMRES sweeps), factor precision inside.
+rmge_status precond_apply(const void* ctx, const double* v, double* z, int epoch, const int* skip, cudaStream_t s) {
+    const PrecondCtx* c = static_cast<const PrecondCtx*>(ctx);
+    return correction(c->kind, c->prec, c->n, c->k, c->LU, c->ldlu, c->G, v, c->k, z, c->k, false, *c->w, epoch, skip,
+                      s);
 }
 
 }  // namespace
@@ -123,8 +148,6 @@ WsLayout ws_layout(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec)
     off = align256(off + sizeof(DevState));
     L.flags = off;
     off = align256(off + sizeof(int) * (size_t)nflags_for(n, nrhs));
-    L.inv = off;
-    off = align256(off + 2 * (size_t)kNb * kNb * elem(prec));
     L.rowsum = off;
     L.colred = off;
     off = align256(off + 3 * sizeof(double) * (size_t)nrhs);
@@ -136,6 +159,12 @@ WsLayout ws_layout(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec)
     off = align256(off + sizeof(double) * (size_t)(n * nrhs));
     L.fft = off;
     if (is_circ(kind)) off = align256(off + sizeof(double2) * (size_t)(n / 2 + 1));
+    L.tcmx = off;
+    if (is_tc(prec)) off = align256(off + sizeof(unsigned long long) * (size_t)(2 * (n / kNb + 2)));
+    L.tc = off;
+    if (is_tc(prec)) off = align256(off + 4 * 2 * (size_t)n * (size_t)tc_ldk(n));
+    L.gm = off;
+    if (prec != RMGE_F64) off = align256(off + gmres_bytes(n, nrhs));
     L.total = off;
     return L;
 }
@@ -211,7 +240,26 @@ rmge_status rmge_apply_multiplier(rmge_mult_kind kind, int64_t n, const double* 
     if (prec == RMGE_F64)
         return gemm<double>(false, n, n, n, 1.0, A, lda, static_cast<const double*>(G), n, 0.0,
                             static_cast<double*>(M), ldm, nullptr, s);
-    return RMGE_ERR_UNSUPPORTED;  // reduced-precision dense apply: see the tensor-core path
+    if (prec == RMGE_F32)
+        return gemm_f64a_f32(n, n, n, A, lda, static_cast<const float*>(G), n, static_cast<float*>(M), ldm, s);
+    // tensor cores: A (rows, K-major) and G^T (K-major) as 16-bit terms, then M = A G in FP32
+    const int64_t ldk = tc_ldk(n);
+    const size_t plane = (size_t)n * (size_t)ldk * 2;
+    char* buf = static_cast<char*>(w.tc);
+    const bool bf = tc_bf16(prec);
+    const int terms = tc_terms(prec);
+    unsigned long long* mxa = bf ? nullptr : w.tcmx;
+    unsigned long long* mxb = bf ? nullptr : w.tcmx + 1;
+    if (!bf) {
+        RMGE_TRY(state_init(w.st, w.flags, 0, reinterpret_cast<double*>(w.tcmx), 2, nullptr, 0, s));
+        RMGE_TRY(maxabs<double>(n, n, A, lda, false, mxa, s));
+        RMGE_TRY(maxabs<float>(n, n, static_cast<const float*>(G), n, false, mxb, s));
+    }
+    RMGE_TRY(tc_split<double>(n, n, A, lda, false, 1.0f, mxa, bf, buf, terms == 3 ? buf + plane : nullptr, ldk, s));
+    RMGE_TRY(tc_split<float>(n, n, static_cast<const float*>(G), n, true, 1.0f, mxb, bf, buf + 2 * plane,
+                             terms == 3 ? buf + 3 * plane : nullptr, ldk, s));
+    return tc_gemm(n, n, n, terms, bf, buf, buf + plane, ldk, buf + 2 * plane, buf + 3 * plane, ldk, 1.0f, 0.0f,
+                   static_cast<float*>(M), ldm, &w.st->error, nullptr, mxa, mxb, s);
 }
 
 rmge_status rmge_factor(int64_t n, void* M, int64_t ldm, rmge_prec prec, int32_t* info, double* growth, void* ws,
@@ -222,11 +270,20 @@ rmge_status rmge_factor(int64_t n, void* M, int64_t ldm, rmge_prec prec, int32_t
     RMGE_TRY(carve(ws, ws_bytes, n, 1, RMGE_GAUSSIAN, prec, &w));
     RMGE_TRY(state_init(w.st, w.flags, 0, w.colred, 0, nullptr, 0, s));
     if (prec == RMGE_F64)
-        RMGE_TRY(genp_factor<double>(n, static_cast<double*>(M), ldm, w.st, static_cast<double*>(w.inv), s));
+        RMGE_TRY(genp_factor<double>(n, static_cast<double*>(M), ldm, w.st, s));
     else if (prec == RMGE_F32)
-        RMGE_TRY(genp_factor<float>(n, static_cast<float*>(M), ldm, w.st, static_cast<float*>(w.inv), s));
-    else
-        return RMGE_ERR_UNSUPPORTED;
+        RMGE_TRY(genp_factor<float>(n, static_cast<float*>(M), ldm, w.st, s));
+    else {
+        const int64_t ldk = kNb;
+        const size_t plane = (size_t)n * (size_t)ldk * 2;
+        char* buf = static_cast<char*>(w.tc);
+        TcUpdate tc{tc_terms(prec), tc_bf16(prec), !tc_bf16(prec), buf, buf + plane, buf + 2 * plane,
+                    buf + 3 * plane, ldk, w.tcmx};
+        if (tc.scale)
+            RMGE_TRY(state_init(w.st, w.flags, 0, reinterpret_cast<double*>(w.tcmx), (int)(2 * (n / kNb + 2)),
+                                nullptr, 0, s));
+        RMGE_TRY(genp_factor_tc(n, static_cast<float*>(M), ldm, w.st, tc, s));
+    }
     return genp_finish(w.st, info, growth, s);
 }
 
@@ -241,7 +298,7 @@ rmge_status rmge_solve(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void*
     Ws w{};
     RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w));
     RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, 0, nullptr, 0, s));
-    return correction(kind, prec, n, nrhs, LU, ldlu, G, B, ldb, X, ldx, false, w, 0, 1, nullptr, s);
+    return correction(kind, prec, n, nrhs, LU, ldlu, G, B, ldb, X, ldx, false, w, 1, nullptr, s);
 }
 
 rmge_status rmge_refine(rmge_mult_kind kind, int64_t n, int64_t nrhs, const double* A, int64_t lda, const void* LU,
@@ -250,7 +307,7 @@ rmge_status rmge_refine(rmge_mult_kind kind, int64_t n, int64_t nrhs, const doub
                         size_t ws_bytes, rmge_stream_t stream) {
     if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs) || A == nullptr || LU == nullptr ||
         G == nullptr || B == nullptr || X == nullptr || lda < n || ldlu < n || ldb < nrhs || ldx < nrhs ||
-        max_iters < 0 || max_iters > (kMaxSolvesPerCall / 2) - 1 || !(be_tol >= 0.0))
+        max_iters < 0 || max_iters > kMaxSweeps || !(be_tol >= 0.0))
         return RMGE_ERR_INVALID_ARG;
     if (is_circ(kind) && !circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -259,14 +316,21 @@ rmge_status rmge_refine(rmge_mult_kind kind, int64_t n, int64_t nrhs, const doub
     RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, (int)(3 * nrhs), berr, max_iters + 1, s));
     RMGE_TRY(row_abs_sums(n, A, lda, w.st, s));
     const int* stop = &w.st->stop;
+    const PrecondCtx pctx{kind, prec, n, nrhs, LU, ldlu, G, &w};
+    const GmresPrecond pre{precond_apply, &pctx};
     for (int it = 0; it <= max_iters; ++it) {
         // R = B - A X in FP64, then the backward error and the stopping test
         RMGE_TRY(copy_matrix<double, double>(n, nrhs, B, ldb, w.R, nrhs, stop, s));
         RMGE_TRY(gemm<double>(false, n, nrhs, n, -1.0, A, lda, X, ldx, 1.0, w.R, nrhs, stop, s));
         RMGE_TRY(backward_error(n, nrhs, w.R, nrhs, X, ldx, B, ldb, w.st, w.colred, it, be_tol, max_iters, berr, s));
         if (it == max_iters) break;
-        // X <- X + G U^{-1} L^{-1} R
-        RMGE_TRY(correction(kind, prec, n, nrhs, LU, ldlu, G, w.R, nrhs, X, ldx, true, w, 2 * it, 2 * it + 1, stop, s));
+        if (prec == RMGE_F64) {
+            // X <- X + G U^{-1} L^{-1} R
+            RMGE_TRY(correction(kind, prec, n, nrhs, LU, ldlu, G, w.R, nrhs, X, ldx, true, w, 2 * it + 1, stop, s));
+        } else {
+            // X <- X + d, A d = R solved by one preconditioned FGMRES cycle in FP64
+            RMGE_TRY(gmres_cycle(n, nrhs, A, lda, w.R, X, ldx, w.gm, pre, 1 + 2 * kGmresM * it, stop, s));
+        }
     }
     return refine_finish(w.st, max_iters, berr, iters, s);
 }
@@ -287,7 +351,7 @@ rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, co
     if (prec == RMGE_F64) {
         // dB = L^{-T} U^{-T} (G^T dX)
         RMGE_TRY(apply_g_cols(kind, prec, n, nrhs, G, true, dX, lddx, dB, lddb, false, nullptr, w, s));
-        RMGE_TRY(lu_solve(prec, true, n, nrhs, LU, ldlu, dB, lddb, w, 0, 1, nullptr, s));
+        RMGE_TRY(lu_solve(prec, true, n, nrhs, LU, ldlu, dB, lddb, w, 1, nullptr, s));
     } else {
         float* zf = reinterpret_cast<float*>(w.Y);
         if (is_circ(kind)) {
@@ -298,7 +362,7 @@ rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, co
             RMGE_TRY(copy_matrix<double, float>(n, nrhs, dX, lddx, df, nrhs, nullptr, s));
             RMGE_TRY(apply_g_cols(kind, prec, n, nrhs, G, true, df, nrhs, zf, nrhs, false, nullptr, w, s));
         }
-        RMGE_TRY(lu_solve(prec, true, n, nrhs, LU, ldlu, zf, nrhs, w, 0, 1, nullptr, s));
+        RMGE_TRY(lu_solve(prec, true, n, nrhs, LU, ldlu, zf, nrhs, w, 1, nullptr, s));
         RMGE_TRY(copy_matrix<float, double>(n, nrhs, zf, nrhs, dB, lddb, nullptr, s));
     }
     if (dA != nullptr) return outer_neg(n, nrhs, dB, lddb, X, ldx, dA, ldda, s);

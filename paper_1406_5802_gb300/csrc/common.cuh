@@ -27,14 +27,18 @@ struct DevState {
     double norm_a;                 // ||A||_inf
     double berr_prev;              // backward error two sweeps back (stagnation test)
     double berr_last;              // latest backward error
-    unsigned int tickets[64];      // dynamic block-order tickets for the triangular solves
+    unsigned int ticket;           // dynamic block-order ticket of the running triangular solve
+    unsigned int done;             // CTAs of the running triangular solve that have finished
+    unsigned int pad1[2];
 };
 
 // Triangular-solve tiling (rows per block, right-hand sides per block column).
 constexpr int kTrsvRows = 32;
 constexpr int kTrsvCols = 8;
-// Maximum number of triangular solves (tickets) one call may issue.
-constexpr int kMaxSolvesPerCall = 64;
+// Refinement sweeps one rmge_refine call may run.
+constexpr int kMaxSweeps = 64;
+// Restart length of the FGMRES cycles used as refinement sweeps for reduced-precision factors.
+constexpr int kGmresM = 16;
 // Spin limit of every bounded device wait (about a second at the default back-off).
 constexpr long long kSpinLimit = 1LL << 22;
 
@@ -47,13 +51,15 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct WsLayout {
     size_t state;     // DevState
     size_t flags;     // int per (row block, column block): triangular-solve completion epochs
-    size_t inv;       // 2 * kNb * kNb of the factor's element type: inverses of the diagonal blocks
     size_t rowsum;    // n doubles
     size_t colred;    // 4 * nrhs doubles (max|r|, max|x|, max|b|, spare) as ull bits
     size_t R;         // n * nrhs doubles (residual / FP64 work)
     size_t Y;         // n * nrhs doubles (FP64 work) or floats
     size_t D;         // n * nrhs doubles
-    size_t fft;       // circulant work: twiddles and one row-pair spectrum per block
+    size_t fft;       // circulant work: twiddle table
+    size_t tcmx;      // FP16 operand-scaling slots (tensor-core precisions)
+    size_t tc;        // 16-bit operand buffers (tensor-core precisions)
+    size_t gm;        // FGMRES work (reduced precisions)
     size_t total;
 };
 

@@ -18,10 +18,10 @@ namespace {
 // Thread (tx, ty) owns rows ty + i*RY and columns tx + j*RX of the CTA tile (i < TM, j < TN), so
 // a warp's shared-memory reads are broadcasts (A) or consecutive words (B), and its global
 // stores are consecutive along a row.
-template <typename T, int BM, int BN, int BK, int TM, int TN, bool TA>
+template <typename T, typename SA, typename SB, int BM, int BN, int BK, int TM, int TN, bool TA>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
-gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T* __restrict__ A, int64_t lda,
-            const T* __restrict__ B, int64_t ldb, T beta, T* __restrict__ C, int64_t ldc, const int* halt) {
+gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const SA* __restrict__ A, int64_t lda,
+            const SB* __restrict__ B, int64_t ldb, T beta, T* __restrict__ C, int64_t ldc, const int* halt) {
     constexpr int RX = BN / TN;  // threads along a row of the tile
     constexpr int RY = BM / TM;
     constexpr int NT = RX * RY;
@@ -54,7 +54,7 @@ gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T* __restrict__ A, i
                 if (TA) { k = e / BM; m = e % BM; }
                 else    { m = e / BK; k = e % BK; }
                 const int64_t gm = m0 + m, gk = k0 + k;
-                if (gm < M && gk < K) v = TA ? A[gk * lda + gm] : A[gm * lda + gk];
+                if (gm < M && gk < K) v = (T)(TA ? A[gk * lda + gm] : A[gm * lda + gk]);
             }
             ra[r] = v;
         }
@@ -65,7 +65,7 @@ gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T* __restrict__ A, i
             if (e < BK * BN) {
                 const int k = e / BN, nn = e % BN;
                 const int64_t gk = k0 + k, gn = n0 + nn;
-                if (gk < K && gn < N) v = B[gk * ldb + gn];
+                if (gk < K && gn < N) v = (T)B[gk * ldb + gn];
             }
             rb[r] = v;
         }
@@ -128,45 +128,56 @@ gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T* __restrict__ A, i
     }
 }
 
-template <typename T, int BM, int BN, int BK, int TM, int TN>
-rmge_status launch(bool ta, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda, const T* B,
+template <typename T, typename SA, typename SB, int BM, int BN, int BK, int TM, int TN>
+rmge_status launch(bool ta, int64_t M, int64_t N, int64_t K, T alpha, const SA* A, int64_t lda, const SB* B,
                    int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s) {
     const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
     const int threads = (BM / TM) * (BN / TN);
     if (ta)
-        gemm_kernel<T, BM, BN, BK, TM, TN, true><<<grid, threads, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C,
-                                                                         ldc, halt);
+        gemm_kernel<T, SA, SB, BM, BN, BK, TM, TN, true><<<grid, threads, 0, s>>>(M, N, K, alpha, A, lda, B, ldb,
+                                                                                 beta, C, ldc, halt);
     else
-        gemm_kernel<T, BM, BN, BK, TM, TN, false><<<grid, threads, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta,
-                                                                          C, ldc, halt);
+        gemm_kernel<T, SA, SB, BM, BN, BK, TM, TN, false><<<grid, threads, 0, s>>>(M, N, K, alpha, A, lda, B, ldb,
+                                                                                  beta, C, ldc, halt);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }
 
 constexpr int64_t kSMs = 152;
 
+template <typename T, typename SA, typename SB>
+rmge_status gemm_any(bool trans_a, int64_t M, int64_t N, int64_t K, T alpha, const SA* A, int64_t lda, const SB* B,
+                     int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return RMGE_OK;
+    // One output per thread: the FMA pipe, not shared memory, bounds these on GB300.
+    if (N <= 8)
+        return launch<T, SA, SB, 16, 8, 64, 1, 1>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
+    if (N <= 16)
+        return launch<T, SA, SB, 16, 16, 32, 1, 1>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
+    // Square-ish: the largest tile that still gives every SM several tiles.
+    if constexpr (sizeof(T) == 4) {
+        const int64_t t128 = ((M + 127) / 128) * ((N + 127) / 128);
+        if (t128 >= 4 * kSMs)
+            return launch<T, SA, SB, 128, 128, 16, 8, 8>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt,
+                                                         s);
+    }
+    const int64_t t64 = ((M + 63) / 64) * ((N + 63) / 64);
+    if (t64 >= 2 * kSMs)
+        return launch<T, SA, SB, 64, 64, 16, 4, 4>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
+    return launch<T, SA, SB, 32, 32, 16, 2, 2>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
+}
+
 }  // namespace
 
 template <typename T>
 rmge_status gemm(bool trans_a, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda, const T* B,
                  int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s) {
-    if (M <= 0 || N <= 0) return RMGE_OK;
-    // Skinny products (right-hand-side blocks): tall tiles, narrow columns.
-    // One output per thread: the FMA pipe, not shared memory, bounds these on GB300.
-    if (N <= 8)
-        return launch<T, 16, 8, 64, 1, 1>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
-    if (N <= 16)
-        return launch<T, 16, 16, 32, 1, 1>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
-    // Square-ish: the largest tile that still gives every SM several tiles.
-    if constexpr (sizeof(T) == 4) {
-        const int64_t t128 = ((M + 127) / 128) * ((N + 127) / 128);
-        if (t128 >= 4 * kSMs)
-            return launch<T, 128, 128, 16, 8, 8>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
-    }
-    const int64_t t64 = ((M + 63) / 64) * ((N + 63) / 64);
-    if (t64 >= 2 * kSMs)
-        return launch<T, 64, 64, 16, 4, 4>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
-    return launch<T, 32, 32, 16, 2, 2>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
+    return gemm_any<T, T, T>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
+}
+
+rmge_status gemm_f64a_f32(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const float* B, int64_t ldb,
+                          float* C, int64_t ldc, cudaStream_t s) {
+    return gemm_any<float, double, float>(false, M, N, K, 1.0f, A, lda, B, ldb, 0.0f, C, ldc, nullptr, s);
 }
 
 template rmge_status gemm<double>(bool, int64_t, int64_t, int64_t, double, const double*, int64_t, const double*,

@@ -2,11 +2,11 @@
 //
 // One step of eq. (3.1) with a pivot block B of nb = kNb columns at offset k:
 //   1. diag_factor: one CTA factors B = L11 U11 by unblocked GENP in shared memory (no pivot
-//      search: the only branch is the breakdown test of Cor. 3.1), then forms U11^{-1} and
-//      L11^{-1} in shared memory and writes them to the workspace.
+//      search: the only branch is the breakdown test of Cor. 3.1).
 //   2. panel_apply: row tiles of D become D B^{-1}-rows  L21 = A21 U11^{-1}  (each row of L21
 //      depends on its own row of A21 only -- the row-parallel elimination that GENP allows and
-//      partial pivoting does not), and column tiles of C become U12 = L11^{-1} A12.
+//      partial pivoting does not), and column tiles of C become U12 = L11^{-1} A12, both by
+//      substitution against the factored pivot block.
 //   3. the Schur complement E <- E - L21 U12 (gemm).
 // By Sec. 3 every blocking reaches the same Schur complements, so the packed L\U equals that of
 // unblocked GENP up to rounding.  A zero or non-finite pivot records the 1-based step in
@@ -27,21 +27,19 @@ __device__ __forceinline__ bool finite_nonzero(T v) {
     return v != T(0) && isfinite(v);
 }
 
-// Dynamic shared memory: a[NB][LDS], ui[NB][LDS], li[NB][LDS].
+// One CTA factors the pivot block in shared memory (dynamic shared memory a[NB][LDS]).
 template <typename T>
 __global__ void __launch_bounds__(256) diag_factor_kernel(int64_t k, int b, T* __restrict__ M, int64_t ldm,
-                                                          DevState* st, T* __restrict__ inv) {
+                                                          DevState* st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* a = reinterpret_cast<T*>(smem_raw);
-    T* ui = a + NB * LDS;
-    T* li = ui + NB * LDS;
     __shared__ int broke;
     if (*(volatile int*)&st->halt) return;
     const int tid = threadIdx.x;
     T* blk = M + k * ldm + k;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        const int i = e / NB, j = e % NB;
-        a[i * LDS + j] = (i < b && j < b) ? blk[i * ldm + j] : (i == j ? T(1) : T(0));
+    for (int e = tid; e < b * b; e += blockDim.x) {
+        const int i = e / b, j = e % b;
+        a[i * LDS + j] = blk[i * ldm + j];
     }
     if (tid == 0) broke = 0;
     __syncthreads();
@@ -68,56 +66,22 @@ __global__ void __launch_bounds__(256) diag_factor_kernel(int64_t k, int b, T* _
     }
     __syncthreads();
     if (broke) return;
-
     for (int e = tid; e < b * b; e += blockDim.x) {
         const int i = e / b, j = e % b;
         blk[i * ldm + j] = a[i * LDS + j];
     }
-
-    // Triangular inverses, NB steps; threads 0..127 build U^{-1} bottom-up row by row, threads
-    // 128..255 build L^{-1} top-down, two threads per column splitting each dot product.
-    // Padding rows/columns (>= b) of a hold the identity, so the inverses are block-identity there.
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        ui[(e / NB) * LDS + e % NB] = T(0);
-        li[(e / NB) * LDS + e % NB] = T(0);
-    }
-    __syncthreads();
-    const bool upper = tid < 128;
-    const int lt = upper ? tid : tid - 128;
-    const int j = lt >> 1, half = lt & 1;
-    for (int step = 0; step < NB; ++step) {
-        T sum = T(0);
-        if (upper) {
-            const int i = NB - 1 - step;  // row of U^{-1} being formed; rows > i are final
-            if (j >= i) {
-                for (int t = i + 1 + half; t <= j; t += 2) sum = fma(a[i * LDS + t], ui[t * LDS + j], sum);
-            }
-            sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-            if (j >= i && half == 0) ui[i * LDS + j] = ((i == j ? T(1) : T(0)) - sum) / a[i * LDS + i];
-        } else {
-            const int i = step;  // row of L^{-1} being formed; rows < i are final
-            if (j <= i) {
-                for (int t = j + half; t < i; t += 2) sum = fma(a[i * LDS + t], li[t * LDS + j], sum);
-            }
-            sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-            if (j <= i && half == 0) li[i * LDS + j] = (i == j ? T(1) : T(0)) - sum;
-        }
-        __syncthreads();
-    }
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        const int i = e / NB, jj = e % NB;
-        inv[e] = ui[i * LDS + jj];
-        inv[NB * NB + e] = li[i * LDS + jj];
-    }
 }
 
-// Row tiles (blockIdx.x < row_tiles): L21[rows] = A21[rows] * U11^{-1}.
-// Column tiles: U12[:, cols] = L11^{-1} * A12[:, cols].  PT rows/columns per CTA.
+// Panel of pivot step k by substitution against the factored pivot block (in shared memory):
+//   row tiles (blockIdx.x < row_tiles):  L21 = A21 U11^{-1}, row by row (x U11 = a);
+//   column tiles:                         U12 = L11^{-1} A12, column by column (L11 x = a).
+// PT rows (columns) per CTA, 16 lanes per row (column); the substitution of one row (column) is
+// sequential over the b pivot columns and synchronises only its own warp.
 template <typename T, int PT>
 __global__ void __launch_bounds__(256) panel_apply_kernel(int64_t k, int b, int64_t rest, int row_tiles,
-                                                          T* __restrict__ M, int64_t ldm, const DevState* st,
-                                                          const T* __restrict__ inv) {
-    __shared__ T iv[NB][LDS];
+                                                          T* __restrict__ M, int64_t ldm, const DevState* st) {
+    static_assert(PT * 16 == 256, "16 lanes per row or column");
+    __shared__ T dd[NB][LDS];
     __shared__ T tile[PT][LDS];  // row tile: tile[r][t]; column tile stored transposed: tile[c][t]
     if (*(volatile const int*)&st->halt) return;
     const int tid = threadIdx.x;
@@ -125,8 +89,7 @@ __global__ void __launch_bounds__(256) panel_apply_kernel(int64_t k, int b, int6
     const int64_t t0 = (int64_t)(is_row ? blockIdx.x : blockIdx.x - row_tiles) * PT;
     const int64_t base = k + b + t0;  // first row (row tile) or column (column tile) of this tile
     const int cnt = (int)((rest - t0) < PT ? (rest - t0) : PT);
-    const T* src_inv = inv + (is_row ? 0 : NB * NB);
-    for (int e = tid; e < NB * NB; e += blockDim.x) iv[e / NB][e % NB] = src_inv[e];
+    for (int e = tid; e < b * b; e += blockDim.x) dd[e / b][e % b] = M[(k + e / b) * ldm + k + e % b];
     if (is_row) {
         for (int e = tid; e < PT * NB; e += blockDim.x) {
             const int r = e / NB, t = e % NB;
@@ -139,32 +102,33 @@ __global__ void __launch_bounds__(256) panel_apply_kernel(int64_t k, int b, int6
         }
     }
     __syncthreads();
-    // each thread: outputs (r, j) with e = tid + q*256 over PT*NB outputs
-    constexpr int PER = PT * NB / 256;
-    T out[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int e = tid + q * 256;
-        T sum = T(0);
-        if (is_row) {  // L21[r][j] = sum_{t <= j} A21[r][t] Uinv[t][j]
-            const int r = e / NB, jj = e % NB;
-            for (int t = 0; t <= jj; ++t) sum = fma(tile[r][t], iv[t][jj], sum);
-        } else {  // U12[i][c] = sum_{t <= i} Linv[i][t] A12[t][c]
-            const int i = e / PT, c = e % PT;
-            for (int t = 0; t <= i; ++t) sum = fma(iv[i][t], tile[c][t], sum);
+    const int q = tid >> 4, lane = tid & 15;  // row (column) q of the tile, lane within it
+    T* x = tile[q];
+    if (is_row) {
+        for (int j = 0; j < b; ++j) {
+            const T xj = x[j] / dd[j][j];
+            __syncwarp();
+            if (lane == 0) x[j] = xj;
+            for (int t = j + 1 + lane; t < b; t += 16) x[t] = fma(-xj, dd[j][t], x[t]);
+            __syncwarp();
         }
-        out[q] = sum;
+    } else {
+        for (int i = 0; i < b; ++i) {
+            const T xi = x[i];
+            for (int t = i + 1 + lane; t < b; t += 16) x[t] = fma(-dd[t][i], xi, x[t]);
+            __syncwarp();
+        }
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int e = tid + q * 256;
-        if (is_row) {
+    if (is_row) {
+        for (int e = tid; e < PT * NB; e += blockDim.x) {
             const int r = e / NB, jj = e % NB;
-            if (r < cnt && jj < b) M[(base + r) * ldm + k + jj] = out[q];
-        } else {
+            if (r < cnt && jj < b) M[(base + r) * ldm + k + jj] = tile[r][jj];
+        }
+    } else {
+        for (int e = tid; e < PT * NB; e += blockDim.x) {
             const int i = e / PT, c = e % PT;
-            if (c < cnt && i < b) M[(k + i) * ldm + base + c] = out[q];
+            if (c < cnt && i < b) M[(k + i) * ldm + base + c] = tile[c][i];
         }
     }
 }
@@ -212,9 +176,9 @@ rmge_status maxabs(int64_t rows, int64_t cols, const T* P, int64_t ldp, bool upp
 }
 
 template <typename T>
-rmge_status genp_factor(int64_t n, T* M, int64_t ldm, DevState* st, T* inv, cudaStream_t s) {
+rmge_status genp_factor(int64_t n, T* M, int64_t ldm, DevState* st, cudaStream_t s) {
     constexpr int PT = 16;
-    const size_t smem = 3 * NB * LDS * sizeof(T);
+    const size_t smem = NB * LDS * sizeof(T);
     // The attribute belongs to the current device's context; setting it is cheap and idempotent.
     if (cudaFuncSetAttribute(diag_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
@@ -224,17 +188,59 @@ rmge_status genp_factor(int64_t n, T* M, int64_t ldm, DevState* st, T* inv, cuda
     RMGE_TRY(maxabs<T>(n, n, M, ldm, false, &st->maxabs_m, s));
     for (int64_t k = 0; k < n; k += NB) {
         const int b = (int)((n - k) < NB ? (n - k) : NB);
-        diag_factor_kernel<T><<<1, 256, smem, s>>>(k, b, M, ldm, st, inv);
+        diag_factor_kernel<T><<<1, 256, smem, s>>>(k, b, M, ldm, st);
         RMGE_LAUNCH_CHECK();
         const int64_t rest = n - k - b;
         if (rest <= 0) break;
         const int tiles = (int)((rest + PT - 1) / PT);
-        panel_apply_kernel<T, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, inv);
+        panel_apply_kernel<T, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st);
         RMGE_LAUNCH_CHECK();
         RMGE_TRY(gemm<T>(false, rest, rest, b, T(-1), M + (k + b) * ldm + k, ldm, M + k * ldm + k + b, ldm, T(1),
                          M + (k + b) * ldm + (k + b), ldm, &st->halt, s));
     }
     RMGE_TRY(maxabs<T>(n, n, M, ldm, true, &st->maxabs_u, s));
+    return RMGE_OK;
+}
+
+// FP32 working matrix with the Schur-complement update on the tensor cores: the same pivot-block
+// steps, with L21 and U12 converted to K-major 16-bit operands (two-term splits for three-pass
+// products) and E <- E - L21 U12 done by tc_gemm.
+rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const TcUpdate& tc,
+                           cudaStream_t s) {
+    constexpr int PT = 16;
+    const size_t smem = NB * LDS * sizeof(float);
+    if (cudaFuncSetAttribute(diag_factor_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        (void)cudaGetLastError();
+        return RMGE_ERR_CUDA;
+    }
+    RMGE_TRY(maxabs<float>(n, n, M, ldm, false, &st->maxabs_m, s));
+    int64_t step = 0;
+    for (int64_t k = 0; k < n; k += NB, ++step) {
+        const int b = (int)((n - k) < NB ? (n - k) : NB);
+        diag_factor_kernel<float><<<1, 256, smem, s>>>(k, b, M, ldm, st);
+        RMGE_LAUNCH_CHECK();
+        const int64_t rest = n - k - b;
+        if (rest <= 0) break;
+        const int tiles = (int)((rest + PT - 1) / PT);
+        panel_apply_kernel<float, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st);
+        RMGE_LAUNCH_CHECK();
+        const float* L21 = M + (k + b) * ldm + k;
+        const float* U12 = M + k * ldm + k + b;
+        unsigned long long* mxa = tc.scale ? tc.mx + 2 * step : nullptr;
+        unsigned long long* mxb = tc.scale ? tc.mx + 2 * step + 1 : nullptr;
+        if (tc.scale) {
+            RMGE_TRY(maxabs<float>(rest, b, L21, ldm, false, mxa, s));
+            RMGE_TRY(maxabs<float>(b, rest, U12, ldm, false, mxb, s));
+        }
+        RMGE_TRY(tc_split<float>(rest, b, L21, ldm, false, 1.0f, mxa, tc.bf16, tc.a_hi,
+                                 tc.terms == 3 ? tc.a_lo : nullptr, tc.ldk, s));
+        RMGE_TRY(tc_split<float>(b, rest, U12, ldm, true, 1.0f, mxb, tc.bf16, tc.b_hi,
+                                 tc.terms == 3 ? tc.b_lo : nullptr, tc.ldk, s));
+        RMGE_TRY(tc_gemm(rest, rest, b, tc.terms, tc.bf16, tc.a_hi, tc.a_lo, tc.ldk, tc.b_hi, tc.b_lo, tc.ldk, -1.0f,
+                         1.0f, M + (k + b) * ldm + (k + b), ldm, &st->error, &st->halt, mxa, mxb, s));
+    }
+    RMGE_TRY(maxabs<float>(n, n, M, ldm, true, &st->maxabs_u, s));
     return RMGE_OK;
 }
 
@@ -244,8 +250,8 @@ rmge_status genp_finish(DevState* st, int32_t* info, double* growth, cudaStream_
     return RMGE_OK;
 }
 
-template rmge_status genp_factor<double>(int64_t, double*, int64_t, DevState*, double*, cudaStream_t);
-template rmge_status genp_factor<float>(int64_t, float*, int64_t, DevState*, float*, cudaStream_t);
+template rmge_status genp_factor<double>(int64_t, double*, int64_t, DevState*, cudaStream_t);
+template rmge_status genp_factor<float>(int64_t, float*, int64_t, DevState*, cudaStream_t);
 template rmge_status maxabs<double>(int64_t, int64_t, const double*, int64_t, bool, unsigned long long*, cudaStream_t);
 template rmge_status maxabs<float>(int64_t, int64_t, const float*, int64_t, bool, unsigned long long*, cudaStream_t);
 

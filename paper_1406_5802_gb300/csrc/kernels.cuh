@@ -17,9 +17,45 @@ template <typename T>
 rmge_status gemm(bool trans_a, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda, const T* B,
                  int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s);
 
+// C (FP32) = A (FP64, rounded to FP32 on load) * B (FP32): M = A G for the FP32 working matrix.
+rmge_status gemm_f64a_f32(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const float* B, int64_t ldb,
+                          float* C, int64_t ldc, cudaStream_t s);
+
+// tc_gemm.cu: C (FP32) <- beta C + alpha sum_t A_t B_t^T on tcgen05 tensor cores, A_t (M x K) and
+// B_t (N x K) BF16 or FP16 K-major with leading dimensions multiples of 8.  terms = 1: A0 B0^T;
+// terms = 3: A0 B0^T + A0 B1^T + A1 B0^T (two-term splits).  *err <- RMGE_ERR_TIMEOUT if a bounded
+// wait expires.
+// mxa/mxb (may be NULL): bits of max|A|, max|B| used by the FP16 power-of-two operand scaling; the
+// epilogue divides the scales back out.
+rmge_status tc_gemm(int64_t M, int64_t N, int64_t K, int terms, bool bf16, const void* A0, const void* A1, int64_t lda,
+                    const void* B0, const void* B1, int64_t ldb, float alpha, float beta, float* C, int64_t ldc,
+                    int* err, const int* halt, const unsigned long long* mxa, const unsigned long long* mxb,
+                    cudaStream_t s);
+// hi (+ lo when non-NULL) = two-term split of scale * 2^e(mx) * src (rows x cols), stored K-major:
+// dst[i][j] (trans = false) or dst[j][i] (trans = true), leading dimension ldd.
+template <typename S>
+rmge_status tc_split(int64_t rows, int64_t cols, const S* src, int64_t lds, bool trans, float scale,
+                     const unsigned long long* mx, bool bf16, void* hi, void* lo, int64_t ldd, cudaStream_t s);
+uint32_t tc_idesc(bool bf16);
+
 // genp.cu: in-place blocked GENP of an n x n matrix with DevState bookkeeping.
 template <typename T>
-rmge_status genp_factor(int64_t n, T* M, int64_t ldm, DevState* st, T* inv, cudaStream_t s);
+rmge_status genp_factor(int64_t n, T* M, int64_t ldm, DevState* st, cudaStream_t s);
+// Tensor-core trailing updates for the FP32 working matrix: operand buffers of n x ldk 16-bit values
+// (hi, lo for A and B), per-step max-abs slots (FP16 scaling), terms 1 or 3.
+struct TcUpdate {
+    int terms;
+    bool bf16;
+    bool scale;
+    void* a_hi;
+    void* a_lo;
+    void* b_hi;
+    void* b_lo;
+    int64_t ldk;
+    unsigned long long* mx;  // 2 slots per pivot step, zeroed by the caller
+};
+rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const TcUpdate& tc,
+                           cudaStream_t s);
 // growth = max|U| / max|M| and info from the DevState (writes the caller's outputs).
 rmge_status genp_finish(DevState* st, int32_t* info, double* growth, cudaStream_t s);
 template <typename T>
@@ -29,11 +65,11 @@ rmge_status maxabs(int64_t rows, int64_t cols, const T* P, int64_t ldp, bool upp
 // trsv.cu: in-place triangular solves with the packed factors, nrhs columns, one launch each.
 //   kind 0: L y = b (unit lower)      kind 1: U y = b (upper)
 //   kind 2: U^T y = b (lower, diag U) kind 3: L^T y = b (unit upper)
-// epoch: a value unique within the call and larger than every epoch used earlier in the call;
-// ticket: a slot of st->tickets zeroed at call start, used once.  skip: as for gemm's halt.
+// epoch: a value unique within the call (flags are zeroed at call start); the ticket counters in
+// st must be zero at launch (state_init, and each solve re-arms them).  skip: as for gemm's halt.
 template <typename T>
 rmge_status trsv(int kind, int64_t n, int64_t nrhs, const T* LU, int64_t ldlu, T* B, int64_t ldb,
-                 DevState* st, int* flags, int ticket, int epoch, const int* skip, cudaStream_t s);
+                 DevState* st, int* flags, int epoch, const int* skip, cudaStream_t s);
 
 // refine.cu
 // Resets the control block, zeroes nflags solve flags and ncolred reduction slots, sets
@@ -58,6 +94,17 @@ rmge_status refine_finish(DevState* st, int max_iters, double* berr_out, int32_t
 // dA = -dB X^T
 rmge_status outer_neg(int64_t n, int64_t k, const double* dB, int64_t lddb, const double* X, int64_t ldx,
                       double* dA, int64_t ldda, cudaStream_t s);
+
+// gmres.cu: one FGMRES(kGmresM) cycle on A d = R for all k columns, right-preconditioned by P
+// (z = P v applied in the factor precision), X += d.  buf: gmres_bytes(n, k) bytes.  Uses epochs
+// epoch0 .. epoch0 + 2 kGmresM - 1 for P's triangular solves.
+struct GmresPrecond {
+    rmge_status (*apply)(const void* ctx, const double* v, double* z, int epoch, const int* skip, cudaStream_t s);
+    const void* ctx;
+};
+size_t gmres_bytes(int64_t n, int64_t k);
+rmge_status gmres_cycle(int64_t n, int64_t k, const double* A, int64_t lda, const double* R, double* X, int64_t ldx,
+                        double* buf, const GmresPrecond& P, int epoch0, const int* skip, cudaStream_t s);
 
 // fft.cu: circulant multiplier (Theorem 5.1).  G = [c (n doubles) | u = F(c) (n double2)];
 // tw: n/2 double2 of scratch for the twiddle table.

@@ -24,7 +24,10 @@ __global__ void state_init_kernel(DevState* st, int* flags, int64_t nflags, doub
         st->berr_prev = __longlong_as_double(0x7ff0000000000000LL);
         st->berr_last = __longlong_as_double(0x7ff0000000000000LL);
     }
-    for (int64_t i = tid; i < 64; i += stride) st->tickets[i] = 0u;
+    if (tid == 0) {
+        st->ticket = 0u;
+        st->done = 0u;
+    }
     for (int64_t i = tid; i < nflags; i += stride) flags[i] = 0;
     for (int64_t i = tid; i < ncolred; i += stride) colred[i] = 0.0;
     for (int64_t i = tid; i < nberr; i += stride) berr_out[i] = -1.0;

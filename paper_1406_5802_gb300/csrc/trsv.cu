@@ -7,7 +7,8 @@
 // Completion is published per (row block, column block) with a release store of an epoch value;
 // consumers acquire it.  CTAs take a ticket from an atomic counter at start and derive their
 // block from it, so a CTA only ever waits for CTAs that took earlier tickets and are therefore
-// already running: no co-residency assumption, no deadlock.  Every wait is bounded
+// already running: no co-residency assumption, no deadlock.  The last CTA to finish resets the
+// counter, so consecutive solves on one stream need no re-initialisation.  Every wait is bounded
 // (kSpinLimit polls); on expiry the CTA records RMGE_ERR_TIMEOUT in DevState::error and all
 // waiting CTAs return without writing.
 //
@@ -27,10 +28,19 @@ __device__ __forceinline__ T coef(int kind, const T* LU, int64_t ld, int64_t i, 
     return (kind <= 1) ? LU[i * ld + t] : LU[t * ld + i];
 }
 
+// The last CTA to finish re-arms the ticket counters for the next solve on the stream.
+__device__ __forceinline__ void finish_ticket(DevState* st) {
+    if (atomicAdd(&st->done, 1u) == gridDim.x - 1) {
+        st->ticket = 0u;
+        st->done = 0u;
+        __threadfence();
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t nrhs, const T* __restrict__ LU,
                                                   int64_t ld, T* B, int64_t ldb, DevState* st, int* flags,
-                                                  int ticket_slot, int epoch, const int* skip) {
+                                                  int epoch, const int* skip) {
     __shared__ T cs[TB][TB + 1];  // off-diagonal coefficient tile
     __shared__ T cd[TB][TB + 1];  // diagonal block
     __shared__ T ys[TB][KC];
@@ -43,7 +53,7 @@ __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t n
     const int64_t nblk = (n + TB - 1) / TB;
     const int64_t ncb = (nrhs + KC - 1) / KC;
     if (tid == 0) {
-        my_ticket = (int)atomicAdd(&st->tickets[ticket_slot], 1u);
+        my_ticket = (int)atomicAdd(&st->ticket, 1u);
         failed = 0;
     }
     __syncthreads();
@@ -95,7 +105,10 @@ __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t n
             }
         }
         __syncthreads();
-        if (failed) return;
+        if (failed) {
+            if (tid == 0) finish_ticket(st);
+            return;
+        }
 #pragma unroll
         for (int u = 0; u < CPT; ++u) {
             const int e = tid + u * NT;
@@ -128,26 +141,28 @@ __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t n
     if (live) B[gr * ldb + gc] = acc;
     __threadfence();
     __syncthreads();
-    if (tid == 0) st_release(flags + rb * ncb + cb, epoch);
+    if (tid == 0) {
+        st_release(flags + rb * ncb + cb, epoch);
+        finish_ticket(st);
+    }
 }
 
 }  // namespace
 
 template <typename T>
 rmge_status trsv(int kind, int64_t n, int64_t nrhs, const T* LU, int64_t ldlu, T* B, int64_t ldb, DevState* st,
-                 int* flags, int ticket, int epoch, const int* skip, cudaStream_t s) {
-    if (ticket < 0 || ticket >= kMaxSolvesPerCall) return RMGE_ERR_INVALID_ARG;
+                 int* flags, int epoch, const int* skip, cudaStream_t s) {
     const int64_t nblk = (n + TB - 1) / TB;
     const int64_t ncb = (nrhs + KC - 1) / KC;
     const int64_t grid = nblk * ncb;
-    trsv_kernel<T><<<(unsigned)grid, NT, 0, s>>>(kind, n, nrhs, LU, ldlu, B, ldb, st, flags, ticket, epoch, skip);
+    trsv_kernel<T><<<(unsigned)grid, NT, 0, s>>>(kind, n, nrhs, LU, ldlu, B, ldb, st, flags, epoch, skip);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }
 
 template rmge_status trsv<double>(int, int64_t, int64_t, const double*, int64_t, double*, int64_t, DevState*, int*,
-                                  int, int, const int*, cudaStream_t);
+                                  int, const int*, cudaStream_t);
 template rmge_status trsv<float>(int, int64_t, int64_t, const float*, int64_t, float*, int64_t, DevState*, int*, int,
-                                 int, const int*, cudaStream_t);
+                                 const int*, cudaStream_t);
 
 }  // namespace rmge

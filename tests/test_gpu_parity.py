@@ -177,7 +177,10 @@ def test_refinement_sweep_matches_oracle(orc):
     berr, iters = rmge.refine("gaussian", dev(A), dev(LU), dev(G), dev(B), Xd, "f64", max_iters=1, be_tol=0.0)
     X1 = host(Xd)
     ref = orc.refine_step(0, A, LU, G, B, X0)
-    assert np.max(np.abs(X1 - ref)) <= 1e-6 * np.max(np.abs(ref - X0)) + 1e-14 * np.max(np.abs(ref))
+    # the GPU residual is plain FP64, the oracle's compensated: they differ by ~n u ||A|| ||X||, which the
+    # correction amplifies by up to kappa(A) = 1e6
+    kappa = np.linalg.cond(A, np.inf)
+    assert np.max(np.abs(X1 - ref)) <= kappa * n * U64 * np.max(np.abs(ref))
     e = host(berr)
     assert e[0] == pytest.approx(orc.backward_error(A, X0, B), rel=1e-3)
     assert e[1] == pytest.approx(orc.backward_error(A, X1, B), rel=0.5)
@@ -208,5 +211,10 @@ def test_adjoint_matches_oracle_gradient(orc, kind, n, k):
     dB, dA = rmge.solve_backward(kind, out["LU"], out["G"], X, dev(Wt), "f64")
     rdB, rdA, info = orc.solve_adjoint_gepp(A, host(X), Wt)
     assert info == 0
-    assert np.max(np.abs(host(dB) - rdB)) <= 1e-10 * np.max(np.abs(rdB))
-    assert np.max(np.abs(host(dA) - rdA)) <= 1e-10 * np.max(np.abs(rdA))
+    # the adjoint solve is unrefined: its error scales with kappa(A G) u (growth aside); the target for
+    # gradients is 1e-6 relative
+    tol = min(1e-6, max(1e-12, 100 * n * np.linalg.cond(orc.apply_multiplier(0 if kind == "gaussian" else 1, A,
+                                                                            host(out["G"]) if kind == "gaussian"
+                                                                            else host(out["G"])[:n])) * U64))
+    assert np.max(np.abs(host(dB) - rdB)) <= tol * np.max(np.abs(rdB))
+    assert np.max(np.abs(host(dA) - rdA)) <= tol * np.max(np.abs(rdA))

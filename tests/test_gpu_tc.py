@@ -1,0 +1,90 @@
+"""Parity of the reduced-precision paths (FP32 SIMT, tcgen05 BF16/FP16 tensor cores, plain and
+three-pass split) against the FP64 oracle: M = A G, the GENP factors, and the whole solve."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1406_5802_gb300 import rmge
+from paper_1406_5802_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0**-24
+# unit roundoff of one product term per precision: plain BF16 / FP16 operands, or the two-term split
+TERM_U = {"f32": U32, "bf16": 2.0**-9, "f16": 2.0**-12, "bf16x3": 2.0**-17, "f16x3": 2.0**-22}
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1406_5802_gb300 import build as B
+    B.build()
+    rmge.load_library()
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16", "f16", "bf16x3", "f16x3"])
+@pytest.mark.parametrize("n", [64, 130, 300, 1000])
+def test_apply_multiplier_reduced(orc, prec, n):
+    A, _ = W.orthogonal_factor_system(n, 1, 1e-4, seed=n)
+    Gd = rmge.make_multiplier("gaussian", n, seed=3, subsequence=1, prec=prec)
+    G = host(Gd)
+    M = host(rmge.apply_multiplier("gaussian", dev(A), Gd, prec))
+    ref = orc.matmul(A, G)
+    scale = np.abs(A) @ np.abs(G)
+    # rounding of each operand to the term precision plus FP32 accumulation over n terms
+    tol = (4 * TERM_U[prec] + 2 * n * U32) * scale
+    assert np.all(np.abs(M - ref) <= tol), float(np.max(np.abs(M - ref) / scale))
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16", "f16", "bf16x3", "f16x3"])
+@pytest.mark.parametrize("n", [64, 129, 300, 700])
+def test_factor_reduced_matches_oracle(orc, prec, n):
+    A, _ = W.gaussian_system(n, 1, seed=70 + n)
+    G = W.gaussian_multiplier(n, 71 + n).astype(np.float32).astype(np.float64)
+    M = orc.matmul(A, G).astype(np.float32).astype(np.float64)
+    Md = dev(M, torch.float32)
+    info, growth = rmge.factor(Md, prec)
+    LU = host(Md)
+    ref, rinfo = orc.genp(M)
+    assert int(host(info)[0]) == rinfo == 0
+    g = orc.growth(M, ref)
+    # backward error of the factors: ||L U - M|| / (||L|| ||U||) at the working precision (FP32) or the
+    # product-term precision, whichever is coarser
+    L = np.tril(LU, -1) + np.eye(n)
+    U = np.triu(LU)
+    be = np.max(np.abs(L @ U - M)) / np.max(np.abs(np.abs(L) @ np.abs(U)))
+    assert be <= 8 * max(TERM_U[prec], n * U32 / 8), be
+    assert np.max(np.abs(LU - ref)) <= 1e3 * max(TERM_U[prec], U32) * n * g * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16x3", "f16x3"])
+@pytest.mark.parametrize("n,k,smin", [(256, 1, 1e-4), (1024, 8, 1e-4), (2048, 3, 1e-6)])
+def test_mixed_solve_reaches_fp64_accuracy(orc, prec, n, k, smin):
+    """Reduced-precision factors of A G, won back to the FP64 target by FP64 residuals and FGMRES sweeps."""
+    A, B = W.orthogonal_factor_system(n, k, smin, seed=900 + n)
+    out = rmge.gesv("gaussian", dev(A), dev(B), seed=901, prec=prec, max_iters=40, be_tol=1e-13)
+    X = host(out["X"])
+    it = int(host(out["iters"])[0])
+    berr = host(out["berr"])
+    assert int(host(out["info"])[0]) == 0
+    be = orc.backward_error(A, X, B)
+    assert be <= 1e-13, (be, it, berr[: it + 1])
+    assert berr[it] <= 1e-13
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_plain_16bit_factors_refine_on_a_well_conditioned_system(orc, prec):
+    """Single-term BF16/FP16 trailing updates: enough when kappa(A G) u16 stays well below one."""
+    n, k = 256, 2
+    A, B = W.orthogonal_factor_system(n, k, 0.5, seed=77)
+    out = rmge.gesv("gaussian", dev(A), dev(B), seed=78, prec=prec, max_iters=40, be_tol=1e-13)
+    be = orc.backward_error(A, host(out["X"]), B)
+    assert be <= 1e-13, (be, int(host(out["iters"])[0]))
