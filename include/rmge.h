@@ -92,6 +92,12 @@ size_t rmge_multiplier_bytes(rmge_mult_kind kind, int64_t n, rmge_prec prec);
 size_t rmge_workspace_size(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec);
 
 /*
+ * The smaller scratch size that rmge_solve and rmge_solve_backward alone need (they use no
+ * tensor-core operand buffers and no refinement work).  0 for an invalid request.
+ */
+size_t rmge_solve_workspace_size(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec);
+
+/*
  * Draw the multiplier (Def. 4.1; Ex. 5.1; Theorem 5.1 for the spectrum).
  * Entries come from the counter-based generator Philox4x32-10 (Salmon et al., SC'11) with
  * key = seed and the 64-bit counter words (2,3) = subsequence; entry e of the stream uses

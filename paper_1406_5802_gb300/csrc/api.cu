@@ -43,10 +43,13 @@ struct Ws {
     unsigned long long* tcmx;  // FP16 scaling slots
 };
 
-rmge_status carve(void* ws, size_t ws_bytes, int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec, Ws* out) {
+// full = false: the call needs no tensor-core operand buffers and no FGMRES work (solves, adjoint),
+// which sit at the end of the layout.
+rmge_status carve(void* ws, size_t ws_bytes, int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec, Ws* out,
+                  bool full = true) {
     if (ws == nullptr || ((uintptr_t)ws & 255) != 0) return RMGE_ERR_WORKSPACE;
     const WsLayout L = ws_layout(n, nrhs, kind, prec);
-    if (ws_bytes < L.total) return RMGE_ERR_WORKSPACE;
+    if (ws_bytes < (full ? L.total : L.tcmx)) return RMGE_ERR_WORKSPACE;
     char* b = static_cast<char*>(ws);
     out->st = reinterpret_cast<DevState*>(b + L.state);
     out->flags = reinterpret_cast<int*>(b + L.flags);
@@ -56,8 +59,9 @@ rmge_status carve(void* ws, size_t ws_bytes, int64_t n, int64_t nrhs, rmge_mult_
     out->D = reinterpret_cast<double*>(b + L.D);
     out->tw = reinterpret_cast<double2*>(b + L.fft);
     out->tc = is_tc(prec) ? b + L.tc : nullptr;
-    out->tcmx = is_tc(prec) ? reinterpret_cast<unsigned long long*>(b + L.tcmx) : nullptr;
-    out->gm = prec != RMGE_F64 ? reinterpret_cast<double*>(b + L.gm) : nullptr;
+    out->tcmx = (full && is_tc(prec)) ? reinterpret_cast<unsigned long long*>(b + L.tcmx) : nullptr;
+    out->gm = (full && prec != RMGE_F64) ? reinterpret_cast<double*>(b + L.gm) : nullptr;
+    if (!full) out->tc = nullptr;
     return RMGE_OK;
 }
 
@@ -198,6 +202,12 @@ size_t rmge_multiplier_bytes(rmge_mult_kind kind, int64_t n, rmge_prec prec) {
     return (size_t)n * (size_t)n * elem(prec);
 }
 
+size_t rmge_solve_workspace_size(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec) {
+    if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs)) return 0;
+    if (is_circ(kind) && !circ_ok(n)) return 0;
+    return ws_layout(n, nrhs, kind, prec).tcmx;
+}
+
 size_t rmge_workspace_size(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec) {
     if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs)) return 0;
     if (is_circ(kind) && !circ_ok(n)) return 0;
@@ -296,7 +306,7 @@ rmge_status rmge_solve(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void*
     if (is_circ(kind) && !circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Ws w{};
-    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w));
+    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w, false));
     RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, 0, nullptr, 0, s));
     return correction(kind, prec, n, nrhs, LU, ldlu, G, B, ldb, X, ldx, false, w, 1, nullptr, s);
 }
@@ -346,7 +356,7 @@ rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, co
     if (is_circ(kind) && !circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Ws w{};
-    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w));
+    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w, false));
     RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, 0, nullptr, 0, s));
     if (prec == RMGE_F64) {
         // dB = L^{-T} U^{-T} (G^T dX)

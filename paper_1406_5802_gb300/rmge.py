@@ -27,7 +27,7 @@ STATUS = {0: "RMGE_OK", 1: "RMGE_ERR_INVALID_ARG", 2: "RMGE_ERR_BREAKDOWN", 3: "
 
 EXPORTED = ["rmge_multiplier_bytes", "rmge_workspace_size", "rmge_make_multiplier", "rmge_apply_multiplier",
             "rmge_factor", "rmge_solve", "rmge_refine", "rmge_solve_backward", "rmge_status_string",
-            "rmge_kernel_launches"]
+            "rmge_kernel_launches", "rmge_solve_workspace_size"]
 
 
 class RmgeError(RuntimeError):
@@ -61,6 +61,7 @@ def load_library(path: str = LIB_PATH):
                                           _i64, C.c_int, _vp, _sz, _vp]),
         "rmge_status_string": (C.c_char_p, [C.c_int]),
         "rmge_kernel_launches": (C.c_ulonglong, []),
+        "rmge_solve_workspace_size": (_sz, [_i64, _i64, C.c_int, C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
