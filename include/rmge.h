@@ -179,6 +179,29 @@ rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, co
                                 double* dB, int64_t lddb, double* dA, int64_t ldda, rmge_prec prec,
                                 void* ws, size_t ws_bytes, rmge_stream_t stream);
 
+/*
+ * rmge_solve for callers that cannot allocate device memory.  The paper has no counterpart: this is
+ * a deployment convenience.  Some callers must not call cudaMalloc at the point where they solve:
+ * a serving loop with latency guarantees (a device allocation can synchronise the whole device),
+ * or a plugin whose host process owns all device memory and passes it only inputs and outputs.
+ * This call takes the same inputs and outputs as rmge_solve but no workspace: its scratch is one
+ * file-scope device array of rmge_noalloc_capacity() bytes (16 MiB), which every GPU that loads the
+ * library holds until the process exits.  The call allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library routine).  On the first call on a device it looks up the array's device
+ * address with cudaGetSymbolAddress (that device must be current) and caches it; make that first
+ * call before any stream capture.  Requests whose rmge_solve_workspace_size exceeds the capacity
+ * return RMGE_ERR_WORKSPACE and enqueue nothing (FP64 with nrhs = 16 fits n up to about 43 000).  Every call
+ * shares the array and leaves its contents behind; each call clears what must start at zero (the
+ * control block and the solve flags) on its stream before use, so calls that follow one another on
+ * a stream are safe, but calls that overlap on the GPU (other streams, other host threads) race.
+ */
+rmge_status rmge_solve_noalloc(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void* LU, int64_t ldlu,
+                               const void* G, const double* B, int64_t ldb, double* X, int64_t ldx, rmge_prec prec,
+                               rmge_stream_t stream);
+
+/* Bytes of the device array rmge_solve_noalloc uses as its scratch. */
+size_t rmge_noalloc_capacity(void);
+
 /* Number of kernel launches this process has enqueued through the library so far (host-side
  * counter; lets a caller count the kernels of a timed region). */
 unsigned long long rmge_kernel_launches(void);

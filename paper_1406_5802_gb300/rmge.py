@@ -27,7 +27,7 @@ STATUS = {0: "RMGE_OK", 1: "RMGE_ERR_INVALID_ARG", 2: "RMGE_ERR_BREAKDOWN", 3: "
 
 EXPORTED = ["rmge_multiplier_bytes", "rmge_workspace_size", "rmge_make_multiplier", "rmge_apply_multiplier",
             "rmge_factor", "rmge_solve", "rmge_refine", "rmge_solve_backward", "rmge_status_string",
-            "rmge_kernel_launches", "rmge_solve_workspace_size"]
+            "rmge_kernel_launches", "rmge_solve_workspace_size", "rmge_solve_noalloc", "rmge_noalloc_capacity"]
 
 
 class RmgeError(RuntimeError):
@@ -62,6 +62,8 @@ def load_library(path: str = LIB_PATH):
         "rmge_status_string": (C.c_char_p, [C.c_int]),
         "rmge_kernel_launches": (C.c_ulonglong, []),
         "rmge_solve_workspace_size": (_sz, [_i64, _i64, C.c_int, C.c_int]),
+        "rmge_solve_noalloc": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, C.c_int, _vp]),
+        "rmge_noalloc_capacity": (_sz, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -193,6 +195,19 @@ def solve(kind, LU, G, B, prec="f64", X=None, ws=None) -> torch.Tensor:
         ws = workspace(n, k, kind, prec)
     _check("rmge_solve", L.rmge_solve(_kind(kind), n, k, _p(LU), _ld(LU), _p(G), _p(B), _ld(B), _p(X), _ld(X),
                                       _prec(prec), _p(ws), ws.numel(), _stream()))
+    return X
+
+
+def solve_noalloc(kind, LU, G, B, prec="f64", X=None) -> torch.Tensor:
+    """rmge_solve with the library's fixed device scratch array instead of a workspace argument."""
+    L = _cuda_lib()
+    _need(B, torch.float64, "B")
+    n, k = B.shape
+    if X is None:
+        X = torch.empty(n, k, dtype=torch.float64, device=B.device)
+    _need(X, torch.float64, "X")
+    _check("rmge_solve_noalloc", L.rmge_solve_noalloc(_kind(kind), n, k, _p(LU), _ld(LU), _p(G), _p(B), _ld(B),
+                                                      _p(X), _ld(X), _prec(prec), _stream()))
     return X
 
 
