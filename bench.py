@@ -34,6 +34,9 @@ BE_TOL, MAX_ITERS = 1e-13, 10
 # FMA-chain microbenchmark); the nominal peak at the 2070 MHz maximum SM clock is
 # 152 SMs x 2 DFMA x 2 flop x 2.070 GHz = 1.2586 TFLOP/s.
 FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# DRAM bytes (read + write) of one A G launch at n = 4096, from an ncu capture of this kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum); reset to None whenever the kernel changes.
+AG_TRAFFIC_BYTES = 3.733360e9 + 0.134520e9
 
 
 def flops_per_solve(n, k, sweeps):
@@ -149,7 +152,9 @@ def main():
     rmge.load_library()
 
     n, k = N_SYS, K_RHS
-    A, Bm = W.orthogonal_factor_system_torch(n, k, SIGMA_MIN, seed=SEED + 7919 * rank, device="cuda")
+    A_np, B_np = W.orthogonal_factor_system(n, k, SIGMA_MIN, seed=SEED + 7919 * rank)
+    A = torch.as_tensor(A_np).cuda()
+    Bm = torch.as_tensor(B_np).cuda()
     kind, prec = "gaussian", "f64"
     ws = rmge.workspace(n, k, kind, prec)
     G = rmge.empty_multiplier(kind, n, prec)
@@ -273,7 +278,8 @@ def main():
                          "oracle_berr_last": be_oracle},
             "roofline": {"kernel": "gemm_kernel (M = A G, FP64 DFMA)", "bound": "alu", "achieved": achieved,
                          "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_ALU_PEAK_TFLOPS,
-                         "traffic": None,
+                         "traffic": AG_TRAFFIC_BYTES,
+                         "algorithmic_bytes": 3 * n * n * 8,
                          "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (FP64 is not in "
                                         "MEASURED_PEAKS.json)",
                          "apply_ms": apply_ms},

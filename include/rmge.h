@@ -92,8 +92,8 @@ size_t rmge_multiplier_bytes(rmge_mult_kind kind, int64_t n, rmge_prec prec);
 size_t rmge_workspace_size(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec);
 
 /*
- * The smaller scratch size that rmge_solve and rmge_solve_backward alone need (they use no
- * tensor-core operand buffers and no refinement work).  0 for an invalid request.
+ * The smaller scratch size that rmge_solve, and rmge_solve_backward without refinement, need
+ * (no tensor-core operand buffers and no refinement work).  0 for an invalid request.
  */
 size_t rmge_solve_workspace_size(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec);
 
@@ -171,12 +171,17 @@ rmge_status rmge_refine(rmge_mult_kind kind, int64_t n, int64_t nrhs, const doub
  * A G = L U, A^{-T} = L^{-T} U^{-T} G^T, so
  *   dB = L^{-T} U^{-T} (G^T dX)   (n x nrhs, FP64 out)
  *   dA = -dB X^T                   (n x n, FP64 out, ldda; may be NULL to skip)
- * X: the solution (n x nrhs FP64).  dB must not overlap dX.  (The paper has no gradients; this is
- * the adjoint of the linear solve its method computes.)
+ * X: the solution (n x nrhs FP64).  dB must not overlap dX.  With max_iters > 0 and A given, dB is
+ * then refined on the transposed system A^T dB = dX exactly as rmge_refine refines X (FP64
+ * residuals; classical sweeps for FP64 factors, FGMRES sweeps otherwise), with berr / iters as
+ * there; max_iters = 0 skips refinement (A, berr, iters may be NULL).  The scratch needed is
+ * rmge_solve_workspace_size without refinement and rmge_workspace_size with it.  (The paper has no
+ * gradients; this is the adjoint of the linear solve its method computes.)
  */
-rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void* LU, int64_t ldlu,
-                                const void* G, const double* X, int64_t ldx, const double* dX, int64_t lddx,
-                                double* dB, int64_t lddb, double* dA, int64_t ldda, rmge_prec prec,
+rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, const double* A, int64_t lda,
+                                const void* LU, int64_t ldlu, const void* G, const double* X, int64_t ldx,
+                                const double* dX, int64_t lddx, double* dB, int64_t lddb, double* dA, int64_t ldda,
+                                rmge_prec prec, int32_t max_iters, double be_tol, double* berr, int32_t* iters,
                                 void* ws, size_t ws_bytes, rmge_stream_t stream);
 
 /*
@@ -201,6 +206,29 @@ rmge_status rmge_solve_noalloc(rmge_mult_kind kind, int64_t n, int64_t nrhs, con
 
 /* Bytes of the device array rmge_solve_noalloc uses as its scratch. */
 size_t rmge_noalloc_capacity(void);
+
+/*
+ * Batched solve: count independent systems A_i x_i = b_i (one right-hand side each) of uneven sizes
+ * n[i] <= nmax, each by the whole method with FP32 factors (Def. 4.1 multiplier G_i, M_i = A_i G_i,
+ * blocked GENP, x_i = G_i U^{-1} L^{-1} b_i) and FP64 refinement sweeps (residual b - A x in FP64,
+ * stop at normwise backward error <= be_tol or after max_sweeps), in ONE persistent kernel launch:
+ * each CTA takes the next system from a queue in the order given (pass decreasing n), so uneven sizes
+ * balance across SMs.  G_i is the FP32 Gaussian multiplier stream (seed, subsequence i) of
+ * rmge_make_multiplier.  Device arrays: n[count]; offA[count] element offsets of A_i (n_i x n_i, FP64,
+ * row-major, ld n_i) in A; offv[count] element offsets of b_i, x_i in b, x (FP64); order[count] a
+ * permutation of 0..count-1; outputs info[i] (0 or first breakdown step), berr[i], sweeps[i].
+ * config selects the compiled tile shape (0: 256 threads, 32x32 tiles; 1: 256 threads, 64x64;
+ * 2: 1024 threads, 64x64) and ctas the number of persistent CTAs -- both chosen by the autotuner of
+ * the Python binding.  ws: rmge_batched_workspace_size(nmax, ctas) bytes, 256-byte aligned (per-CTA
+ * scratch for G_i, M_i and vectors).  The launch (one memset of the queue head + one kernel) can be
+ * captured in a CUDA graph and replayed.
+ */
+size_t rmge_batched_workspace_size(int64_t nmax, int32_t ctas);
+rmge_status rmge_solve_batched(int64_t count, const int32_t* n, const int64_t* offA, const int64_t* offv,
+                               const int32_t* order, const double* A, const double* b, double* x, int32_t* info,
+                               double* berr, int32_t* sweeps, uint64_t seed, int32_t max_sweeps, double be_tol,
+                               int64_t nmax, int32_t config, int32_t ctas, void* ws, size_t ws_bytes,
+                               rmge_stream_t stream);
 
 /* Number of kernel launches this process has enqueued through the library so far (host-side
  * counter; lets a caller count the kernels of a timed region). */

@@ -99,11 +99,33 @@ rmge_status lu_solve(rmge_prec prec, bool transposed, int64_t n, int64_t k, cons
                        epoch + 1, skip, s);
 }
 
-// X (+)= G U^{-1} L^{-1} V for FP64 V (n x k, ldv), using w.Y (and w.D) as scratch.
+// X (+)= G U^{-1} L^{-1} V for FP64 V (n x k, ldv), using w.Y (and w.D) as scratch; with trans,
+// X (+)= L^{-T} U^{-T} G^T V (the same approximate inverse for the transposed system).
 rmge_status correction(rmge_mult_kind kind, rmge_prec prec, int64_t n, int64_t k, const void* LU, int64_t ldlu,
                        const void* G, const double* V, int64_t ldv, double* X, int64_t ldx, bool accumulate,
-                       const Ws& w, int epoch, const int* skip, cudaStream_t s) {
+                       const Ws& w, int epoch, const int* skip, cudaStream_t s, bool trans = false) {
     const bool low = prec != RMGE_F64;
+    if (trans) {
+        // z = G^T v first (FP64 for FP64 factors or a circulant G, else FP32), then U^T, L^T solves
+        if (!low) {
+            RMGE_TRY(apply_g_cols(kind, prec, n, k, G, true, V, ldv, w.Y, k, false, skip, w, s));
+            RMGE_TRY(lu_solve(prec, true, n, k, LU, ldlu, w.Y, k, w, epoch, skip, s));
+            if (accumulate) return add_update<double>(n, k, w.Y, k, X, ldx, skip, s);
+            return copy_matrix<double, double>(n, k, w.Y, k, X, ldx, skip, s);
+        }
+        float* zf = reinterpret_cast<float*>(w.Y);
+        if (is_circ(kind)) {
+            RMGE_TRY(apply_g_cols(kind, RMGE_F64, n, k, G, true, V, ldv, w.D, k, false, skip, w, s));
+            RMGE_TRY(copy_matrix<double, float>(n, k, w.D, k, zf, k, skip, s));
+        } else {
+            float* vf = reinterpret_cast<float*>(w.D);
+            RMGE_TRY(copy_matrix<double, float>(n, k, V, ldv, vf, k, skip, s));
+            RMGE_TRY(apply_g_cols(kind, prec, n, k, G, true, vf, k, zf, k, false, skip, w, s));
+        }
+        RMGE_TRY(lu_solve(prec, true, n, k, LU, ldlu, zf, k, w, epoch, skip, s));
+        if (accumulate) return add_update<float>(n, k, zf, k, X, ldx, skip, s);
+        return copy_matrix<float, double>(n, k, zf, k, X, ldx, skip, s);
+    }
     if (!low || is_circ(kind)) {
         if (!low) {
             RMGE_TRY(copy_matrix<double, double>(n, k, V, ldv, w.Y, k, skip, s));
@@ -134,13 +156,43 @@ struct PrecondCtx {
     int64_t ldlu;
     const void* G;
     const Ws* w;
+    bool trans;
 };
 
-// z = G U^{-1} L^{-1} v (the preconditioner of the FGMRES sweeps), factor precision inside.
+// z = G U^{-1} L^{-1} v (the preconditioner of the FGMRES sweeps; transposed for A^T), factor
+// precision inside.
 rmge_status precond_apply(const void* ctx, const double* v, double* z, int epoch, const int* skip, cudaStream_t s) {
     const PrecondCtx* c = static_cast<const PrecondCtx*>(ctx);
     return correction(c->kind, c->prec, c->n, c->k, c->LU, c->ldlu, c->G, v, c->k, z, c->k, false, *c->w, epoch, skip,
-                      s);
+                      s, c->trans);
+}
+
+// Refinement sweeps for A X = B (trans = false) or A^T X = B (trans = true); see rmge_refine.
+rmge_status refine_loop(rmge_mult_kind kind, rmge_prec prec, bool trans, int64_t n, int64_t nrhs, const double* A,
+                        int64_t lda, const void* LU, int64_t ldlu, const void* G, const double* B, int64_t ldb,
+                        double* X, int64_t ldx, int32_t max_iters, double be_tol, double* berr, int32_t* iters,
+                        const Ws& w, int epoch0, cudaStream_t s) {
+    RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, (int)(3 * nrhs), berr, max_iters + 1, s));
+    RMGE_TRY(abs_sums_max(n, A, lda, trans, w.st, s));
+    const int* stop = &w.st->stop;
+    const PrecondCtx pctx{kind, prec, n, nrhs, LU, ldlu, G, &w, trans};
+    const GmresPrecond pre{precond_apply, &pctx};
+    for (int it = 0; it <= max_iters; ++it) {
+        // R = B - op(A) X in FP64, then the backward error and the stopping test
+        RMGE_TRY(copy_matrix<double, double>(n, nrhs, B, ldb, w.R, nrhs, stop, s));
+        RMGE_TRY(gemm<double>(trans, n, nrhs, n, -1.0, A, lda, X, ldx, 1.0, w.R, nrhs, stop, s));
+        RMGE_TRY(backward_error(n, nrhs, w.R, nrhs, X, ldx, B, ldb, w.st, w.colred, it, be_tol, max_iters, berr, s));
+        if (it == max_iters) break;
+        const int epoch = epoch0 + 2 * kGmresM * it;
+        if (prec == RMGE_F64) {
+            // X <- X + G U^{-1} L^{-1} R  (transposed: L^{-T} U^{-T} G^T R)
+            RMGE_TRY(correction(kind, prec, n, nrhs, LU, ldlu, G, w.R, nrhs, X, ldx, true, w, epoch, stop, s, trans));
+        } else {
+            // X <- X + d, op(A) d = R solved by one preconditioned FGMRES cycle in FP64
+            RMGE_TRY(gmres_cycle(n, nrhs, A, lda, trans, w.R, X, ldx, w.gm, pre, epoch, stop, s));
+        }
+    }
+    return refine_finish(w.st, max_iters, berr, iters, s);
 }
 
 }  // namespace
@@ -323,60 +375,58 @@ rmge_status rmge_refine(rmge_mult_kind kind, int64_t n, int64_t nrhs, const doub
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Ws w{};
     RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w));
-    RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, (int)(3 * nrhs), berr, max_iters + 1, s));
-    RMGE_TRY(row_abs_sums(n, A, lda, w.st, s));
-    const int* stop = &w.st->stop;
-    const PrecondCtx pctx{kind, prec, n, nrhs, LU, ldlu, G, &w};
-    const GmresPrecond pre{precond_apply, &pctx};
-    for (int it = 0; it <= max_iters; ++it) {
-        // R = B - A X in FP64, then the backward error and the stopping test
-        RMGE_TRY(copy_matrix<double, double>(n, nrhs, B, ldb, w.R, nrhs, stop, s));
-        RMGE_TRY(gemm<double>(false, n, nrhs, n, -1.0, A, lda, X, ldx, 1.0, w.R, nrhs, stop, s));
-        RMGE_TRY(backward_error(n, nrhs, w.R, nrhs, X, ldx, B, ldb, w.st, w.colred, it, be_tol, max_iters, berr, s));
-        if (it == max_iters) break;
-        if (prec == RMGE_F64) {
-            // X <- X + G U^{-1} L^{-1} R
-            RMGE_TRY(correction(kind, prec, n, nrhs, LU, ldlu, G, w.R, nrhs, X, ldx, true, w, 2 * it + 1, stop, s));
-        } else {
-            // X <- X + d, A d = R solved by one preconditioned FGMRES cycle in FP64
-            RMGE_TRY(gmres_cycle(n, nrhs, A, lda, w.R, X, ldx, w.gm, pre, 1 + 2 * kGmresM * it, stop, s));
-        }
-    }
-    return refine_finish(w.st, max_iters, berr, iters, s);
+    return refine_loop(kind, prec, false, n, nrhs, A, lda, LU, ldlu, G, B, ldb, X, ldx, max_iters, be_tol, berr, iters,
+                       w, 1, s);
 }
 
-rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void* LU, int64_t ldlu,
-                                const void* G, const double* X, int64_t ldx, const double* dX, int64_t lddx, double* dB,
-                                int64_t lddb, double* dA, int64_t ldda, rmge_prec prec, void* ws, size_t ws_bytes,
-                                rmge_stream_t stream) {
+rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, const double* A, int64_t lda,
+                                const void* LU, int64_t ldlu, const void* G, const double* X, int64_t ldx,
+                                const double* dX, int64_t lddx, double* dB, int64_t lddb, double* dA, int64_t ldda,
+                                rmge_prec prec, int32_t max_iters, double be_tol, double* berr, int32_t* iters,
+                                void* ws, size_t ws_bytes, rmge_stream_t stream) {
     if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs) || LU == nullptr || G == nullptr ||
-        dX == nullptr || dB == nullptr || ldlu < n || lddx < nrhs || lddb < nrhs || (dA != nullptr && (X == nullptr ||
-        ldda < n || ldx < nrhs)))
+        dX == nullptr || dB == nullptr || ldlu < n || lddx < nrhs || lddb < nrhs ||
+        (dA != nullptr && (X == nullptr || ldda < n || ldx < nrhs)) || max_iters < 0 || max_iters > kMaxSweeps ||
+        (max_iters > 0 && (A == nullptr || lda < n)) || !(be_tol >= 0.0))
         return RMGE_ERR_INVALID_ARG;
     if (is_circ(kind) && !circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Ws w{};
-    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w, false));
+    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w, max_iters > 0));
     RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, 0, nullptr, 0, s));
-    if (prec == RMGE_F64) {
-        // dB = L^{-T} U^{-T} (G^T dX)
-        RMGE_TRY(apply_g_cols(kind, prec, n, nrhs, G, true, dX, lddx, dB, lddb, false, nullptr, w, s));
-        RMGE_TRY(lu_solve(prec, true, n, nrhs, LU, ldlu, dB, lddb, w, 1, nullptr, s));
-    } else {
-        float* zf = reinterpret_cast<float*>(w.Y);
-        if (is_circ(kind)) {
-            RMGE_TRY(apply_g_cols(kind, RMGE_F64, n, nrhs, G, true, dX, lddx, w.D, nrhs, false, nullptr, w, s));
-            RMGE_TRY(copy_matrix<double, float>(n, nrhs, w.D, nrhs, zf, nrhs, nullptr, s));
-        } else {
-            float* df = reinterpret_cast<float*>(w.D);
-            RMGE_TRY(copy_matrix<double, float>(n, nrhs, dX, lddx, df, nrhs, nullptr, s));
-            RMGE_TRY(apply_g_cols(kind, prec, n, nrhs, G, true, df, nrhs, zf, nrhs, false, nullptr, w, s));
-        }
-        RMGE_TRY(lu_solve(prec, true, n, nrhs, LU, ldlu, zf, nrhs, w, 1, nullptr, s));
-        RMGE_TRY(copy_matrix<float, double>(n, nrhs, zf, nrhs, dB, lddb, nullptr, s));
-    }
+    // dB = A^{-T} dX ~= L^{-T} U^{-T} G^T dX
+    RMGE_TRY(correction(kind, prec, n, nrhs, LU, ldlu, G, dX, lddx, dB, lddb, false, w, 1, nullptr, s, true));
+    if (max_iters > 0)
+        RMGE_TRY(refine_loop(kind, prec, true, n, nrhs, A, lda, LU, ldlu, G, dX, lddx, dB, lddb, max_iters, be_tol,
+                             berr, iters, w, 3, s));
     if (dA != nullptr) return outer_neg(n, nrhs, dB, lddb, X, ldx, dA, ldda, s);
     return RMGE_OK;
+}
+
+size_t rmge_batched_workspace_size(int64_t nmax, int32_t ctas) {
+    if (nmax < 1 || nmax > 4096 || ctas < 1 || ctas > 65535) return 0;
+    return batched_scratch_bytes(nmax, ctas);
+}
+
+rmge_status rmge_solve_batched(int64_t count, const int32_t* n, const int64_t* offA, const int64_t* offv,
+                               const int32_t* order, const double* A, const double* b, double* x, int32_t* info,
+                               double* berr, int32_t* sweeps, uint64_t seed, int32_t max_sweeps, double be_tol,
+                               int64_t nmax, int32_t config, int32_t ctas, void* ws, size_t ws_bytes,
+                               rmge_stream_t stream) {
+    if (count < 1 || count > INT32_MAX || n == nullptr || offA == nullptr || offv == nullptr || order == nullptr ||
+        A == nullptr || b == nullptr || x == nullptr || info == nullptr || berr == nullptr || sweeps == nullptr ||
+        max_sweeps < 0 || max_sweeps > kMaxSweeps || !(be_tol >= 0.0) || config < 0 || config > 2)
+        return RMGE_ERR_INVALID_ARG;
+    const size_t need = rmge_batched_workspace_size(nmax, ctas);
+    if (need == 0) return RMGE_ERR_INVALID_ARG;
+    if (ws == nullptr || ((uintptr_t)ws & 255) != 0 || ws_bytes < need) return RMGE_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(ws, 0, 256, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RMGE_ERR_CUDA;
+    }
+    return batched_solve(count, n, offA, offv, order, A, b, x, info, berr, sweeps, seed, max_sweeps, be_tol, nmax,
+                         config, ctas, ws, s);
 }
 
 }  // extern "C"

@@ -1,0 +1,417 @@
+// batched.cu -- thousands of independent randomized GENP solves of uneven size in one persistent launch.
+//
+// Each system i (size n_i, one right-hand side) runs the whole method inside one CTA:
+//   G_i  = FP32 Gaussian multiplier (Def. 4.1), Philox stream (seed, subsequence i)
+//   M_i  = A_i G_i                       (Fact 4.1; A_i FP64, rounded to FP32 on load)
+//   M_i  = L U  by blocked GENP           (eq. (3.1), 32-column pivot blocks, FP32)
+//   x_i  = G_i U^{-1} L^{-1} b_i          (Fact 4.1)
+//   sweeps of r = b - A x (FP64), x += G U^{-1} L^{-1} r, until the normwise backward error is
+//   below tol (Sec. 1.2, Sec. 7.1)
+// CTAs are persistent: each takes the next system from a queue ordered by decreasing n (longest
+// first), so uneven sizes balance across the SMs.  The queue counter re-arms itself when the last
+// CTA finishes, so the launch can be captured once in a CUDA graph and replayed.  Per-CTA scratch
+// (G, M and vectors, sized for the largest system) lives in the caller's workspace.  The tile size
+// and thread count are template parameters chosen by the host-side autotuner.
+#include <climits>
+
+#include "kernels.cuh"
+
+namespace rmge {
+namespace {
+
+struct BatchArgs {
+    int64_t count;
+    const int32_t* n;          // sizes
+    const int64_t* offA;       // element offset of A_i (n_i x n_i, row-major, ld n_i)
+    const int64_t* offv;       // element offset of b_i, x_i
+    const int32_t* order;      // processing order (decreasing n)
+    const double* A;
+    const double* b;
+    double* x;
+    int32_t* info;             // per system: 0 or first breakdown step
+    double* berr;              // per system: final backward error
+    int32_t* sweeps;           // per system: refinement sweeps
+    uint64_t seed;
+    int max_sweeps;
+    double tol;
+    float* scratch;            // per CTA: G (nmax^2), M (nmax^2), y, t (nmax each) floats
+    double* dscratch;          // per CTA: r (nmax) doubles
+    int64_t nmax;
+    unsigned int* queue;       // [0] next system, [1] finished CTAs
+};
+
+// ---------------------------------------------------------------------------------------------
+// Philox4x32-10 (same stream definition as gen.cu's FP32 Gaussian multipliers)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi_a = __umulhi(0xD2511F53u, c.x), lo_a = 0xD2511F53u * c.x;
+        const uint32_t hi_b = __umulhi(0xCD9E8D57u, c.z), lo_b = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+template <int T>
+__device__ void gen_gaussian_f32(int64_t count, uint64_t seed, uint64_t subseq, float* out) {
+    for (int64_t p = threadIdx.x; p < (count + 1) / 2; p += T) {
+        const uint4 x = philox(make_uint4((uint32_t)p, (uint32_t)(p >> 32), (uint32_t)subseq, (uint32_t)(subseq >> 32)),
+                               (uint32_t)seed, (uint32_t)(seed >> 32));
+        const float u1 = (float)((x.x >> 8) + 1u) * 0x1p-24f;
+        const float u2 = (float)(x.z >> 8) * 0x1p-24f;
+        const float r = sqrtf(-2.0f * logf(u1));
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        out[2 * p] = r * cs;
+        if (2 * p + 1 < count) out[2 * p + 1] = r * sn;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// CTA-wide FP32 GEMM: C (M x N, ldc) = alpha A B + beta C, A (M x K) of type SA, B (K x N) FP32.
+// TILE x TILE output tiles, each thread an (TILE/RT) x (TILE/RT) micro-tile, RT = sqrt(T).
+// ---------------------------------------------------------------------------------------------
+template <int T, int TILE, typename SA>
+__device__ void cta_gemm(int M, int N, int K, const SA* __restrict__ A, int lda, const float* __restrict__ B, int ldb,
+                         float* __restrict__ C, int ldc, float alpha, float beta, float* smem) {
+    constexpr int BK = 16;
+    constexpr int RT = (T == 256) ? 16 : 32;  // threads per tile row
+    constexpr int RY = T / RT;
+    constexpr int TM = TILE / RY, TN = TILE / RT;
+    float* As = smem;                  // [BK][TILE]
+    float* Bs = smem + BK * TILE;      // [BK][TILE]
+    const int tx = threadIdx.x % RT, ty = threadIdx.x / RT;
+    for (int t0 = 0; t0 < ((M + TILE - 1) / TILE) * ((N + TILE - 1) / TILE); ++t0) {
+        const int tm = t0 / ((N + TILE - 1) / TILE), tn = t0 % ((N + TILE - 1) / TILE);
+        const int m0 = tm * TILE, n0 = tn * TILE;
+        float acc[TM][TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = 0.0f;
+        for (int k0 = 0; k0 < K; k0 += BK) {
+            for (int e = threadIdx.x; e < TILE * BK; e += T) {
+                const int m = e / BK, kk = e % BK;
+                const int gm = m0 + m, gk = k0 + kk;
+                As[kk * TILE + m] = (gm < M && gk < K) ? (float)A[(int64_t)gm * lda + gk] : 0.0f;
+                const int kb = e / TILE, nn = e % TILE;
+                const int gkb = k0 + kb, gn = n0 + nn;
+                Bs[kb * TILE + nn] = (gkb < K && gn < N) ? B[(int64_t)gkb * ldb + gn] : 0.0f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                float a[TM], bb[TN];
+#pragma unroll
+                for (int i = 0; i < TM; ++i) a[i] = As[kk * TILE + ty + i * RY];
+#pragma unroll
+                for (int j = 0; j < TN; ++j) bb[j] = Bs[kk * TILE + tx + j * RT];
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int gm = m0 + ty + i * RY;
+            if (gm >= M) continue;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int gn = n0 + tx + j * RT;
+                if (gn >= N) continue;
+                float* c = C + (int64_t)gm * ldc + gn;
+                *c = (beta == 0.0f) ? alpha * acc[i][j] : fmaf(beta, *c, alpha * acc[i][j]);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------------
+// CTA-wide blocked GENP of M (n x n, ld n) with 32-column pivot blocks; returns 0 or the first
+// breakdown step.
+// ---------------------------------------------------------------------------------------------
+constexpr int PB = 32;
+
+template <int T, int TILE>
+__device__ int cta_genp(int n, float* M, float* smem, int* flag) {
+    float* d = smem;  // [PB][PB + 1] pivot block
+    for (int k = 0; k < n; k += PB) {
+        const int b = min(PB, n - k);
+        for (int e = threadIdx.x; e < b * b; e += T) d[(e / b) * (PB + 1) + e % b] = M[(int64_t)(k + e / b) * n + k + e % b];
+        if (threadIdx.x == 0) *flag = 0;
+        __syncthreads();
+        for (int s = 0; s < b; ++s) {
+            const float piv = d[s * (PB + 1) + s];
+            if (piv == 0.0f || !isfinite(piv)) {
+                __syncthreads();
+                return k + s + 1;
+            }
+            for (int i = s + 1 + threadIdx.x; i < b; i += T) d[i * (PB + 1) + s] /= piv;
+            __syncthreads();
+            const int w = b - s - 1;
+            for (int e = threadIdx.x; e < w * w; e += T) {
+                const int i = s + 1 + e / w, j = s + 1 + e % w;
+                d[i * (PB + 1) + j] = fmaf(-d[i * (PB + 1) + s], d[s * (PB + 1) + j], d[i * (PB + 1) + j]);
+            }
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < b * b; e += T) M[(int64_t)(k + e / b) * n + k + e % b] = d[(e / b) * (PB + 1) + e % b];
+        const int rest = n - k - b;
+        if (rest > 0) {
+            // L21 rows: x U11 = a, one thread per row; U12 columns: L11 x = a, one thread per column
+            for (int q = threadIdx.x; q < 2 * rest; q += T) {
+                if (q < rest) {
+                    float* row = M + (int64_t)(k + b + q) * n + k;
+                    for (int j = 0; j < b; ++j) {
+                        float v = row[j];
+                        for (int t = 0; t < j; ++t) v = fmaf(-row[t], d[t * (PB + 1) + j], v);
+                        row[j] = v / d[j * (PB + 1) + j];
+                    }
+                } else {
+                    float* col = M + (int64_t)k * n + k + b + (q - rest);
+                    for (int i = 0; i < b; ++i) {
+                        float v = col[(int64_t)i * n];
+                        for (int t = 0; t < i; ++t) v = fmaf(-d[i * (PB + 1) + t], col[(int64_t)t * n], v);
+                        col[(int64_t)i * n] = v;
+                    }
+                }
+            }
+            __syncthreads();
+            cta_gemm<T, TILE, float>(rest, rest, b, M + (int64_t)(k + b) * n + k, n, M + (int64_t)k * n + k + b, n,
+                                     M + (int64_t)(k + b) * n + k + b, n, -1.0f, 1.0f, smem + PB * (PB + 1));
+        }
+    }
+    return 0;
+}
+
+// In-place y <- U^{-1} L^{-1} y (FP32 vector, n), warp 0 solving 32-row diagonal blocks, all threads
+// updating the rows below (above) with the solved block.
+template <int T>
+__device__ void cta_lu_solve(int n, const float* M, float* y) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < n; k += 32) {  // L z = y
+        const int b = min(32, n - k);
+        if (warp == 0) {
+            float v = lane < b ? y[k + lane] : 0.0f;
+            for (int j = 0; j < b; ++j) {
+                const float zj = __shfl_sync(0xffffffffu, v, j);
+                if (lane > j && lane < b) v = fmaf(-M[(int64_t)(k + lane) * n + k + j], zj, v);
+            }
+            if (lane < b) y[k + lane] = v;
+        }
+        __syncthreads();
+        for (int i = k + b + threadIdx.x; i < n; i += T) {
+            float v = y[i];
+            for (int j = 0; j < b; ++j) v = fmaf(-M[(int64_t)i * n + k + j], y[k + j], v);
+            y[i] = v;
+        }
+        __syncthreads();
+    }
+    for (int k = ((n - 1) / 32) * 32; k >= 0; k -= 32) {  // U x = z
+        const int b = min(32, n - k);
+        if (warp == 0) {
+            float v = lane < b ? y[k + lane] : 0.0f;
+            for (int j = b - 1; j >= 0; --j) {
+                float xj = 0.0f;
+                if (lane == j) v = v / M[(int64_t)(k + j) * n + k + j];
+                xj = __shfl_sync(0xffffffffu, v, j);
+                if (lane < j) v = fmaf(-M[(int64_t)(k + lane) * n + k + j], xj, v);
+            }
+            if (lane < b) y[k + lane] = v;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < k; i += T) {
+            float v = y[i];
+            for (int j = 0; j < b; ++j) v = fmaf(-M[(int64_t)i * n + k + j], y[k + j], v);
+            y[i] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// out (FP32 or FP64, accumulate or assign) = G v, one warp per row
+template <int T>
+__device__ void cta_gemv_f32(int n, const float* G, const float* v, double* out, bool accumulate) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < n; i += T / 32) {
+        float s = 0.0f;
+        for (int j = lane; j < n; j += 32) s = fmaf(G[(int64_t)i * n + j], v[j], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[i] = accumulate ? out[i] + (double)s : (double)s;
+    }
+    __syncthreads();
+}
+
+template <int T, int TILE>
+__global__ void __launch_bounds__(T) batched_kernel(BatchArgs a) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int sys_s, flag, stop_s;
+    __shared__ double red[T / 32];
+    __shared__ double red2[T / 32];
+    float* G = a.scratch + (int64_t)blockIdx.x * (2 * a.nmax * a.nmax + 2 * a.nmax);
+    float* M = G + a.nmax * a.nmax;
+    float* y = M + a.nmax * a.nmax;
+    double* r = a.dscratch + (int64_t)blockIdx.x * a.nmax;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned int q = atomicAdd(&a.queue[0], 1u);
+            sys_s = (q < (unsigned int)a.count) ? a.order[q] : -1;
+        }
+        __syncthreads();
+        const int sys = sys_s;
+        __syncthreads();
+        if (sys < 0) break;
+        const int n = a.n[sys];
+        const double* A = a.A + a.offA[sys];
+        const double* b = a.b + a.offv[sys];
+        double* x = a.x + a.offv[sys];
+
+        gen_gaussian_f32<T>((int64_t)n * n, a.seed, (uint64_t)sys, G);
+        __syncthreads();
+        cta_gemm<T, TILE, double>(n, n, n, A, n, G, n, M, n, 1.0f, 0.0f, smem);
+        const int info = cta_genp<T, TILE>(n, M, smem, &flag);
+        if (info != 0) {
+            if (threadIdx.x == 0) {
+                a.info[sys] = info;
+                a.berr[sys] = __longlong_as_double(0x7ff8000000000000LL);
+                a.sweeps[sys] = 0;
+            }
+            for (int i = threadIdx.x; i < n; i += T) x[i] = __longlong_as_double(0x7ff8000000000000LL);
+            __syncthreads();
+            continue;
+        }
+        // x = G U^{-1} L^{-1} b
+        for (int i = threadIdx.x; i < n; i += T) y[i] = (float)b[i];
+        __syncthreads();
+        cta_lu_solve<T>(n, M, y);
+        cta_gemv_f32<T>(n, G, y, x, false);
+        // sweeps: r = b - A x in FP64, eta = ||r|| / (||A|| ||x|| + ||b||), x += G U^{-1} L^{-1} r
+        double norm_a = 0.0;
+        int sw = 0;
+        double eta = 0.0;
+        for (;; ++sw) {
+            double rmax = 0.0, amax = 0.0;
+            for (int i = warp; i < n; i += T / 32) {
+                double s = b[i], as = 0.0;
+                for (int j = lane; j < n; j += 32) {
+                    const double aij = A[(int64_t)i * n + j];
+                    s = fma(-aij, x[j], s);
+                    as += fabs(aij);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    s += __shfl_xor_sync(0xffffffffu, s, o);
+                    as += __shfl_xor_sync(0xffffffffu, as, o);
+                }
+                if (lane == 0) r[i] = s;
+                rmax = fmax(rmax, fabs(s));
+                amax = fmax(amax, as);
+            }
+            if (lane == 0) {
+                red[warp] = rmax;
+                red2[warp] = amax;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double rm = 0.0, am = 0.0, xm = 0.0, bm = 0.0;
+                for (int w = 0; w < T / 32; ++w) {
+                    rm = fmax(rm, red[w]);
+                    am = fmax(am, red2[w]);
+                }
+                for (int i = 0; i < n; ++i) {
+                    xm = fmax(xm, fabs(x[i]));
+                    bm = fmax(bm, fabs(b[i]));
+                }
+                if (sw == 0) norm_a = am;
+                const double den = norm_a * xm + bm;
+                double e = den > 0.0 ? rm / den : 0.0;
+                if (!isfinite(e) || !isfinite(xm)) e = __longlong_as_double(0x7ff0000000000000LL);
+                red[0] = e;
+                stop_s = (e <= a.tol || sw >= a.max_sweeps || !isfinite(e)) ? 1 : 0;
+            }
+            __syncthreads();
+            eta = red[0];
+            if (stop_s) break;
+            for (int i = threadIdx.x; i < n; i += T) y[i] = (float)r[i];
+            __syncthreads();
+            cta_lu_solve<T>(n, M, y);
+            cta_gemv_f32<T>(n, G, y, x, true);
+        }
+        if (threadIdx.x == 0) {
+            a.info[sys] = 0;
+            a.berr[sys] = eta;
+            a.sweeps[sys] = sw;
+        }
+        __syncthreads();
+    }
+    // the last CTA to leave re-arms the queue for the next launch (or graph replay)
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&a.queue[1], 1u) == gridDim.x - 1) {
+            a.queue[0] = 0u;
+            a.queue[1] = 0u;
+            __threadfence();
+        }
+    }
+}
+
+template <int T, int TILE>
+rmge_status launch_batched(const BatchArgs& a, int ctas, cudaStream_t s) {
+    const size_t smem = (size_t)(2 * 16 * TILE + PB * (PB + 1)) * sizeof(float);
+    if (cudaFuncSetAttribute(batched_kernel<T, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        (void)cudaGetLastError();
+        return RMGE_ERR_CUDA;
+    }
+    batched_kernel<T, TILE><<<ctas, T, smem, s>>>(a);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
+}  // namespace
+
+size_t batched_scratch_bytes(int64_t nmax, int ctas) {
+    return align256((size_t)ctas * (size_t)(2 * nmax * nmax + 2 * nmax) * sizeof(float)) +
+           align256((size_t)ctas * (size_t)nmax * sizeof(double)) + 256;
+}
+
+rmge_status batched_solve(int64_t count, const int32_t* n, const int64_t* offA, const int64_t* offv,
+                          const int32_t* order, const double* A, const double* b, double* x, int32_t* info,
+                          double* berr, int32_t* sweeps, uint64_t seed, int max_sweeps, double tol, int64_t nmax,
+                          int config, int ctas, void* ws, cudaStream_t s) {
+    char* base = static_cast<char*>(ws);
+    BatchArgs a{};
+    a.count = count;
+    a.n = n;
+    a.offA = offA;
+    a.offv = offv;
+    a.order = order;
+    a.A = A;
+    a.b = b;
+    a.x = x;
+    a.info = info;
+    a.berr = berr;
+    a.sweeps = sweeps;
+    a.seed = seed;
+    a.max_sweeps = max_sweeps;
+    a.tol = tol;
+    a.nmax = nmax;
+    a.queue = reinterpret_cast<unsigned int*>(base);
+    a.scratch = reinterpret_cast<float*>(base + 256);
+    a.dscratch = reinterpret_cast<double*>(base + 256 +
+                                           align256((size_t)ctas * (size_t)(2 * nmax * nmax + 2 * nmax) * sizeof(float)));
+    switch (config) {
+        case 0: return launch_batched<256, 32>(a, ctas, s);
+        case 1: return launch_batched<256, 64>(a, ctas, s);
+        case 2: return launch_batched<1024, 64>(a, ctas, s);
+        default: return RMGE_ERR_INVALID_ARG;
+    }
+}
+
+}  // namespace rmge

@@ -171,8 +171,8 @@ size_t gmres_bytes(int64_t n, int64_t k) {
     return (size_t)(2 * m + 2) * vec + small;
 }
 
-rmge_status gmres_cycle(int64_t n, int64_t k, const double* A, int64_t lda, const double* R, double* X, int64_t ldx,
-                        double* buf, const GmresPrecond& P, int epoch0, const int* skip, cudaStream_t s) {
+rmge_status gmres_cycle(int64_t n, int64_t k, const double* A, int64_t lda, bool trans_a, const double* R, double* X,
+                        int64_t ldx, double* buf, const GmresPrecond& P, int epoch0, const int* skip, cudaStream_t s) {
     const int m = kGmresM;
     const int64_t vec = n * k;
     double* V = buf;                          // (m + 1) vectors
@@ -192,8 +192,8 @@ rmge_status gmres_cycle(int64_t n, int64_t k, const double* A, int64_t lda, cons
         double* zj = Z + (int64_t)j * vec;
         // z_j = P v_j in the factor precision, widened to FP64
         RMGE_TRY(P.apply(P.ctx, vj, zj, epoch0 + 2 * j, skip, s));
-        // w = A z_j in FP64
-        RMGE_TRY(gemm<double>(false, n, k, n, 1.0, A, lda, zj, k, 0.0, W, k, skip, s));
+        // w = op(A) z_j in FP64
+        RMGE_TRY(gemm<double>(trans_a, n, k, n, 1.0, A, lda, zj, k, 0.0, W, k, skip, s));
         // classical Gram-Schmidt, twice
         for (int pass = 0; pass < 2; ++pass) {
             dots_kernel<<<dim3((unsigned)(j + 1), (unsigned)k), RT, 0, s>>>(n, k, m, j, V, W, hc, H, pass == 1,

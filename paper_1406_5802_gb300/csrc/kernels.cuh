@@ -76,8 +76,8 @@ rmge_status trsv(int kind, int64_t n, int64_t nrhs, const T* LU, int64_t ldlu, T
 // berr_out[0..nberr) to -1 (berr_out may be NULL).
 rmge_status state_init(DevState* st, int* flags, int64_t nflags, double* colred, int ncolred, double* berr_out,
                        int nberr, cudaStream_t s);
-// st->norm_a = ||A||_inf
-rmge_status row_abs_sums(int64_t n, const double* A, int64_t lda, DevState* st, cudaStream_t s);
+// st->norm_a = ||A||_inf (transposed: ||A^T||_inf)
+rmge_status abs_sums_max(int64_t n, const double* A, int64_t lda, bool transposed, DevState* st, cudaStream_t s);
 // R = B (copy, n x k)
 template <typename Tin, typename Tout>
 rmge_status copy_matrix(int64_t rows, int64_t cols, const Tin* src, int64_t lds, Tout* dst, int64_t ldd,
@@ -95,7 +95,7 @@ rmge_status refine_finish(DevState* st, int max_iters, double* berr_out, int32_t
 rmge_status outer_neg(int64_t n, int64_t k, const double* dB, int64_t lddb, const double* X, int64_t ldx,
                       double* dA, int64_t ldda, cudaStream_t s);
 
-// gmres.cu: one FGMRES(kGmresM) cycle on A d = R for all k columns, right-preconditioned by P
+// gmres.cu: one FGMRES(kGmresM) cycle on op(A) d = R (op(A) = A^T when trans_a) for all k columns, right-preconditioned by P
 // (z = P v applied in the factor precision), X += d.  buf: gmres_bytes(n, k) bytes.  Uses epochs
 // epoch0 .. epoch0 + 2 kGmresM - 1 for P's triangular solves.
 struct GmresPrecond {
@@ -103,8 +103,15 @@ struct GmresPrecond {
     const void* ctx;
 };
 size_t gmres_bytes(int64_t n, int64_t k);
-rmge_status gmres_cycle(int64_t n, int64_t k, const double* A, int64_t lda, const double* R, double* X, int64_t ldx,
-                        double* buf, const GmresPrecond& P, int epoch0, const int* skip, cudaStream_t s);
+rmge_status gmres_cycle(int64_t n, int64_t k, const double* A, int64_t lda, bool trans_a, const double* R, double* X,
+                        int64_t ldx, double* buf, const GmresPrecond& P, int epoch0, const int* skip, cudaStream_t s);
+
+// batched.cu: persistent one-CTA-per-system solves (see rmge_solve_batched).
+size_t batched_scratch_bytes(int64_t nmax, int ctas);
+rmge_status batched_solve(int64_t count, const int32_t* n, const int64_t* offA, const int64_t* offv,
+                          const int32_t* order, const double* A, const double* b, double* x, int32_t* info,
+                          double* berr, int32_t* sweeps, uint64_t seed, int max_sweeps, double tol, int64_t nmax,
+                          int config, int ctas, void* ws, cudaStream_t s);
 
 // fft.cu: circulant multiplier (Theorem 5.1).  G = [c (n doubles) | u = F(c) (n double2)];
 // tw: n/2 double2 of scratch for the twiddle table.

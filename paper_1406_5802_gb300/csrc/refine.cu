@@ -133,6 +133,22 @@ __global__ void outer_neg_kernel(int64_t n, int64_t k, const double* __restrict_
     }
 }
 
+// ||A^T||_inf = max_j sum_i |a_ij|: one thread per column (consecutive threads, consecutive columns).
+__global__ void col_abs_sums_kernel(int64_t n, const double* __restrict__ A, int64_t lda, DevState* st) {
+    unsigned long long best = 0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int64_t i = 0; i < n; ++i) s += fabs(A[i * lda + j]);
+        const unsigned long long b = abs_bits(s);
+        best = b > best ? b : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = other > best ? other : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best != 0) atomicMax(reinterpret_cast<unsigned long long*>(&st->norm_a), best);
+}
+
 unsigned grid_for(int64_t work, int threads) {
     int64_t g = (work + threads - 1) / threads;
     if (g > 152 * 8) g = 152 * 8;
@@ -151,8 +167,11 @@ rmge_status state_init(DevState* st, int* flags, int64_t nflags, double* colred,
     return RMGE_OK;
 }
 
-rmge_status row_abs_sums(int64_t n, const double* A, int64_t lda, DevState* st, cudaStream_t s) {
-    row_abs_sums_kernel<<<grid_for(n * 32, 256), 256, 0, s>>>(n, A, lda, st);
+rmge_status abs_sums_max(int64_t n, const double* A, int64_t lda, bool transposed, DevState* st, cudaStream_t s) {
+    if (transposed)
+        col_abs_sums_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, A, lda, st);
+    else
+        row_abs_sums_kernel<<<grid_for(n * 32, 256), 256, 0, s>>>(n, A, lda, st);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }

@@ -57,8 +57,8 @@ def load_library(path: str = LIB_PATH):
         "rmge_solve": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, C.c_int, _vp, _sz, _vp]),
         "rmge_refine": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, C.c_int,
                                   C.c_int32, C.c_double, _vp, _vp, _vp, _sz, _vp]),
-        "rmge_solve_backward": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp,
-                                          _i64, C.c_int, _vp, _sz, _vp]),
+        "rmge_solve_backward": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _vp,
+                                          _i64, _vp, _i64, C.c_int, C.c_int32, C.c_double, _vp, _vp, _vp, _sz, _vp]),
         "rmge_status_string": (C.c_char_p, [C.c_int]),
         "rmge_kernel_launches": (C.c_ulonglong, []),
         "rmge_solve_workspace_size": (_sz, [_i64, _i64, C.c_int, C.c_int]),
@@ -225,19 +225,24 @@ def refine(kind, A, LU, G, B, X, prec="f64", max_iters=10, be_tol=1e-13, ws=None
     return berr, iters
 
 
-def solve_backward(kind, LU, G, X, dX, prec="f64", want_dA=True, ws=None):
-    """(dB, dA) for X = A^{-1} B given dX; dA is None when want_dA is False."""
+def solve_backward(kind, LU, G, X, dX, prec="f64", want_dA=True, A=None, max_iters=0, be_tol=1e-13, ws=None):
+    """(dB, dA, berr, iters) for X = A^{-1} B given dX; dA is None when want_dA is False.  With A and
+    max_iters > 0, dB is refined on A^T dB = dX (berr/iters then describe that refinement)."""
     L = _cuda_lib()
     n, k = dX.shape
     dB = torch.empty(n, k, dtype=torch.float64, device=dX.device)
     dA = torch.empty(n, n, dtype=torch.float64, device=dX.device) if want_dA else None
+    refine_it = int(max_iters) if A is not None else 0
+    berr = torch.empty(refine_it + 1, dtype=torch.float64, device=dX.device)
+    iters = torch.zeros(1, dtype=torch.int32, device=dX.device)
     if ws is None:
         ws = workspace(n, k, kind, prec)
-    _check("rmge_solve_backward", L.rmge_solve_backward(_kind(kind), n, k, _p(LU), _ld(LU), _p(G), _p(X),
-                                                        _ld(X) if X is not None else 0, _p(dX), _ld(dX), _p(dB),
-                                                        _ld(dB), _p(dA), _ld(dA) if dA is not None else 0, _prec(prec),
-                                                        _p(ws), ws.numel(), _stream()))
-    return dB, dA
+    _check("rmge_solve_backward", L.rmge_solve_backward(
+        _kind(kind), n, k, _p(A), _ld(A) if A is not None else 0, _p(LU), _ld(LU), _p(G), _p(X),
+        _ld(X) if X is not None else 0, _p(dX), _ld(dX), _p(dB), _ld(dB), _p(dA), _ld(dA) if dA is not None else 0,
+        _prec(prec), refine_it, float(be_tol), _p(berr) if refine_it > 0 else None, _p(iters) if refine_it > 0 else None,
+        _p(ws), ws.numel(), _stream()))
+    return dB, dA, berr, iters
 
 
 def gesv(kind, A, B, seed, prec="f64", max_iters=10, be_tol=1e-13, subsequence=1):

@@ -1,0 +1,58 @@
+"""The batched persistent launch: thousands of uneven systems, each solved by the whole method in one
+CTA, against the oracle (backward error per system, agreement with GEPP), plus autotuning and graph replay."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1406_5802_gb300 import rmge
+from paper_1406_5802_gb300 import workloads as W
+from paper_1406_5802_gb300.batch import CONFIGS, BatchedSolver
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1406_5802_gb300 import build as B
+    B.build()
+    rmge.load_library()
+
+
+def _batch(count, lo, hi, seed):
+    sizes = W.batch_sizes(count, lo, hi, seed)
+    systems = W.batch_systems(sizes, seed + 1)
+    return [a for a, _, _ in systems], [b for _, b, _ in systems]
+
+
+@pytest.mark.parametrize("config", sorted(CONFIGS))
+def test_batched_matches_oracle(orc, config):
+    As, bs = _batch(60, 1, 300, seed=41)  # includes n = 1 and ragged sizes around the 32-column blocks
+    bs_ = BatchedSolver(As, bs, seed=9, max_sweeps=10, be_tol=1e-13)
+    bs_.launch(config, 2 * 152)
+    torch.cuda.synchronize()
+    info = bs_.info.cpu().numpy()
+    berr = bs_.berr.cpu().numpy()
+    assert np.all(info == 0)
+    for i, (a, b) in enumerate(zip(As, bs)):
+        x = bs_.solution(i).cpu().numpy().reshape(-1, 1)
+        be = orc.backward_error(a, x, b)
+        assert be <= 1e-13, (i, a.shape[0], be, berr[i])
+        assert berr[i] <= 1e-13
+        assert abs(berr[i] - be) <= 0.5 * be + 1e-17
+
+
+def test_batched_graph_replay_and_tuning(orc):
+    As, bs = _batch(400, 32, 160, seed=7)
+    s = BatchedSolver(As, bs, seed=3)
+    entry = s.tune(reps=1, use_cache=False)
+    assert entry["config"] in CONFIGS
+    s.capture()
+    for _ in range(2):  # the queue re-arms itself: replays repeat the same work
+        s.x.zero_()
+        s.run()
+        torch.cuda.synchronize()
+        assert np.all(s.info.cpu().numpy() == 0)
+        assert np.all(s.berr.cpu().numpy() <= 1e-13)
+    for i in (0, 57, 399):
+        x = s.solution(i).cpu().numpy().reshape(-1, 1)
+        assert orc.backward_error(As[i], x, bs[i]) <= 1e-13

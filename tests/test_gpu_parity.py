@@ -208,7 +208,7 @@ def test_adjoint_matches_oracle_gradient(orc, kind, n, k):
     A, B, Wt = W.grad_system(n, k, seed=W.SEED_BASE + 5 + n)
     out = rmge.gesv(kind, dev(A), dev(B), seed=3, prec="f64")
     X = out["X"]
-    dB, dA = rmge.solve_backward(kind, out["LU"], out["G"], X, dev(Wt), "f64")
+    dB, dA, _, _ = rmge.solve_backward(kind, out["LU"], out["G"], X, dev(Wt), "f64")
     rdB, rdA, info = orc.solve_adjoint_gepp(A, host(X), Wt)
     assert info == 0
     # the adjoint solve is unrefined: its error scales with kappa(A G) u (growth aside); the target for
