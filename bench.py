@@ -116,6 +116,124 @@ def run_reference(args):
     return 0
 
 
+def extra_workloads(W, rmge, peaks):
+    """The other measured workloads (one JSON object each, added to the main line): the n = 16384
+    precision comparison (FP64 form vs reduced-precision factors + FP64 refinement), the batch of 4096
+    uneven systems in one persistent graph-captured launch, and the differentiable batch of 64 systems."""
+    import numpy as np
+    import torch
+
+    out = {}
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    # -- precision: n = 16384, sigma 1 .. 1e-4, 8 RHS -------------------------------------------------
+    try:
+        n, k = 16384, 8
+        A, B = W.orthogonal_factor_system_torch(n, k, 1e-4, seed=W.SEED_BASE + 3, device="cuda")
+        res = {"workload": "n=16384, 8 RHS, A = U diag(sigma) V^T, sigma log-spaced 1..1e-4, Gaussian G"}
+        for prec in ("f64", "bf16x3", "f16x3", "bf16"):
+            ws = rmge.workspace(n, k, "gaussian", prec)
+            G = rmge.empty_multiplier("gaussian", n, prec)
+            M = torch.empty(n, n, dtype=rmge.factor_dtype(prec), device="cuda")
+            X = torch.empty(n, k, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0, t1, a0, a1 = ev(), ev(), ev(), ev()
+            t0.record()
+            rmge.make_multiplier("gaussian", n, W.SEED_BASE + 3, 1, prec, G=G)
+            a0.record()
+            rmge.apply_multiplier("gaussian", A, G, prec, M=M, ws=ws)
+            a1.record()
+            info, growth = rmge.factor(M, prec, ws=ws)
+            rmge.solve("gaussian", M, G, B, prec, X=X, ws=ws)
+            berr, iters = rmge.refine("gaussian", A, M, G, B, X, prec, 10, 1e-13, ws=ws)
+            t1.record()
+            torch.cuda.synchronize()
+            it = int(iters.item())
+            ms, ams = t0.elapsed_time(t1), a0.elapsed_time(a1)
+            terms = {"f64": 1, "bf16x3": 3, "f16x3": 3, "bf16": 1}[prec]
+            entry = {"ms_per_solve": ms, "solves_per_s": 1e3 / ms, "berr_final": float(berr[it].item()),
+                     "sweeps": it, "reached_1e-13": bool(berr[it].item() <= 1e-13), "growth": float(growth.item()),
+                     "info": int(info.item()), "apply_ms": ams,
+                     "tflops_algorithmic": flops_per_solve(n, k, it) / (ms / 1e3) / 1e12}
+            if prec != "f64":
+                tc_tflops = terms * 2 * n**3 / (ams / 1e3) / 1e12
+                entry["apply_tensor_tflops"] = tc_tflops
+                entry["apply_tensor_frac_of_bf16_peak"] = tc_tflops / peaks.get("bf16_tflops", 1958.3)
+            res[prec] = entry
+            del ws, G, M, X
+            torch.cuda.empty_cache()
+        out["precision_n16384"] = res
+        del A, B
+        torch.cuda.empty_cache()
+    except Exception as e:  # reported, never fatal for the main line
+        out["precision_n16384"] = {"error": repr(e)}
+
+    # -- batching: 4096 systems, n ~ U{32..512}, one persistent CUDA-graph launch -----------------------
+    try:
+        from paper_1406_5802_gb300.batch import BatchedSolver
+        sizes = W.batch_sizes(4096, 32, 512, W.SEED_BASE + 4)
+        bs = BatchedSolver.synthetic(sizes, seed=W.SEED_BASE + 4, max_sweeps=40, be_tol=1e-13)
+        tune = bs.tune(reps=1)
+        bs.capture()
+        bs.run()
+        torch.cuda.synchronize()
+        t0, t1 = ev(), ev()
+        reps = 3
+        t0.record()
+        for _ in range(reps):
+            bs.run()
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / reps
+        berr = bs.berr.cpu().numpy()
+        info = bs.info.cpu().numpy()
+        ffma_peak = 152 * 128 * 2 * 2.070e9 / 1e12
+        tf = bs.flops() / (ms / 1e3) / 1e12
+        out["batch_4096"] = {"workload": "4096 systems, n ~ U{32..512}, A[0,0] x 1e-10, 1 RHS, FP32 GENP + FP64 "
+                                         "refinement, one graph-captured persistent launch",
+                             "ms_per_batch": ms, "systems_per_s": 4096 / (ms / 1e3), "tflops_fp32": tf,
+                             "frac_of_fp32_fma_peak": tf / ffma_peak, "fp32_peak_tflops": ffma_peak,
+                             "all_info_zero": bool(np.all(info == 0)),
+                             "systems_be_le_1e-13": int(np.sum(berr <= 1e-13)), "max_berr": float(np.max(berr)),
+                             "tuned": {"config": tune["config"], "ctas": tune["ctas"]}}
+    except Exception as e:
+        out["batch_4096"] = {"error": repr(e)}
+
+    # -- differentiation: 64 systems, n = 2048, FP32, forward + backward --------------------------------
+    try:
+        from paper_1406_5802_gb300.autograd import rmge_solve_batched
+        n, k, count = 2048, 4, 64
+        g = torch.Generator(device="cuda")
+        g.manual_seed(W.SEED_BASE + 5)
+        As = [(4 * torch.eye(n, device="cuda") + torch.randn(n, n, generator=g, device="cuda") / n**0.5)
+              .requires_grad_(True) for _ in range(count)]
+        Bs = [torch.randn(n, k, generator=g, device="cuda").requires_grad_(True) for _ in range(count)]
+        Ws = [torch.randn(n, k, generator=g, device="cuda") for _ in range(count)]
+
+        def step():
+            Xs = rmge_solve_batched(As, Bs, seeds=list(range(count)), prec="f32", streams=8)
+            loss = sum((X * Wt).sum() for X, Wt in zip(Xs, Ws))
+            loss.backward()
+            return loss
+
+        step()
+        torch.cuda.synchronize()
+        t0, t1 = ev(), ev()
+        t0.record()
+        step()
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        out["grad_64x2048"] = {"workload": "64 systems, n=2048, 4 RHS, FP32, A = 4I + N(0,1)/sqrt(n), loss = sum(X*W), "
+                                           "forward + adjoint backward",
+                               "ms_per_batch": ms, "systems_per_s": count / (ms / 1e3)}
+    except Exception as e:
+        out["grad_64x2048"] = {"error": repr(e)}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -123,6 +241,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rmge", choices=["rmge", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other measured workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -291,6 +410,8 @@ def main():
             "cpu_baseline": cpu,
             "hbm_gbs_measured_peak": peaks.get("hbm_gbs"),
         }
+        if not args.no_extras:
+            line["extras"] = extra_workloads(W, rmge, peaks)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

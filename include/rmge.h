@@ -71,13 +71,16 @@ typedef enum {
     RMGE_F16_TC = 3, /* as RMGE_BF16_TC with FP16 operands (power-of-two operand scaling for range) */
     RMGE_BF16X3_TC = 4, /* as RMGE_BF16_TC, each FP32 operand split x = x_hi + x_lo into two BF16 terms and the
                            product formed as x_hi y_hi + x_hi y_lo + x_lo y_hi (three tensor-core passes) */
-    RMGE_F16X3_TC = 5   /* the three-pass split with FP16 terms */
+    RMGE_F16X3_TC = 5,  /* the three-pass split with FP16 terms */
+    RMGE_F64X_TC = 6    /* FP64 working matrix and factors; A G and the Schur updates are FP64 products
+                           emulated on the BF16 tensor cores (7 base-128 digits per entry, exact 1024-deep
+                           FP32 chunks, double-float accumulation: about 48 correct bits) */
 } rmge_prec;
 
 /*
  * Multiplier storage (what `G` points to in every call below):
- * - RMGE_GAUSSIAN: n x n row-major, leading dimension n; FP64 for RMGE_F64, FP32 for the other
- *   precisions.
+ * - RMGE_GAUSSIAN: n x n row-major, leading dimension n; FP64 for RMGE_F64 and RMGE_F64X_TC, FP32
+ *   for the other precisions.
  * - circulant kinds: 3n FP64 values: the first column c[0..n-1], then its DFT u = Omega c
  *   (Theorem 5.1; Omega = (w^{ij}), w = exp(2 pi sqrt(-1) / n)) stored as n interleaved
  *   (re, im) pairs.  n must be a power of two, 2 <= n <= 8192.

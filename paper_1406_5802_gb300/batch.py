@@ -70,6 +70,44 @@ class BatchedSolver:
         self.ws = None
         self.graph = None
 
+    @classmethod
+    def synthetic(cls, sizes, seed: int, leading_scale: float = 1e-10, **kw):
+        """The uneven-batch workload drawn on the device: A_i i.i.d. N(0,1) with A_i[0,0] scaled by
+        leading_scale, b_i i.i.d. N(0,1) (torch's generator, seeded)."""
+        self = cls.__new__(cls)
+        sizes = np.asarray(sizes, dtype=np.int32)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(int(seed))
+        offA = np.zeros(len(sizes), np.int64)
+        offv = np.zeros(len(sizes), np.int64)
+        offA[1:] = np.cumsum(sizes.astype(np.int64) ** 2)[:-1]
+        offv[1:] = np.cumsum(sizes.astype(np.int64))[:-1]
+        A = torch.randn(int((sizes.astype(np.int64) ** 2).sum()), generator=g, dtype=torch.float64, device="cuda")
+        A[torch.as_tensor(offA, device="cuda")] *= leading_scale
+        b = torch.randn(int(sizes.sum()), generator=g, dtype=torch.float64, device="cuda")
+        self._init_packed(sizes, offA, offv, A, b, seed, **kw)
+        return self
+
+    def _init_packed(self, sizes, offA, offv, A, b, seed, max_sweeps=10, be_tol=1e-13):
+        device = A.device
+        self.count = len(sizes)
+        self.nmax = int(sizes.max())
+        self.sizes, self.offA, self.offv = sizes, offA, offv
+        order = np.argsort(-sizes, kind="stable").astype(np.int32)
+        self.d_n = torch.as_tensor(sizes).to(device)
+        self.d_offA = torch.as_tensor(offA).to(device)
+        self.d_offv = torch.as_tensor(offv).to(device)
+        self.d_order = torch.as_tensor(order).to(device)
+        self.A, self.b = A, b
+        self.x = torch.empty_like(b)
+        self.info = torch.empty(self.count, dtype=torch.int32, device=device)
+        self.berr = torch.empty(self.count, dtype=torch.float64, device=device)
+        self.sweeps = torch.empty(self.count, dtype=torch.int32, device=device)
+        self.seed, self.max_sweeps, self.be_tol = int(seed), int(max_sweeps), float(be_tol)
+        self.config, self.ctas = 1, torch.cuda.get_device_properties(device).multi_processor_count
+        self.ws = None
+        self.graph = None
+
     def flops(self) -> float:
         """Algorithmic flops of one pass: per system A G (2n^3 - n^2) and GENP (2n^3/3 - n^2/2 - n/6)."""
         n = self.sizes.astype(np.float64)

@@ -16,15 +16,17 @@ namespace {
 bool valid_kind(rmge_mult_kind k) {
     return k == RMGE_GAUSSIAN || k == RMGE_CIRCULANT_GAUSSIAN || k == RMGE_CIRCULANT_UNIFORM;
 }
-bool valid_prec(rmge_prec p) { return (int)p >= (int)RMGE_F64 && (int)p <= (int)RMGE_F16X3_TC; }
-bool is_tc(rmge_prec p) { return (int)p >= (int)RMGE_BF16_TC; }
+bool valid_prec(rmge_prec p) { return (int)p >= (int)RMGE_F64 && (int)p <= (int)RMGE_F64X_TC; }
+bool is_tc(rmge_prec p) { return (int)p >= (int)RMGE_BF16_TC && (int)p <= (int)RMGE_F16X3_TC; }
+// RMGE_F64X_TC keeps FP64 data everywhere; only the engine of A G and of the Schur updates differs.
+rmge_prec data_prec(rmge_prec p) { return p == RMGE_F64X_TC ? RMGE_F64 : p; }
 bool tc_bf16(rmge_prec p) { return p == RMGE_BF16_TC || p == RMGE_BF16X3_TC; }
 int tc_terms(rmge_prec p) { return (p == RMGE_BF16X3_TC || p == RMGE_F16X3_TC) ? 3 : 1; }
 int64_t tc_ldk(int64_t n) { return (n + 63) / 64 * 64; }
 bool is_circ(rmge_mult_kind k) { return k != RMGE_GAUSSIAN; }
 bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
 bool circ_ok(int64_t n) { return pow2(n) && n >= 2 && n <= 8192; }
-size_t elem(rmge_prec p) { return p == RMGE_F64 ? 8 : 4; }
+size_t elem(rmge_prec p) { return data_prec(p) == RMGE_F64 ? 8 : 4; }
 
 int64_t nflags_for(int64_t n, int64_t nrhs) {
     return ((n + kTrsvRows - 1) / kTrsvRows) * ((nrhs + kTrsvCols - 1) / kTrsvCols);
@@ -41,6 +43,7 @@ struct Ws {
     void* tc;                  // 16-bit operand buffers: A hi, A lo, B hi, B lo, each n x tc_ldk(n)
     double* gm;                // FGMRES work
     unsigned long long* tcmx;  // FP16 scaling slots
+    char* oz;                  // digit planes and exponents of the emulated FP64 products
 };
 
 // full = false: the call needs no tensor-core operand buffers and no FGMRES work (solves, adjoint),
@@ -60,9 +63,21 @@ rmge_status carve(void* ws, size_t ws_bytes, int64_t n, int64_t nrhs, rmge_mult_
     out->tw = reinterpret_cast<double2*>(b + L.fft);
     out->tc = is_tc(prec) ? b + L.tc : nullptr;
     out->tcmx = (full && is_tc(prec)) ? reinterpret_cast<unsigned long long*>(b + L.tcmx) : nullptr;
-    out->gm = (full && prec != RMGE_F64) ? reinterpret_cast<double*>(b + L.gm) : nullptr;
+    out->gm = (full && data_prec(prec) != RMGE_F64) ? reinterpret_cast<double*>(b + L.gm) : nullptr;
+    out->oz = (full && prec == RMGE_F64X_TC) ? b + L.oz : nullptr;
     if (!full) out->tc = nullptr;
     return RMGE_OK;
+}
+
+// Digit planes (A side, B side) and line exponents of the emulated FP64 products, in w.oz.
+OzUpdate oz_buffers(const Ws& w, int64_t n) {
+    const size_t pb = oz_plane_bytes(n, n, kOzSlices);
+    OzUpdate o{};
+    o.planesA = w.oz;
+    o.planesB = w.oz + pb;
+    o.ea = reinterpret_cast<int*>(w.oz + 2 * pb);
+    o.eb = o.ea + n + 128;
+    return o;
 }
 
 bool check_dims(int64_t n, int64_t nrhs) { return n >= 1 && n <= RMGE_MAX_N && nrhs >= 1 && nrhs <= RMGE_MAX_N; }
@@ -220,7 +235,10 @@ WsLayout ws_layout(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec)
     L.tc = off;
     if (is_tc(prec)) off = align256(off + 4 * 2 * (size_t)n * (size_t)tc_ldk(n));
     L.gm = off;
-    if (prec != RMGE_F64) off = align256(off + gmres_bytes(n, nrhs));
+    if (data_prec(prec) != RMGE_F64) off = align256(off + gmres_bytes(n, nrhs));
+    L.oz = off;
+    if (prec == RMGE_F64X_TC)
+        off = align256(off + 2 * oz_plane_bytes(n, n, kOzSlices) + 2 * sizeof(int) * (size_t)(n + 128));
     L.total = off;
     return L;
 }
@@ -272,7 +290,7 @@ rmge_status rmge_make_multiplier(rmge_mult_kind kind, int64_t n, uint64_t seed, 
         return RMGE_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (kind == RMGE_GAUSSIAN) {
-        if (prec == RMGE_F64) return launch_gaussian(n * n, seed, subsequence, static_cast<double*>(G), s);
+        if (data_prec(prec) == RMGE_F64) return launch_gaussian(n * n, seed, subsequence, static_cast<double*>(G), s);
         return launch_gaussian(n * n, seed, subsequence, static_cast<float*>(G), s);
     }
     if (!circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
@@ -298,7 +316,13 @@ rmge_status rmge_apply_multiplier(rmge_mult_kind kind, int64_t n, const double* 
     Ws w{};
     RMGE_TRY(carve(ws, ws_bytes, n, 1, kind, prec, &w));
     if (is_circ(kind))
-        return circulant_apply_rows(n, A, lda, static_cast<const double*>(G), w.tw, M, ldm, prec != RMGE_F64, s);
+        return circulant_apply_rows(n, A, lda, static_cast<const double*>(G), w.tw, M, ldm,
+                                    data_prec(prec) != RMGE_F64, s);
+    if (prec == RMGE_F64X_TC) {
+        const OzUpdate oz = oz_buffers(w, n);
+        return oz_gemm(n, n, n, kOzSlices, 1.0, A, lda, static_cast<const double*>(G), n, 0.0, static_cast<double*>(M),
+                       ldm, oz.planesA, oz.planesB, oz.ea, oz.eb, &w.st->error, nullptr, s);
+    }
     if (prec == RMGE_F64)
         return gemm<double>(false, n, n, n, 1.0, A, lda, static_cast<const double*>(G), n, 0.0,
                             static_cast<double*>(M), ldm, nullptr, s);
@@ -333,6 +357,8 @@ rmge_status rmge_factor(int64_t n, void* M, int64_t ldm, rmge_prec prec, int32_t
     RMGE_TRY(state_init(w.st, w.flags, 0, w.colred, 0, nullptr, 0, s));
     if (prec == RMGE_F64)
         RMGE_TRY(genp_factor<double>(n, static_cast<double*>(M), ldm, w.st, s));
+    else if (prec == RMGE_F64X_TC)
+        RMGE_TRY(genp_factor_oz(n, static_cast<double*>(M), ldm, w.st, oz_buffers(w, n), s));
     else if (prec == RMGE_F32)
         RMGE_TRY(genp_factor<float>(n, static_cast<float*>(M), ldm, w.st, s));
     else {
@@ -360,7 +386,7 @@ rmge_status rmge_solve(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void*
     Ws w{};
     RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w, false));
     RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, 0, nullptr, 0, s));
-    return correction(kind, prec, n, nrhs, LU, ldlu, G, B, ldb, X, ldx, false, w, 1, nullptr, s);
+    return correction(kind, data_prec(prec), n, nrhs, LU, ldlu, G, B, ldb, X, ldx, false, w, 1, nullptr, s);
 }
 
 rmge_status rmge_refine(rmge_mult_kind kind, int64_t n, int64_t nrhs, const double* A, int64_t lda, const void* LU,
@@ -375,8 +401,8 @@ rmge_status rmge_refine(rmge_mult_kind kind, int64_t n, int64_t nrhs, const doub
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Ws w{};
     RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w));
-    return refine_loop(kind, prec, false, n, nrhs, A, lda, LU, ldlu, G, B, ldb, X, ldx, max_iters, be_tol, berr, iters,
-                       w, 1, s);
+    return refine_loop(kind, data_prec(prec), false, n, nrhs, A, lda, LU, ldlu, G, B, ldb, X, ldx, max_iters, be_tol,
+                       berr, iters, w, 1, s);
 }
 
 rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, const double* A, int64_t lda,
@@ -393,6 +419,7 @@ rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, co
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Ws w{};
     RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w, max_iters > 0));
+    prec = data_prec(prec);
     RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, 0, nullptr, 0, s));
     // dB = A^{-T} dX ~= L^{-T} U^{-T} G^T dX
     RMGE_TRY(correction(kind, prec, n, nrhs, LU, ldlu, G, dX, lddx, dB, lddb, false, w, 1, nullptr, s, true));

@@ -6,7 +6,8 @@
 //   M_i  = L U  by blocked GENP           (eq. (3.1), 32-column pivot blocks, FP32)
 //   x_i  = G_i U^{-1} L^{-1} b_i          (Fact 4.1)
 //   sweeps of r = b - A x (FP64), x += G U^{-1} L^{-1} r, until the normwise backward error is
-//   below tol (Sec. 1.2, Sec. 7.1)
+//   below tol (Sec. 1.2, Sec. 7.1); once a sweep fails to halve the error, the remaining sweeps are
+//   right-preconditioned GMRES cycles in FP64 (preconditioner G U^{-1} L^{-1} in FP32)
 // CTAs are persistent: each takes the next system from a queue ordered by decreasing n (longest
 // first), so uneven sizes balance across the SMs.  The queue counter re-arms itself when the last
 // CTA finishes, so the launch can be captured once in a CUDA graph and replayed.  Per-CTA scratch
@@ -248,6 +249,124 @@ __device__ void cta_gemv_f32(int n, const float* G, const float* v, double* out,
     __syncthreads();
 }
 
+// CTA-wide sum of one double per thread; every thread gets the total.
+template <int T>
+__device__ double cta_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < T / 32; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+constexpr int GM = 16;  // restart length of the per-system GMRES cycles
+
+// z (FP64) = G U^{-1} L^{-1} v with the FP32 factors: the preconditioner P of Fact 4.1.
+template <int T>
+__device__ void cta_precond(int n, const float* M, const float* G, const double* v, float* y, double* z) {
+    for (int i = threadIdx.x; i < n; i += T) y[i] = (float)v[i];
+    __syncthreads();
+    cta_lu_solve<T>(n, M, y);
+    cta_gemv_f32<T>(n, G, y, z, false);
+}
+
+// One right-preconditioned GMRES(GM) cycle in FP64 on A d = r (r in rz on entry), x += P V y.
+// V: (GM + 1) x n doubles of scratch; rz is reused as the preconditioned vector.
+template <int T>
+__device__ void cta_gmres_cycle(int n, const double* A, const float* M, const float* G, double* x, double* rz,
+                                double* V, float* y, double* red) {
+    __shared__ double H[(GM + 1) * GM], cs[GM], sn[GM], g[GM + 1], hs[GM + 1], ys[GM];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += T) acc = fma(rz[i], rz[i], acc);
+    const double beta = sqrt(cta_sum<T>(acc, red));
+    if (!(beta > 0.0) || !isfinite(beta)) return;
+    for (int i = threadIdx.x; i < n; i += T) V[i] = rz[i] / beta;
+    if (threadIdx.x == 0) {
+        g[0] = beta;
+        for (int i = 1; i <= GM; ++i) g[i] = 0.0;
+        for (int i = 0; i < (GM + 1) * GM; ++i) H[i] = 0.0;
+    }
+    __syncthreads();
+    int m = GM;
+    for (int j = 0; j < GM; ++j) {
+        double* vj = V + (int64_t)j * n;
+        double* w = V + (int64_t)(j + 1) * n;
+        cta_precond<T>(n, M, G, vj, y, rz);  // rz = P v_j
+        for (int i = warp; i < n; i += T / 32) {  // w = A z
+            double s = 0.0;
+            for (int k = lane; k < n; k += 32) s = fma(A[(int64_t)i * n + k], rz[k], s);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) w[i] = s;
+        }
+        __syncthreads();
+        for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+            for (int l = 0; l <= j; ++l) {
+                double d = 0.0;
+                for (int i = threadIdx.x; i < n; i += T) d = fma(V[(int64_t)l * n + i], w[i], d);
+                d = cta_sum<T>(d, red);
+                if (threadIdx.x == 0) {
+                    hs[l] = d;
+                    H[l * GM + j] += d;
+                }
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += T) {
+                double v = w[i];
+                for (int l = 0; l <= j; ++l) v = fma(-hs[l], V[(int64_t)l * n + i], v);
+                w[i] = v;
+            }
+            __syncthreads();
+        }
+        acc = 0.0;
+        for (int i = threadIdx.x; i < n; i += T) acc = fma(w[i], w[i], acc);
+        const double h = sqrt(cta_sum<T>(acc, red));
+        const double inv = h > 0.0 ? 1.0 / h : 0.0;
+        for (int i = threadIdx.x; i < n; i += T) w[i] *= inv;
+        if (threadIdx.x == 0) {
+            H[(j + 1) * GM + j] = h;
+            for (int i = 0; i < j; ++i) {  // previous rotations on column j
+                const double a0 = H[i * GM + j], b0 = H[(i + 1) * GM + j];
+                H[i * GM + j] = cs[i] * a0 + sn[i] * b0;
+                H[(i + 1) * GM + j] = -sn[i] * a0 + cs[i] * b0;
+            }
+            const double a0 = H[j * GM + j], b0 = H[(j + 1) * GM + j];
+            const double rr = hypot(a0, b0);
+            cs[j] = rr > 0.0 ? a0 / rr : 1.0;
+            sn[j] = rr > 0.0 ? b0 / rr : 0.0;
+            H[j * GM + j] = rr;
+            H[(j + 1) * GM + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+        }
+        __syncthreads();
+        if (h == 0.0) {  // the Krylov space is exhausted: the solution lies in V_(j+1)
+            m = j + 1;
+            break;
+        }
+    }
+    if (threadIdx.x == 0) {  // y = H^{-1} g
+        for (int i = m - 1; i >= 0; --i) {
+            double sacc = g[i];
+            for (int t = i + 1; t < m; ++t) sacc = fma(-H[i * GM + t], ys[t], sacc);
+            ys[i] = H[i * GM + i] != 0.0 ? sacc / H[i * GM + i] : 0.0;
+        }
+    }
+    __syncthreads();
+    // u = V y (into the first basis vector's slot), x += P u
+    for (int i = threadIdx.x; i < n; i += T) {
+        double u = 0.0;
+        for (int l = 0; l < m; ++l) u = fma(ys[l], V[(int64_t)l * n + i], u);
+        V[i] = u;
+    }
+    __syncthreads();
+    cta_precond<T>(n, M, G, V, y, rz);
+    for (int i = threadIdx.x; i < n; i += T) x[i] += rz[i];
+    __syncthreads();
+}
+
 template <int T, int TILE>
 __global__ void __launch_bounds__(T) batched_kernel(BatchArgs a) {
     extern __shared__ __align__(16) float smem[];
@@ -257,7 +376,8 @@ __global__ void __launch_bounds__(T) batched_kernel(BatchArgs a) {
     float* G = a.scratch + (int64_t)blockIdx.x * (2 * a.nmax * a.nmax + 2 * a.nmax);
     float* M = G + a.nmax * a.nmax;
     float* y = M + a.nmax * a.nmax;
-    double* r = a.dscratch + (int64_t)blockIdx.x * a.nmax;
+    double* r = a.dscratch + (int64_t)blockIdx.x * a.nmax * (GM + 2);
+    double* V = r + a.nmax;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -292,14 +412,17 @@ __global__ void __launch_bounds__(T) batched_kernel(BatchArgs a) {
         __syncthreads();
         cta_lu_solve<T>(n, M, y);
         cta_gemv_f32<T>(n, G, y, x, false);
-        // sweeps: r = b - A x in FP64, eta = ||r|| / (||A|| ||x|| + ||b||), x += G U^{-1} L^{-1} r
+        // sweeps: r = b - A x in FP64, eta = ||r|| / (||A|| ||x|| + ||b||); the correction is
+        // x += G U^{-1} L^{-1} r while that at least halves eta, and one preconditioned GMRES cycle in
+        // FP64 from the first sweep that does not (FP32 factors too inexact for kappa(A G)).
         double norm_a = 0.0;
         int sw = 0;
-        double eta = 0.0;
+        double eta = 0.0, eta_prev = 0.0;
+        bool krylov = false;
         for (;; ++sw) {
             double rmax = 0.0, amax = 0.0;
             for (int i = warp; i < n; i += T / 32) {
-                double s = b[i], as = 0.0;
+                double s = (lane == 0) ? b[i] : 0.0, as = 0.0;  // b enters the warp sum once
                 for (int j = lane; j < n; j += 32) {
                     const double aij = A[(int64_t)i * n + j];
                     s = fma(-aij, x[j], s);
@@ -337,11 +460,18 @@ __global__ void __launch_bounds__(T) batched_kernel(BatchArgs a) {
             }
             __syncthreads();
             eta = red[0];
-            if (stop_s) break;
-            for (int i = threadIdx.x; i < n; i += T) y[i] = (float)r[i];
             __syncthreads();
-            cta_lu_solve<T>(n, M, y);
-            cta_gemv_f32<T>(n, G, y, x, true);
+            if (stop_s) break;
+            if (sw > 0 && !(eta <= 0.5 * eta_prev)) krylov = true;
+            eta_prev = eta;
+            if (krylov) {
+                cta_gmres_cycle<T>(n, A, M, G, x, r, V, y, red);
+            } else {
+                for (int i = threadIdx.x; i < n; i += T) y[i] = (float)r[i];
+                __syncthreads();
+                cta_lu_solve<T>(n, M, y);
+                cta_gemv_f32<T>(n, G, y, x, true);
+            }
         }
         if (threadIdx.x == 0) {
             a.info[sys] = 0;
@@ -378,7 +508,7 @@ rmge_status launch_batched(const BatchArgs& a, int ctas, cudaStream_t s) {
 
 size_t batched_scratch_bytes(int64_t nmax, int ctas) {
     return align256((size_t)ctas * (size_t)(2 * nmax * nmax + 2 * nmax) * sizeof(float)) +
-           align256((size_t)ctas * (size_t)nmax * sizeof(double)) + 256;
+           align256((size_t)ctas * (size_t)nmax * (GM + 2) * sizeof(double)) + 256;
 }
 
 rmge_status batched_solve(int64_t count, const int32_t* n, const int64_t* offA, const int64_t* offv,

@@ -60,6 +60,7 @@ struct WsLayout {
     size_t tcmx;      // FP16 operand-scaling slots (tensor-core precisions)
     size_t tc;        // 16-bit operand buffers (tensor-core precisions)
     size_t gm;        // FGMRES work (reduced precisions)
+    size_t oz;        // digit planes of the emulated FP64 products
     size_t total;
 };
 

@@ -38,6 +38,23 @@ rmge_status tc_split(int64_t rows, int64_t cols, const S* src, int64_t lds, bool
                      const unsigned long long* mx, bool bf16, void* hi, void* lo, int64_t ldd, cudaStream_t s);
 uint32_t tc_idesc(bool bf16);
 
+// oz_gemm.cu: C (FP64) <- beta C + alpha A B with the product emulated on BF16 tensor cores from
+// s base-128 digit planes of A (rows) and B (columns).  planesA/planesB: oz_plane_bytes(M, K, s) and
+// oz_plane_bytes(N, K, s) bytes; ea[M], eb[N] ints of scratch.  *err <- RMGE_ERR_TIMEOUT if a bounded
+// wait expires; nothing happens while *halt != 0 (halt may be NULL).
+constexpr int kOzSlices = 7;
+size_t oz_plane_bytes(int64_t rows, int64_t k, int s);
+rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const double* A, int64_t lda,
+                    const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* planesA, void* planesB,
+                    int* ea, int* eb, int* err, const int* halt, cudaStream_t st);
+struct OzUpdate {
+    void* planesA;
+    void* planesB;
+    int* ea;
+    int* eb;
+};
+rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s);
+
 // genp.cu: in-place blocked GENP of an n x n matrix with DevState bookkeeping.
 template <typename T>
 rmge_status genp_factor(int64_t n, T* M, int64_t ldm, DevState* st, cudaStream_t s);

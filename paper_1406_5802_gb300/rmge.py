@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_build", "librmge.so")
 GAUSSIAN, CIRCULANT_GAUSSIAN, CIRCULANT_UNIFORM = 0, 1, 2
 F64, F32, BF16_TC, F16_TC = 0, 1, 2, 3
 KINDS = {"gaussian": GAUSSIAN, "circulant": CIRCULANT_GAUSSIAN, "circulant_uniform": CIRCULANT_UNIFORM}
-PRECS = {"f64": F64, "f32": F32, "bf16": BF16_TC, "f16": F16_TC, "bf16x3": 4, "f16x3": 5}
+PRECS = {"f64": F64, "f32": F32, "bf16": BF16_TC, "f16": F16_TC, "bf16x3": 4, "f16x3": 5, "f64x": 6}
 STATUS = {0: "RMGE_OK", 1: "RMGE_ERR_INVALID_ARG", 2: "RMGE_ERR_BREAKDOWN", 3: "RMGE_ERR_GROWTH",
           4: "RMGE_ERR_NOT_CONVERGED", 5: "RMGE_ERR_CUDA", 6: "RMGE_ERR_TIMEOUT", 7: "RMGE_ERR_WORKSPACE",
           8: "RMGE_ERR_UNSUPPORTED"}
@@ -119,7 +119,7 @@ def kernel_launches() -> int:
 
 
 def factor_dtype(prec) -> torch.dtype:
-    return torch.float64 if _prec(prec) == F64 else torch.float32
+    return torch.float64 if _prec(prec) in (F64, PRECS["f64x"]) else torch.float32
 
 
 def multiplier_bytes(kind, n, prec) -> int:

@@ -27,7 +27,7 @@ def _batch(count, lo, hi, seed):
 @pytest.mark.parametrize("config", sorted(CONFIGS))
 def test_batched_matches_oracle(orc, config):
     As, bs = _batch(60, 1, 300, seed=41)  # includes n = 1 and ragged sizes around the 32-column blocks
-    bs_ = BatchedSolver(As, bs, seed=9, max_sweeps=10, be_tol=1e-13)
+    bs_ = BatchedSolver(As, bs, seed=9, max_sweeps=40, be_tol=1e-13)
     bs_.launch(config, 2 * 152)
     torch.cuda.synchronize()
     info = bs_.info.cpu().numpy()
@@ -43,7 +43,7 @@ def test_batched_matches_oracle(orc, config):
 
 def test_batched_graph_replay_and_tuning(orc):
     As, bs = _batch(400, 32, 160, seed=7)
-    s = BatchedSolver(As, bs, seed=3)
+    s = BatchedSolver(As, bs, seed=3, max_sweeps=40)
     entry = s.tune(reps=1, use_cache=False)
     assert entry["config"] in CONFIGS
     s.capture()
