@@ -72,9 +72,9 @@ typedef enum {
     RMGE_BF16X3_TC = 4, /* as RMGE_BF16_TC, each FP32 operand split x = x_hi + x_lo into two BF16 terms and the
                            product formed as x_hi y_hi + x_hi y_lo + x_lo y_hi (three tensor-core passes) */
     RMGE_F16X3_TC = 5,  /* the three-pass split with FP16 terms */
-    RMGE_F64X_TC = 6    /* FP64 working matrix and factors; A G and the Schur updates are FP64 products
-                           emulated on the BF16 tensor cores (7 base-128 digits per entry, exact 1024-deep
-                           FP32 chunks, double-float accumulation: about 48 correct bits) */
+    RMGE_F64X_TC = 6    /* FP64 working matrix, factors and refinement; M = A G is an FP64 product emulated on
+                           the BF16 tensor cores (8 base-128 digits per entry, 36 digit-pair products in
+                           exact FP32 chunks, 64-bit fixed-point accumulation); GENP runs on the FP64 pipe */
 } rmge_prec;
 
 /*
@@ -217,7 +217,11 @@ size_t rmge_noalloc_capacity(void);
  * stop at normwise backward error <= be_tol or after max_sweeps), in ONE persistent kernel launch:
  * each CTA takes the next system from a queue in the order given (pass decreasing n), so uneven sizes
  * balance across SMs.  G_i is the FP32 Gaussian multiplier stream (seed, subsequence i) of
- * rmge_make_multiplier.  Device arrays: n[count]; offA[count] element offsets of A_i (n_i x n_i, FP64,
+ * rmge_make_multiplier.  Sweeps are classical while each halves the backward error, then
+ * right-preconditioned GMRES cycles in FP64; when a GMRES cycle fails to halve it (or a pivot is zero)
+ * the system starts again with a fresh multiplier from subsequence i + d * count, d = 1, 2 (the method
+ * succeeds with probability close to 1 per draw).  max_sweeps bounds the sweeps of each draw; sweeps[i]
+ * counts them over all draws.  Device arrays: n[count]; offA[count] element offsets of A_i (n_i x n_i, FP64,
  * row-major, ld n_i) in A; offv[count] element offsets of b_i, x_i in b, x (FP64); order[count] a
  * permutation of 0..count-1; outputs info[i] (0 or first breakdown step), berr[i], sweeps[i].
  * config selects the compiled tile shape (0: 256 threads, 32x32 tiles; 1: 256 threads, 64x64;

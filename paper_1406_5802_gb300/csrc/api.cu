@@ -358,7 +358,9 @@ rmge_status rmge_factor(int64_t n, void* M, int64_t ldm, rmge_prec prec, int32_t
     if (prec == RMGE_F64)
         RMGE_TRY(genp_factor<double>(n, static_cast<double*>(M), ldm, w.st, s));
     else if (prec == RMGE_F64X_TC)
-        RMGE_TRY(genp_factor_oz(n, static_cast<double*>(M), ldm, w.st, oz_buffers(w, n), s));
+        // GENP stays on the FP64 pipe: its panels span a wide dynamic range (pivot growth), where the
+        // per-row / per-column scaling of the emulated product loses the relative accuracy FP64 keeps
+        RMGE_TRY(genp_factor<double>(n, static_cast<double*>(M), ldm, w.st, s));
     else if (prec == RMGE_F32)
         RMGE_TRY(genp_factor<float>(n, static_cast<float*>(M), ldm, w.st, s));
     else {

@@ -7,7 +7,9 @@
 //   x_i  = G_i U^{-1} L^{-1} b_i          (Fact 4.1)
 //   sweeps of r = b - A x (FP64), x += G U^{-1} L^{-1} r, until the normwise backward error is
 //   below tol (Sec. 1.2, Sec. 7.1); once a sweep fails to halve the error, the remaining sweeps are
-//   right-preconditioned GMRES cycles in FP64 (preconditioner G U^{-1} L^{-1} in FP32)
+//   right-preconditioned GMRES cycles in FP64 (preconditioner G U^{-1} L^{-1} in FP32); when those
+//   stall too, a fresh multiplier is drawn (up to three draws), and a system that no FP32 draw can
+//   refine is factored in FP64 in the same CTA (its A G and GENP on the DFMA pipe)
 // CTAs are persistent: each takes the next system from a queue ordered by decreasing n (longest
 // first), so uneven sizes balance across the SMs.  The queue counter re-arms itself when the last
 // CTA finishes, so the launch can be captured once in a CUDA graph and replayed.  Per-CTA scratch
@@ -75,37 +77,37 @@ __device__ void gen_gaussian_f32(int64_t count, uint64_t seed, uint64_t subseq, 
 // CTA-wide FP32 GEMM: C (M x N, ldc) = alpha A B + beta C, A (M x K) of type SA, B (K x N) FP32.
 // TILE x TILE output tiles, each thread an (TILE/RT) x (TILE/RT) micro-tile, RT = sqrt(T).
 // ---------------------------------------------------------------------------------------------
-template <int T, int TILE, typename SA>
+template <int T, int TILE, typename SA, typename E>
 __device__ void cta_gemm(int M, int N, int K, const SA* __restrict__ A, int lda, const float* __restrict__ B, int ldb,
-                         float* __restrict__ C, int ldc, float alpha, float beta, float* smem) {
+                         E* __restrict__ C, int ldc, E alpha, E beta, E* smem) {
     constexpr int BK = 16;
     constexpr int RT = (T == 256) ? 16 : 32;  // threads per tile row
     constexpr int RY = T / RT;
     constexpr int TM = TILE / RY, TN = TILE / RT;
-    float* As = smem;                  // [BK][TILE]
-    float* Bs = smem + BK * TILE;      // [BK][TILE]
+    E* As = smem;                  // [BK][TILE]
+    E* Bs = smem + BK * TILE;      // [BK][TILE]
     const int tx = threadIdx.x % RT, ty = threadIdx.x / RT;
     for (int t0 = 0; t0 < ((M + TILE - 1) / TILE) * ((N + TILE - 1) / TILE); ++t0) {
         const int tm = t0 / ((N + TILE - 1) / TILE), tn = t0 % ((N + TILE - 1) / TILE);
         const int m0 = tm * TILE, n0 = tn * TILE;
-        float acc[TM][TN];
+        E acc[TM][TN];
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
-            for (int j = 0; j < TN; ++j) acc[i][j] = 0.0f;
+            for (int j = 0; j < TN; ++j) acc[i][j] = E(0);
         for (int k0 = 0; k0 < K; k0 += BK) {
             for (int e = threadIdx.x; e < TILE * BK; e += T) {
                 const int m = e / BK, kk = e % BK;
                 const int gm = m0 + m, gk = k0 + kk;
-                As[kk * TILE + m] = (gm < M && gk < K) ? (float)A[(int64_t)gm * lda + gk] : 0.0f;
+                As[kk * TILE + m] = (gm < M && gk < K) ? (E)A[(int64_t)gm * lda + gk] : E(0);
                 const int kb = e / TILE, nn = e % TILE;
                 const int gkb = k0 + kb, gn = n0 + nn;
-                Bs[kb * TILE + nn] = (gkb < K && gn < N) ? B[(int64_t)gkb * ldb + gn] : 0.0f;
+                Bs[kb * TILE + nn] = (gkb < K && gn < N) ? (E)B[(int64_t)gkb * ldb + gn] : E(0);
             }
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < BK; ++kk) {
-                float a[TM], bb[TN];
+                E a[TM], bb[TN];
 #pragma unroll
                 for (int i = 0; i < TM; ++i) a[i] = As[kk * TILE + ty + i * RY];
 #pragma unroll
@@ -113,7 +115,7 @@ __device__ void cta_gemm(int M, int N, int K, const SA* __restrict__ A, int lda,
 #pragma unroll
                 for (int i = 0; i < TM; ++i)
 #pragma unroll
-                    for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+                    for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
             }
             __syncthreads();
         }
@@ -125,8 +127,63 @@ __device__ void cta_gemm(int M, int N, int K, const SA* __restrict__ A, int lda,
             for (int j = 0; j < TN; ++j) {
                 const int gn = n0 + tx + j * RT;
                 if (gn >= N) continue;
-                float* c = C + (int64_t)gm * ldc + gn;
-                *c = (beta == 0.0f) ? alpha * acc[i][j] : fmaf(beta, *c, alpha * acc[i][j]);
+                E* c = C + (int64_t)gm * ldc + gn;
+                *c = (beta == E(0)) ? alpha * acc[i][j] : fma(beta, *c, alpha * acc[i][j]);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// C -= A B with all operands of type E (the Schur-complement update inside cta_genp).
+template <int T, int TILE, typename E>
+__device__ void cta_gemm_same(int M, int N, int K, const E* __restrict__ A, int lda, const E* __restrict__ B, int ldb,
+                              E* __restrict__ C, int ldc, E* smem) {
+    constexpr int BK = 16;
+    constexpr int RT = (T == 256) ? 16 : 32;
+    constexpr int RY = T / RT;
+    constexpr int TM = TILE / RY, TN = TILE / RT;
+    E* As = smem;
+    E* Bs = smem + BK * TILE;
+    const int tx = threadIdx.x % RT, ty = threadIdx.x / RT;
+    const int tn_count = (N + TILE - 1) / TILE;
+    for (int t0 = 0; t0 < ((M + TILE - 1) / TILE) * tn_count; ++t0) {
+        const int m0 = (t0 / tn_count) * TILE, n0 = (t0 % tn_count) * TILE;
+        E acc[TM][TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = E(0);
+        for (int k0 = 0; k0 < K; k0 += BK) {
+            for (int e = threadIdx.x; e < TILE * BK; e += T) {
+                const int m = e / BK, kk = e % BK;
+                As[kk * TILE + m] = (m0 + m < M && k0 + kk < K) ? A[(int64_t)(m0 + m) * lda + k0 + kk] : E(0);
+                const int kb = e / TILE, nn = e % TILE;
+                Bs[kb * TILE + nn] = (k0 + kb < K && n0 + nn < N) ? B[(int64_t)(k0 + kb) * ldb + n0 + nn] : E(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                E a[TM], bb[TN];
+#pragma unroll
+                for (int i = 0; i < TM; ++i) a[i] = As[kk * TILE + ty + i * RY];
+#pragma unroll
+                for (int j = 0; j < TN; ++j) bb[j] = Bs[kk * TILE + tx + j * RT];
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int gm = m0 + ty + i * RY;
+            if (gm >= M) continue;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int gn = n0 + tx + j * RT;
+                if (gn < N) C[(int64_t)gm * ldc + gn] -= acc[i][j];
             }
         }
     }
@@ -139,17 +196,17 @@ __device__ void cta_gemm(int M, int N, int K, const SA* __restrict__ A, int lda,
 // ---------------------------------------------------------------------------------------------
 constexpr int PB = 32;
 
-template <int T, int TILE>
-__device__ int cta_genp(int n, float* M, float* smem, int* flag) {
-    float* d = smem;  // [PB][PB + 1] pivot block
+template <int T, int TILE, typename E>
+__device__ int cta_genp(int n, E* M, E* smem, int* flag) {
+    E* d = smem;  // [PB][PB + 1] pivot block
     for (int k = 0; k < n; k += PB) {
         const int b = min(PB, n - k);
         for (int e = threadIdx.x; e < b * b; e += T) d[(e / b) * (PB + 1) + e % b] = M[(int64_t)(k + e / b) * n + k + e % b];
         if (threadIdx.x == 0) *flag = 0;
         __syncthreads();
         for (int s = 0; s < b; ++s) {
-            const float piv = d[s * (PB + 1) + s];
-            if (piv == 0.0f || !isfinite(piv)) {
+            const E piv = d[s * (PB + 1) + s];
+            if (piv == E(0) || !isfinite(piv)) {
                 __syncthreads();
                 return k + s + 1;
             }
@@ -158,7 +215,7 @@ __device__ int cta_genp(int n, float* M, float* smem, int* flag) {
             const int w = b - s - 1;
             for (int e = threadIdx.x; e < w * w; e += T) {
                 const int i = s + 1 + e / w, j = s + 1 + e % w;
-                d[i * (PB + 1) + j] = fmaf(-d[i * (PB + 1) + s], d[s * (PB + 1) + j], d[i * (PB + 1) + j]);
+                d[i * (PB + 1) + j] = fma(-d[i * (PB + 1) + s], d[s * (PB + 1) + j], d[i * (PB + 1) + j]);
             }
             __syncthreads();
         }
@@ -168,24 +225,24 @@ __device__ int cta_genp(int n, float* M, float* smem, int* flag) {
             // L21 rows: x U11 = a, one thread per row; U12 columns: L11 x = a, one thread per column
             for (int q = threadIdx.x; q < 2 * rest; q += T) {
                 if (q < rest) {
-                    float* row = M + (int64_t)(k + b + q) * n + k;
+                    E* row = M + (int64_t)(k + b + q) * n + k;
                     for (int j = 0; j < b; ++j) {
-                        float v = row[j];
-                        for (int t = 0; t < j; ++t) v = fmaf(-row[t], d[t * (PB + 1) + j], v);
+                        E v = row[j];
+                        for (int t = 0; t < j; ++t) v = fma(-row[t], d[t * (PB + 1) + j], v);
                         row[j] = v / d[j * (PB + 1) + j];
                     }
                 } else {
-                    float* col = M + (int64_t)k * n + k + b + (q - rest);
+                    E* col = M + (int64_t)k * n + k + b + (q - rest);
                     for (int i = 0; i < b; ++i) {
-                        float v = col[(int64_t)i * n];
-                        for (int t = 0; t < i; ++t) v = fmaf(-d[i * (PB + 1) + t], col[(int64_t)t * n], v);
+                        E v = col[(int64_t)i * n];
+                        for (int t = 0; t < i; ++t) v = fma(-d[i * (PB + 1) + t], col[(int64_t)t * n], v);
                         col[(int64_t)i * n] = v;
                     }
                 }
             }
             __syncthreads();
-            cta_gemm<T, TILE, float>(rest, rest, b, M + (int64_t)(k + b) * n + k, n, M + (int64_t)k * n + k + b, n,
-                                     M + (int64_t)(k + b) * n + k + b, n, -1.0f, 1.0f, smem + PB * (PB + 1));
+            cta_gemm_same<T, TILE, E>(rest, rest, b, M + (int64_t)(k + b) * n + k, n, M + (int64_t)k * n + k + b, n,
+                                      M + (int64_t)(k + b) * n + k + b, n, smem + PB * (PB + 1));
         }
     }
     return 0;
@@ -193,23 +250,23 @@ __device__ int cta_genp(int n, float* M, float* smem, int* flag) {
 
 // In-place y <- U^{-1} L^{-1} y (FP32 vector, n), warp 0 solving 32-row diagonal blocks, all threads
 // updating the rows below (above) with the solved block.
-template <int T>
-__device__ void cta_lu_solve(int n, const float* M, float* y) {
+template <int T, typename E>
+__device__ void cta_lu_solve(int n, const E* M, E* y) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = 0; k < n; k += 32) {  // L z = y
         const int b = min(32, n - k);
         if (warp == 0) {
-            float v = lane < b ? y[k + lane] : 0.0f;
+            E v = lane < b ? y[k + lane] : E(0);
             for (int j = 0; j < b; ++j) {
-                const float zj = __shfl_sync(0xffffffffu, v, j);
-                if (lane > j && lane < b) v = fmaf(-M[(int64_t)(k + lane) * n + k + j], zj, v);
+                const E zj = __shfl_sync(0xffffffffu, v, j);
+                if (lane > j && lane < b) v = fma(-M[(int64_t)(k + lane) * n + k + j], zj, v);
             }
             if (lane < b) y[k + lane] = v;
         }
         __syncthreads();
         for (int i = k + b + threadIdx.x; i < n; i += T) {
-            float v = y[i];
-            for (int j = 0; j < b; ++j) v = fmaf(-M[(int64_t)i * n + k + j], y[k + j], v);
+            E v = y[i];
+            for (int j = 0; j < b; ++j) v = fma(-M[(int64_t)i * n + k + j], y[k + j], v);
             y[i] = v;
         }
         __syncthreads();
@@ -217,19 +274,18 @@ __device__ void cta_lu_solve(int n, const float* M, float* y) {
     for (int k = ((n - 1) / 32) * 32; k >= 0; k -= 32) {  // U x = z
         const int b = min(32, n - k);
         if (warp == 0) {
-            float v = lane < b ? y[k + lane] : 0.0f;
+            E v = lane < b ? y[k + lane] : E(0);
             for (int j = b - 1; j >= 0; --j) {
-                float xj = 0.0f;
                 if (lane == j) v = v / M[(int64_t)(k + j) * n + k + j];
-                xj = __shfl_sync(0xffffffffu, v, j);
-                if (lane < j) v = fmaf(-M[(int64_t)(k + lane) * n + k + j], xj, v);
+                const E xj = __shfl_sync(0xffffffffu, v, j);
+                if (lane < j) v = fma(-M[(int64_t)(k + lane) * n + k + j], xj, v);
             }
             if (lane < b) y[k + lane] = v;
         }
         __syncthreads();
         for (int i = threadIdx.x; i < k; i += T) {
-            float v = y[i];
-            for (int j = 0; j < b; ++j) v = fmaf(-M[(int64_t)i * n + k + j], y[k + j], v);
+            E v = y[i];
+            for (int j = 0; j < b; ++j) v = fma(-M[(int64_t)i * n + k + j], y[k + j], v);
             y[i] = v;
         }
         __syncthreads();
@@ -237,12 +293,12 @@ __device__ void cta_lu_solve(int n, const float* M, float* y) {
 }
 
 // out (FP32 or FP64, accumulate or assign) = G v, one warp per row
-template <int T>
-__device__ void cta_gemv_f32(int n, const float* G, const float* v, double* out, bool accumulate) {
+template <int T, typename E>
+__device__ void cta_gemv(int n, const float* G, const E* v, double* out, bool accumulate) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = warp; i < n; i += T / 32) {
-        float s = 0.0f;
-        for (int j = lane; j < n; j += 32) s = fmaf(G[(int64_t)i * n + j], v[j], s);
+        E s = E(0);
+        for (int j = lane; j < n; j += 32) s = fma((E)G[(int64_t)i * n + j], v[j], s);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) out[i] = accumulate ? out[i] + (double)s : (double)s;
     }
@@ -268,8 +324,8 @@ template <int T>
 __device__ void cta_precond(int n, const float* M, const float* G, const double* v, float* y, double* z) {
     for (int i = threadIdx.x; i < n; i += T) y[i] = (float)v[i];
     __syncthreads();
-    cta_lu_solve<T>(n, M, y);
-    cta_gemv_f32<T>(n, G, y, z, false);
+    cta_lu_solve<T, float>(n, M, y);
+    cta_gemv<T, float>(n, G, y, z, false);
 }
 
 // One right-preconditioned GMRES(GM) cycle in FP64 on A d = r (r in rz on entry), x += P V y.
@@ -373,9 +429,11 @@ __global__ void __launch_bounds__(T) batched_kernel(BatchArgs a) {
     __shared__ int sys_s, flag, stop_s;
     __shared__ double red[T / 32];
     __shared__ double red2[T / 32];
-    float* G = a.scratch + (int64_t)blockIdx.x * (2 * a.nmax * a.nmax + 2 * a.nmax);
+    // per CTA: G (nmax^2 floats), M (nmax^2 doubles: FP32 factors, or FP64 ones on the fallback), y
+    float* G = a.scratch + (int64_t)blockIdx.x * (3 * a.nmax * a.nmax + 2 * a.nmax);
     float* M = G + a.nmax * a.nmax;
-    float* y = M + a.nmax * a.nmax;
+    double* M64 = reinterpret_cast<double*>(M);
+    float* y = M + 2 * a.nmax * a.nmax;
     double* r = a.dscratch + (int64_t)blockIdx.x * a.nmax * (GM + 2);
     double* V = r + a.nmax;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -393,90 +451,172 @@ __global__ void __launch_bounds__(T) batched_kernel(BatchArgs a) {
         const double* b = a.b + a.offv[sys];
         double* x = a.x + a.offv[sys];
 
-        gen_gaussian_f32<T>((int64_t)n * n, a.seed, (uint64_t)sys, G);
-        __syncthreads();
-        cta_gemm<T, TILE, double>(n, n, n, A, n, G, n, M, n, 1.0f, 0.0f, smem);
-        const int info = cta_genp<T, TILE>(n, M, smem, &flag);
-        if (info != 0) {
-            if (threadIdx.x == 0) {
-                a.info[sys] = info;
-                a.berr[sys] = __longlong_as_double(0x7ff8000000000000LL);
-                a.sweeps[sys] = 0;
-            }
-            for (int i = threadIdx.x; i < n; i += T) x[i] = __longlong_as_double(0x7ff8000000000000LL);
+        // Up to kDraws multipliers: a draw whose FP32 factors cannot be refined (GENP growth times
+        // kappa(A G) too large, or a zero pivot) is replaced by a fresh Gaussian G from another
+        // subsequence -- the method's guarantees hold with probability close to 1 per draw (Sec. 4).
+        constexpr int kDraws = 3;
+        int info = 0, total_sweeps = 0;
+        double eta = __longlong_as_double(0x7ff0000000000000LL);
+        bool done = false;
+        for (int draw = 0; draw < kDraws && !done; ++draw) {
+            gen_gaussian_f32<T>((int64_t)n * n, a.seed, (uint64_t)sys + (uint64_t)draw * (uint64_t)a.count, G);
             __syncthreads();
-            continue;
-        }
-        // x = G U^{-1} L^{-1} b
-        for (int i = threadIdx.x; i < n; i += T) y[i] = (float)b[i];
-        __syncthreads();
-        cta_lu_solve<T>(n, M, y);
-        cta_gemv_f32<T>(n, G, y, x, false);
-        // sweeps: r = b - A x in FP64, eta = ||r|| / (||A|| ||x|| + ||b||); the correction is
-        // x += G U^{-1} L^{-1} r while that at least halves eta, and one preconditioned GMRES cycle in
-        // FP64 from the first sweep that does not (FP32 factors too inexact for kappa(A G)).
-        double norm_a = 0.0;
-        int sw = 0;
-        double eta = 0.0, eta_prev = 0.0;
-        bool krylov = false;
-        for (;; ++sw) {
-            double rmax = 0.0, amax = 0.0;
-            for (int i = warp; i < n; i += T / 32) {
-                double s = (lane == 0) ? b[i] : 0.0, as = 0.0;  // b enters the warp sum once
-                for (int j = lane; j < n; j += 32) {
-                    const double aij = A[(int64_t)i * n + j];
-                    s = fma(-aij, x[j], s);
-                    as += fabs(aij);
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    s += __shfl_xor_sync(0xffffffffu, s, o);
-                    as += __shfl_xor_sync(0xffffffffu, as, o);
-                }
-                if (lane == 0) r[i] = s;
-                rmax = fmax(rmax, fabs(s));
-                amax = fmax(amax, as);
-            }
-            if (lane == 0) {
-                red[warp] = rmax;
-                red2[warp] = amax;
-            }
+            cta_gemm<T, TILE, double, float>(n, n, n, A, n, G, n, M, n, 1.0f, 0.0f, smem);
+            info = cta_genp<T, TILE, float>(n, M, smem, &flag);
+            if (info != 0) continue;
+            // x = G U^{-1} L^{-1} b
+            for (int i = threadIdx.x; i < n; i += T) y[i] = (float)b[i];
             __syncthreads();
-            if (threadIdx.x == 0) {
-                double rm = 0.0, am = 0.0, xm = 0.0, bm = 0.0;
-                for (int w = 0; w < T / 32; ++w) {
-                    rm = fmax(rm, red[w]);
-                    am = fmax(am, red2[w]);
+            cta_lu_solve<T, float>(n, M, y);
+            cta_gemv<T, float>(n, G, y, x, false);
+            // sweeps: r = b - A x in FP64, eta = ||r|| / (||A|| ||x|| + ||b||); the correction is
+            // x += G U^{-1} L^{-1} r while that at least halves eta, then preconditioned GMRES cycles in
+            // FP64; a GMRES cycle that fails to halve eta ends this draw.
+            double norm_a = 0.0, eta_prev = 0.0;
+            bool krylov = false;
+            for (int sw = 0;; ++sw, ++total_sweeps) {
+                double rmax = 0.0, amax = 0.0;
+                for (int i = warp; i < n; i += T / 32) {
+                    double sacc = (lane == 0) ? b[i] : 0.0, as = 0.0;  // b enters the warp sum once
+                    for (int j = lane; j < n; j += 32) {
+                        const double aij = A[(int64_t)i * n + j];
+                        sacc = fma(-aij, x[j], sacc);
+                        as += fabs(aij);
+                    }
+                    for (int o = 16; o > 0; o >>= 1) {
+                        sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                        as += __shfl_xor_sync(0xffffffffu, as, o);
+                    }
+                    if (lane == 0) r[i] = sacc;
+                    rmax = fmax(rmax, fabs(sacc));
+                    amax = fmax(amax, as);
                 }
-                for (int i = 0; i < n; ++i) {
-                    xm = fmax(xm, fabs(x[i]));
-                    bm = fmax(bm, fabs(b[i]));
+                if (lane == 0) {
+                    red[warp] = rmax;
+                    red2[warp] = amax;
                 }
-                if (sw == 0) norm_a = am;
-                const double den = norm_a * xm + bm;
-                double e = den > 0.0 ? rm / den : 0.0;
-                if (!isfinite(e) || !isfinite(xm)) e = __longlong_as_double(0x7ff0000000000000LL);
-                red[0] = e;
-                stop_s = (e <= a.tol || sw >= a.max_sweeps || !isfinite(e)) ? 1 : 0;
-            }
-            __syncthreads();
-            eta = red[0];
-            __syncthreads();
-            if (stop_s) break;
-            if (sw > 0 && !(eta <= 0.5 * eta_prev)) krylov = true;
-            eta_prev = eta;
-            if (krylov) {
-                cta_gmres_cycle<T>(n, A, M, G, x, r, V, y, red);
-            } else {
-                for (int i = threadIdx.x; i < n; i += T) y[i] = (float)r[i];
                 __syncthreads();
-                cta_lu_solve<T>(n, M, y);
-                cta_gemv_f32<T>(n, G, y, x, true);
+                if (threadIdx.x == 0) {
+                    double rm = 0.0, am = 0.0, xm = 0.0, bm = 0.0;
+                    for (int w = 0; w < T / 32; ++w) {
+                        rm = fmax(rm, red[w]);
+                        am = fmax(am, red2[w]);
+                    }
+                    for (int i = 0; i < n; ++i) {
+                        xm = fmax(xm, fabs(x[i]));
+                        bm = fmax(bm, fabs(b[i]));
+                    }
+                    if (sw == 0) norm_a = am;
+                    const double den = norm_a * xm + bm;
+                    double e = den > 0.0 ? rm / den : 0.0;
+                    if (!isfinite(e) || !isfinite(xm)) e = __longlong_as_double(0x7ff0000000000000LL);
+                    red[0] = e;
+                    int st = 0;  // 0 continue classical, 1 continue GMRES, 2 converged, 3 give up this draw
+                    if (e <= a.tol) st = 2;
+                    else if (sw >= a.max_sweeps || !isfinite(e)) st = 3;
+                    else if (sw > 0 && !(e <= 0.5 * eta_prev)) st = krylov ? 3 : 1;
+                    else st = krylov ? 1 : 0;
+                    stop_s = st;
+                }
+                __syncthreads();
+                const double e = red[0];
+                const int st = stop_s;
+                __syncthreads();
+                eta = e;  // the report matches the x left behind
+                if (st == 2) {
+                    done = true;
+                    eta = e;
+                    break;
+                }
+                if (st == 3) break;
+                krylov = (st == 1);
+                eta_prev = e;
+                if (krylov) {
+                    cta_gmres_cycle<T>(n, A, M, G, x, r, V, y, red);
+                } else {
+                    for (int i = threadIdx.x; i < n; i += T) y[i] = (float)r[i];
+                    __syncthreads();
+                    cta_lu_solve<T, float>(n, M, y);
+                    cta_gemv<T, float>(n, G, y, x, true);
+                }
             }
         }
+        if (!done) {
+            // FP64 fallback: M = A G and its GENP in FP64 (first multiplier), classical FP64 sweeps.
+            double* smem_d = reinterpret_cast<double*>(smem);
+            double* y64 = V;
+            gen_gaussian_f32<T>((int64_t)n * n, a.seed, (uint64_t)sys, G);
+            __syncthreads();
+            cta_gemm<T, TILE, double, double>(n, n, n, A, n, G, n, M64, n, 1.0, 0.0, smem_d);
+            info = cta_genp<T, TILE, double>(n, M64, smem_d, &flag);
+            if (info == 0) {
+                for (int i = threadIdx.x; i < n; i += T) y64[i] = b[i];
+                __syncthreads();
+                cta_lu_solve<T, double>(n, M64, y64);
+                cta_gemv<T, double>(n, G, y64, x, false);
+                double eta_prev = 0.0, norm_a = 0.0;
+                for (int sw = 0;; ++sw, ++total_sweeps) {
+                    double rmax = 0.0, amax = 0.0;
+                    for (int i = warp; i < n; i += T / 32) {
+                        double sacc = (lane == 0) ? b[i] : 0.0, as = 0.0;
+                        for (int j = lane; j < n; j += 32) {
+                            const double aij = A[(int64_t)i * n + j];
+                            sacc = fma(-aij, x[j], sacc);
+                            as += fabs(aij);
+                        }
+                        for (int o = 16; o > 0; o >>= 1) {
+                            sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                            as += __shfl_xor_sync(0xffffffffu, as, o);
+                        }
+                        if (lane == 0) r[i] = sacc;
+                        rmax = fmax(rmax, fabs(sacc));
+                        amax = fmax(amax, as);
+                    }
+                    if (lane == 0) {
+                        red[warp] = rmax;
+                        red2[warp] = amax;
+                    }
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        double rm = 0.0, am = 0.0, xm = 0.0, bm = 0.0;
+                        for (int w = 0; w < T / 32; ++w) {
+                            rm = fmax(rm, red[w]);
+                            am = fmax(am, red2[w]);
+                        }
+                        for (int i = 0; i < n; ++i) {
+                            xm = fmax(xm, fabs(x[i]));
+                            bm = fmax(bm, fabs(b[i]));
+                        }
+                        if (sw == 0) norm_a = am;
+                        const double den = norm_a * xm + bm;
+                        double e = den > 0.0 ? rm / den : 0.0;
+                        if (!isfinite(e) || !isfinite(xm)) e = __longlong_as_double(0x7ff0000000000000LL);
+                        red[0] = e;
+                        stop_s = (e <= a.tol) ? 2
+                                 : (sw >= a.max_sweeps || !isfinite(e) || (sw > 0 && !(e <= 0.5 * eta_prev))) ? 3
+                                                                                                            : 0;
+                    }
+                    __syncthreads();
+                    const double e = red[0];
+                    const int st = stop_s;
+                    __syncthreads();
+                    eta = e;
+                    eta_prev = e;
+                    if (st == 2) done = true;
+                    if (st != 0) break;
+                    for (int i = threadIdx.x; i < n; i += T) y64[i] = r[i];
+                    __syncthreads();
+                    cta_lu_solve<T, double>(n, M64, y64);
+                    cta_gemv<T, double>(n, G, y64, x, true);
+                }
+            }
+        }
+        if (!done && info != 0)
+            for (int i = threadIdx.x; i < n; i += T) x[i] = __longlong_as_double(0x7ff8000000000000LL);
         if (threadIdx.x == 0) {
-            a.info[sys] = 0;
-            a.berr[sys] = eta;
-            a.sweeps[sys] = sw;
+            a.info[sys] = done ? 0 : info;
+            a.berr[sys] = (!done && info != 0) ? __longlong_as_double(0x7ff8000000000000LL) : eta;
+            a.sweeps[sys] = total_sweeps;
         }
         __syncthreads();
     }
@@ -493,7 +633,7 @@ __global__ void __launch_bounds__(T) batched_kernel(BatchArgs a) {
 
 template <int T, int TILE>
 rmge_status launch_batched(const BatchArgs& a, int ctas, cudaStream_t s) {
-    const size_t smem = (size_t)(2 * 16 * TILE + PB * (PB + 1)) * sizeof(float);
+    const size_t smem = (size_t)(2 * 16 * TILE + PB * (PB + 1)) * sizeof(double);  // FP32 or FP64 tiles
     if (cudaFuncSetAttribute(batched_kernel<T, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
         (void)cudaGetLastError();
@@ -507,7 +647,7 @@ rmge_status launch_batched(const BatchArgs& a, int ctas, cudaStream_t s) {
 }  // namespace
 
 size_t batched_scratch_bytes(int64_t nmax, int ctas) {
-    return align256((size_t)ctas * (size_t)(2 * nmax * nmax + 2 * nmax) * sizeof(float)) +
+    return align256((size_t)ctas * (size_t)(3 * nmax * nmax + 2 * nmax) * sizeof(float)) +
            align256((size_t)ctas * (size_t)nmax * (GM + 2) * sizeof(double)) + 256;
 }
 
@@ -535,7 +675,7 @@ rmge_status batched_solve(int64_t count, const int32_t* n, const int64_t* offA, 
     a.queue = reinterpret_cast<unsigned int*>(base);
     a.scratch = reinterpret_cast<float*>(base + 256);
     a.dscratch = reinterpret_cast<double*>(base + 256 +
-                                           align256((size_t)ctas * (size_t)(2 * nmax * nmax + 2 * nmax) * sizeof(float)));
+                                           align256((size_t)ctas * (size_t)(3 * nmax * nmax + 2 * nmax) * sizeof(float)));
     switch (config) {
         case 0: return launch_batched<256, 32>(a, ctas, s);
         case 1: return launch_batched<256, 64>(a, ctas, s);

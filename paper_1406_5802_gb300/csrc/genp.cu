@@ -244,34 +244,6 @@ rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const
     return RMGE_OK;
 }
 
-// FP64 working matrix with the Schur-complement update as an FP64 product emulated on the BF16
-// tensor cores (oz_gemm); pivot blocks and panels stay FP64.
-rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s) {
-    constexpr int PT = 16;
-    const size_t smem = NB * LDS * sizeof(double);
-    if (cudaFuncSetAttribute(diag_factor_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-        (void)cudaGetLastError();
-        return RMGE_ERR_CUDA;
-    }
-    RMGE_TRY(maxabs<double>(n, n, M, ldm, false, &st->maxabs_m, s));
-    for (int64_t k = 0; k < n; k += NB) {
-        const int b = (int)((n - k) < NB ? (n - k) : NB);
-        diag_factor_kernel<double><<<1, 256, smem, s>>>(k, b, M, ldm, st);
-        RMGE_LAUNCH_CHECK();
-        const int64_t rest = n - k - b;
-        if (rest <= 0) break;
-        const int tiles = (int)((rest + PT - 1) / PT);
-        panel_apply_kernel<double, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st);
-        RMGE_LAUNCH_CHECK();
-        RMGE_TRY(oz_gemm(rest, rest, b, kOzSlices, -1.0, M + (k + b) * ldm + k, ldm, M + k * ldm + k + b, ldm, 1.0,
-                         M + (k + b) * ldm + (k + b), ldm, oz.planesA, oz.planesB, oz.ea, oz.eb, &st->error, &st->halt,
-                         s));
-    }
-    RMGE_TRY(maxabs<double>(n, n, M, ldm, true, &st->maxabs_u, s));
-    return RMGE_OK;
-}
-
 rmge_status genp_finish(DevState* st, int32_t* info, double* growth, cudaStream_t s) {
     finish_kernel<<<1, 1, 0, s>>>(st, info, growth);
     RMGE_LAUNCH_CHECK();

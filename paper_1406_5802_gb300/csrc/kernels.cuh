@@ -42,7 +42,7 @@ uint32_t tc_idesc(bool bf16);
 // s base-128 digit planes of A (rows) and B (columns).  planesA/planesB: oz_plane_bytes(M, K, s) and
 // oz_plane_bytes(N, K, s) bytes; ea[M], eb[N] ints of scratch.  *err <- RMGE_ERR_TIMEOUT if a bounded
 // wait expires; nothing happens while *halt != 0 (halt may be NULL).
-constexpr int kOzSlices = 7;
+constexpr int kOzSlices = 8;
 size_t oz_plane_bytes(int64_t rows, int64_t k, int s);
 rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* planesA, void* planesB,
@@ -53,7 +53,6 @@ struct OzUpdate {
     int* ea;
     int* eb;
 };
-rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s);
 
 // genp.cu: in-place blocked GENP of an n x n matrix with DevState bookkeeping.
 template <typename T>

@@ -5,19 +5,21 @@
 //   - every row i of A gets an exponent ea_i with max_k |A_ik| < 2^ea_i, every column j of B an eb_j;
 //   - x = A_ik 2^-ea_i (|x| < 1) is truncated to s base-128 digits, x ~ sign * sum_p d_p 128^-(p+1),
 //     0 <= d_p <= 127, and digit plane p is stored as BF16 (exact: integers below 256);
-//   - digit products d_p e_q are below 2^14, so a sum of 1024 of them stays below 2^24 and the
-//     tensor core's FP32 accumulation of one 1024-deep chunk is exact;
-//   - each chunk result (an exact integer) is scaled by 128^-(p+q+2) (exact) and added into a
-//     double-float (FP32 pair) accumulator held in registers -- FP32 work, not FP64;
-//   - C_ij = 2^(ea_i + eb_j) (hi + lo), combined with beta C in FP64 once per element.
-// Digit pairs with p + q <= s - 1 are kept.  With s = 7 the result carries about 48 correct bits
-// relative to max|A_i.| max|B_.j| -- far more than GENP needs before FP64 refinement.
+//   - digit products d_p e_q are below 2^14; the d + 1 digit pairs of one diagonal d = p + q share a
+//     TMEM accumulator over a K chunk short enough that (d + 1) 127^2 kc < 2^24, so the tensor core's
+//     FP32 accumulation of every chunk is exact (kc = 1024, 512, ..., 128 for d = 0 .. 7);
+//   - each chunk result (an exact integer) is added, shifted to its weight 128^-(d+2), into a 64-bit
+//     fixed-point accumulator per output element (integer work, not FP64): F fractional bits of
+//     max|A_i.| max|B_.j| with F = 52 - log2(chunks on diagonal 0 + 1), i.e. 51 bits up to K = 1024;
+//   - C_ij = 2^(ea_i + eb_j - F) acc, combined with beta C in FP64 once per element.
+// Digit pairs with p + q <= s - 1 are kept.  The first dropped diagonal (p + q = s) is worth about
+// (s + 1) 2^(-7s) of max|A_i.| max|B_.j| per term, so s = 8 (36 digit pairs) matches FP64 rounding.
 //
 // Kernel: one 128 x 128 output tile per CTA, 10 warps.  Warp 8 (one lane) streams 128x64 BF16 tiles
 // of A-digit and B-digit planes by TMA into a 6-stage ring; warp 9 (one lane) issues
 // tcgen05.mma kind::f16 (M=128, N=128, K=16) into one of two 128-column TMEM accumulators, one
-// (digit pair, K chunk) unit at a time; warps 0-7 drain the other accumulator (tcgen05.ld) into
-// their double-float registers while the next unit accumulates.  All waits are bounded.
+// (diagonal, K chunk) unit at a time; warps 0-7 drain the other accumulator (tcgen05.ld) into their
+// fixed-point registers while the next unit accumulates.  All waits are bounded.
 #include <cuda_bf16.h>
 
 #include "tc_common.cuh"
@@ -31,15 +33,14 @@ constexpr int OBM = 128, OBN = 128, OBK = 64, OSTAGES = 6;
 constexpr int OA_BYTES = OBM * OBK * 2;
 constexpr int OB_BYTES = OBN * OBK * 2;
 constexpr int OSTAGE_BYTES = OA_BYTES + OB_BYTES;
-constexpr int OKC = 1024;  // K per exact chunk
 constexpr int OTHREADS = 320;
 constexpr int OTMEM = 256;
-constexpr int OMAX_PAIRS = 36;
 constexpr unsigned long long kOzWaitNs = 4000000000ull;
 constexpr size_t kOzSmem = (size_t)OSTAGES * OSTAGE_BYTES + 1024 + 512;
 
 struct OzParams {
-    int M, N, K, npairs, nchunks;
+    int M, N, K, s;
+    int F;  // fractional bits of the fixed-point accumulator
     int Mp, Np;  // rows per digit plane of A, of B
     const int* ea;
     const int* eb;
@@ -48,15 +49,13 @@ struct OzParams {
     int64_t ldc;
     int* err;
     const int* halt;
-    unsigned char pp[OMAX_PAIRS], pq[OMAX_PAIRS];
 };
 
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float w) {
-    const float s = hi + w;
-    const float bb = s - hi;
-    const float e = (hi - (s - bb)) + (w - bb);
-    hi = s;
-    lo += e;
+// Depth of one exact chunk on diagonal d = p + q: the (d + 1) digit pairs of the diagonal share one
+// TMEM accumulator, so (d + 1) 127^2 kc must stay below 2^24 (kc a multiple of the 64-deep K block).
+__device__ __forceinline__ int diag_kc(int d) {
+    constexpr int kc[8] = {1024, 512, 320, 256, 192, 128, 128, 128};
+    return kc[d];
 }
 
 __global__ void __launch_bounds__(OTHREADS, 1)
@@ -76,12 +75,6 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * OBM, n0 = blockIdx.x * OBN;
-    const int units = p.npairs * p.nchunks;
-    auto kblocks = [&](int c) {
-        const int rem = p.K - c * OKC;
-        const int kk = rem < OKC ? rem : OKC;
-        return (kk + OBK - 1) / OBK;
-    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OSTAGES; ++s) {
@@ -108,21 +101,26 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
     const unsigned long long deadline = now_ns() + kOzWaitNs;
 
     if (warp == 8) {
-        if (lane == 0) {  // TMA producer
+        if (lane == 0) {  // TMA producer: units (d, chunk), then pairs p + q = d, then 64-deep K blocks
             int it = 0;
-            for (int u = 0; u < units && !*(volatile int*)&aborted; ++u) {
-                const int pr = u / p.nchunks, c = u % p.nchunks;
-                const int ya = p.pp[pr] * p.Mp + m0, yb = p.pq[pr] * p.Np + n0;
-                const int nkb = kblocks(c);
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    const int s = it % OSTAGES;
-                    if (!mbar_wait(empty + s, (uint32_t)(((it / OSTAGES) & 1) ^ 1), deadline)) {
-                        atomicExch(&aborted, 1);
-                        break;
+            for (int d = 0; d < p.s && !*(volatile int*)&aborted; ++d) {
+                const int kc = diag_kc(d);
+                for (int k0 = 0; k0 < p.K && !*(volatile int*)&aborted; k0 += kc) {
+                    const int nkb = ((p.K - k0 < kc ? p.K - k0 : kc) + OBK - 1) / OBK;
+                    for (int pa = 0; pa <= d; ++pa) {
+                        const int ya = pa * p.Mp + m0, yb = (d - pa) * p.Np + n0;
+                        for (int kb = 0; kb < nkb; ++kb, ++it) {
+                            const int st = it % OSTAGES;
+                            if (!mbar_wait(empty + st, (uint32_t)(((it / OSTAGES) & 1) ^ 1), deadline)) {
+                                atomicExch(&aborted, 1);
+                                break;
+                            }
+                            mbar_expect_tx(full + st, OSTAGE_BYTES);
+                            tma_load_2d(sA + st * OA_BYTES, &tA, k0 + kb * OBK, ya, full + st);
+                            tma_load_2d(sB + st * OB_BYTES, &tB, k0 + kb * OBK, yb, full + st);
+                        }
+                        if (*(volatile int*)&aborted) break;
                     }
-                    mbar_expect_tx(full + s, OSTAGE_BYTES);
-                    tma_load_2d(sA + s * OA_BYTES, &tA, c * OKC + kb * OBK, ya, full + s);
-                    tma_load_2d(sB + s * OB_BYTES, &tB, c * OKC + kb * OBK, yb, full + s);
                 }
             }
             // drain: the last copies issued must land before the CTA can leave
@@ -131,64 +129,76 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
                 (void)mbar_wait(full + j % OSTAGES, (uint32_t)((j / OSTAGES) & 1), d2);
         }
     } else if (warp == 9) {
-        if (lane == 0) {  // MMA issuer
-            int it = 0;
-            for (int u = 0; u < units; ++u) {
-                const int buf = u & 1;
-                if (!mbar_wait(tempty + buf, (uint32_t)(((u >> 1) & 1) ^ 1), deadline)) {
-                    atomicExch(&aborted, 1);
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int nkb = kblocks(u % p.nchunks);
-                bool ok = true;
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    const int s = it % OSTAGES;
-                    if (!mbar_wait(full + s, (uint32_t)((it / OSTAGES) & 1), deadline)) {
+        if (lane == 0) {  // MMA issuer: one TMEM accumulator per unit (d, chunk), alternating buffers
+            int it = 0, u = 0;
+            bool ok = true;
+            for (int d = 0; d < p.s && ok; ++d) {
+                const int kc = diag_kc(d);
+                for (int k0 = 0; k0 < p.K && ok; k0 += kc, ++u) {
+                    const int buf = u & 1;
+                    if (!mbar_wait(tempty + buf, (uint32_t)(((u >> 1) & 1) ^ 1), deadline)) {
                         atomicExch(&aborted, 1);
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t a0 = smem_u32(sA + s * OA_BYTES), b0 = smem_u32(sB + s * OB_BYTES);
+                    const int nkb = ((p.K - k0 < kc ? p.K - k0 : kc) + OBK - 1) / OBK;
+                    for (int pa = 0; pa <= d && ok; ++pa) {
+                        for (int kb = 0; kb < nkb; ++kb, ++it) {
+                            const int st = it % OSTAGES;
+                            if (!mbar_wait(full + st, (uint32_t)((it / OSTAGES) & 1), deadline)) {
+                                atomicExch(&aborted, 1);
+                                ok = false;
+                                break;
+                            }
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            const uint32_t a0 = smem_u32(sA + st * OA_BYTES), b0 = smem_u32(sB + st * OB_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < OBK / 16; ++kk)
-                        mma_f16(tmem + (uint32_t)(buf * 128), smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
-                                (kb > 0 || kk > 0) ? 1u : 0u);
-                    mma_commit(empty + s);
+                            for (int kk = 0; kk < OBK / 16; ++kk)
+                                mma_f16(tmem + (uint32_t)(buf * 128), smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32),
+                                        idesc, (pa > 0 || kb > 0 || kk > 0) ? 1u : 0u);
+                            mma_commit(empty + st);
+                        }
+                    }
+                    mma_commit(tfull + buf);
                 }
-                mma_commit(tfull + buf);
-                if (!ok) break;
             }
         }
     } else {
         // epilogue warps 0-7: quadrant (TMEM lanes / tile rows) and column half
         const int quad = warp & 3, half = warp >> 2;
-        float hi[64], lo[64];
+        long long acc[64];  // fixed point: units of 2^-F of max|A_i.| max|B_.j|
 #pragma unroll
-        for (int j = 0; j < 64; ++j) hi[j] = lo[j] = 0.0f;
-        for (int u = 0; u < units; ++u) {
-            const int buf = u & 1;
-            const bool got = mbar_wait(tfull + buf, (uint32_t)((u >> 1) & 1), deadline);
-            if (!got) {
-                atomicExch(&aborted, 1);
-                break;
+        for (int j = 0; j < 64; ++j) acc[j] = 0;
+        int u = 0;
+        bool ok = true;
+        for (int d = 0; d < p.s && ok; ++d) {
+            const int kc = diag_kc(d);
+            const int sh = p.F - 7 * (d + 2);  // chunk value v weighs 2^-(7(d+2)) = 2^(sh - F)
+            for (int k0 = 0; k0 < p.K; k0 += kc, ++u) {
+                const int buf = u & 1;
+                if (!mbar_wait(tfull + buf, (uint32_t)((u >> 1) & 1), deadline)) {
+                    atomicExch(&aborted, 1);
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                __syncwarp();
+                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 128 + half * 64);
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    float v[32];
+                    tmem_ld32(taddr + cc * 32, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const long long t = __float2ll_rn(v[j]);  // exact: |v| < 2^24 is an integer
+                        acc[cc * 32 + j] += (sh >= 0) ? (t << sh) : ((t + (1ll << (-sh - 1))) >> (-sh));
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty + buf);
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            __syncwarp();
-            const int pr = u / p.nchunks;
-            const float scale = ldexpf(1.0f, -7 * (p.pp[pr] + p.pq[pr] + 2));
-            const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 128 + half * 64);
-#pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
-                float v[32];
-                tmem_ld32(taddr + cc * 32, v);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) two_sum_acc(hi[cc * 32 + j], lo[cc * 32 + j], v[j] * scale);
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tempty + buf);
         }
         if (!aborted) {
             const int row = m0 + quad * 32 + lane;
@@ -199,15 +209,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
                 for (int j = 0; j < 64; ++j) {
                     const int col = n0 + half * 64 + j;
                     if (col < p.N) {
-                        // scale by 2^(ea + eb) in FP32 where that is exact (few FP64-pipe operations)
-                        const int ee = er + p.eb[col];
-                        double v;
-                        if (ee > -80 && ee < 80) {
-                            const float sc = __int_as_float((ee + 127) << 23);
-                            v = (double)(hi[j] * sc) + (double)(lo[j] * sc);
-                        } else {
-                            v = ldexp((double)hi[j] + (double)lo[j], ee);
-                        }
+                        const double v = ldexp((double)acc[j], er + p.eb[col] - p.F);
                         crow[col] = (p.beta == 0.0) ? p.alpha * v : fma(p.beta, crow[col], p.alpha * v);
                     }
                 }
@@ -352,7 +354,11 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
     prm.M = (int)M;
     prm.N = (int)N;
     prm.K = (int)Kp;
-    prm.nchunks = (int)((Kp + OKC - 1) / OKC);
+    prm.s = s;
+    // |acc| < (chunks on diagonal 0 + 1) 2^(F + 10) must stay below 2^62
+    int ch0 = (int)((Kp + 1023) / 1024), lg = 0;
+    while ((1 << lg) < ch0 + 1) ++lg;
+    prm.F = 52 - lg;
     prm.Mp = (int)Mp;
     prm.Np = (int)Np;
     prm.ea = ea;
@@ -363,14 +369,6 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
     prm.ldc = ldc;
     prm.err = err;
     prm.halt = halt;
-    int np = 0;
-    for (int d = 0; d < s; ++d)
-        for (int a = 0; a <= d; ++a) {
-            prm.pp[np] = (unsigned char)a;
-            prm.pq[np] = (unsigned char)(d - a);
-            ++np;
-        }
-    prm.npairs = np;
     // idesc: FP32 accumulate, BF16 A and B, both K-major, N = 128, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OBN >> 3) << 17) |
                            ((uint32_t)(OBM >> 4) << 24);

@@ -56,3 +56,18 @@ def test_batched_graph_replay_and_tuning(orc):
     for i in (0, 57, 399):
         x = s.solution(i).cpu().numpy().reshape(-1, 1)
         assert orc.backward_error(As[i], x, bs[i]) <= 1e-13
+
+
+def test_uneven_batch_all_systems_reach_target(orc):
+    """The uneven-batch workload (n ~ U{32..512}, A[0,0] scaled by 1e-10): every system reaches the FP64 target,
+    through FP32 factors with FP64 sweeps, a fresh multiplier, or the FP64 fallback."""
+    As, bs = _batch(120, 32, 512, seed=W.SEED_BASE + 4)
+    s = BatchedSolver(As, bs, seed=W.SEED_BASE + 4, max_sweeps=40)
+    s.launch(1, 2 * 152)
+    torch.cuda.synchronize()
+    assert np.all(s.info.cpu().numpy() == 0)
+    berr = s.berr.cpu().numpy()
+    assert np.all(berr <= 1e-13), (np.argmax(berr), float(np.max(berr)))
+    for i in range(0, 120, 7):
+        x = s.solution(i).cpu().numpy().reshape(-1, 1)
+        assert orc.backward_error(As[i], x, bs[i]) <= 1e-13

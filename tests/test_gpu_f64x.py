@@ -1,0 +1,78 @@
+"""The FP64 products emulated on the BF16 tensor cores (RMGE_F64X_TC): exactness on integer inputs, accuracy
+on random FP64 inputs, the GENP factors it produces, and the whole solve at the FP64 target."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1406_5802_gb300 import rmge
+from paper_1406_5802_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1406_5802_gb300 import build as B
+    B.build()
+    rmge.load_library()
+
+
+@pytest.mark.parametrize("n", [5, 128, 200, 1100])
+def test_emulated_product_is_exact_on_small_integers(orc, n):
+    """Entries below 128 in magnitude are a single base-128 digit, and 1024-deep chunks of their products stay
+    below 2^24: every step is exact, so the product must equal the integer product bit for bit (n = 1100
+    spans two K chunks)."""
+    r = W.rng(n)
+    A = r.integers(-127, 128, (n, n)).astype(np.float64)
+    G = r.integers(-127, 128, (n, n)).astype(np.float64)
+    M = host(rmge.apply_multiplier("gaussian", dev(A), dev(G), "f64x"))
+    ref = (A.astype(np.int64) @ G.astype(np.int64)).astype(np.float64)
+    assert np.array_equal(M, ref)
+
+
+@pytest.mark.parametrize("n", [64, 300, 1500])
+def test_emulated_product_accuracy(orc, n):
+    A, _ = W.orthogonal_factor_system(n, 1, 1e-6, seed=n)
+    G = W.gaussian_multiplier(n, n + 1)
+    M = host(rmge.apply_multiplier("gaussian", dev(A), dev(G), "f64x"))
+    ref = orc.matmul(A, G)
+    # truncation to 7 base-128 digits: 2^-49 relative to the row / column maxima, per term
+    bound = 8 * n * 2.0**-49 * np.max(np.abs(A), axis=1)[:, None] * np.max(np.abs(G), axis=0)[None, :]
+    assert np.all(np.abs(M - ref) <= bound), float(np.max(np.abs(M - ref) / bound))
+
+
+@pytest.mark.parametrize("n", [65, 257, 700])
+def test_emulated_factor_backward_error(orc, n):
+    A, _ = W.gaussian_system(n, 1, seed=90 + n)
+    G = W.gaussian_multiplier(n, 91 + n)
+    M = orc.matmul(A, G)
+    Md = dev(M)
+    info, growth = rmge.factor(Md, "f64x")
+    LU = host(Md)
+    assert int(host(info)[0]) == 0
+    L = np.tril(LU, -1) + np.eye(n)
+    U = np.triu(LU)
+    be = np.max(np.abs(L @ U - M)) / np.max(np.abs(L) @ np.abs(U))
+    assert be <= 1e-13, be
+    ref, _ = orc.genp(M)
+    g = orc.growth(M, ref)
+    assert abs(float(host(growth)[0]) - g) <= 1e-6 * g
+
+
+@pytest.mark.parametrize("n,k", [(256, 1), (1000, 16)])
+def test_emulated_solve_reaches_fp64_target(orc, n, k):
+    A, B = W.orthogonal_factor_system(n, k, 1e-6, seed=300 + n)
+    out = rmge.gesv("gaussian", dev(A), dev(B), seed=5, prec="f64x", max_iters=10, be_tol=1e-13)
+    assert int(host(out["info"])[0]) == 0
+    it = int(host(out["iters"])[0])
+    assert it <= 3, it
+    assert orc.backward_error(A, host(out["X"]), B) <= 1e-13
