@@ -72,9 +72,11 @@ typedef enum {
     RMGE_BF16X3_TC = 4, /* as RMGE_BF16_TC, each FP32 operand split x = x_hi + x_lo into two BF16 terms and the
                            product formed as x_hi y_hi + x_hi y_lo + x_lo y_hi (three tensor-core passes) */
     RMGE_F16X3_TC = 5,  /* the three-pass split with FP16 terms */
-    RMGE_F64X_TC = 6    /* FP64 working matrix, factors and refinement; M = A G is an FP64 product emulated on
-                           the BF16 tensor cores (8 base-128 digits per entry, 36 digit-pair products in
-                           exact FP32 chunks, 64-bit fixed-point accumulation); GENP runs on the FP64 pipe */
+    RMGE_F64X_TC = 6    /* FP64 working matrix, factors and refinement; M = A G and GENP's Schur-complement
+                           updates are FP64 products emulated on the BF16 tensor cores (8 base-128 digits per
+                           entry, 36 digit-pair products in exact FP32 chunks, 64-bit fixed-point sums; the
+                           updates first balance column k of L21 against row k of U12 by a power of two);
+                           pivot blocks, panels, solves and residuals run on the FP64 pipe */
 } rmge_prec;
 
 /*

@@ -77,8 +77,12 @@ OzUpdate oz_buffers(const Ws& w, int64_t n) {
     o.planesB = w.oz + pb;
     o.ea = reinterpret_cast<int*>(w.oz + 2 * pb);
     o.eb = o.ea + n + 128;
+    o.kmax = reinterpret_cast<unsigned long long*>(w.oz + 2 * pb + 2 * sizeof(int) * (size_t)(n + 128));
     return o;
 }
+
+// 128 per-k maxima slots per 64-wide pivot-block step of the emulated-update GENP.
+size_t oz_kmax_slots(int64_t n) { return 128 * (size_t)((n + kNb - 1) / kNb); }
 
 bool check_dims(int64_t n, int64_t nrhs) { return n >= 1 && n <= RMGE_MAX_N && nrhs >= 1 && nrhs <= RMGE_MAX_N; }
 
@@ -238,7 +242,8 @@ WsLayout ws_layout(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec)
     if (data_prec(prec) != RMGE_F64) off = align256(off + gmres_bytes(n, nrhs));
     L.oz = off;
     if (prec == RMGE_F64X_TC)
-        off = align256(off + 2 * oz_plane_bytes(n, n, kOzSlices) + 2 * sizeof(int) * (size_t)(n + 128));
+        off = align256(off + 2 * oz_plane_bytes(n, n, kOzSlices) + 2 * sizeof(int) * (size_t)(n + 128) +
+                       oz_kmax_slots(n) * sizeof(unsigned long long));
     L.total = off;
     return L;
 }
@@ -321,7 +326,7 @@ rmge_status rmge_apply_multiplier(rmge_mult_kind kind, int64_t n, const double* 
     if (prec == RMGE_F64X_TC) {
         const OzUpdate oz = oz_buffers(w, n);
         return oz_gemm(n, n, n, kOzSlices, 1.0, A, lda, static_cast<const double*>(G), n, 0.0, static_cast<double*>(M),
-                       ldm, oz.planesA, oz.planesB, oz.ea, oz.eb, &w.st->error, nullptr, s);
+                       ldm, oz.planesA, oz.planesB, oz.ea, oz.eb, nullptr, nullptr, &w.st->error, nullptr, s);
     }
     if (prec == RMGE_F64)
         return gemm<double>(false, n, n, n, 1.0, A, lda, static_cast<const double*>(G), n, 0.0,
@@ -357,10 +362,11 @@ rmge_status rmge_factor(int64_t n, void* M, int64_t ldm, rmge_prec prec, int32_t
     RMGE_TRY(state_init(w.st, w.flags, 0, w.colred, 0, nullptr, 0, s));
     if (prec == RMGE_F64)
         RMGE_TRY(genp_factor<double>(n, static_cast<double*>(M), ldm, w.st, s));
-    else if (prec == RMGE_F64X_TC)
-        // GENP stays on the FP64 pipe: its panels span a wide dynamic range (pivot growth), where the
-        // per-row / per-column scaling of the emulated product loses the relative accuracy FP64 keeps
-        RMGE_TRY(genp_factor<double>(n, static_cast<double*>(M), ldm, w.st, s));
+    else if (prec == RMGE_F64X_TC) {
+        const OzUpdate oz = oz_buffers(w, n);
+        RMGE_TRY(state_init(w.st, w.flags, 0, reinterpret_cast<double*>(oz.kmax), (int)oz_kmax_slots(n), nullptr, 0, s));
+        RMGE_TRY(genp_factor_oz(n, static_cast<double*>(M), ldm, w.st, oz, s));
+    }
     else if (prec == RMGE_F32)
         RMGE_TRY(genp_factor<float>(n, static_cast<float*>(M), ldm, w.st, s));
     else {

@@ -27,49 +27,58 @@ __device__ __forceinline__ bool finite_nonzero(T v) {
     return v != T(0) && isfinite(v);
 }
 
-// One CTA factors the pivot block in shared memory (dynamic shared memory a[NB][LDS]).
+// One CTA factors the pivot block in shared memory.  GB300 retires 2 FP64 operations per clock per
+// SM, so the kernel keeps every lane of every FP64 instruction busy: step s first scales column s of L
+// by the reciprocal of the pivot (one division per step, formed by the thread that finished the
+// pivot), then the (b-s-1)^2 trailing entries are spread evenly over the 256 threads, the entry index
+// e split into (row, column) by a multiply-shift reciprocal of the width instead of an integer division.
 template <typename T>
 __global__ void __launch_bounds__(256) diag_factor_kernel(int64_t k, int b, T* __restrict__ M, int64_t ldm,
                                                           DevState* st) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* a = reinterpret_cast<T*>(smem_raw);
-    __shared__ int broke;
+    __shared__ T a[NB * LDS];
+    __shared__ T rp;
     if (*(volatile int*)&st->halt) return;
     const int tid = threadIdx.x;
     T* blk = M + k * ldm + k;
-    for (int e = tid; e < b * b; e += blockDim.x) {
-        const int i = e / b, j = e % b;
-        a[i * LDS + j] = blk[i * ldm + j];
-    }
-    if (tid == 0) broke = 0;
+    for (int i = tid >> 6; i < b; i += 4)
+        if ((tid & 63) < b) a[i * LDS + (tid & 63)] = blk[i * ldm + (tid & 63)];
+    __syncthreads();
+    if (tid == 0) rp = T(1) / a[0];
     __syncthreads();
 
-    // Unblocked GENP of the pivot block: step s is eq. (3.1) with a 1 x 1 pivot block.
-    for (int s = 0; s < b; ++s) {
+    int s = 0;
+    bool broke = false;
+    for (; s < b; ++s) {
         const T piv = a[s * LDS + s];
-        if (!finite_nonzero(piv)) {
-            if (tid == 0) {
-                atomicMin(&st->info, (int)(k + s + 1));
-                atomicExch(&st->halt, 1);
-                broke = 1;
-            }
-            break;  // uniform: every thread read the same pivot
+        if (!finite_nonzero(piv)) {  // uniform: every thread read the same pivot
+            broke = true;
+            break;
         }
-        for (int i = s + 1 + tid; i < b; i += blockDim.x) a[i * LDS + s] /= piv;
-        __syncthreads();
         const int w = b - s - 1;
-        for (int e = tid; e < w * w; e += blockDim.x) {
-            const int i = s + 1 + e / w, j = s + 1 + e % w;
-            a[i * LDS + j] = fma(-a[i * LDS + s], a[s * LDS + j], a[i * LDS + j]);
+        if (w == 0) break;
+        if (tid < w) a[(s + 1 + tid) * LDS + s] *= rp;  // column s of L
+        __syncthreads();
+        // e < w^2 <= 63^2: floor(e / w) = (e * ceil(2^20 / w)) >> 20 exactly for e < 2^20 / w
+        const unsigned mw = ((1u << 20) + (unsigned)w - 1u) / (unsigned)w;
+        const T* us = a + s * LDS + s + 1;
+        for (int e = tid; e < w * w; e += 256) {
+            const int ii = (int)(((unsigned)e * mw) >> 20), jj = e - ii * w;
+            T* dst = a + (s + 1 + ii) * LDS + s + 1 + jj;
+            const T v = fma(-a[(s + 1 + ii) * LDS + s], us[jj], *dst);
+            *dst = v;
+            if (ii == 0 && jj == 0) rp = T(1) / v;  // the next pivot is final now
         }
         __syncthreads();
     }
-    __syncthreads();
-    if (broke) return;
-    for (int e = tid; e < b * b; e += blockDim.x) {
-        const int i = e / b, j = e % b;
-        blk[i * ldm + j] = a[i * LDS + j];
+    if (broke) {
+        if (tid == 0) {
+            atomicMin(&st->info, (int)(k + s + 1));
+            atomicExch(&st->halt, 1);
+        }
+        return;
     }
+    for (int i = tid >> 6; i < b; i += 4)
+        if ((tid & 63) < b) blk[i * ldm + (tid & 63)] = a[i * LDS + (tid & 63)];
 }
 
 // Panel of pivot step k by substitution against the factored pivot block (in shared memory):
@@ -83,6 +92,7 @@ __global__ void __launch_bounds__(256) panel_apply_kernel(int64_t k, int b, int6
     static_assert(PT * 16 == 256, "16 lanes per row or column");
     __shared__ T dd[NB][LDS];
     __shared__ T tile[PT][LDS];  // row tile: tile[r][t]; column tile stored transposed: tile[c][t]
+    __shared__ T rdiag[NB];      // 1 / u_jj, once per CTA (FP64 division is costly on GB300's FP64 pipe)
     if (*(volatile const int*)&st->halt) return;
     const int tid = threadIdx.x;
     const bool is_row = (int)blockIdx.x < row_tiles;
@@ -90,6 +100,8 @@ __global__ void __launch_bounds__(256) panel_apply_kernel(int64_t k, int b, int6
     const int64_t base = k + b + t0;  // first row (row tile) or column (column tile) of this tile
     const int cnt = (int)((rest - t0) < PT ? (rest - t0) : PT);
     for (int e = tid; e < b * b; e += blockDim.x) dd[e / b][e % b] = M[(k + e / b) * ldm + k + e % b];
+    __syncthreads();
+    if (is_row && tid < b) rdiag[tid] = T(1) / dd[tid][tid];
     if (is_row) {
         for (int e = tid; e < PT * NB; e += blockDim.x) {
             const int r = e / NB, t = e % NB;
@@ -106,7 +118,7 @@ __global__ void __launch_bounds__(256) panel_apply_kernel(int64_t k, int b, int6
     T* x = tile[q];
     if (is_row) {
         for (int j = 0; j < b; ++j) {
-            const T xj = x[j] / dd[j][j];
+            const T xj = x[j] * rdiag[j];
             __syncwarp();
             if (lane == 0) x[j] = xj;
             for (int t = j + 1 + lane; t < b; t += 16) x[t] = fma(-xj, dd[j][t], x[t]);
@@ -178,17 +190,10 @@ rmge_status maxabs(int64_t rows, int64_t cols, const T* P, int64_t ldp, bool upp
 template <typename T>
 rmge_status genp_factor(int64_t n, T* M, int64_t ldm, DevState* st, cudaStream_t s) {
     constexpr int PT = 16;
-    const size_t smem = NB * LDS * sizeof(T);
-    // The attribute belongs to the current device's context; setting it is cheap and idempotent.
-    if (cudaFuncSetAttribute(diag_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-        (void)cudaGetLastError();
-        return RMGE_ERR_CUDA;
-    }
     RMGE_TRY(maxabs<T>(n, n, M, ldm, false, &st->maxabs_m, s));
     for (int64_t k = 0; k < n; k += NB) {
         const int b = (int)((n - k) < NB ? (n - k) : NB);
-        diag_factor_kernel<T><<<1, 256, smem, s>>>(k, b, M, ldm, st);
+        diag_factor_kernel<T><<<1, 256, 0, s>>>(k, b, M, ldm, st);
         RMGE_LAUNCH_CHECK();
         const int64_t rest = n - k - b;
         if (rest <= 0) break;
@@ -208,17 +213,11 @@ rmge_status genp_factor(int64_t n, T* M, int64_t ldm, DevState* st, cudaStream_t
 rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const TcUpdate& tc,
                            cudaStream_t s) {
     constexpr int PT = 16;
-    const size_t smem = NB * LDS * sizeof(float);
-    if (cudaFuncSetAttribute(diag_factor_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-        (void)cudaGetLastError();
-        return RMGE_ERR_CUDA;
-    }
     RMGE_TRY(maxabs<float>(n, n, M, ldm, false, &st->maxabs_m, s));
     int64_t step = 0;
     for (int64_t k = 0; k < n; k += NB, ++step) {
         const int b = (int)((n - k) < NB ? (n - k) : NB);
-        diag_factor_kernel<float><<<1, 256, smem, s>>>(k, b, M, ldm, st);
+        diag_factor_kernel<float><<<1, 256, 0, s>>>(k, b, M, ldm, st);
         RMGE_LAUNCH_CHECK();
         const int64_t rest = n - k - b;
         if (rest <= 0) break;
@@ -241,6 +240,34 @@ rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const
                          1.0f, M + (k + b) * ldm + (k + b), ldm, &st->error, &st->halt, mxa, mxb, s));
     }
     RMGE_TRY(maxabs<float>(n, n, M, ldm, true, &st->maxabs_u, s));
+    return RMGE_OK;
+}
+
+// The Schur update E <- E - L21 U12 as an emulated FP64 product.  Column k of L21 carries 1 / u_kk and
+// row k of U12 carries u_kk, so the pair is first balanced by an exact power of two per k (oz_kmax);
+// without it the per-row scaling of L21 and per-column scaling of U12 pair the large column of a small
+// pivot with the large rows of other pivots and the update loses most of its relative accuracy.
+rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s) {
+    constexpr int PT = 16;
+    RMGE_TRY(maxabs<double>(n, n, M, ldm, false, &st->maxabs_m, s));
+    int64_t step = 0;
+    for (int64_t k = 0; k < n; k += NB, ++step) {
+        const int b = (int)((n - k) < NB ? (n - k) : NB);
+        diag_factor_kernel<double><<<1, 256, 0, s>>>(k, b, M, ldm, st);
+        RMGE_LAUNCH_CHECK();
+        const int64_t rest = n - k - b;
+        if (rest <= 0) break;
+        const int tiles = (int)((rest + PT - 1) / PT);
+        panel_apply_kernel<double, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st);
+        RMGE_LAUNCH_CHECK();
+        const double* L21 = M + (k + b) * ldm + k;
+        const double* U12 = M + k * ldm + k + b;
+        unsigned long long* kmA = oz.kmax + 128 * step;
+        RMGE_TRY(oz_kmax(rest, rest, b, L21, ldm, U12, ldm, kmA, kmA + 64, s));
+        RMGE_TRY(oz_gemm(rest, rest, b, kOzSlices, -1.0, L21, ldm, U12, ldm, 1.0, M + (k + b) * ldm + (k + b), ldm,
+                         oz.planesA, oz.planesB, oz.ea, oz.eb, kmA, kmA + 64, &st->error, &st->halt, s));
+    }
+    RMGE_TRY(maxabs<double>(n, n, M, ldm, true, &st->maxabs_u, s));
     return RMGE_OK;
 }
 

@@ -40,18 +40,23 @@ uint32_t tc_idesc(bool bf16);
 
 // oz_gemm.cu: C (FP64) <- beta C + alpha A B with the product emulated on BF16 tensor cores from
 // s base-128 digit planes of A (rows) and B (columns).  planesA/planesB: oz_plane_bytes(M, K, s) and
-// oz_plane_bytes(N, K, s) bytes; ea[M], eb[N] ints of scratch.  *err <- RMGE_ERR_TIMEOUT if a bounded
-// wait expires; nothing happens while *halt != 0 (halt may be NULL).
+// oz_plane_bytes(N, K, s) bytes; ea[M], eb[N] ints of scratch.  kmaxA/kmaxB (both or neither): the
+// per-k maxima from oz_kmax, which balance column k of A against row k of B by an exact power of two.
+// *err <- RMGE_ERR_TIMEOUT if a bounded wait expires; nothing happens while *halt != 0 (halt may be NULL).
 constexpr int kOzSlices = 8;
 size_t oz_plane_bytes(int64_t rows, int64_t k, int s);
+rmge_status oz_kmax(int64_t M, int64_t N, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
+                    unsigned long long* kmaxA, unsigned long long* kmaxB, cudaStream_t st);
 rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* planesA, void* planesB,
-                    int* ea, int* eb, int* err, const int* halt, cudaStream_t st);
+                    int* ea, int* eb, const unsigned long long* kmaxA, const unsigned long long* kmaxB, int* err,
+                    const int* halt, cudaStream_t st);
 struct OzUpdate {
     void* planesA;
     void* planesB;
     int* ea;
     int* eb;
+    unsigned long long* kmax;  // 128 zeroed slots per pivot-block step: column maxima of L21, row maxima of U12
 };
 
 // genp.cu: in-place blocked GENP of an n x n matrix with DevState bookkeeping.
@@ -72,6 +77,9 @@ struct TcUpdate {
 };
 rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const TcUpdate& tc,
                            cudaStream_t s);
+// FP64 working matrix with the Schur-complement updates as balanced FP64 products emulated on the
+// tensor cores (oz_gemm); pivot blocks and panels on the FP64 pipe.
+rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s);
 // growth = max|U| / max|M| and info from the DevState (writes the caller's outputs).
 rmge_status genp_finish(DevState* st, int32_t* info, double* growth, cudaStream_t s);
 template <typename T>

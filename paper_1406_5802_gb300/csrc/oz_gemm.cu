@@ -15,12 +15,16 @@
 // Digit pairs with p + q <= s - 1 are kept.  The first dropped diagonal (p + q = s) is worth about
 // (s + 1) 2^(-7s) of max|A_i.| max|B_.j| per term, so s = 8 (36 digit pairs) matches FP64 rounding.
 //
-// Kernel: one 128 x 128 output tile per CTA, 10 warps.  Warp 8 (one lane) streams 128x64 BF16 tiles
-// of A-digit and B-digit planes by TMA into a 6-stage ring; warp 9 (one lane) issues
+// Kernel: one 128 x 128 output tile per CTA, 18 warps.  Warp 16 (one lane) streams 128x64 BF16 tiles
+// of A-digit and B-digit planes by TMA into a 6-stage ring; warp 17 (one lane) issues
 // tcgen05.mma kind::f16 (M=128, N=128, K=16) into one of two 128-column TMEM accumulators, one
-// (diagonal, K chunk) unit at a time; warps 0-7 drain the other accumulator (tcgen05.ld) into their
-// fixed-point registers while the next unit accumulates.  All waits are bounded.
+// (diagonal, K chunk) unit at a time; warps 0-15 drain the other accumulator (tcgen05.ld, 32 columns
+// each) into their fixed-point registers while the next unit accumulates, then stage the scaled tile in
+// the idle ring and update C one row per warp.  All waits are bounded.
 #include <cuda_bf16.h>
+
+#include <algorithm>
+#include <climits>
 
 #include "tc_common.cuh"
 
@@ -33,10 +37,13 @@ constexpr int OBM = 128, OBN = 128, OBK = 64, OSTAGES = 6;
 constexpr int OA_BYTES = OBM * OBK * 2;
 constexpr int OB_BYTES = OBN * OBK * 2;
 constexpr int OSTAGE_BYTES = OA_BYTES + OB_BYTES;
-constexpr int OTHREADS = 320;
+constexpr int OEPI = 16;                    // epilogue warps: 4 TMEM lane quadrants x 4 column groups of 32
+constexpr int OTHREADS = (OEPI + 2) * 32;   // + the TMA producer warp and the MMA warp
+constexpr int OSTG = OBN + 1;               // row stride (doubles) of the staged output tile
 constexpr int OTMEM = 256;
 constexpr unsigned long long kOzWaitNs = 4000000000ull;
 constexpr size_t kOzSmem = (size_t)OSTAGES * OSTAGE_BYTES + 1024 + 512;
+static_assert((size_t)OBM * OSTG * sizeof(double) <= (size_t)OSTAGES * OSTAGE_BYTES, "staged tile must fit the ring");
 
 struct OzParams {
     int M, N, K, s;
@@ -44,7 +51,9 @@ struct OzParams {
     int Mp, Np;  // rows per digit plane of A, of B
     const int* ea;
     const int* eb;
-    double alpha, beta;
+    double alpha, beta;  // general combine (mode 2): C = beta C + alpha v
+    long long alpha_sign;  // modes 0 and 1: alpha = alpha_sign = +-1 is applied to the fixed-point sum
+    int mode;              // 0: C = alpha A B; 1: C += alpha A B; 2: general alpha, beta
     double* C;
     int64_t ldc;
     int* err;
@@ -56,6 +65,33 @@ struct OzParams {
 __device__ __forceinline__ int diag_kc(int d) {
     constexpr int kc[8] = {1024, 512, 320, 256, 192, 128, 128, 128};
     return kc[d];
+}
+
+// a 2^E rounded to the nearest FP64 value (ties to even), assembled from the IEEE-754 fields with
+// integer operations only: GB300's FP64 pipe retires 2 operations per clock per SM, so the integer
+// -> FP64 conversion and the scaling are kept off it.  Results that would be subnormal or overflow
+// take the FP64 route.
+__device__ __forceinline__ double fixed_to_double(long long a, int E) {
+    if (a == 0) return 0.0;
+    const unsigned long long sgn = a < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long m = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
+    int p = 63 - __clzll((long long)m);  // position of the leading bit
+    unsigned long long q;
+    if (p > 52) {
+        const int r = p - 52;
+        q = m >> r;
+        const unsigned long long rem = m & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+        if (rem > half || (rem == half && (q & 1ull))) ++q;
+        if (q >> 53) {  // the rounding carried into a new leading bit
+            q >>= 1;
+            ++p;
+        }
+    } else {
+        q = m << (52 - p);
+    }
+    const int ex = p + E + 1023;
+    if (ex <= 0 || ex >= 2047) return ldexp((double)a, E);
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)ex << 52) | (q & ((1ull << 52) - 1ull))));
 }
 
 __global__ void __launch_bounds__(OTHREADS, 1)
@@ -83,7 +119,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull + b, 1);
-            mbar_init(tempty + b, 8);
+            mbar_init(tempty + b, OEPI);
         }
         aborted = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -100,7 +136,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
     const uint32_t tmem = *tmem_holder;
     const unsigned long long deadline = now_ns() + kOzWaitNs;
 
-    if (warp == 8) {
+    if (warp == OEPI) {
         if (lane == 0) {  // TMA producer: units (d, chunk), then pairs p + q = d, then 64-deep K blocks
             int it = 0;
             for (int d = 0; d < p.s && !*(volatile int*)&aborted; ++d) {
@@ -128,7 +164,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
             for (int j = it - OSTAGES < 0 ? 0 : it - OSTAGES; j < it; ++j)
                 (void)mbar_wait(full + j % OSTAGES, (uint32_t)((j / OSTAGES) & 1), d2);
         }
-    } else if (warp == 9) {
+    } else if (warp == OEPI + 1) {
         if (lane == 0) {  // MMA issuer: one TMEM accumulator per unit (d, chunk), alternating buffers
             int it = 0, u = 0;
             bool ok = true;
@@ -165,16 +201,22 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
             }
         }
     } else {
-        // epilogue warps 0-7: quadrant (TMEM lanes / tile rows) and column half
-        const int quad = warp & 3, half = warp >> 2;
-        long long acc[64];  // fixed point: units of 2^-F of max|A_i.| max|B_.j|
+        // epilogue warps 0-15: TMEM lane quadrant (tile rows) and group of 32 columns
+        const int quad = warp & 3, cg = warp >> 2;
+        long long acc[32];  // fixed point: units of 2^-F of max|A_i.| max|B_.j|
 #pragma unroll
-        for (int j = 0; j < 64; ++j) acc[j] = 0;
+        for (int j = 0; j < 32; ++j) acc[j] = 0;
         int u = 0;
         bool ok = true;
         for (int d = 0; d < p.s && ok; ++d) {
             const int kc = diag_kc(d);
-            const int sh = p.F - 7 * (d + 2);  // chunk value v weighs 2^-(7(d+2)) = 2^(sh - F)
+            // chunk value v weighs 2^-(7(d+2)) = 2^(sh - F).  v is an integer below 2^24, converted to int32
+            // (the FP32 -> int64 conversion runs on GB300's narrow FP64 pipe; this one does not).
+            // Right shifts (sh < 0) are done exactly in FP32 (a power-of-two scaling of an integer below
+            // 2^24) and rounded to the nearest integer by the conversion; left shifts in 64-bit integers.
+            const int sh = p.F - 7 * (d + 2);
+            const float rscale = __int_as_float((127 + (sh < 0 ? sh : 0)) << 23);
+            const int lsh = sh > 0 ? sh : 0;
             for (int k0 = 0; k0 < p.K; k0 += kc, ++u) {
                 const int buf = u & 1;
                 if (!mbar_wait(tfull + buf, (uint32_t)((u >> 1) & 1), deadline)) {
@@ -184,33 +226,50 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 __syncwarp();
-                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 128 + half * 64);
+                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 128 + cg * 32);
 #pragma unroll
-                for (int cc = 0; cc < 2; ++cc) {
-                    float v[32];
-                    tmem_ld32(taddr + cc * 32, v);
+                for (int h = 0; h < 2; ++h) {  // two 16-column loads keep acc + v within the register budget
+                    float v[16];
+                    tmem_ld16(taddr + h * 16, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const long long t = __float2ll_rn(v[j]);  // exact: |v| < 2^24 is an integer
-                        acc[cc * 32 + j] += (sh >= 0) ? (t << sh) : ((t + (1ll << (-sh - 1))) >> (-sh));
-                    }
+                    for (int j = 0; j < 16; ++j) acc[h * 16 + j] += (long long)__float2int_rn(v[j] * rscale) << lsh;
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tempty + buf);
             }
         }
-        if (!aborted) {
-            const int row = m0 + quad * 32 + lane;
-            if (row < p.M) {
-                const int er = p.ea[row];
+        // The last unit's commit follows every MMA, and every TMA load was consumed by one of them:
+        // the ring is idle, and the scaled tile is staged there (128 x OSTG doubles) for row-wise,
+        // coalesced read-modify-write of C by the 16 epilogue warps.
+        double* stg = reinterpret_cast<double*>(base);
+        if (ok && !*(volatile int*)&aborted) {
+            const int r = quad * 32 + lane;
+            const int er = (m0 + r < p.M) ? p.ea[m0 + r] : 0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int c = cg * 32 + j;
+                const int ec = (n0 + c < p.N) ? p.eb[n0 + c] : 0;
+                stg[r * OSTG + c] = fixed_to_double(p.alpha_sign * acc[j], er + ec - p.F);
+            }
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(OEPI * 32) : "memory");
+        if (!*(volatile int*)&aborted) {
+            for (int r = warp; r < OBM; r += OEPI) {
+                const int row = m0 + r;
+                if (row >= p.M) break;
                 double* crow = p.C + (int64_t)row * p.ldc;
 #pragma unroll
-                for (int j = 0; j < 64; ++j) {
-                    const int col = n0 + half * 64 + j;
+                for (int q = 0; q < OBN / 32; ++q) {
+                    const int c = q * 32 + lane, col = n0 + c;
                     if (col < p.N) {
-                        const double v = ldexp((double)acc[j], er + p.eb[col] - p.F);
-                        crow[col] = (p.beta == 0.0) ? p.alpha * v : fma(p.beta, crow[col], p.alpha * v);
+                        const double v = stg[r * OSTG + c];  // already carries the sign of alpha
+                        if (p.mode == 0)
+                            crow[col] = v;  // alpha = +-1, beta = 0
+                        else if (p.mode == 1)
+                            crow[col] += v;  // alpha = +-1, beta = 1 (one FP64 add)
+                        else
+                            crow[col] = (p.beta == 0.0) ? p.alpha * v : fma(p.beta, crow[col], p.alpha * v);
                     }
                 }
             }
@@ -228,28 +287,100 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
 // planes of rows_p x kp (K-major, zero padded): plane[p][r][k].
 // ---------------------------------------------------------------------------------------------
 
-__device__ __forceinline__ int line_exp(double m) { return (m > 0.0 && isfinite(m)) ? ilogb(m) + 1 : 0; }
+// Exact per-k balancing of a product A B (used for GENP's Schur updates, where column k of L scales
+// like 1 / u_kk and row k of U like u_kk): column k of A is taken as A_.k 2^t_k and row k of B as
+// 2^-t_k B_k., which leaves A B unchanged.  t_k = floor((log2 max|B_k.| - log2 max|A_.k|) / 2) brings
+// both maxima to about their geometric mean, so the per-row / per-column digit scaling below no longer
+// pairs a large column of A with a large row of B.  kmaxA, kmaxB hold the FP64 bit patterns of those
+// maxima; NULL means no balancing.
+__device__ __forceinline__ int bal_shift(const unsigned long long* kmaxA, const unsigned long long* kmaxB, int64_t k) {
+    if (kmaxA == nullptr) return 0;
+    const double a = __longlong_as_double((long long)kmaxA[k]), b = __longlong_as_double((long long)kmaxB[k]);
+    if (!(a > 0.0) || !(b > 0.0) || !isfinite(a) || !isfinite(b)) return 0;
+    return (ilogb(b) - ilogb(a)) >> 1;
+}
 
-// e[r] = smallest integer with max_k |A_rk| < 2^e (0 for an all-zero row): one warp per row.
+// Exponent of one entry, q + 1 for |x| in [2^q, 2^(q+1)), shifted by the balancing; INT_MIN for zero
+// or non-finite entries (which store_digits handles on its own).
+__device__ __forceinline__ int entry_exp(double x, int t) {
+    return (x != 0.0 && isfinite(x)) ? ilogb(x) + 1 + t : INT_MIN;
+}
+
+// e[r] = smallest integer with max_k |A_rk 2^t_k| < 2^e (0 for an all-zero row): one warp per row.
 __global__ void row_exponent_kernel(int64_t rows, int64_t cols, const double* __restrict__ src, int64_t lds,
-                                    int* __restrict__ e) {
+                                    const unsigned long long* __restrict__ kmaxA,
+                                    const unsigned long long* __restrict__ kmaxB, int* __restrict__ e) {
     const int lane = threadIdx.x & 31;
     const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (r >= rows) return;
-    double m = 0.0;
-    for (int64_t k = lane; k < cols; k += 32) m = fmax(m, fabs(src[r * lds + k]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) e[r] = line_exp(m);
+    int m = INT_MIN;
+    for (int64_t k = lane; k < cols; k += 32) m = max(m, entry_exp(src[r * lds + k], bal_shift(kmaxA, kmaxB, k)));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) e[r] = (m == INT_MIN) ? 0 : m;
 }
 
-// e[c] = the same for column c: one thread per column, consecutive threads on consecutive columns.
+// e[c] = the same for column c of B 2^-t_k: 32 columns per block (consecutive threads on consecutive
+// columns), rows split over 8 thread groups and reduced in shared memory.
 __global__ void col_exponent_kernel(int64_t rows, int64_t cols, const double* __restrict__ src, int64_t lds,
-                                    int* __restrict__ e) {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= cols) return;
-    double m = 0.0;
-    for (int64_t k = 0; k < rows; ++k) m = fmax(m, fabs(src[k * lds + c]));
-    e[c] = line_exp(m);
+                                    const unsigned long long* __restrict__ kmaxA,
+                                    const unsigned long long* __restrict__ kmaxB, int* __restrict__ e) {
+    __shared__ int part[8][32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * 32 + tx;
+    int m = INT_MIN;
+    if (c < cols)
+        for (int64_t k = ty; k < rows; k += 8) m = max(m, entry_exp(src[k * lds + c], -bal_shift(kmaxA, kmaxB, k)));
+    part[ty][tx] = m;
+    __syncthreads();
+    if (ty == 0 && c < cols) {
+#pragma unroll
+        for (int g = 1; g < 8; ++g) m = max(m, part[g][tx]);
+        e[c] = (m == INT_MIN) ? 0 : m;
+    }
+}
+
+// kmaxA[k] = max_r |A_rk| (k < K <= 64) and kmaxB[k] = max_c |B_kc| as FP64 bit patterns, by atomicMax
+// into zeroed slots; non-finite entries are skipped.  blockIdx.y = 0: 32 rows of A per block, a warp
+// reading 32 consecutive entries of one row; blockIdx.y = 1: 64 columns of B per block, a warp per row.
+constexpr int kKmaxRows = 32, kKmaxCols = 64;
+__global__ void kmax_kernel(int64_t M, int64_t N, int K, const double* __restrict__ A, int64_t lda,
+                            const double* __restrict__ B, int64_t ldb, unsigned long long* __restrict__ kmaxA,
+                            unsigned long long* __restrict__ kmaxB) {
+    __shared__ unsigned long long part[64];
+    if (blockIdx.y == 0) {
+        if (threadIdx.x < 64) part[threadIdx.x] = 0ull;
+        __syncthreads();
+        const int c = threadIdx.x & 63, r = threadIdx.x >> 6;
+        const int64_t r0 = (int64_t)blockIdx.x * kKmaxRows;
+        double m = 0.0;
+        if (c < K)
+#pragma unroll
+            for (int i = r; i < kKmaxRows; i += 4) {
+                if (r0 + i >= M) break;
+                const double x = fabs(A[(r0 + i) * lda + c]);
+                if (isfinite(x)) m = fmax(m, x);
+            }
+        if (m > 0.0) atomicMax(&part[c], (unsigned long long)__double_as_longlong(m));
+        __syncthreads();
+        if (threadIdx.x < K && part[threadIdx.x] != 0ull) atomicMax(&kmaxA[threadIdx.x], part[threadIdx.x]);
+    } else {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int64_t c0 = (int64_t)blockIdx.x * kKmaxCols;
+        if (c0 >= N) return;
+        for (int k = warp; k < K; k += 8) {
+            double m = 0.0;
+#pragma unroll
+            for (int h = 0; h < kKmaxCols / 32; ++h) {
+                const int64_t c = c0 + h * 32 + lane;
+                if (c < N) {
+                    const double x = fabs(B[(int64_t)k * ldb + c]);
+                    if (isfinite(x)) m = fmax(m, x);
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0 && m > 0.0) atomicMax(&kmaxB[k], (unsigned long long)__double_as_longlong(m));
+        }
+    }
 }
 
 // The 7s-bit magnitude |x| 2^(7s), x = v 2^-e, by integer shifts of the FP64 significand.
@@ -284,22 +415,24 @@ __device__ __forceinline__ void store_digits(double v, int er, int s, __nv_bfloa
     }
 }
 
-// Row digits: plane[q][r][k] = digit q of A_rk (rows_p x kp per plane, zero padded).
+// Row digits: plane[q][r][k] = digit q of A_rk 2^t_k (rows_p x kp per plane, zero padded).
 __global__ void row_digits_kernel(int64_t rows, int64_t cols, const double* __restrict__ src, int64_t lds,
-                                  const int* __restrict__ e, int s, int64_t rows_p, int64_t kp,
+                                  const int* __restrict__ e, const unsigned long long* __restrict__ kmaxA,
+                                  const unsigned long long* __restrict__ kmaxB, int s, int64_t rows_p, int64_t kp,
                                   __nv_bfloat16* __restrict__ planes) {
     const int64_t total = rows_p * kp;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = idx / kp, k = idx % kp;
         const bool in = r < rows && k < cols;
-        store_digits(in ? src[r * lds + k] : 0.0, in ? e[r] : 0, s, planes + idx, total);
+        store_digits(in ? src[r * lds + k] : 0.0, in ? e[r] - bal_shift(kmaxA, kmaxB, k) : 0, s, planes + idx, total);
     }
 }
 
-// Column digits, transposed through shared memory: plane[q][c][k] = digit q of B_kc.
+// Column digits, transposed through shared memory: plane[q][c][k] = digit q of 2^-t_k B_kc.
 __global__ void col_digits_kernel(int64_t rows, int64_t cols, const double* __restrict__ src, int64_t lds,
-                                  const int* __restrict__ e, int s, int64_t cols_p, int64_t kp,
+                                  const int* __restrict__ e, const unsigned long long* __restrict__ kmaxA,
+                                  const unsigned long long* __restrict__ kmaxB, int s, int64_t cols_p, int64_t kp,
                                   __nv_bfloat16* __restrict__ planes) {
     __shared__ double t[32][33];
     const int64_t k0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
@@ -312,7 +445,9 @@ __global__ void col_digits_kernel(int64_t rows, int64_t cols, const double* __re
     const int64_t total = cols_p * kp;
     for (int i = ty; i < 32; i += 8) {
         const int64_t c = c0 + i, k = k0 + tx;  // write along k
-        if (c < cols_p && k < kp) store_digits(t[tx][i], c < cols ? e[c] : 0, s, planes + c * kp + k, total);
+        if (c < cols_p && k < kp)
+            store_digits(t[tx][i], (c < cols && k < rows) ? e[c] + bal_shift(kmaxA, kmaxB, k) : 0, s, planes + c * kp + k,
+                         total);
     }
 }
 
@@ -329,22 +464,36 @@ size_t oz_plane_bytes(int64_t rows, int64_t k, int s) {
     return (size_t)s * (size_t)rp * (size_t)kp * 2;
 }
 
+rmge_status oz_kmax(int64_t M, int64_t N, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
+                    unsigned long long* kmaxA, unsigned long long* kmaxB, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || K <= 0) return RMGE_OK;
+    if (K > 64) return RMGE_ERR_INVALID_ARG;
+    const int64_t gx = std::max((M + kKmaxRows - 1) / kKmaxRows, (N + kKmaxCols - 1) / kKmaxCols);
+    if (gx > 65535 * 64) return RMGE_ERR_INVALID_ARG;
+    kmax_kernel<<<dim3((unsigned)gx, 2), 256, 0, st>>>(M, N, K, A, lda, B, ldb, kmaxA, kmaxB);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
 rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* planesA, void* planesB,
-                    int* ea, int* eb, int* err, const int* halt, cudaStream_t st) {
+                    int* ea, int* eb, const unsigned long long* kmaxA, const unsigned long long* kmaxB, int* err,
+                    const int* halt, cudaStream_t st) {
+    if ((kmaxA == nullptr) != (kmaxB == nullptr)) return RMGE_ERR_INVALID_ARG;
     if (M <= 0 || N <= 0) return RMGE_OK;
     if (K <= 0 || s < 1 || s > 8 || M > INT32_MAX / 16 || N > INT32_MAX / 16 || K > INT32_MAX / 2)
         return RMGE_ERR_INVALID_ARG;
     const int64_t Mp = (M + 127) / 128 * 128, Np = (N + 127) / 128 * 128, Kp = (K + 63) / 64 * 64;
     __nv_bfloat16* pa = static_cast<__nv_bfloat16*>(planesA);
     __nv_bfloat16* pb = static_cast<__nv_bfloat16*>(planesB);
-    row_exponent_kernel<<<(unsigned)((M * 32 + 255) / 256), 256, 0, st>>>(M, K, A, lda, ea);
+    row_exponent_kernel<<<(unsigned)((M * 32 + 255) / 256), 256, 0, st>>>(M, K, A, lda, kmaxA, kmaxB, ea);
     RMGE_LAUNCH_CHECK();
-    col_exponent_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(K, N, B, ldb, eb);
+    col_exponent_kernel<<<(unsigned)((N + 31) / 32), 256, 0, st>>>(K, N, B, ldb, kmaxA, kmaxB, eb);
     RMGE_LAUNCH_CHECK();
-    row_digits_kernel<<<grid_for(Mp * Kp), 256, 0, st>>>(M, K, A, lda, ea, s, Mp, Kp, pa);
+    row_digits_kernel<<<grid_for(Mp * Kp), 256, 0, st>>>(M, K, A, lda, ea, kmaxA, kmaxB, s, Mp, Kp, pa);
     RMGE_LAUNCH_CHECK();
-    col_digits_kernel<<<dim3((unsigned)(Np / 32), (unsigned)(Kp / 32)), 256, 0, st>>>(K, N, B, ldb, eb, s, Np, Kp, pb);
+    col_digits_kernel<<<dim3((unsigned)(Np / 32), (unsigned)(Kp / 32)), 256, 0, st>>>(K, N, B, ldb, eb, kmaxA, kmaxB,
+                                                                                      s, Np, Kp, pb);
     RMGE_LAUNCH_CHECK();
 
     CUtensorMap ta, tb;
@@ -363,7 +512,10 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
     prm.Np = (int)Np;
     prm.ea = ea;
     prm.eb = eb;
-    prm.alpha = alpha;
+    const bool unit_alpha = (alpha == 1.0 || alpha == -1.0);
+    prm.mode = (unit_alpha && beta == 0.0) ? 0 : (unit_alpha && beta == 1.0) ? 1 : 2;
+    prm.alpha_sign = (prm.mode < 2 && alpha < 0.0) ? -1 : 1;
+    prm.alpha = (prm.mode < 2) ? 1.0 : alpha;
     prm.beta = beta;
     prm.C = C;
     prm.ldc = ldc;
