@@ -61,10 +61,25 @@ struct OzParams {
 };
 
 // Depth of one exact chunk on diagonal d = p + q: the (d + 1) digit pairs of the diagonal share one
-// TMEM accumulator, so (d + 1) 127^2 kc must stay below 2^24 (kc a multiple of the 64-deep K block).
+// TMEM accumulator, so (d + 1) 127^2 kc must stay below 2^24; kc is a multiple of the 64-deep K block
+// and divides the 1024-deep super-chunk.  The K loop runs over super-chunks and, inside each, over all
+// diagonals, so the digit planes of one super-chunk are re-read for every diagonal while they are still
+// in L2 (a diagonal-major order re-fetched plane q from DRAM for every diagonal d >= q).
+constexpr int kSuper = 1024;
 __device__ __forceinline__ int diag_kc(int d) {
-    constexpr int kc[8] = {1024, 512, 320, 256, 192, 128, 128, 128};
+    constexpr int kc[8] = {1024, 512, 256, 256, 128, 128, 128, 128};
     return kc[d];
+}
+
+// Grouped tile order: bands of kGroupM row blocks, column-major inside a band, so the CTAs resident at
+// one time cover a roughly square patch of C (fewer distinct A and B panels per wave).
+constexpr int kGroupM = 12;
+__device__ __forceinline__ void tile_of(int t, int tm, int tn, int& m, int& n) {
+    const int per = kGroupM * tn, g = t / per, first = g * kGroupM;
+    const int gm = (tm - first < kGroupM) ? tm - first : kGroupM;
+    const int tl = t - g * per;
+    m = first + tl % gm;
+    n = tl / gm;
 }
 
 // a 2^E rounded to the nearest FP64 value (ties to even), assembled from the IEEE-754 fields with
@@ -110,7 +125,9 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
     __shared__ int aborted;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * OBM, n0 = blockIdx.x * OBN;
+    int tmb, tnb;
+    tile_of((int)blockIdx.x, p.Mp / OBM, p.Np / OBN, tmb, tnb);
+    const int m0 = tmb * OBM, n0 = tnb * OBN;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OSTAGES; ++s) {
@@ -139,10 +156,11 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
     if (warp == OEPI) {
         if (lane == 0) {  // TMA producer: units (d, chunk), then pairs p + q = d, then 64-deep K blocks
             int it = 0;
+            for (int sc = 0; sc < p.K && !*(volatile int*)&aborted; sc += kSuper)
             for (int d = 0; d < p.s && !*(volatile int*)&aborted; ++d) {
-                const int kc = diag_kc(d);
-                for (int k0 = 0; k0 < p.K && !*(volatile int*)&aborted; k0 += kc) {
-                    const int nkb = ((p.K - k0 < kc ? p.K - k0 : kc) + OBK - 1) / OBK;
+                const int kc = diag_kc(d), se = (p.K - sc < kSuper) ? p.K : sc + kSuper;
+                for (int k0 = sc; k0 < se && !*(volatile int*)&aborted; k0 += kc) {
+                    const int nkb = ((se - k0 < kc ? se - k0 : kc) + OBK - 1) / OBK;
                     for (int pa = 0; pa <= d; ++pa) {
                         const int ya = pa * p.Mp + m0, yb = (d - pa) * p.Np + n0;
                         for (int kb = 0; kb < nkb; ++kb, ++it) {
@@ -168,9 +186,10 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
         if (lane == 0) {  // MMA issuer: one TMEM accumulator per unit (d, chunk), alternating buffers
             int it = 0, u = 0;
             bool ok = true;
+            for (int sc = 0; sc < p.K && ok; sc += kSuper)
             for (int d = 0; d < p.s && ok; ++d) {
-                const int kc = diag_kc(d);
-                for (int k0 = 0; k0 < p.K && ok; k0 += kc, ++u) {
+                const int kc = diag_kc(d), se = (p.K - sc < kSuper) ? p.K : sc + kSuper;
+                for (int k0 = sc; k0 < se && ok; k0 += kc, ++u) {
                     const int buf = u & 1;
                     if (!mbar_wait(tempty + buf, (uint32_t)(((u >> 1) & 1) ^ 1), deadline)) {
                         atomicExch(&aborted, 1);
@@ -178,7 +197,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const int nkb = ((p.K - k0 < kc ? p.K - k0 : kc) + OBK - 1) / OBK;
+                    const int nkb = ((se - k0 < kc ? se - k0 : kc) + OBK - 1) / OBK;
                     for (int pa = 0; pa <= d && ok; ++pa) {
                         for (int kb = 0; kb < nkb; ++kb, ++it) {
                             const int st = it % OSTAGES;
@@ -208,8 +227,9 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
         for (int j = 0; j < 32; ++j) acc[j] = 0;
         int u = 0;
         bool ok = true;
+        for (int sc = 0; sc < p.K && ok; sc += kSuper)
         for (int d = 0; d < p.s && ok; ++d) {
-            const int kc = diag_kc(d);
+            const int kc = diag_kc(d), se = (p.K - sc < kSuper) ? p.K : sc + kSuper;
             // chunk value v weighs 2^-(7(d+2)) = 2^(sh - F).  v is an integer below 2^24, converted to int32
             // (the FP32 -> int64 conversion runs on GB300's narrow FP64 pipe; this one does not).
             // Right shifts (sh < 0) are done exactly in FP32 (a power-of-two scaling of an integer below
@@ -217,7 +237,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
             const int sh = p.F - 7 * (d + 2);
             const float rscale = __int_as_float((127 + (sh < 0 ? sh : 0)) << 23);
             const int lsh = sh > 0 ? sh : 0;
-            for (int k0 = 0; k0 < p.K; k0 += kc, ++u) {
+            for (int k0 = sc; k0 < se; k0 += kc, ++u) {
                 const int buf = u & 1;
                 if (!mbar_wait(tfull + buf, (uint32_t)((u >> 1) & 1), deadline)) {
                     atomicExch(&aborted, 1);
@@ -280,6 +300,267 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
     if (aborted && threadIdx.x == 0 && p.err != nullptr) atomicExch(p.err, (int)RMGE_ERR_TIMEOUT);
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OTMEM) : "memory");
+}
+
+// ---------------------------------------------------------------------------------------------
+// Products with K <= 64 (GENP's Schur updates: one 64-deep K block).  A persistent CTA walks its
+// share of 128 x 64 output tiles in row-major order, so the 8 A digit planes of a row block (128 KB)
+// are loaded once and stay in shared memory; the B digit planes of each tile stream through a 4-stage
+// ring.  The 36 digit pairs run in two passes of four diagonals (d = 0-3, then 4-7), each diagonal in
+// its own 64-column TMEM accumulator; the two passes use the two halves of TMEM, so one pass's MMAs
+// overlap the drain of the other and the tile's final store.  Per tile the TMA moves 12 B planes (96 KB)
+// instead of 36 A and 36 B tiles.  (d + 1) 127^2 64 < 2^24 keeps every accumulator exact.
+// ---------------------------------------------------------------------------------------------
+constexpr int UBM = 128, UBN = 64;
+constexpr int UA_PLANE = UBM * OBK * 2;  // 16 KB
+constexpr int UB_PLANE = UBN * OBK * 2;  // 8 KB
+constexpr int URING = 4;
+constexpr size_t kUpdSmem = 1024 + (size_t)8 * UA_PLANE + (size_t)URING * UB_PLANE + (size_t)UBM * UBN * 8 + 256;
+static_assert(kUpdSmem <= 232448, "update kernel shared memory");
+
+struct UpdParams {
+    int M, N;            // output rows, columns
+    int F;               // fractional bits of the fixed-point accumulator
+    int Mp, Np;          // rows per digit plane of A, of B
+    int tiles_n, tiles;  // column tiles, all tiles
+    const int* ea;
+    const int* eb;
+    long long alpha_sign;
+    int mode;
+    double alpha, beta;
+    double* C;
+    int64_t ldc;
+    int* err;
+    const int* halt;
+};
+
+// Pass P streams B planes q = 0 .. upd_nq(P)-1 and pairs each with the A planes p in [upd_p0, upd_p1],
+// so that p + q covers the diagonals 4P .. 4P + 3; q = 0 opens every diagonal of the pass.
+__device__ __forceinline__ int upd_nq(int P) { return P == 0 ? 4 : 8; }
+__device__ __forceinline__ int upd_p0(int P, int q) { return P == 0 ? 0 : (q < 4 ? 4 - q : 0); }
+__device__ __forceinline__ int upd_p1(int P, int q) { return P == 0 ? 3 - q : 7 - q; }
+
+__global__ void __launch_bounds__(OTHREADS, 1)
+oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, UpdParams p,
+                 uint32_t idesc) {
+    if (p.halt != nullptr && *(volatile const int*)p.halt != 0) return;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = base;
+    uint8_t* sB = sA + 8 * UA_PLANE;
+    double* stg = reinterpret_cast<double*>(sB + URING * UB_PLANE);  // 128 x 64, columns XOR-swizzled by row
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(stg + UBM * UBN);
+    uint64_t* doneA = fullA + 1;   // the MMAs reading the resident A planes have completed
+    uint64_t* mmaEnd = fullA + 2;  // every MMA of the CTA has completed
+    uint64_t* fullB = fullA + 3;
+    uint64_t* emptyB = fullB + URING;
+    uint64_t* tfull = emptyB + URING;  // [2]
+    uint64_t* tempty = tfull + 2;      // [2]
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tempty + 2);
+    __shared__ int aborted;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t0 = (int)((long long)blockIdx.x * p.tiles / gridDim.x);
+    const int t1 = (int)((long long)(blockIdx.x + 1) * p.tiles / gridDim.x);
+
+    if (threadIdx.x == 0) {
+        mbar_init(fullA, 1);
+        mbar_init(doneA, 1);
+        mbar_init(mmaEnd, 1);
+        for (int i = 0; i < URING; ++i) {
+            mbar_init(fullB + i, 1);
+            mbar_init(emptyB + i, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull + b, 1);
+            mbar_init(tempty + b, OEPI);
+        }
+        aborted = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_holder;
+    const unsigned long long deadline = now_ns() + kOzWaitNs;
+
+    if (warp == OEPI) {
+        if (lane == 0) {  // TMA producer
+            int it = 0, na = 0, cur = -1;
+            bool ok = true;
+            for (int t = t0; t < t1 && ok; ++t) {
+                const int mb = t / p.tiles_n, nb = t % p.tiles_n;
+                if (mb != cur) {
+                    if (na > 0 && !mbar_wait(doneA, (uint32_t)((na - 1) & 1), deadline)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(fullA, 8 * UA_PLANE);
+                    for (int pl = 0; pl < 8; ++pl) tma_load_2d(sA + pl * UA_PLANE, &tA, 0, pl * p.Mp + mb * UBM, fullA);
+                    ++na;
+                    cur = mb;
+                }
+                for (int P = 0; P < 2 && ok; ++P)
+                    for (int q = 0; q < upd_nq(P); ++q, ++it) {
+                        const int st = it % URING;
+                        if (!mbar_wait(emptyB + st, (uint32_t)(((it / URING) & 1) ^ 1), deadline)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(fullB + st, UB_PLANE);
+                        tma_load_2d(sB + st * UB_PLANE, &tB, 0, q * p.Np + nb * UBN, fullB + st);
+                    }
+            }
+            if (!ok) atomicExch(&aborted, 1);
+            // the copies issued last must land before the CTA can leave
+            const unsigned long long d2 = now_ns() + kOzWaitNs;
+            for (int j = it - URING < 0 ? 0 : it - URING; j < it; ++j)
+                (void)mbar_wait(fullB + j % URING, (uint32_t)((j / URING) & 1), d2);
+            if (na > 0) (void)mbar_wait(fullA, (uint32_t)((na - 1) & 1), d2);
+        }
+    } else if (warp == OEPI + 1) {
+        if (lane == 0) {  // MMA issuer
+            int it = 0, u = 0, na = 0, cur = -1;
+            bool ok = true;
+            for (int t = t0; t < t1 && ok; ++t) {
+                const int mb = t / p.tiles_n;
+                if (mb != cur) {
+                    if (!mbar_wait(fullA, (uint32_t)(na & 1), deadline)) {
+                        ok = false;
+                        break;
+                    }
+                    ++na;
+                    cur = mb;
+                }
+                for (int P = 0; P < 2 && ok; ++P, ++u) {
+                    const int bank = u & 1;
+                    if (!mbar_wait(tempty + bank, (uint32_t)(((u >> 1) & 1) ^ 1), deadline)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    for (int q = 0; q < upd_nq(P); ++q, ++it) {
+                        const int st = it % URING;
+                        if (!mbar_wait(fullB + st, (uint32_t)((it / URING) & 1), deadline)) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t b0 = smem_u32(sB + st * UB_PLANE);
+                        for (int pa = upd_p0(P, q); pa <= upd_p1(P, q); ++pa) {
+                            const uint32_t a0 = smem_u32(sA + pa * UA_PLANE);
+                            const uint32_t dcol = tmem + (uint32_t)(bank * 256 + (pa + q - 4 * P) * UBN);
+#pragma unroll
+                            for (int kk = 0; kk < OBK / 16; ++kk)
+                                mma_f16(dcol, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
+                                        (q > 0 || kk > 0) ? 1u : 0u);
+                        }
+                        mma_commit(emptyB + st);
+                    }
+                    if (ok) mma_commit(tfull + bank);
+                }
+                if (ok && (t + 1 == t1 || (t + 1) / p.tiles_n != mb)) mma_commit(doneA);
+            }
+            if (!ok) atomicExch(&aborted, 1);
+            mma_commit(mmaEnd);  // arrives once every MMA issued above has completed
+            (void)mbar_wait(mmaEnd, 0u, now_ns() + kOzWaitNs);
+        }
+    } else {
+        // epilogue warps 0-15: TMEM lane quadrant (tile rows) and group of 16 columns.  Every warp runs
+        // every tile and both named barriers, also after a timeout (expired waits return at once).
+        const int quad = warp & 3, cg = warp >> 2;
+        const int r = quad * 32 + lane;
+        int u = 0;
+        bool ok = true;
+        for (int t = t0; t < t1; ++t) {
+            const int mb = t / p.tiles_n, nb = t % p.tiles_n;
+            long long acc[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = 0;
+            for (int P = 0; P < 2; ++P, ++u) {
+                const int bank = u & 1;
+                if (!mbar_wait(tfull + bank, (uint32_t)((u >> 1) & 1), deadline)) {
+                    atomicExch(&aborted, 1);
+                    ok = false;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (ok) {
+#pragma unroll
+                    for (int sl = 0; sl < 4; ++sl) {
+                        const int sh = p.F - 7 * (4 * P + sl + 2);
+                        const float rscale = __int_as_float((127 + (sh < 0 ? sh : 0)) << 23);
+                        const int lsh = sh > 0 ? sh : 0;
+                        float v[16];
+                        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(bank * 256 + sl * UBN + cg * 16), v);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) acc[j] += (long long)__float2int_rn(v[j] * rscale) << lsh;
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty + bank);
+            }
+            if (ok) {
+                const int row = mb * UBM + r;
+                const int er = (row < p.M) ? p.ea[row] : 0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int c = cg * 16 + j, col = nb * UBN + c;
+                    const int ec = (col < p.N) ? p.eb[col] : 0;
+                    stg[r * UBN + (c ^ (r & 15))] = fixed_to_double(p.alpha_sign * acc[j], er + ec - p.F);
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(OEPI * 32) : "memory");
+            if (!*(volatile int*)&aborted) {
+                // rows warp + 16 i in two groups of four rows: the 8 loads of C of a group are issued before
+                // its first add (one memory latency per group instead of one per row)
+                constexpr int NR = UBM / OEPI, NG = 4, NH = UBN / 32;
+                const bool need_c = p.mode != 0 && p.beta != 0.0;
+#pragma unroll
+                for (int g0 = 0; g0 < NR; g0 += NG) {
+                    double cv[NG][NH];
+#pragma unroll
+                    for (int i = 0; i < NG; ++i)
+#pragma unroll
+                        for (int h = 0; h < NH; ++h) {
+                            const int row = mb * UBM + warp + OEPI * (g0 + i), col = nb * UBN + h * 32 + lane;
+                            cv[i][h] = (need_c && row < p.M && col < p.N) ? p.C[(int64_t)row * p.ldc + col] : 0.0;
+                        }
+#pragma unroll
+                    for (int i = 0; i < NG; ++i)
+#pragma unroll
+                        for (int h = 0; h < NH; ++h) {
+                            const int rr = warp + OEPI * (g0 + i), c = h * 32 + lane;
+                            const int row = mb * UBM + rr, col = nb * UBN + c;
+                            if (row < p.M && col < p.N) {
+                                const double v = stg[rr * UBN + (c ^ (rr & 15))];
+                                double out;
+                                if (p.mode == 0)
+                                    out = v;
+                                else if (p.mode == 1)
+                                    out = cv[i][h] + v;
+                                else
+                                    out = (p.beta == 0.0) ? p.alpha * v : fma(p.beta, cv[i][h], p.alpha * v);
+                                p.C[(int64_t)row * p.ldc + col] = out;
+                            }
+                        }
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(OEPI * 32) : "memory");  // the staging area is reused
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (aborted && threadIdx.x == 0 && p.err != nullptr) atomicExch(p.err, (int)RMGE_ERR_TIMEOUT);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -451,10 +732,81 @@ __global__ void col_digits_kernel(int64_t rows, int64_t cols, const double* __re
     }
 }
 
+// K <= 64 (one K block): the exponent and the digits of a row in one pass, one warp per padded row
+// (lanes hold k = lane and lane + 32).
+__global__ void row_prep64_kernel(int64_t rows, int cols, const double* __restrict__ src, int64_t lds,
+                                  const unsigned long long* __restrict__ kmaxA,
+                                  const unsigned long long* __restrict__ kmaxB, int s, int64_t rows_p,
+                                  int* __restrict__ e, __nv_bfloat16* __restrict__ planes) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= rows_p) return;
+    const bool live = r < rows;
+    const int k0 = lane, k1 = lane + 32;
+    const double v0 = (live && k0 < cols) ? src[r * lds + k0] : 0.0;
+    const double v1 = (live && k1 < cols) ? src[r * lds + k1] : 0.0;
+    const int t0 = (k0 < cols) ? bal_shift(kmaxA, kmaxB, k0) : 0;
+    const int t1 = (k1 < cols) ? bal_shift(kmaxA, kmaxB, k1) : 0;
+    int m = max(entry_exp(v0, t0), entry_exp(v1, t1));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int er = (m == INT_MIN) ? 0 : m;
+    if (lane == 0 && live) e[r] = er;
+    const int64_t total = rows_p * 64;
+    store_digits(v0, er - t0, s, planes + r * 64 + k0, total);
+    store_digits(v1, er - t1, s, planes + r * 64 + k1, total);
+}
+
+// K <= 64: the exponent and the (transposed) digits of 32 columns per block; 256 threads = 32 columns x
+// 8 row groups for the exponent, then consecutive threads along k for the digit stores.
+__global__ void col_prep64_kernel(int rows, int64_t cols, const double* __restrict__ src, int64_t lds,
+                                  const unsigned long long* __restrict__ kmaxA,
+                                  const unsigned long long* __restrict__ kmaxB, int s, int64_t cols_p,
+                                  int* __restrict__ e, __nv_bfloat16* __restrict__ planes) {
+    __shared__ double t[64][33];
+    __shared__ int part[8][32];
+    __shared__ int tk[64];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t c0 = (int64_t)blockIdx.x * 32, c = c0 + tx;
+    if (threadIdx.x < 64) tk[threadIdx.x] = ((int)threadIdx.x < rows) ? bal_shift(kmaxA, kmaxB, threadIdx.x) : 0;
+    for (int i = ty; i < 64; i += 8) t[i][tx] = (i < rows && c < cols) ? src[(int64_t)i * lds + c] : 0.0;
+    __syncthreads();
+    int m = INT_MIN;
+    for (int i = ty; i < rows; i += 8) m = max(m, entry_exp(t[i][tx], -tk[i]));
+    part[ty][tx] = m;
+    __syncthreads();
+    if (ty == 0) {
+#pragma unroll
+        for (int g = 1; g < 8; ++g) m = max(m, part[g][tx]);
+        part[0][tx] = (m == INT_MIN) ? 0 : m;
+        if (c < cols) e[c] = part[0][tx];
+    }
+    __syncthreads();
+    const int64_t total = cols_p * 64;
+    for (int idx = threadIdx.x; idx < 32 * 64; idx += 256) {
+        const int cl = idx >> 6, k = idx & 63;
+        if (c0 + cl < cols_p)
+            store_digits(t[k][cl], (c0 + cl < cols && k < rows) ? part[0][cl] + tk[k] : 0, s,
+                         planes + (c0 + cl) * 64 + k, total);
+    }
+}
+
 unsigned grid_for(int64_t work) {
     int64_t g = (work + 255) / 256;
     if (g > 152 * 16) g = 152 * 16;
     return (unsigned)(g < 1 ? 1 : g);
+}
+
+// Multiprocessors of the current device (persistent grids), cached per device.
+int sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cached[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+        cached[dev] = v;
+    }
+    return cached[dev];
 }
 
 }  // namespace
@@ -486,15 +838,65 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
     const int64_t Mp = (M + 127) / 128 * 128, Np = (N + 127) / 128 * 128, Kp = (K + 63) / 64 * 64;
     __nv_bfloat16* pa = static_cast<__nv_bfloat16*>(planesA);
     __nv_bfloat16* pb = static_cast<__nv_bfloat16*>(planesB);
-    row_exponent_kernel<<<(unsigned)((M * 32 + 255) / 256), 256, 0, st>>>(M, K, A, lda, kmaxA, kmaxB, ea);
-    RMGE_LAUNCH_CHECK();
-    col_exponent_kernel<<<(unsigned)((N + 31) / 32), 256, 0, st>>>(K, N, B, ldb, kmaxA, kmaxB, eb);
-    RMGE_LAUNCH_CHECK();
-    row_digits_kernel<<<grid_for(Mp * Kp), 256, 0, st>>>(M, K, A, lda, ea, kmaxA, kmaxB, s, Mp, Kp, pa);
-    RMGE_LAUNCH_CHECK();
-    col_digits_kernel<<<dim3((unsigned)(Np / 32), (unsigned)(Kp / 32)), 256, 0, st>>>(K, N, B, ldb, eb, kmaxA, kmaxB,
-                                                                                      s, Np, Kp, pb);
-    RMGE_LAUNCH_CHECK();
+    if (Kp == OBK) {
+        row_prep64_kernel<<<(unsigned)((Mp * 32 + 255) / 256), 256, 0, st>>>(M, (int)K, A, lda, kmaxA, kmaxB, s, Mp, ea,
+                                                                          pa);
+        RMGE_LAUNCH_CHECK();
+        col_prep64_kernel<<<(unsigned)(Np / 32), 256, 0, st>>>((int)K, N, B, ldb, kmaxA, kmaxB, s, Np, eb, pb);
+        RMGE_LAUNCH_CHECK();
+    } else {
+        row_exponent_kernel<<<(unsigned)((M * 32 + 255) / 256), 256, 0, st>>>(M, K, A, lda, kmaxA, kmaxB, ea);
+        RMGE_LAUNCH_CHECK();
+        col_exponent_kernel<<<(unsigned)((N + 31) / 32), 256, 0, st>>>(K, N, B, ldb, kmaxA, kmaxB, eb);
+        RMGE_LAUNCH_CHECK();
+        row_digits_kernel<<<grid_for(Mp * Kp), 256, 0, st>>>(M, K, A, lda, ea, kmaxA, kmaxB, s, Mp, Kp, pa);
+        RMGE_LAUNCH_CHECK();
+        col_digits_kernel<<<dim3((unsigned)(Np / 32), (unsigned)(Kp / 32)), 256, 0, st>>>(K, N, B, ldb, eb, kmaxA,
+                                                                                          kmaxB, s, Np, Kp, pb);
+        RMGE_LAUNCH_CHECK();
+    }
+
+    const bool unit_alpha = (alpha == 1.0 || alpha == -1.0);
+    const int mode = (unit_alpha && beta == 0.0) ? 0 : (unit_alpha && beta == 1.0) ? 1 : 2;
+    const long long alpha_sign = (mode < 2 && alpha < 0.0) ? -1 : 1;
+    const double alpha_g = (mode < 2) ? 1.0 : alpha;
+
+    if (Kp == OBK && s == 8) {  // one K block: the persistent update kernel
+        CUtensorMap ta, tb;
+        if (!tc_make_map(&ta, pa, true, (int64_t)s * Mp, Kp, Kp, UBM) ||
+            !tc_make_map(&tb, pb, true, (int64_t)s * Np, Kp, Kp, UBN))
+            return RMGE_ERR_CUDA;
+        UpdParams u{};
+        u.M = (int)M;
+        u.N = (int)N;
+        u.F = 51;  // one chunk per diagonal: |acc| < 2^(F + 10)
+        u.Mp = (int)Mp;
+        u.Np = (int)Np;
+        u.tiles_n = (int)((N + UBN - 1) / UBN);
+        u.tiles = (int)((M + UBM - 1) / UBM) * u.tiles_n;
+        u.ea = ea;
+        u.eb = eb;
+        u.alpha_sign = alpha_sign;
+        u.mode = mode;
+        u.alpha = alpha_g;
+        u.beta = beta;
+        u.C = C;
+        u.ldc = ldc;
+        u.err = err;
+        u.halt = halt;
+        // idesc: FP32 accumulate, BF16 A and B, both K-major, N = 64, M = 128
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UBN >> 3) << 17) |
+                               ((uint32_t)(UBM >> 4) << 24);
+        if (cudaFuncSetAttribute(oz_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpdSmem) !=
+            cudaSuccess) {
+            (void)cudaGetLastError();
+            return RMGE_ERR_CUDA;
+        }
+        const int grid = u.tiles < sm_count() ? u.tiles : sm_count();
+        oz_update_kernel<<<grid, OTHREADS, kUpdSmem, st>>>(ta, tb, u, idesc);
+        RMGE_LAUNCH_CHECK();
+        return RMGE_OK;
+    }
 
     CUtensorMap ta, tb;
     if (!tc_make_map(&ta, pa, true, (int64_t)s * Mp, Kp, Kp, OBM) || !tc_make_map(&tb, pb, true, (int64_t)s * Np, Kp, Kp, OBN))
@@ -512,10 +914,9 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
     prm.Np = (int)Np;
     prm.ea = ea;
     prm.eb = eb;
-    const bool unit_alpha = (alpha == 1.0 || alpha == -1.0);
-    prm.mode = (unit_alpha && beta == 0.0) ? 0 : (unit_alpha && beta == 1.0) ? 1 : 2;
-    prm.alpha_sign = (prm.mode < 2 && alpha < 0.0) ? -1 : 1;
-    prm.alpha = (prm.mode < 2) ? 1.0 : alpha;
+    prm.mode = mode;
+    prm.alpha_sign = alpha_sign;
+    prm.alpha = alpha_g;
     prm.beta = beta;
     prm.C = C;
     prm.ldc = ldc;
@@ -528,8 +929,7 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
         (void)cudaGetLastError();
         return RMGE_ERR_CUDA;
     }
-    const dim3 grid((unsigned)(Np / OBN), (unsigned)(Mp / OBM));
-    oz_gemm_kernel<<<grid, OTHREADS, kOzSmem, st>>>(ta, tb, prm, idesc);
+    oz_gemm_kernel<<<(unsigned)((Np / OBN) * (Mp / OBM)), OTHREADS, kOzSmem, st>>>(ta, tb, prm, idesc);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }

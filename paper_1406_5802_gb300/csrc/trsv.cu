@@ -12,7 +12,11 @@
 // (kSpinLimit polls); on expiry the CTA records RMGE_ERR_TIMEOUT in DevState::error and all
 // waiting CTAs return without writing.
 //
-// The factor is read once from HBM per column block; FP64 runs on the DFMA pipe.
+// The factor is read once from HBM per column block; FP64 runs on the DFMA pipe.  GB300 retires 2 FP64
+// operations per clock per SM, so the chain of row blocks is bound by the FP64 work of each link (the
+// product with the block just solved plus the diagonal substitution): narrow column blocks (KC = 4)
+// give more independent chains with less FP64 work per link, and the diagonal substitution multiplies
+// by reciprocals formed before the CTA starts waiting, keeping FP64 divisions off the chain.
 #include "kernels.cuh"
 
 namespace rmge {
@@ -44,6 +48,7 @@ __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t n
     __shared__ T cs[TB][TB + 1];  // off-diagonal coefficient tile
     __shared__ T cd[TB][TB + 1];  // diagonal block
     __shared__ T ys[TB][KC];
+    __shared__ T rd[TB];  // reciprocals of the diagonal (non-unit kinds)
     __shared__ int my_ticket;
     __shared__ int failed;
     if (skip != nullptr && *(volatile const int*)skip != 0) return;
@@ -75,6 +80,9 @@ __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t n
         const int64_t gi = r0 + i, gt = r0 + t;
         cd[i][t] = (gi < n && gt < n) ? coef(kind, LU, ld, gi, gt) : ((i == t) ? T(1) : T(0));
     }
+    __syncthreads();
+    if (!unit && tid < TB) rd[tid] = T(1) / cd[tid][tid];
+    __syncthreads();
 
     constexpr int CPT = TB * TB / NT;  // coefficients per thread per tile
     for (int64_t qq = 0; qq < q; ++qq) {
@@ -131,7 +139,7 @@ __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t n
     for (int step = 0; step < TB; ++step) {
         const int p = forward ? step : TB - 1 - step;  // row finalised in this step
         if (r == p) {
-            const T y = unit ? acc : acc / cd[p][p];
+            const T y = unit ? acc : acc * rd[p];
             acc = y;
             ys[p][c] = y;
         }

@@ -50,7 +50,7 @@ def test_emulated_product_accuracy(orc, n):
     assert np.all(np.abs(M - ref) <= bound), float(np.max(np.abs(M - ref) / bound))
 
 
-@pytest.mark.parametrize("n", [65, 257, 700])
+@pytest.mark.parametrize("n", [65, 257, 700, 2048])
 def test_emulated_factor_backward_error(orc, n):
     A, _ = W.gaussian_system(n, 1, seed=90 + n)
     G = W.gaussian_multiplier(n, 91 + n)
