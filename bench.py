@@ -118,8 +118,9 @@ def run_reference(args):
 
 def extra_workloads(W, rmge, peaks):
     """The other measured workloads (one JSON object each, added to the main line): the n = 16384
-    precision comparison (FP64 form vs reduced-precision factors + FP64 refinement), the batch of 4096
-    uneven systems in one persistent graph-captured launch, and the differentiable batch of 64 systems."""
+    precision comparison (the FP64 form against the tensor-core forms with FP64 refinement: emulated FP64
+    products (f64x), three-pass and one-pass BF16/FP16 splits), the batch of 4096 uneven systems in one
+    persistent graph-captured launch, and the differentiable batch of 64 systems."""
     import numpy as np
     import torch
 
@@ -133,7 +134,7 @@ def extra_workloads(W, rmge, peaks):
         n, k = 16384, 8
         A, B = W.orthogonal_factor_system_torch(n, k, 1e-4, seed=W.SEED_BASE + 3, device="cuda")
         res = {"workload": "n=16384, 8 RHS, A = U diag(sigma) V^T, sigma log-spaced 1..1e-4, Gaussian G"}
-        for prec in ("f64", "bf16x3", "f16x3", "bf16"):
+        for prec in ("f64", "f64x", "bf16x3", "f16x3", "bf16"):
             ws = rmge.workspace(n, k, "gaussian", prec)
             G = rmge.empty_multiplier("gaussian", n, prec)
             M = torch.empty(n, n, dtype=rmge.factor_dtype(prec), device="cuda")
@@ -152,7 +153,7 @@ def extra_workloads(W, rmge, peaks):
             torch.cuda.synchronize()
             it = int(iters.item())
             ms, ams = t0.elapsed_time(t1), a0.elapsed_time(a1)
-            terms = {"f64": 1, "bf16x3": 3, "f16x3": 3, "bf16": 1}[prec]
+            terms = {"f64": 1, "f64x": 36, "bf16x3": 3, "f16x3": 3, "bf16": 1}[prec]
             entry = {"ms_per_solve": ms, "solves_per_s": 1e3 / ms, "berr_final": float(berr[it].item()),
                      "sweeps": it, "reached_1e-13": bool(berr[it].item() <= 1e-13), "growth": float(growth.item()),
                      "info": int(info.item()), "apply_ms": ams,
@@ -234,6 +235,80 @@ def extra_workloads(W, rmge, peaks):
     return out
 
 
+FORMS = {"f64x": ("gaussian", "f64x"), "circ_f64": ("circulant", "f64"), "circ_f64x": ("circulant", "f64x")}
+FORM_TEXT = {
+    "f64x": "Gaussian G; A G and GENP's Schur updates as FP64 products emulated on the BF16 tensor cores (8 base-128 "
+            "digits, 36 digit-pair MMAs, exact FP32 chunks, 64-bit fixed-point sums); pivot blocks, panels, solves, "
+            "residuals and refinement in FP64",
+    "circ_f64": "random circulant G (Gaussian first column) applied by FFT; GENP, solves and refinement in FP64",
+    "circ_f64x": "random circulant G applied by FFT; GENP's Schur updates emulated on the BF16 tensor cores; solves and "
+                 "refinement in FP64",
+}
+
+
+def timed_form(rmge, A, Bm, M, X, kind, prec, args, stream, barrier, world, value_f64):
+    """Whole solves (multiplier, A G, GENP, solve, refinement to the target) in one form, timed like the main
+    line; the apply step is also timed on its own for the roofline of its kernel."""
+    import torch
+    import torch.distributed as dist
+    n, k = A.shape[0], Bm.shape[1]
+    ws = rmge.workspace(n, k, kind, prec)
+    G = rmge.empty_multiplier(kind, n, prec)
+
+    def one(i, rec=None):
+        rmge.make_multiplier(kind, n, SEED + i, 1, prec, G=G)
+        if rec is not None:
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+        rmge.apply_multiplier(kind, A, G, prec, M=M, ws=ws)
+        if rec is not None:
+            a1.record(stream)
+            rec.append((a0, a1))
+        info, _ = rmge.factor(M, prec, ws=ws)
+        rmge.solve(kind, M, G, Bm, prec, X=X, ws=ws)
+        berr, it = rmge.refine(kind, A, M, G, Bm, X, prec, MAX_ITERS, BE_TOL, ws=ws)
+        return info, berr, it
+
+    for i in range(args.warmup):
+        one(i)
+    barrier()
+    torch.cuda.synchronize()
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res, ev = [], []
+    m0.record(stream)
+    for i in range(args.steps):
+        res.append(one(args.warmup + i, ev))
+    m1.record(stream)
+    torch.cuda.synchronize()
+    mt = torch.tensor([m0.elapsed_time(m1)], device="cuda")
+    if world > 1:
+        dist.all_reduce(mt, op=dist.ReduceOp.MAX)
+    ms = float(mt.item())
+    sw = [int(r[2].item()) for r in res]
+    be = [float(r[1][q].item()) for r, q in zip(res, sw)]
+    ok = all(int(r[0].item()) == 0 for r in res) and all(b <= BE_TOL for b in be)
+    apply_ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+    val = args.steps * world / (ms / 1e3)
+    out = {"form": FORM_TEXT[args_form_key(kind, prec)], "value": val, "unit": "solves/s",
+           "ms_per_step": ms / args.steps, "all_steps_be_le_1e-13": ok, "max_berr": max(be),
+           "mean_sweeps": sum(sw) / len(sw), "apply_ms": apply_ms, "speedup_vs_f64": val / value_f64,
+           "tflops": flops_per_solve(n, k, sum(sw) / len(sw)) * val / 1e12}
+    if kind == "gaussian" and prec == "f64x":
+        pairs = 36  # base-128 digit pairs kept by the emulated FP64 product (8 digits per entry)
+        out["roofline"] = {"kernel": "oz_gemm_kernel (M = A G)", "bound": "tensor",
+                           "achieved": pairs * 2 * n**3 / (apply_ms / 1e3) / 1e12, "peak": None,
+                           "unit": "TFLOP/s (BF16 MMA)", "frac": None, "traffic": None}
+    del ws, G
+    return out
+
+
+def args_form_key(kind, prec):
+    for key, (fk, fp) in FORMS.items():
+        if fk == kind and fp == prec:
+            return key
+    return "f64"
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -242,6 +317,9 @@ def main():
     ap.add_argument("--impl", default="rmge", choices=["rmge", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other measured workloads")
+    ap.add_argument("--forms", default="f64x,circ_f64,circ_f64x",
+                    help="comma list of the other forms timed on the same inputs (f64x, circ_f64, circ_f64x; "
+                         "'none' for the main line only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -345,59 +423,17 @@ def main():
     apply_ms = sum(a.elapsed_time(b) for a, b in ev_apply) / len(ev_apply)
     achieved = (2 * n**3 - n**2) / (apply_ms / 1e3) / 1e12
 
-    # the mixed form on the same inputs: A G as an FP64 product emulated on the BF16 tensor cores
-    # (RMGE_F64X_TC), GENP, solves, residuals and refinement in FP64, same accuracy target
-    mixed = None
-    try:
-        mprec = "f64x"
-        mws = rmge.workspace(n, k, kind, mprec)
-        for i in range(args.warmup):
-            rmge.make_multiplier(kind, n, SEED + i, 1, mprec, G=G)
-            rmge.apply_multiplier(kind, A, G, mprec, M=M, ws=mws)
-            rmge.factor(M, mprec, ws=mws)
-            rmge.solve(kind, M, G, Bm, mprec, X=X, ws=mws)
-            rmge.refine(kind, A, M, G, Bm, X, mprec, MAX_ITERS, BE_TOL, ws=mws)
-        barrier()
-        torch.cuda.synchronize()
-        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        mres, mapply = [], []
-        m0.record(stream)
-        for i in range(args.steps):
-            rmge.make_multiplier(kind, n, SEED + args.warmup + i, 1, mprec, G=G)
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            rmge.apply_multiplier(kind, A, G, mprec, M=M, ws=mws)
-            a1.record(stream)
-            mapply.append((a0, a1))
-            info_m, _ = rmge.factor(M, mprec, ws=mws)
-            rmge.solve(kind, M, G, Bm, mprec, X=X, ws=mws)
-            berr_m, it_m = rmge.refine(kind, A, M, G, Bm, X, mprec, MAX_ITERS, BE_TOL, ws=mws)
-            mres.append((info_m, berr_m, it_m))
-        m1.record(stream)
-        torch.cuda.synchronize()
-        mms = m0.elapsed_time(m1)
-        mt = torch.tensor([mms], device="cuda")
-        if world > 1:
-            dist.all_reduce(mt, op=dist.ReduceOp.MAX)
-        msw = [int(r[2].item()) for r in mres]
-        mbe = [float(r[1][q].item()) for r, q in zip(mres, msw)]
-        mok = all(int(r[0].item()) == 0 for r in mres) and all(b <= BE_TOL for b in mbe)
-        apply_ms_m = sum(a.elapsed_time(b) for a, b in mapply) / len(mapply)
-        pairs = 36  # base-128 digit pairs kept by the emulated FP64 product (8 digits per entry)
-        tensor_tflops = pairs * 2 * n**3 / (apply_ms_m / 1e3) / 1e12
-        mixed = {"precision": "f64x: A G as an FP64 product emulated on the BF16 tensor cores "
-                              "(8 base-128 digits, 36 digit-pair MMAs, exact FP32 chunks, 64-bit fixed-point "
-                              "sums); GENP, solves, residuals and refinement in FP64",
-                 "value": solves / (float(mt.item()) / 1e3), "unit": "solves/s",
-                 "ms_per_step": float(mt.item()) / args.steps, "all_steps_be_le_1e-13": mok, "max_berr": max(mbe),
-                 "mean_sweeps": sum(msw) / len(msw), "apply_ms": apply_ms_m,
-                 "speedup_vs_f64": (solves / (float(mt.item()) / 1e3)) / value,
-                 "roofline": {"kernel": "oz_gemm_kernel (M = A G)", "bound": "tensor",
-                              "achieved": tensor_tflops, "peak": None, "unit": "TFLOP/s (BF16 MMA)",
-                              "frac": None, "traffic": None}}
-        del mws
-    except Exception as e:  # reported, never fatal for the main line
-        mixed = {"error": repr(e)}
+    # the other forms on the same inputs and the same accuracy target: the mixed form (A G and GENP's
+    # Schur updates as FP64 products emulated on the BF16 tensor cores, RMGE_F64X_TC) and the random
+    # circulant multiplier applied by FFT (Sec. 5), in FP64 and in the mixed form
+    forms = {}
+    wanted = [f for f in args.forms.split(",") if f and f != "none"]
+    for name in wanted:
+        fkind, fprec = FORMS[name]
+        try:
+            forms[name] = timed_form(rmge, A, Bm, M, X, fkind, fprec, args, stream, barrier, world, value)
+        except Exception as e:  # reported, never fatal for the main line
+            forms[name] = {"error": repr(e)}
 
     # end to end through the public API with host buffers: H2D of A and B, D2H of X and berr each step
     A_h = A.cpu().pin_memory()
@@ -463,13 +499,14 @@ def main():
             "clocks": clocks_summary(clk),
             "cpu_baseline": cpu,
             "hbm_gbs_measured_peak": peaks.get("hbm_gbs"),
-            "mixed": mixed,
+            "forms": forms,
         }
-        if isinstance(mixed, dict) and "roofline" in mixed:
-            pk = peaks.get("bf16_tflops", 1958.3)
-            mixed["roofline"]["peak"] = pk
-            mixed["roofline"]["frac"] = mixed["roofline"]["achieved"] / pk
-            mixed["roofline"]["peak_source"] = "MEASURED_PEAKS.json bf16_tflops (burst), of measured"
+        for f in forms.values():
+            if isinstance(f, dict) and isinstance(f.get("roofline"), dict) and f["roofline"].get("unit", "").startswith("TFLOP/s (BF16"):
+                pk = peaks.get("bf16_tflops", 1958.3)
+                f["roofline"]["peak"] = pk
+                f["roofline"]["frac"] = f["roofline"]["achieved"] / pk
+                f["roofline"]["peak_source"] = "MEASURED_PEAKS.json bf16_tflops (burst), of measured"
         if not args.no_extras:
             line["extras"] = extra_workloads(W, rmge, peaks)
         print(json.dumps(line), flush=True)
