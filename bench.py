@@ -37,6 +37,8 @@ FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of one A G launch at n = 4096, from an ncu capture of this kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum); reset to None whenever the kernel changes.
 AG_TRAFFIC_BYTES = 3.733360e9 + 0.134520e9
+# The same for the emulated-FP64 A G kernel of the mixed form (oz_gemm_kernel) at n = 4096.
+OZ_AG_TRAFFIC_BYTES = 2.257836e9 + 0.189575e9
 
 
 def flops_per_solve(n, k, sweeps):
@@ -297,7 +299,9 @@ def timed_form(rmge, A, Bm, M, X, kind, prec, args, stream, barrier, world, valu
         pairs = 36  # base-128 digit pairs kept by the emulated FP64 product (8 digits per entry)
         out["roofline"] = {"kernel": "oz_gemm_kernel (M = A G)", "bound": "tensor",
                            "achieved": pairs * 2 * n**3 / (apply_ms / 1e3) / 1e12, "peak": None,
-                           "unit": "TFLOP/s (BF16 MMA)", "frac": None, "traffic": None}
+                           "unit": "TFLOP/s (BF16 MMA)", "frac": None,
+                           "traffic": OZ_AG_TRAFFIC_BYTES if n == N_SYS else None,
+                           "algorithmic_bytes": 3 * n * n * 8 + 2 * 8 * n * n * 2}
     del ws, G
     return out
 
