@@ -869,7 +869,9 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
         UpdParams u{};
         u.M = (int)M;
         u.N = (int)N;
-        u.F = 51;  // one chunk per diagonal: |acc| < 2^(F + 10)
+        // one chunk per diagonal, K <= 64: |acc| <= sum_d (d + 1) 127^2 64 2^(F - 7(d + 2)) < 0.99 2^62 at
+        // F = 56, so the fixed-point sum keeps the 56 bits of the 8-digit operands
+        u.F = 56;
         u.Mp = (int)Mp;
         u.Np = (int)Np;
         u.tiles_n = (int)((N + UBN - 1) / UBN);
