@@ -14,7 +14,7 @@
 //
 // The factor is read once from HBM per column block; FP64 runs on the DFMA pipe.  GB300 retires 2 FP64
 // operations per clock per SM, so the chain of row blocks is bound by the FP64 work of each link (the
-// product with the block just solved plus the diagonal substitution): narrow column blocks (KC = 4)
+// product with the block just solved plus the diagonal substitution): narrow column blocks (KC = 2)
 // give more independent chains with less FP64 work per link, and the diagonal substitution multiplies
 // by reciprocals formed before the CTA starts waiting, keeping FP64 divisions off the chain.
 #include "kernels.cuh"
