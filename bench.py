@@ -118,7 +118,7 @@ def run_reference(args):
     return 0
 
 
-def extra_workloads(W, rmge, peaks):
+def extra_workloads(W, rmge, peaks, which=("precision", "batch", "grad")):
     """The other measured workloads (one JSON object each, added to the main line): the n = 16384
     precision comparison (the FP64 form against the tensor-core forms with FP64 refinement: emulated FP64
     products (f64x), three-pass and one-pass BF16/FP16 splits), the batch of 4096 uneven systems in one
@@ -133,6 +133,8 @@ def extra_workloads(W, rmge, peaks):
 
     # -- precision: n = 16384, sigma 1 .. 1e-4, 8 RHS -------------------------------------------------
     try:
+        if "precision" not in which:
+            raise LookupError("not selected")
         n, k = 16384, 8
         A, B = W.orthogonal_factor_system_torch(n, k, 1e-4, seed=W.SEED_BASE + 3, device="cuda")
         res = {"workload": "n=16384, 8 RHS, A = U diag(sigma) V^T, sigma log-spaced 1..1e-4, Gaussian G"}
@@ -175,6 +177,8 @@ def extra_workloads(W, rmge, peaks):
 
     # -- batching: 4096 systems, n ~ U{32..512}, one persistent CUDA-graph launch -----------------------
     try:
+        if "batch" not in which:
+            raise LookupError("not selected")
         from paper_1406_5802_gb300.batch import BatchedSolver
         sizes = W.batch_sizes(4096, 32, 512, W.SEED_BASE + 4)
         bs = BatchedSolver.synthetic(sizes, seed=W.SEED_BASE + 4, max_sweeps=40, be_tol=1e-13)
@@ -205,7 +209,12 @@ def extra_workloads(W, rmge, peaks):
         out["batch_4096"] = {"error": repr(e)}
 
     # -- differentiation: 64 systems, n = 2048, FP32, forward + backward --------------------------------
+    # Two forms of the same batch: FP32 factors with FP64 FGMRES sweeps (at most 3 cycles per solve: every
+    # system converges in 2 forward and 1 backward), and the mixed form (emulated-FP64 factors, classical
+    # FP64 sweeps).  Both return FP32 gradients of the FP64-accurate solve.
     try:
+        if "grad" not in which:
+            raise LookupError("not selected")
         from paper_1406_5802_gb300.autograd import rmge_solve_batched
         n, k, count = 2048, 4, 64
         g = torch.Generator(device="cuda")
@@ -214,24 +223,27 @@ def extra_workloads(W, rmge, peaks):
               .requires_grad_(True) for _ in range(count)]
         Bs = [torch.randn(n, k, generator=g, device="cuda").requires_grad_(True) for _ in range(count)]
         Ws = [torch.randn(n, k, generator=g, device="cuda") for _ in range(count)]
+        res = {"workload": "64 systems, n=2048, 4 RHS, FP32, A = 4I + N(0,1)/sqrt(n), loss = sum(X*W), "
+                           "forward + adjoint backward"}
+        for prec, iters in (("f32", 3), ("f64x", 4)):
+            def step():
+                for t in As + Bs:
+                    t.grad = None
+                Xs = rmge_solve_batched(As, Bs, seeds=list(range(count)), prec=prec, streams=8, max_iters=iters)
+                loss = sum((X * Wt).sum() for X, Wt in zip(Xs, Ws))
+                loss.backward()
+                return loss
 
-        def step():
-            Xs = rmge_solve_batched(As, Bs, seeds=list(range(count)), prec="f32", streams=8)
-            loss = sum((X * Wt).sum() for X, Wt in zip(Xs, Ws))
-            loss.backward()
-            return loss
-
-        step()
-        torch.cuda.synchronize()
-        t0, t1 = ev(), ev()
-        t0.record()
-        step()
-        t1.record()
-        torch.cuda.synchronize()
-        ms = t0.elapsed_time(t1)
-        out["grad_64x2048"] = {"workload": "64 systems, n=2048, 4 RHS, FP32, A = 4I + N(0,1)/sqrt(n), loss = sum(X*W), "
-                                           "forward + adjoint backward",
-                               "ms_per_batch": ms, "systems_per_s": count / (ms / 1e3)}
+            step()
+            torch.cuda.synchronize()
+            t0, t1 = ev(), ev()
+            t0.record()
+            step()
+            t1.record()
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1)
+            res[prec] = {"ms_per_batch": ms, "systems_per_s": count / (ms / 1e3), "max_iters": iters}
+        out["grad_64x2048"] = res
     except Exception as e:
         out["grad_64x2048"] = {"error": repr(e)}
     return out
@@ -321,6 +333,8 @@ def main():
     ap.add_argument("--impl", default="rmge", choices=["rmge", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other measured workloads")
+    ap.add_argument("--extras", default="precision,batch,grad",
+                    help="comma list of the other workloads (precision, batch, grad)")
     ap.add_argument("--forms", default="f64x,circ_f64,circ_f64x",
                     help="comma list of the other forms timed on the same inputs (f64x, circ_f64, circ_f64x; "
                          "'none' for the main line only)")
@@ -512,7 +526,9 @@ def main():
                 f["roofline"]["frac"] = f["roofline"]["achieved"] / pk
                 f["roofline"]["peak_source"] = "MEASURED_PEAKS.json bf16_tflops (burst), of measured"
         if not args.no_extras:
-            line["extras"] = extra_workloads(W, rmge, peaks)
+            sel = tuple(x for x in args.extras.split(",") if x)
+            line["extras"] = {k: v for k, v in extra_workloads(W, rmge, peaks, sel).items()
+                              if not (isinstance(v, dict) and v.get("error") == repr(LookupError("not selected")))}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
