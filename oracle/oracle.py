@@ -23,6 +23,9 @@ _u64 = C.c_uint64
 GAUSSIAN = 0
 CIRCULANT_GAUSSIAN = 1
 CIRCULANT_UNIFORM = 2
+CIRCULANT_UNITARY = 3
+TOEPLITZ_GAUSSIAN = 4
+TOEPLITZ_UNIFORM = 5
 
 
 def lib():
@@ -36,6 +39,11 @@ def lib():
             "orc_philox4x32_10": (None, [_up, _up, _up]),
             "orc_gaussian": (None, [_i64, _u64, _u64, _dp]),
             "orc_uniform_pm1": (None, [_i64, _u64, _u64, _dp]),
+            "orc_uniform01": (None, [_i64, _u64, _u64, _dp]),
+            "orc_unitary_spectrum": (None, [_i64, _u64, _u64, _dp, _dp]),
+            "orc_toeplitz_dense": (None, [_i64, _dp, _dp]),
+            "orc_unitary_circulant_column": (None, [_i64, _u64, _u64, _dp, _dp]),
+            "orc_multiplier_dense": (None, [C.c_int, _i64, _dp, _dp]),
             "orc_gaussian_f32": (None, [_i64, _u64, _u64, np.ctypeslib.ndpointer(dtype=np.float32,
                                                                                flags="C_CONTIGUOUS")]),
             "orc_matmul": (None, [_i64, _i64, _i64, _dp, _dp, _dp]),
@@ -109,15 +117,57 @@ def uniform_pm1(count, seed, subseq=0):
     return out
 
 
+def uniform01(count, seed, subseq=0):
+    out = np.empty(int(count), np.float64)
+    lib().orc_uniform01(int(count), int(seed), int(subseq), out)
+    return out
+
+
+def unitary_spectrum(n, seed, subseq=1):
+    """Hermitian-symmetric unit-modulus spectrum u (complex, length n) of a random unitary circulant."""
+    ur = np.empty(int(n), np.float64)
+    ui = np.empty(int(n), np.float64)
+    lib().orc_unitary_spectrum(int(n), int(seed), int(subseq), ur, ui)
+    return ur + 1j * ui
+
+
+def unitary_circulant_column(n, seed, subseq=1):
+    """First column c = Omega^{-1} u of the random unitary circulant (Ex. 5.2), by the naive inverse
+    DFT (sign -1, divided by n); returns (c real part, imaginary part left by rounding)."""
+    c = np.empty(int(n), np.float64)
+    cim = np.empty(int(n), np.float64)
+    lib().orc_unitary_circulant_column(int(n), int(seed), int(subseq), c, cim)
+    return c, cim
+
+
 def make_multiplier(kind, n, seed, subseq=1):
-    """Dense Gaussian G (n x n) for GAUSSIAN; first column c (n,) for the circulant kinds."""
+    """Dense Gaussian G (n x n) for GAUSSIAN; the first column c (n,) of the circulant kinds; the first
+    column c2 (2n,) of the 2n x 2n circulant whose leading n x n block is the Toeplitz multiplier."""
     if kind == GAUSSIAN:
         return gaussian(n * n, seed, subseq).reshape(n, n)
-    if kind == CIRCULANT_GAUSSIAN:
-        return gaussian(n, seed, subseq)
-    if kind == CIRCULANT_UNIFORM:
-        return uniform_pm1(n, seed, subseq)
-    raise ValueError(kind)
+    if kind in (CIRCULANT_GAUSSIAN, CIRCULANT_UNIFORM, CIRCULANT_UNITARY):
+        base, m = kind, n
+    elif kind in (TOEPLITZ_GAUSSIAN, TOEPLITZ_UNIFORM):
+        base, m = kind - 3, 2 * n
+    else:
+        raise ValueError(kind)
+    if base == CIRCULANT_GAUSSIAN:
+        return gaussian(m, seed, subseq)
+    if base == CIRCULANT_UNIFORM:
+        return uniform_pm1(m, seed, subseq)
+    return unitary_circulant_column(m, seed, subseq)[0]
+
+
+def toeplitz_dense(n, c2):
+    out = np.empty((int(n), int(n)), np.float64)
+    lib().orc_toeplitz_dense(int(n), _f64(c2), out)
+    return out
+
+
+def multiplier_dense(kind, n, H):
+    out = np.empty((int(n), int(n)), np.float64)
+    lib().orc_multiplier_dense(int(kind), int(n), _f64(H), out)
+    return out
 
 
 def matmul(A, B):

@@ -132,6 +132,43 @@ void orc_uniform_pm1(int64_t count, uint64_t seed, uint64_t subseq, double* out)
     }
 }
 
+/*
+ * Uniform phases in [0, 1): the same stream layout, value m/2^53.
+ */
+void orc_uniform01(int64_t count, uint64_t seed, uint64_t subseq, double* out) {
+    const double two_m53 = 1.0 / 9007199254740992.0;
+    for (int64_t e = 0; e < count; e += 2) {
+        uint32_t x[4];
+        draw_block((uint64_t)(e / 2), seed, subseq, x);
+        out[e] = (double)bits53(x[0], x[1]) * two_m53;
+        if (e + 1 < count) out[e + 1] = (double)bits53(x[2], x[3]) * two_m53;
+    }
+}
+
+/*
+ * Spectrum of a random unitary circulant (Ex. 5.2): u_j = exp(2 pi phi_j sqrt(-1)) with phi_j
+ * uniform in [0, 1).  The draw is made Hermitian-symmetric (u_{n-j} = conj(u_j), u_0 and u_{n/2}
+ * real), so that c = Omega^{-1} u is real and C a real orthogonal matrix: phi_0 .. phi_{n/2} are
+ * entries 0 .. n/2 of the phase stream, u_0 = +1 if phi_0 < 1/2 else -1, likewise u_{n/2}
+ * (n even).
+ */
+void orc_unitary_spectrum(int64_t n, uint64_t seed, uint64_t subseq, double* ur, double* ui) {
+    const int64_t h = n / 2;
+    double* phi = (double*)malloc(sizeof(double) * (size_t)(h + 1));
+    orc_uniform01(h + 1, seed, subseq, phi);
+    ur[0] = (phi[0] < 0.5) ? 1.0 : -1.0;
+    ui[0] = 0.0;
+    for (int64_t j = 1; j < h; ++j) {
+        ur[j] = cos(2.0 * ORC_PI * phi[j]);
+        ui[j] = sin(2.0 * ORC_PI * phi[j]);
+        ur[n - j] = ur[j];
+        ui[n - j] = -ui[j];
+    }
+    ur[h] = (phi[h] < 0.5) ? 1.0 : -1.0;
+    ui[h] = 0.0;
+    free(phi);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Dense products and the circulant multiplier                              */
 /* ------------------------------------------------------------------------ */
@@ -157,6 +194,17 @@ void orc_circulant_dense(int64_t n, const double* c, double* C) {
 }
 
 /*
+ * Toeplitz multiplier T (n x n) = the leading n x n block of the 2n x 2n circulant with first
+ * column c2 (length 2n): T_ij = c2[(i - j) mod 2n] (the paper's Toeplitz multipliers are leading
+ * submatrices of random circulant matrices, Sec. 7.2).
+ */
+void orc_toeplitz_dense(int64_t n, const double* c2, double* T) {
+    const int64_t N = 2 * n;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) T[i * n + j] = c2[((i - j) % N + N) % N];
+}
+
+/*
  * Plain O(n^2) DFT y_f = sum_t x_t w^{f t}, w = exp(sign * 2 pi i / n).
  * With sign = +1 this is the matrix Omega of Sec. 5 applied to x.
  */
@@ -172,6 +220,24 @@ void orc_dft(int64_t n, const double* xr, const double* xi, double* yr, double* 
         yr[f] = sr;
         yi[f] = si;
     }
+}
+
+/*
+ * First column of the random unitary circulant of Ex. 5.2: c = Omega^{-1} u = (1/n) Omega^H u for the
+ * Hermitian-symmetric spectrum of orc_unitary_spectrum, by the plain inverse DFT.  c is real; cim
+ * receives the imaginary parts left by rounding.
+ */
+void orc_unitary_circulant_column(int64_t n, uint64_t seed, uint64_t subseq, double* c, double* cim) {
+    double* ur = (double*)malloc(sizeof(double) * (size_t)n);
+    double* ui = (double*)malloc(sizeof(double) * (size_t)n);
+    orc_unitary_spectrum(n, seed, subseq, ur, ui);
+    orc_dft(n, ur, ui, c, cim, -1);
+    for (int64_t t = 0; t < n; ++t) {
+        c[t] /= (double)n;
+        cim[t] /= (double)n;
+    }
+    free(ur);
+    free(ui);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -417,28 +483,33 @@ double orc_growth(int64_t n, const double* M, const double* LU) {
 /* The randomized GENP solve (Fact 4.1 with F = I, H = G)                   */
 /* ------------------------------------------------------------------------ */
 
-/* multiplier kinds: 0 dense Gaussian H (n x n); 1 / 2 circulant H given by its first column */
-static void apply_H(int kind, int64_t n, int64_t k, const double* H, const double* Y, double* X) {
-    if (kind == 0) {
-        orc_matmul(n, n, k, H, Y, X);
-    } else {
-        double* C = (double*)malloc(sizeof(double) * (size_t)(n * n));
-        orc_circulant_dense(n, H, C);
-        orc_matmul(n, n, k, C, Y, X);
-        free(C);
-    }
+/*
+ * Multiplier kinds: 0 dense Gaussian H (n x n); 1, 2, 3 circulant H given by its first column (n);
+ * 4, 5 Toeplitz H given by the first column of the 2n x 2n circulant it is the leading block of.
+ * The dense matrix of H, for the products below.
+ */
+void orc_multiplier_dense(int kind, int64_t n, const double* H, double* D) {
+    if (kind == 0)
+        memcpy(D, H, sizeof(double) * (size_t)(n * n));
+    else if (kind <= 3)
+        orc_circulant_dense(n, H, D);
+    else
+        orc_toeplitz_dense(n, H, D);
 }
 
-/* M = A H (post-multiplication, Fact 4.1), dense circulant for kinds 1, 2. */
+static void apply_H(int kind, int64_t n, int64_t k, const double* H, const double* Y, double* X) {
+    double* D = (double*)malloc(sizeof(double) * (size_t)(n * n));
+    orc_multiplier_dense(kind, n, H, D);
+    orc_matmul(n, n, k, D, Y, X);
+    free(D);
+}
+
+/* M = A H (post-multiplication, Fact 4.1), with the dense matrix of a structured H. */
 void orc_apply_multiplier(int kind, int64_t n, const double* A, const double* H, double* M) {
-    if (kind == 0) {
-        orc_matmul(n, n, n, A, H, M);
-    } else {
-        double* C = (double*)malloc(sizeof(double) * (size_t)(n * n));
-        orc_circulant_dense(n, H, C);
-        orc_matmul(n, n, n, A, C, M);
-        free(C);
-    }
+    double* D = (double*)malloc(sizeof(double) * (size_t)(n * n));
+    orc_multiplier_dense(kind, n, H, D);
+    orc_matmul(n, n, n, A, D, M);
+    free(D);
 }
 
 /*
