@@ -60,7 +60,14 @@ typedef enum {
 typedef enum {
     RMGE_GAUSSIAN = 0,           /* dense n x n, i.i.d. N(0,1) entries (Def. 4.1) */
     RMGE_CIRCULANT_GAUSSIAN = 1, /* circulant whose first column is i.i.d. N(0,1) (Sec. 5) */
-    RMGE_CIRCULANT_UNIFORM = 2   /* circulant whose first column is i.i.d. U[-1,1) (Ex. 5.1) */
+    RMGE_CIRCULANT_UNIFORM = 2,  /* circulant whose first column is i.i.d. U[-1,1) (Ex. 5.1) */
+    RMGE_CIRCULANT_UNITARY = 3,  /* unitary circulant of Ex. 5.2: spectrum u_j = exp(2 pi phi_j sqrt(-1)),
+                                    phi_j i.i.d. U[0,1), drawn Hermitian-symmetric (u_{n-j} = conj(u_j),
+                                    u_0, u_{n/2} = +-1) so that C is real orthogonal; c = Omega^{-1} u */
+    RMGE_TOEPLITZ_GAUSSIAN = 4,  /* Toeplitz multiplier: the leading n x n block of the 2n x 2n circulant
+                                    with an i.i.d. N(0,1) first column (Sec. 7.2's leading blocks of
+                                    random circulants), applied by 2n-point FFTs */
+    RMGE_TOEPLITZ_UNIFORM = 5    /* the same from an i.i.d. U[-1,1) first column (Ex. 5.1) */
 } rmge_mult_kind;
 
 /* Precision of the working matrix M and of its factorization. */
@@ -86,6 +93,10 @@ typedef enum {
  * - circulant kinds: 3n FP64 values: the first column c[0..n-1], then its DFT u = Omega c
  *   (Theorem 5.1; Omega = (w^{ij}), w = exp(2 pi sqrt(-1) / n)) stored as n interleaved
  *   (re, im) pairs.  n must be a power of two, 2 <= n <= 8192.
+ * - Toeplitz kinds: 6n FP64 values, the same for the 2n x 2n circulant whose leading n x n block
+ *   is the multiplier: c2[0..2n-1], then its 2n-point DFT.  n a power of two, 2 <= n <= 4096.
+ *   (No square Toeplitz multiplier is cut from a unitary circulant: that block is singular exactly
+ *   when u_0 u_n = -1.)
  * rmge_multiplier_bytes returns the size (0 for an invalid request).
  */
 size_t rmge_multiplier_bytes(rmge_mult_kind kind, int64_t n, rmge_prec prec);

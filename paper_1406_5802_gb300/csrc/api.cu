@@ -13,9 +13,7 @@ std::atomic<unsigned long long> g_launches{0};
 
 namespace {
 
-bool valid_kind(rmge_mult_kind k) {
-    return k == RMGE_GAUSSIAN || k == RMGE_CIRCULANT_GAUSSIAN || k == RMGE_CIRCULANT_UNIFORM;
-}
+bool valid_kind(rmge_mult_kind k) { return (int)k >= (int)RMGE_GAUSSIAN && (int)k <= (int)RMGE_TOEPLITZ_UNIFORM; }
 bool valid_prec(rmge_prec p) { return (int)p >= (int)RMGE_F64 && (int)p <= (int)RMGE_F64X_TC; }
 bool is_tc(rmge_prec p) { return (int)p >= (int)RMGE_BF16_TC && (int)p <= (int)RMGE_F16X3_TC; }
 // RMGE_F64X_TC keeps FP64 data everywhere; only the engine of A G and of the Schur updates differs.
@@ -23,9 +21,13 @@ rmge_prec data_prec(rmge_prec p) { return p == RMGE_F64X_TC ? RMGE_F64 : p; }
 bool tc_bf16(rmge_prec p) { return p == RMGE_BF16_TC || p == RMGE_BF16X3_TC; }
 int tc_terms(rmge_prec p) { return (p == RMGE_BF16X3_TC || p == RMGE_F16X3_TC) ? 3 : 1; }
 int64_t tc_ldk(int64_t n) { return (n + 63) / 64 * 64; }
+// the FFT kinds: circulants (transform length n) and Toeplitz multipliers (the leading n x n block of a
+// 2n x 2n circulant, transform length 2n)
 bool is_circ(rmge_mult_kind k) { return k != RMGE_GAUSSIAN; }
+bool is_toeplitz(rmge_mult_kind k) { return k == RMGE_TOEPLITZ_GAUSSIAN || k == RMGE_TOEPLITZ_UNIFORM; }
+int64_t fft_len(rmge_mult_kind k, int64_t n) { return is_toeplitz(k) ? 2 * n : n; }
 bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
-bool circ_ok(int64_t n) { return pow2(n) && n >= 2 && n <= 8192; }
+bool circ_ok(rmge_mult_kind k, int64_t n) { return pow2(n) && n >= 2 && fft_len(k, n) <= 8192; }
 size_t elem(rmge_prec p) { return data_prec(p) == RMGE_F64 ? 8 : 4; }
 
 int64_t nflags_for(int64_t n, int64_t nrhs) {
@@ -92,7 +94,7 @@ rmge_status apply_g_cols(rmge_mult_kind kind, rmge_prec prec, int64_t n, int64_t
                          const void* y, int64_t ldy, void* d, int64_t ldd, bool accumulate, const int* skip,
                          const Ws& w, cudaStream_t s) {
     if (is_circ(kind))
-        return circulant_apply_cols(n, k, static_cast<const double*>(G), w.tw, transpose,
+        return circulant_apply_cols(n, fft_len(kind, n), k, static_cast<const double*>(G), w.tw, transpose,
                                     static_cast<const double*>(y), ldy, static_cast<double*>(d), ldd, accumulate, skip,
                                     s);
     if (prec == RMGE_F64)
@@ -233,7 +235,7 @@ WsLayout ws_layout(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec)
     L.D = off;
     off = align256(off + sizeof(double) * (size_t)(n * nrhs));
     L.fft = off;
-    if (is_circ(kind)) off = align256(off + sizeof(double2) * (size_t)(n / 2 + 1));
+    if (is_circ(kind)) off = align256(off + sizeof(double2) * (size_t)(fft_len(kind, n) / 2 + 1));
     L.tcmx = off;
     if (is_tc(prec)) off = align256(off + sizeof(unsigned long long) * (size_t)(2 * (n / kNb + 2)));
     L.tc = off;
@@ -273,19 +275,19 @@ const char* rmge_status_string(rmge_status s) {
 
 size_t rmge_multiplier_bytes(rmge_mult_kind kind, int64_t n, rmge_prec prec) {
     if (!valid_kind(kind) || !valid_prec(prec) || n < 1 || n > RMGE_MAX_N) return 0;
-    if (is_circ(kind)) return circ_ok(n) ? 3 * sizeof(double) * (size_t)n : 0;
+    if (is_circ(kind)) return circ_ok(kind, n) ? 3 * sizeof(double) * (size_t)fft_len(kind, n) : 0;
     return (size_t)n * (size_t)n * elem(prec);
 }
 
 size_t rmge_solve_workspace_size(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec) {
     if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs)) return 0;
-    if (is_circ(kind) && !circ_ok(n)) return 0;
+    if (is_circ(kind) && !circ_ok(kind, n)) return 0;
     return ws_layout(n, nrhs, kind, prec).tcmx;
 }
 
 size_t rmge_workspace_size(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec) {
     if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs)) return 0;
-    if (is_circ(kind) && !circ_ok(n)) return 0;
+    if (is_circ(kind) && !circ_ok(kind, n)) return 0;
     return ws_layout(n, nrhs, kind, prec).total;
 }
 
@@ -298,17 +300,24 @@ rmge_status rmge_make_multiplier(rmge_mult_kind kind, int64_t n, uint64_t seed, 
         if (data_prec(prec) == RMGE_F64) return launch_gaussian(n * n, seed, subsequence, static_cast<double*>(G), s);
         return launch_gaussian(n * n, seed, subsequence, static_cast<float*>(G), s);
     }
-    if (!circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
+    if (!circ_ok(kind, n)) return RMGE_ERR_UNSUPPORTED;
     if (((uintptr_t)G & 15) != 0) return RMGE_ERR_INVALID_ARG;
     double* g = static_cast<double*>(G);
-    if (kind == RMGE_CIRCULANT_GAUSSIAN)
-        RMGE_TRY(launch_gaussian(n, seed, subsequence, g, s));
+    const int64_t N = fft_len(kind, n);
+    if (kind == RMGE_CIRCULANT_UNITARY) {
+        // Ex. 5.2: the unit spectrum is drawn, c = Omega^{-1} u follows; the twiddle table lives in c's
+        // slot until the inverse transform overwrites it (the CTA reads the table first)
+        RMGE_TRY(launch_unitary_spectrum(N, seed, subsequence, reinterpret_cast<double2*>(g + N), s));
+        return circulant_from_spectrum(N, g, reinterpret_cast<double2*>(g), s);
+    }
+    if (kind == RMGE_CIRCULANT_GAUSSIAN || kind == RMGE_TOEPLITZ_GAUSSIAN)
+        RMGE_TRY(launch_gaussian(N, seed, subsequence, g, s));
     else
-        RMGE_TRY(launch_uniform_pm1(n, seed, subsequence, g, s));
+        RMGE_TRY(launch_uniform_pm1(N, seed, subsequence, g, s));
     // The spectrum's twiddle table lives in the third block of G until the FFT overwrites it:
-    // u occupies G[n .. 3n) as n double2 and the table needs n/2 double2 -- use the tail half.
+    // u occupies G[N .. 3N) as N double2 and the table needs N/2 double2 -- use the tail half.
     // The FFT reads the table into shared memory before writing u, so the overlap is safe.
-    return circulant_spectrum(n, g, reinterpret_cast<double2*>(g + 2 * n), s);
+    return circulant_spectrum(N, g, reinterpret_cast<double2*>(g + 2 * N), s);
 }
 
 rmge_status rmge_apply_multiplier(rmge_mult_kind kind, int64_t n, const double* A, int64_t lda, const void* G, void* M,
@@ -316,12 +325,12 @@ rmge_status rmge_apply_multiplier(rmge_mult_kind kind, int64_t n, const double* 
     if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, 1) || A == nullptr || G == nullptr || M == nullptr ||
         lda < n || ldm < n)
         return RMGE_ERR_INVALID_ARG;
-    if (is_circ(kind) && !circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
+    if (is_circ(kind) && !circ_ok(kind, n)) return RMGE_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Ws w{};
     RMGE_TRY(carve(ws, ws_bytes, n, 1, kind, prec, &w));
     if (is_circ(kind))
-        return circulant_apply_rows(n, A, lda, static_cast<const double*>(G), w.tw, M, ldm,
+        return circulant_apply_rows(n, fft_len(kind, n), A, lda, static_cast<const double*>(G), w.tw, M, ldm,
                                     data_prec(prec) != RMGE_F64, s);
     if (prec == RMGE_F64X_TC) {
         const OzUpdate oz = oz_buffers(w, n);
@@ -389,7 +398,7 @@ rmge_status rmge_solve(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void*
     if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs) || LU == nullptr || G == nullptr ||
         B == nullptr || X == nullptr || ldlu < n || ldb < nrhs || ldx < nrhs)
         return RMGE_ERR_INVALID_ARG;
-    if (is_circ(kind) && !circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
+    if (is_circ(kind) && !circ_ok(kind, n)) return RMGE_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Ws w{};
     RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w, false));
@@ -405,7 +414,7 @@ rmge_status rmge_refine(rmge_mult_kind kind, int64_t n, int64_t nrhs, const doub
         G == nullptr || B == nullptr || X == nullptr || lda < n || ldlu < n || ldb < nrhs || ldx < nrhs ||
         max_iters < 0 || max_iters > kMaxSweeps || !(be_tol >= 0.0))
         return RMGE_ERR_INVALID_ARG;
-    if (is_circ(kind) && !circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
+    if (is_circ(kind) && !circ_ok(kind, n)) return RMGE_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Ws w{};
     RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w));
@@ -423,7 +432,7 @@ rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, co
         (dA != nullptr && (X == nullptr || ldda < n || ldx < nrhs)) || max_iters < 0 || max_iters > kMaxSweeps ||
         (max_iters > 0 && (A == nullptr || lda < n)) || !(be_tol >= 0.0))
         return RMGE_ERR_INVALID_ARG;
-    if (is_circ(kind) && !circ_ok(n)) return RMGE_ERR_UNSUPPORTED;
+    if (is_circ(kind) && !circ_ok(kind, n)) return RMGE_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Ws w{};
     RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w, max_iters > 0));

@@ -1,4 +1,4 @@
-// fft.cu -- the circulant multiplier applied by FFT (Sec. 5, Theorem 5.1).
+// fft.cu -- the circulant and Toeplitz multipliers applied by FFT (Sec. 5, Theorem 5.1).
 //
 // C = (c_{(i-j) mod n}) is diagonalised by the DFT: with F(x)_f = sum_t x_t w^{f t},
 // w = exp(2 pi sqrt(-1) / n) (the matrix Omega of Sec. 5) and u = F(c):
@@ -69,9 +69,13 @@ __device__ __forceinline__ int bitrev(int t, int logn) { return (int)(__brev((un
 
 // mode 0: spectrum only (G's DFT: out_spec = F(c)), one vector
 // mode 1: filter: y -> F^{-1}(s .* F(y)) with s = u (conv) or conj(u) (corr)
-// Vectors are rows (src[v*lds + t]) or columns (src[t*lds + v]).
+// mode 2: inverse of a stored spectrum: dst = Re F^{-1}(spec), one vector (the first column of the
+//         circulant whose spectrum was drawn)
+// Vectors are rows (src[v*lds + t]) or columns (src[t*lds + v]) of length nin <= n, zero-padded to the
+// transform length n; the first nout outputs are written (a Toeplitz multiplier is the leading block of
+// a circulant of twice its size).
 struct FftArgs {
-    int n, logn, count, mode;
+    int n, logn, count, mode, nin, nout;
     bool cols, conj_spec, out_f32, accumulate;
     const double* src;
     int64_t lds;
@@ -92,14 +96,24 @@ __global__ void __launch_bounds__(kFftThreads) fft_filter_kernel(FftArgs a) {
     const int v0 = 2 * blockIdx.x;
     const bool has1 = v0 + 1 < a.count;
     for (int m = threadIdx.x; m < n / 2; m += blockDim.x) tw[m] = a.tw[m];
+    if (a.mode == 2) {
+        for (int t = threadIdx.x; t < n; t += blockDim.x) x[t] = a.spec[t];
+        __syncthreads();
+        ifft_dif(x, tw, n);
+        double* d = static_cast<double*>(a.dst);
+        for (int t = threadIdx.x; t < a.nout; t += blockDim.x) d[t] = x[bitrev(t, a.logn)].x / (double)n;
+        return;
+    }
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        double re, im = 0.0;
-        if (a.cols) {
-            re = a.src[(int64_t)t * a.lds + v0];
-            if (has1) im = a.src[(int64_t)t * a.lds + v0 + 1];
-        } else {
-            re = a.src[(int64_t)v0 * a.lds + t];
-            if (has1) im = a.src[(int64_t)(v0 + 1) * a.lds + t];
+        double re = 0.0, im = 0.0;
+        if (t < a.nin) {
+            if (a.cols) {
+                re = a.src[(int64_t)t * a.lds + v0];
+                if (has1) im = a.src[(int64_t)t * a.lds + v0 + 1];
+            } else {
+                re = a.src[(int64_t)v0 * a.lds + t];
+                if (has1) im = a.src[(int64_t)(v0 + 1) * a.lds + t];
+            }
         }
         x[bitrev(t, a.logn)] = make_double2(re, im);
     }
@@ -117,7 +131,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_filter_kernel(FftArgs a) {
     __syncthreads();
     ifft_dif(x, tw, n);
     const double scale = 1.0 / (double)n;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    for (int t = threadIdx.x; t < a.nout; t += blockDim.x) {
         const double2 w = x[bitrev(t, a.logn)];
         const double re = w.x * scale, im = w.y * scale;
         if (a.cols) {
@@ -156,61 +170,83 @@ rmge_status launch_fft(FftArgs a, int blocks, cudaStream_t s) {
 
 }  // namespace
 
-// G layout for circulant kinds: c[0..n), then u = F(c) as n double2 (16-byte aligned because
-// G is 256-byte aligned and n is even: offset 8n bytes).  tw: n/2 double2 of scratch.
-rmge_status circulant_spectrum(int64_t n, double* G, double2* tw, cudaStream_t s) {
-    twiddle_kernel<<<(unsigned)((n / 2 + 255) / 256), 256, 0, s>>>((int)n, tw);
+// G layout for the FFT kinds, with N the transform length (n for a circulant, 2n for a Toeplitz
+// multiplier): c[0..N), then u = F(c) as N double2 (16-byte aligned because G is 256-byte aligned and N
+// is even: offset 8N bytes).  tw: N/2 double2 of scratch.
+rmge_status circulant_spectrum(int64_t N, double* G, double2* tw, cudaStream_t s) {
+    twiddle_kernel<<<(unsigned)((N / 2 + 255) / 256), 256, 0, s>>>((int)N, tw);
     RMGE_LAUNCH_CHECK();
     FftArgs a{};
-    a.n = (int)n;
-    a.logn = ilog2(n);
+    a.n = (int)N;
+    a.logn = ilog2(N);
     a.count = 1;
     a.mode = 0;
+    a.nin = a.nout = (int)N;
     a.cols = false;
     a.src = G;
-    a.lds = n;
+    a.lds = N;
     a.tw = tw;
-    a.out_spec = reinterpret_cast<double2*>(G + n);
+    a.out_spec = reinterpret_cast<double2*>(G + N);
     return launch_fft(a, 1, s);
 }
 
-rmge_status circulant_apply_rows(int64_t n, const double* A, int64_t lda, const double* G, double2* tw, void* M,
-                                 int64_t ldm, bool out_f32, cudaStream_t s) {
-    twiddle_kernel<<<(unsigned)((n / 2 + 255) / 256), 256, 0, s>>>((int)n, tw);
+// c = Re F^{-1}(u) into G[0..N) from the spectrum already in G[N..3N) (Theorem 5.1: c = Omega^{-1} u).
+// The twiddle table may live in G[0..N): the CTA reads it before writing c.
+rmge_status circulant_from_spectrum(int64_t N, double* G, double2* tw, cudaStream_t s) {
+    twiddle_kernel<<<(unsigned)((N / 2 + 255) / 256), 256, 0, s>>>((int)N, tw);
     RMGE_LAUNCH_CHECK();
     FftArgs a{};
-    a.n = (int)n;
-    a.logn = ilog2(n);
+    a.n = (int)N;
+    a.logn = ilog2(N);
+    a.count = 1;
+    a.mode = 2;
+    a.nin = a.nout = (int)N;
+    a.spec = reinterpret_cast<const double2*>(G + N);
+    a.tw = tw;
+    a.dst = G;
+    return launch_fft(a, 1, s);
+}
+
+rmge_status circulant_apply_rows(int64_t n, int64_t N, const double* A, int64_t lda, const double* G, double2* tw,
+                                 void* M, int64_t ldm, bool out_f32, cudaStream_t s) {
+    twiddle_kernel<<<(unsigned)((N / 2 + 255) / 256), 256, 0, s>>>((int)N, tw);
+    RMGE_LAUNCH_CHECK();
+    FftArgs a{};
+    a.n = (int)N;
+    a.logn = ilog2(N);
     a.count = (int)n;
     a.mode = 1;
+    a.nin = a.nout = (int)n;
     a.cols = false;
     a.conj_spec = true;  // row of A C = cross-correlation of the row with c
     a.out_f32 = out_f32;
     a.src = A;
     a.lds = lda;
-    a.spec = reinterpret_cast<const double2*>(G + n);
+    a.spec = reinterpret_cast<const double2*>(G + N);
     a.tw = tw;
     a.dst = M;
     a.ldd = ldm;
     return launch_fft(a, (int)((n + 1) / 2), s);
 }
 
-rmge_status circulant_apply_cols(int64_t n, int64_t k, const double* G, double2* tw, bool transpose, const double* Y,
-                                 int64_t ldy, double* X, int64_t ldx, bool accumulate, const int* skip, cudaStream_t s) {
-    twiddle_kernel<<<(unsigned)((n / 2 + 255) / 256), 256, 0, s>>>((int)n, tw);
+rmge_status circulant_apply_cols(int64_t n, int64_t N, int64_t k, const double* G, double2* tw, bool transpose,
+                                 const double* Y, int64_t ldy, double* X, int64_t ldx, bool accumulate, const int* skip,
+                                 cudaStream_t s) {
+    twiddle_kernel<<<(unsigned)((N / 2 + 255) / 256), 256, 0, s>>>((int)N, tw);
     RMGE_LAUNCH_CHECK();
     FftArgs a{};
-    a.n = (int)n;
-    a.logn = ilog2(n);
+    a.n = (int)N;
+    a.logn = ilog2(N);
     a.count = (int)k;
     a.mode = 1;
+    a.nin = a.nout = (int)n;
     a.cols = true;
     a.conj_spec = transpose;  // C y: convolution; C^T y: correlation
     a.out_f32 = false;
     a.accumulate = accumulate;
     a.src = Y;
     a.lds = ldy;
-    a.spec = reinterpret_cast<const double2*>(G + n);
+    a.spec = reinterpret_cast<const double2*>(G + N);
     a.tw = tw;
     a.dst = X;
     a.ldd = ldx;

@@ -1,4 +1,5 @@
-// gen.cu -- random multiplier draws (Def. 4.1 Gaussian entries, Ex. 5.1 uniform entries).
+// gen.cu -- random multiplier draws (Def. 4.1 Gaussian entries, Ex. 5.1 uniform entries, Ex. 5.2 unit
+// spectra of unitary circulants).
 //
 // Counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): a 128-bit counter and a
 // 64-bit key pass through ten rounds, each two 32x32 multiplies (published multipliers) whose
@@ -85,6 +86,27 @@ __global__ void uniform_pm1_kernel(int64_t count, uint64_t seed, uint64_t subseq
     }
 }
 
+// Spectrum of a random unitary circulant of size N (Ex. 5.2): phases phi_j = m_j 2^-53 in [0, 1) are
+// entries j = 0 .. N/2 of the same stream (even entries from x0:x1, odd ones from x2:x3 of block j/2);
+// u_j = exp(2 pi phi_j sqrt(-1)) and u_{N-j} = conj(u_j) for 0 < j < N/2, while u_0 and u_{N/2} are
+// +1 if phi < 1/2 else -1.  The Hermitian symmetry makes the circulant real (and orthogonal).
+__global__ void unitary_spectrum_kernel(int64_t N, uint64_t seed, uint64_t subseq, double2* __restrict__ u) {
+    const int64_t h = N / 2;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= h; j += (int64_t)gridDim.x * blockDim.x) {
+        const U4 x = block_for((uint64_t)(j / 2), seed, subseq);
+        const uint64_t m = (j & 1) ? join53(x.z, x.w) : join53(x.x, x.y);
+        const double phi = (double)m * 0x1p-53;
+        if (j == 0 || j == h) {
+            u[j] = make_double2(phi < 0.5 ? 1.0 : -1.0, 0.0);
+        } else {
+            double sn, cs;
+            sincospi(2.0 * phi, &sn, &cs);
+            u[j] = make_double2(cs, sn);
+            u[N - j] = make_double2(cs, -sn);
+        }
+    }
+}
+
 int grid_for(int64_t pairs, int threads) {
     int64_t g = (pairs + threads - 1) / threads;
     const int64_t cap = 152 * 16;  // grid-stride beyond 16 blocks per SM
@@ -104,6 +126,12 @@ rmge_status launch_gaussian(int64_t count, uint64_t seed, uint64_t subseq, doubl
 rmge_status launch_gaussian(int64_t count, uint64_t seed, uint64_t subseq, float* out, cudaStream_t s) {
     const int64_t pairs = (count + 1) / 2;
     gaussian_f32_kernel<<<grid_for(pairs, 256), 256, 0, s>>>(count, seed, subseq, out);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
+rmge_status launch_unitary_spectrum(int64_t N, uint64_t seed, uint64_t subseq, double2* u, cudaStream_t s) {
+    unitary_spectrum_kernel<<<grid_for(N / 2 + 1, 256), 256, 0, s>>>(N, seed, subseq, u);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }

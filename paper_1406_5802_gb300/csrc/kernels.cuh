@@ -9,6 +9,7 @@ namespace rmge {
 rmge_status launch_gaussian(int64_t count, uint64_t seed, uint64_t subseq, double* out, cudaStream_t s);
 rmge_status launch_gaussian(int64_t count, uint64_t seed, uint64_t subseq, float* out, cudaStream_t s);
 rmge_status launch_uniform_pm1(int64_t count, uint64_t seed, uint64_t subseq, double* out, cudaStream_t s);
+rmge_status launch_unitary_spectrum(int64_t N, uint64_t seed, uint64_t subseq, double2* u, cudaStream_t s);
 
 // gemm.cu: C = alpha * op(A) * B + beta * C on the SIMT FMA pipes (op(A) = A, or A^T when trans_a).
 // A is M x K (or K x M when trans_a), B is K x N, C is M x N; all row-major.  beta == 0 never
@@ -138,13 +139,16 @@ rmge_status batched_solve(int64_t count, const int32_t* n, const int64_t* offA, 
                           int config, int ctas, void* ws, cudaStream_t s);
 
 // fft.cu: circulant multiplier (Theorem 5.1).  G = [c (n doubles) | u = F(c) (n double2)];
-// tw: n/2 double2 of scratch for the twiddle table.
-rmge_status circulant_spectrum(int64_t n, double* G, double2* tw, cudaStream_t s);
-// M = A C (rows of A correlated with c), M in FP64 or FP32.
-rmge_status circulant_apply_rows(int64_t n, const double* A, int64_t lda, const double* G, double2* tw, void* M,
-                                 int64_t ldm, bool out_f32, cudaStream_t s);
-// X (+)= C Y, or C^T Y when transpose, k columns, FP64; nothing when *skip != 0.
-rmge_status circulant_apply_cols(int64_t n, int64_t k, const double* G, double2* tw, bool transpose,
+// FFT kinds (fft.cu), N the transform length (n for a circulant, 2n for a Toeplitz multiplier, the
+// leading n x n block of an N x N circulant); G = [c (N) | u = F(c) (N complex)]; tw: N/2 double2.
+rmge_status circulant_spectrum(int64_t N, double* G, double2* tw, cudaStream_t s);
+// c = Re F^{-1}(u) from the spectrum in G (the drawn unitary circulant).
+rmge_status circulant_from_spectrum(int64_t N, double* G, double2* tw, cudaStream_t s);
+// M = A H (rows of A correlated with c), M in FP64 or FP32.
+rmge_status circulant_apply_rows(int64_t n, int64_t N, const double* A, int64_t lda, const double* G, double2* tw,
+                                 void* M, int64_t ldm, bool out_f32, cudaStream_t s);
+// X (+)= H Y, or H^T Y when transpose, k columns, FP64; nothing when *skip != 0.
+rmge_status circulant_apply_cols(int64_t n, int64_t N, int64_t k, const double* G, double2* tw, bool transpose,
                                  const double* Y, int64_t ldy, double* X, int64_t ldx, bool accumulate,
                                  const int* skip, cudaStream_t s);
 

@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(HERE, "_build", "librmge.so")
 # enums (include/rmge.h)
 GAUSSIAN, CIRCULANT_GAUSSIAN, CIRCULANT_UNIFORM = 0, 1, 2
 F64, F32, BF16_TC, F16_TC = 0, 1, 2, 3
-KINDS = {"gaussian": GAUSSIAN, "circulant": CIRCULANT_GAUSSIAN, "circulant_uniform": CIRCULANT_UNIFORM}
+KINDS = {"gaussian": GAUSSIAN, "circulant": CIRCULANT_GAUSSIAN, "circulant_uniform": CIRCULANT_UNIFORM,
+         "circulant_unitary": 3, "toeplitz": 4, "toeplitz_uniform": 5}
 PRECS = {"f64": F64, "f32": F32, "bf16": BF16_TC, "f16": F16_TC, "bf16x3": 4, "f16x3": 5, "f64x": 6}
 STATUS = {0: "RMGE_OK", 1: "RMGE_ERR_INVALID_ARG", 2: "RMGE_ERR_BREAKDOWN", 3: "RMGE_ERR_GROWTH",
           4: "RMGE_ERR_NOT_CONVERGED", 5: "RMGE_ERR_CUDA", 6: "RMGE_ERR_TIMEOUT", 7: "RMGE_ERR_WORKSPACE",
@@ -142,7 +143,7 @@ def empty_multiplier(kind, n, prec, device="cuda") -> torch.Tensor:
     kind, prec = _kind(kind), _prec(prec)
     if kind == GAUSSIAN:
         return torch.empty(n, n, dtype=factor_dtype(prec), device=device)
-    return torch.empty(3 * n, dtype=torch.float64, device=device)
+    return torch.empty((6 if kind >= 4 else 3) * n, dtype=torch.float64, device=device)
 
 
 def make_multiplier(kind, n, seed, subsequence=1, prec="f64", G=None) -> torch.Tensor:

@@ -45,6 +45,13 @@ def test_workspace_and_multiplier_sizes(lib):
     assert rmge.multiplier_bytes("gaussian", 256, "f32") == 256 * 256 * 4
     assert rmge.multiplier_bytes("circulant", 256, "f64") == 3 * 256 * 8
     assert rmge.multiplier_bytes("circulant", 16384, "f64") == 0
+    # the unitary circulant stores like the others; a Toeplitz multiplier stores its 2n circulant
+    assert rmge.multiplier_bytes("circulant_unitary", 8192, "f64") == 3 * 8192 * 8
+    assert rmge.multiplier_bytes("toeplitz", 4096, "f64") == 6 * 4096 * 8
+    assert rmge.multiplier_bytes("toeplitz_uniform", 64, "f32") == 6 * 64 * 8
+    assert rmge.multiplier_bytes("toeplitz", 8192, "f64") == 0  # its 16384-point transform is too long
+    assert rmge.multiplier_bytes("toeplitz", 1000, "f64") == 0  # not a power of two
+    assert rmge.workspace_size(1000, 1, "toeplitz", "f64") == 0
 
 
 def test_bad_arguments_are_rejected_without_gpu_work(lib):
