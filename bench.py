@@ -249,7 +249,8 @@ def extra_workloads(W, rmge, peaks, which=("precision", "batch", "grad")):
     return out
 
 
-FORMS = {"f64x": ("gaussian", "f64x"), "circ_f64": ("circulant", "f64"), "circ_f64x": ("circulant", "f64x")}
+FORMS = {"f64x": ("gaussian", "f64x"), "circ_f64": ("circulant", "f64"), "circ_f64x": ("circulant", "f64x"),
+         "unitary_f64x": ("circulant_unitary", "f64x"), "toeplitz_f64x": ("toeplitz", "f64x")}
 FORM_TEXT = {
     "f64x": "Gaussian G; A G and GENP's Schur updates as FP64 products emulated on the BF16 tensor cores (8 base-128 "
             "digits, 36 digit-pair MMAs, exact FP32 chunks, 64-bit fixed-point sums); pivot blocks, panels, solves, "
@@ -257,6 +258,8 @@ FORM_TEXT = {
     "circ_f64": "random circulant G (Gaussian first column) applied by FFT; GENP, solves and refinement in FP64",
     "circ_f64x": "random circulant G applied by FFT; GENP's Schur updates emulated on the BF16 tensor cores; solves and "
                  "refinement in FP64",
+    "unitary_f64x": "random unitary circulant G of Ex. 5.2 (real orthogonal, unit spectrum) applied by FFT; mixed form",
+    "toeplitz_f64x": "Toeplitz G = leading block of a 2n Gaussian circulant, applied by 2n-point FFTs; mixed form",
 }
 
 
@@ -335,8 +338,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other measured workloads")
     ap.add_argument("--extras", default="precision,batch,grad",
                     help="comma list of the other workloads (precision, batch, grad)")
-    ap.add_argument("--forms", default="f64x,circ_f64,circ_f64x",
-                    help="comma list of the other forms timed on the same inputs (f64x, circ_f64, circ_f64x; "
+    ap.add_argument("--forms", default="f64x,circ_f64,circ_f64x,unitary_f64x,toeplitz_f64x",
+                    help="comma list of the other forms timed on the same inputs (f64x, circ_f64, circ_f64x, "
+                         "unitary_f64x, toeplitz_f64x; "
                          "'none' for the main line only)")
     args = ap.parse_args()
     if args.impl == "reference":
