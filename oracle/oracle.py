@@ -65,6 +65,8 @@ def lib():
             "orc_rmge_solve": (C.c_int, [C.c_int, _i64, _i64, _dp, _dp, _dp, _dp, _dp, C.c_int,
                                          C.c_double, _dp, C.POINTER(C.c_int)]),
             "orc_solve_adjoint_gepp": (C.c_int, [_i64, _i64, _dp, _dp, _dp, _dp, _dp]),
+            "orc_rmge_solve_two_sided": (C.c_int, [C.c_int, _dp, C.c_int, _dp, _i64, _i64, _dp, _dp, _dp, _dp,
+                                                   C.c_int, C.c_double, _dp, C.POINTER(C.c_int)]),
             "orc_genp_complex": (C.c_int, [_i64, _dp, _dp, _dp, _dp]),
         }
         for name, (res, args) in sig.items():
@@ -287,6 +289,24 @@ def rmge_solve(kind, A, H, B, max_iters=10, be_tol=1e-13):
     iters = C.c_int(0)
     info = lib().orc_rmge_solve(int(kind), n, k, A, _f64(H), B, X, LU, int(max_iters), float(be_tol),
                                 berr, C.byref(iters))
+    return {"X": X, "LU": LU, "info": info, "iters": iters.value,
+            "berr": [float(v) for v in berr[: iters.value + 1]] if info == 0 else []}
+
+
+def rmge_solve_two_sided(kindF, F, kindH, H, A, B, max_iters=10, be_tol=1e-13):
+    """Two-sided randomized GENP solve (F A H y = F b, x = H y); kind None (or < 0) for the identity.
+    Returns dict(X, LU, info, iters, berr[list])."""
+    A, B = _f64(A), _cols(B)
+    n, k = B.shape
+    kF = -1 if kindF is None else int(kindF)
+    kH = -1 if kindH is None else int(kindH)
+    dummy = np.zeros(1, np.float64)
+    X = np.zeros((n, k), np.float64)
+    LU = np.empty((n, n), np.float64)
+    berr = np.full(max_iters + 1, np.nan)
+    iters = C.c_int(0)
+    info = lib().orc_rmge_solve_two_sided(kF, _f64(F) if kF >= 0 else dummy, kH, _f64(H) if kH >= 0 else dummy,
+                                          n, k, A, B, X, LU, int(max_iters), float(be_tol), berr, C.byref(iters))
     return {"X": X, "LU": LU, "info": info, "iters": iters.value,
             "berr": [float(v) for v in berr[: iters.value + 1]] if info == 0 else []}
 

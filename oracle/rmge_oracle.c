@@ -560,6 +560,65 @@ int orc_rmge_solve(int kind, int64_t n, int64_t k, const double* A, const double
     return 0;
 }
 
+/* D (n x n) = the dense matrix of a multiplier, or the identity when kind < 0 (one-sided forms). */
+static void multiplier_or_identity(int kind, int64_t n, const double* H, double* D) {
+    if (kind < 0) {
+        memset(D, 0, sizeof(double) * (size_t)(n * n));
+        for (int64_t i = 0; i < n; ++i) D[i * n + i] = 1.0;
+    } else {
+        orc_multiplier_dense(kind, n, H, D);
+    }
+}
+
+/*
+ * Two-sided randomized GENP solve (Fact 4.1: A^{-1} = H (F A H)^{-1} F, so F A H y = F b and x = H y):
+ * M = F A H, GENP M = L U, X = H U^{-1} L^{-1} F B, then refinement sweeps
+ * X <- X + H U^{-1} L^{-1} F (B - A X) until the backward error is <= be_tol or max_iters sweeps ran.
+ * kindF < 0 means F = I (post-multiplication only), kindH < 0 means H = I (pre-multiplication only).
+ * Outputs as for orc_rmge_solve.
+ */
+int orc_rmge_solve_two_sided(int kindF, const double* F, int kindH, const double* H, int64_t n, int64_t k,
+                             const double* A, const double* B, double* X, double* LU, int max_iters, double be_tol,
+                             double* berr, int* iters) {
+    double* DF = (double*)malloc(sizeof(double) * (size_t)(n * n));
+    double* DH = (double*)malloc(sizeof(double) * (size_t)(n * n));
+    double* T = (double*)malloc(sizeof(double) * (size_t)(n * n));
+    double* V = (double*)malloc(sizeof(double) * (size_t)(n * k));
+    double* Y = (double*)malloc(sizeof(double) * (size_t)(n * k));
+    multiplier_or_identity(kindF, n, F, DF);
+    multiplier_or_identity(kindH, n, H, DH);
+    orc_matmul(n, n, n, A, DH, T);   /* A H */
+    orc_matmul(n, n, n, DF, T, LU);  /* F A H */
+    const int info = orc_genp(n, LU);
+    *iters = 0;
+    if (info == 0) {
+        /* X = H U^{-1} L^{-1} F B */
+        orc_matmul(n, n, k, DF, B, Y);
+        orc_lu_solve(n, k, LU, Y);
+        orc_matmul(n, n, k, DH, Y, X);
+        double be = orc_backward_error(n, k, A, X, B);
+        berr[0] = be;
+        int it = 0;
+        while (it < max_iters && !(be <= be_tol)) {
+            orc_residual(n, k, A, X, B, V);
+            orc_matmul(n, n, k, DF, V, Y);
+            orc_lu_solve(n, k, LU, Y);
+            orc_matmul(n, n, k, DH, Y, V);
+            for (int64_t i = 0; i < n * k; ++i) X[i] += V[i];
+            be = orc_backward_error(n, k, A, X, B);
+            ++it;
+            berr[it] = be;
+        }
+        *iters = it;
+    }
+    free(DF);
+    free(DH);
+    free(T);
+    free(V);
+    free(Y);
+    return info;
+}
+
 /*
  * Reference gradient of a loss L(X) with X = A^{-1} B, given Wbar = dL/dX:
  * dB = A^{-T} Wbar by GEPP on A^T (independent of the GENP factors),
