@@ -201,6 +201,39 @@ rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, co
                                 void* ws, size_t ws_bytes, rmge_stream_t stream);
 
 /*
+ * Pre-multiplied and two-sided forms (Fact 4.1: A^{-1} = (F A)^{-1} F and A^{-1} = H (F A H)^{-1} F,
+ * so F A H y = F b and x = H y; Remark 5.1 proposes random pre- and post-multipliers together).
+ * F (pre-multiplier) and H (post-multiplier) are multipliers drawn by rmge_make_multiplier, with
+ * kinds kindF and kindH and the storage above; either pointer may be NULL, meaning the identity
+ * (H = NULL is pre-multiplication alone; F = NULL is the post-multiplied solve of the calls above).
+ * Data precision FP64 only: RMGE_F64, or RMGE_F64X_TC (dense products emulated on the tensor cores);
+ * other precisions return RMGE_ERR_UNSUPPORTED, as do FFT kinds with an unsupported n.
+ *
+ * rmge_workspace_size_two_sided: scratch bytes for any of the three calls with these kinds (pass the
+ * kind of an absent side as RMGE_GAUSSIAN); 0 for an invalid request.
+ * rmge_apply_two_sided: M = F A H (n x n, FP64, row-major).  With both F and H, T (n x n, leading
+ * dimension ldt >= n, caller-owned FP64 device memory) receives A H first; T may be NULL otherwise.
+ * The FFT kinds apply F to the columns (circular convolution) and H to the rows (correlation).
+ * rmge_solve_two_sided: X = H U^{-1} L^{-1} F B from the factors of M (rmge_factor).
+ * rmge_refine_two_sided: sweeps X <- X + H U^{-1} L^{-1} F (B - A X), residuals in FP64, with the
+ * stopping rule, berr and iters of rmge_refine.
+ * Errors as for the one-sided calls; every call is asynchronous on `stream`.
+ */
+size_t rmge_workspace_size_two_sided(int64_t n, int64_t nrhs, rmge_mult_kind kindF, rmge_mult_kind kindH,
+                                     rmge_prec prec);
+rmge_status rmge_apply_two_sided(rmge_mult_kind kindF, const void* F, rmge_mult_kind kindH, const void* H, int64_t n,
+                                 const double* A, int64_t lda, double* M, int64_t ldm, double* T, int64_t ldt,
+                                 rmge_prec prec, void* ws, size_t ws_bytes, rmge_stream_t stream);
+rmge_status rmge_solve_two_sided(rmge_mult_kind kindF, const void* F, rmge_mult_kind kindH, const void* H, int64_t n,
+                                 int64_t nrhs, const void* LU, int64_t ldlu, const double* B, int64_t ldb, double* X,
+                                 int64_t ldx, rmge_prec prec, void* ws, size_t ws_bytes, rmge_stream_t stream);
+rmge_status rmge_refine_two_sided(rmge_mult_kind kindF, const void* F, rmge_mult_kind kindH, const void* H, int64_t n,
+                                  int64_t nrhs, const double* A, int64_t lda, const void* LU, int64_t ldlu,
+                                  const double* B, int64_t ldb, double* X, int64_t ldx, rmge_prec prec,
+                                  int32_t max_iters, double be_tol, double* berr, int32_t* iters, void* ws,
+                                  size_t ws_bytes, rmge_stream_t stream);
+
+/*
  * rmge_solve for callers that cannot allocate device memory.  The paper has no counterpart: this is
  * a deployment convenience.  Some callers must not call cudaMalloc at the point where they solve:
  * a serving loop with latency guarantees (a device allocation can synchronise the whole device),

@@ -216,6 +216,72 @@ rmge_status refine_loop(rmge_mult_kind kind, rmge_prec prec, bool trans, int64_t
     return refine_finish(w.st, max_iters, berr, iters, s);
 }
 
+// ---- two-sided forms (Fact 4.1: A^{-1} = H (F A H)^{-1} F), FP64 data ------------------------------------
+
+// The layout kind whose workspace serves both multipliers: the longer FFT wins.
+rmge_mult_kind layout_kind(const void* F, rmge_mult_kind kF, const void* H, rmge_mult_kind kH) {
+    if ((F != nullptr && is_toeplitz(kF)) || (H != nullptr && is_toeplitz(kH))) return RMGE_TOEPLITZ_GAUSSIAN;
+    if ((F != nullptr && is_circ(kF)) || (H != nullptr && is_circ(kH))) return RMGE_CIRCULANT_GAUSSIAN;
+    return RMGE_GAUSSIAN;
+}
+
+// d (+)= P y for a multiplier P (FP64 or FFT kind), or d (+)= y when P is the identity (NULL); n x k.
+rmge_status apply_side(rmge_mult_kind kind, const void* P, int64_t n, int64_t k, const double* y, int64_t ldy,
+                       double* d, int64_t ldd, bool accumulate, const int* skip, const Ws& w, cudaStream_t s) {
+    if (P == nullptr)
+        return accumulate ? add_update<double>(n, k, y, ldy, d, ldd, skip, s)
+                          : copy_matrix<double, double>(n, k, y, ldy, d, ldd, skip, s);
+    return apply_g_cols(kind, RMGE_F64, n, k, P, false, y, ldy, d, ldd, accumulate, skip, w, s);
+}
+
+// X (+)= H U^{-1} L^{-1} F V with FP64 factors, w.Y as scratch.
+rmge_status two_sided_correction(rmge_mult_kind kF, const void* F, rmge_mult_kind kH, const void* H, int64_t n,
+                                 int64_t k, const void* LU, int64_t ldlu, const double* V, int64_t ldv, double* X,
+                                 int64_t ldx, bool accumulate, const Ws& w, int epoch, const int* skip,
+                                 cudaStream_t s) {
+    RMGE_TRY(apply_side(kF, F, n, k, V, ldv, w.Y, k, false, skip, w, s));
+    RMGE_TRY(lu_solve(RMGE_F64, false, n, k, LU, ldlu, w.Y, k, w, epoch, skip, s));
+    return apply_side(kH, H, n, k, w.Y, k, X, ldx, accumulate, skip, w, s);
+}
+
+// M = A H (FP64 data; emulated on the tensor cores for RMGE_F64X_TC and a dense H).
+rmge_status right_multiply(rmge_mult_kind kH, const void* H, rmge_prec prec, int64_t n, const double* A, int64_t lda,
+                           double* M, int64_t ldm, const Ws& w, cudaStream_t s) {
+    if (is_circ(kH))
+        return circulant_apply_rows(n, fft_len(kH, n), A, lda, static_cast<const double*>(H), w.tw, M, ldm, false, s);
+    if (prec == RMGE_F64X_TC) {
+        const OzUpdate oz = oz_buffers(w, n);
+        return oz_gemm(n, n, n, kOzSlices, 1.0, A, lda, static_cast<const double*>(H), n, 0.0, M, ldm, oz.planesA,
+                       oz.planesB, oz.ea, oz.eb, nullptr, nullptr, &w.st->error, nullptr, s);
+    }
+    return gemm<double>(false, n, n, n, 1.0, A, lda, static_cast<const double*>(H), n, 0.0, M, ldm, nullptr, s);
+}
+
+// M = F A: the columns of A convolved with F's first column for the FFT kinds, else a product.
+rmge_status left_multiply(rmge_mult_kind kF, const void* F, rmge_prec prec, int64_t n, const double* A, int64_t lda,
+                          double* M, int64_t ldm, const Ws& w, cudaStream_t s) {
+    if (is_circ(kF))
+        return circulant_apply_cols(n, fft_len(kF, n), n, static_cast<const double*>(F), w.tw, false, A, lda, M, ldm,
+                                    false, nullptr, s);
+    if (prec == RMGE_F64X_TC) {
+        const OzUpdate oz = oz_buffers(w, n);
+        return oz_gemm(n, n, n, kOzSlices, 1.0, static_cast<const double*>(F), n, A, lda, 0.0, M, ldm, oz.planesA,
+                       oz.planesB, oz.ea, oz.eb, nullptr, nullptr, &w.st->error, nullptr, s);
+    }
+    return gemm<double>(false, n, n, n, 1.0, static_cast<const double*>(F), n, A, lda, 0.0, M, ldm, nullptr, s);
+}
+
+bool two_sided_ok(rmge_mult_kind kF, const void* F, rmge_mult_kind kH, const void* H, int64_t n, rmge_prec prec,
+                  rmge_status* why) {
+    *why = RMGE_ERR_INVALID_ARG;
+    if (!valid_kind(kF) || !valid_kind(kH) || !valid_prec(prec)) return false;
+    *why = RMGE_ERR_UNSUPPORTED;
+    if (data_prec(prec) != RMGE_F64) return false;
+    if (F != nullptr && is_circ(kF) && !circ_ok(kF, n)) return false;
+    if (H != nullptr && is_circ(kH) && !circ_ok(kH, n)) return false;
+    return true;
+}
+
 }  // namespace
 
 WsLayout ws_layout(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec) {
@@ -445,6 +511,77 @@ rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, co
                              berr, iters, w, 3, s));
     if (dA != nullptr) return outer_neg(n, nrhs, dB, lddb, X, ldx, dA, ldda, s);
     return RMGE_OK;
+}
+
+size_t rmge_workspace_size_two_sided(int64_t n, int64_t nrhs, rmge_mult_kind kindF, rmge_mult_kind kindH,
+                                     rmge_prec prec) {
+    rmge_status why;
+    const int present = 1;  // both sides are sized as present
+    const void* P = &present;
+    if (!check_dims(n, nrhs) || !two_sided_ok(kindF, P, kindH, P, n, prec, &why)) return 0;
+    return ws_layout(n, nrhs, layout_kind(P, kindF, P, kindH), prec).total;
+}
+
+rmge_status rmge_apply_two_sided(rmge_mult_kind kindF, const void* F, rmge_mult_kind kindH, const void* H, int64_t n,
+                                 const double* A, int64_t lda, double* M, int64_t ldm, double* T, int64_t ldt,
+                                 rmge_prec prec, void* ws, size_t ws_bytes, rmge_stream_t stream) {
+    rmge_status why;
+    if (!check_dims(n, 1) || A == nullptr || M == nullptr || lda < n || ldm < n ||
+        (F != nullptr && H != nullptr && (T == nullptr || ldt < n)))
+        return RMGE_ERR_INVALID_ARG;
+    if (!two_sided_ok(kindF, F, kindH, H, n, prec, &why)) return why;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Ws w{};
+    RMGE_TRY(carve(ws, ws_bytes, n, 1, layout_kind(F, kindF, H, kindH), prec, &w));
+    if (F == nullptr && H == nullptr) return copy_matrix<double, double>(n, n, A, lda, M, ldm, nullptr, s);
+    if (F == nullptr) return right_multiply(kindH, H, prec, n, A, lda, M, ldm, w, s);
+    if (H == nullptr) return left_multiply(kindF, F, prec, n, A, lda, M, ldm, w, s);
+    RMGE_TRY(right_multiply(kindH, H, prec, n, A, lda, T, ldt, w, s));
+    return left_multiply(kindF, F, prec, n, T, ldt, M, ldm, w, s);
+}
+
+rmge_status rmge_solve_two_sided(rmge_mult_kind kindF, const void* F, rmge_mult_kind kindH, const void* H, int64_t n,
+                                 int64_t nrhs, const void* LU, int64_t ldlu, const double* B, int64_t ldb, double* X,
+                                 int64_t ldx, rmge_prec prec, void* ws, size_t ws_bytes, rmge_stream_t stream) {
+    rmge_status why;
+    if (!check_dims(n, nrhs) || LU == nullptr || B == nullptr || X == nullptr || ldlu < n || ldb < nrhs ||
+        ldx < nrhs)
+        return RMGE_ERR_INVALID_ARG;
+    if (!two_sided_ok(kindF, F, kindH, H, n, prec, &why)) return why;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Ws w{};
+    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, layout_kind(F, kindF, H, kindH), prec, &w, false));
+    RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, 0, nullptr, 0, s));
+    return two_sided_correction(kindF, F, kindH, H, n, nrhs, LU, ldlu, B, ldb, X, ldx, false, w, 1, nullptr, s);
+}
+
+rmge_status rmge_refine_two_sided(rmge_mult_kind kindF, const void* F, rmge_mult_kind kindH, const void* H, int64_t n,
+                                  int64_t nrhs, const double* A, int64_t lda, const void* LU, int64_t ldlu,
+                                  const double* B, int64_t ldb, double* X, int64_t ldx, rmge_prec prec,
+                                  int32_t max_iters, double be_tol, double* berr, int32_t* iters, void* ws,
+                                  size_t ws_bytes, rmge_stream_t stream) {
+    rmge_status why;
+    if (!check_dims(n, nrhs) || A == nullptr || LU == nullptr || B == nullptr || X == nullptr || lda < n ||
+        ldlu < n || ldb < nrhs || ldx < nrhs || max_iters < 0 || max_iters > kMaxSweeps || !(be_tol >= 0.0))
+        return RMGE_ERR_INVALID_ARG;
+    if (!two_sided_ok(kindF, F, kindH, H, n, prec, &why)) return why;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Ws w{};
+    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, layout_kind(F, kindF, H, kindH), prec, &w));
+    RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, (int)(3 * nrhs), berr, max_iters + 1, s));
+    RMGE_TRY(abs_sums_max(n, A, lda, false, w.st, s));
+    const int* stop = &w.st->stop;
+    for (int it = 0; it <= max_iters; ++it) {
+        // R = B - A X in FP64, the backward error and the stopping test (Sec. 1.2, Sec. 7.1)
+        RMGE_TRY(copy_matrix<double, double>(n, nrhs, B, ldb, w.R, nrhs, stop, s));
+        RMGE_TRY(gemm<double>(false, n, nrhs, n, -1.0, A, lda, X, ldx, 1.0, w.R, nrhs, stop, s));
+        RMGE_TRY(backward_error(n, nrhs, w.R, nrhs, X, ldx, B, ldb, w.st, w.colred, it, be_tol, max_iters, berr, s));
+        if (it == max_iters) break;
+        // X <- X + H U^{-1} L^{-1} F R
+        RMGE_TRY(two_sided_correction(kindF, F, kindH, H, n, nrhs, LU, ldlu, w.R, nrhs, X, ldx, true, w, 3 + 2 * it,
+                                      stop, s));
+    }
+    return refine_finish(w.st, max_iters, berr, iters, s);
 }
 
 size_t rmge_batched_workspace_size(int64_t nmax, int32_t ctas) {

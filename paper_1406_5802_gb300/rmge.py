@@ -28,7 +28,8 @@ STATUS = {0: "RMGE_OK", 1: "RMGE_ERR_INVALID_ARG", 2: "RMGE_ERR_BREAKDOWN", 3: "
 
 EXPORTED = ["rmge_multiplier_bytes", "rmge_workspace_size", "rmge_make_multiplier", "rmge_apply_multiplier",
             "rmge_factor", "rmge_solve", "rmge_refine", "rmge_solve_backward", "rmge_status_string",
-            "rmge_kernel_launches", "rmge_solve_workspace_size", "rmge_solve_noalloc", "rmge_noalloc_capacity"]
+            "rmge_kernel_launches", "rmge_solve_workspace_size", "rmge_solve_noalloc", "rmge_noalloc_capacity",
+            "rmge_workspace_size_two_sided", "rmge_apply_two_sided", "rmge_solve_two_sided", "rmge_refine_two_sided"]
 
 
 class RmgeError(RuntimeError):
@@ -65,6 +66,14 @@ def load_library(path: str = LIB_PATH):
         "rmge_solve_workspace_size": (_sz, [_i64, _i64, C.c_int, C.c_int]),
         "rmge_solve_noalloc": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, C.c_int, _vp]),
         "rmge_noalloc_capacity": (_sz, []),
+        "rmge_workspace_size_two_sided": (_sz, [_i64, _i64, C.c_int, C.c_int, C.c_int]),
+        "rmge_apply_two_sided": (C.c_int, [C.c_int, _vp, C.c_int, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
+                                           C.c_int, _vp, _sz, _vp]),
+        "rmge_solve_two_sided": (C.c_int, [C.c_int, _vp, C.c_int, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
+                                           C.c_int, _vp, _sz, _vp]),
+        "rmge_refine_two_sided": (C.c_int, [C.c_int, _vp, C.c_int, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp,
+                                            _i64, _vp, _i64, C.c_int, C.c_int32, C.c_double, _vp, _vp, _vp, _sz,
+                                            _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -244,6 +253,72 @@ def solve_backward(kind, LU, G, X, dX, prec="f64", want_dA=True, A=None, max_ite
         _prec(prec), refine_it, float(be_tol), _p(berr) if refine_it > 0 else None, _p(iters) if refine_it > 0 else None,
         _p(ws), ws.numel(), _stream()))
     return dB, dA, berr, iters
+
+
+def _side(kind):
+    return GAUSSIAN if kind is None else _kind(kind)
+
+
+def workspace_two_sided(n, nrhs, kindF, kindH, prec, device="cuda") -> torch.Tensor:
+    nb = int(load_library().rmge_workspace_size_two_sided(int(n), int(nrhs), _side(kindF), _side(kindH), _prec(prec)))
+    if nb == 0:
+        raise ValueError("invalid workspace request")
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def apply_two_sided(kindF, F, kindH, H, A, prec="f64", M=None, ws=None) -> torch.Tensor:
+    """M = F A H (F or H None for the identity)."""
+    L = _cuda_lib()
+    n = A.shape[0]
+    if M is None:
+        M = torch.empty(n, n, dtype=torch.float64, device=A.device)
+    T = torch.empty(n, n, dtype=torch.float64, device=A.device) if (F is not None and H is not None) else None
+    if ws is None:
+        ws = workspace_two_sided(n, 1, kindF, kindH, prec)
+    _check("rmge_apply_two_sided", L.rmge_apply_two_sided(
+        _side(kindF), _p(F), _side(kindH), _p(H), n, _p(A), _ld(A), _p(M), _ld(M), _p(T), n if T is not None else 0,
+        _prec(prec), _p(ws), ws.numel(), _stream()))
+    return M
+
+
+def solve_two_sided(kindF, F, kindH, H, LU, B, prec="f64", X=None, ws=None) -> torch.Tensor:
+    L = _cuda_lib()
+    n, k = B.shape
+    if X is None:
+        X = torch.empty(n, k, dtype=torch.float64, device=B.device)
+    if ws is None:
+        ws = workspace_two_sided(n, k, kindF, kindH, prec)
+    _check("rmge_solve_two_sided", L.rmge_solve_two_sided(
+        _side(kindF), _p(F), _side(kindH), _p(H), n, k, _p(LU), _ld(LU), _p(B), _ld(B), _p(X), _ld(X), _prec(prec),
+        _p(ws), ws.numel(), _stream()))
+    return X
+
+
+def refine_two_sided(kindF, F, kindH, H, A, LU, B, X, prec="f64", max_iters=10, be_tol=1e-13, ws=None):
+    L = _cuda_lib()
+    n, k = B.shape
+    berr = torch.empty(max_iters + 1, dtype=torch.float64, device=B.device)
+    iters = torch.zeros(1, dtype=torch.int32, device=B.device)
+    if ws is None:
+        ws = workspace_two_sided(n, k, kindF, kindH, prec)
+    _check("rmge_refine_two_sided", L.rmge_refine_two_sided(
+        _side(kindF), _p(F), _side(kindH), _p(H), n, k, _p(A), _ld(A), _p(LU), _ld(LU), _p(B), _ld(B), _p(X), _ld(X),
+        _prec(prec), int(max_iters), float(be_tol), _p(berr), _p(iters), _p(ws), ws.numel(), _stream()))
+    return berr, iters
+
+
+def gesv_two_sided(kindF, kindH, A, B, seed, prec="f64", max_iters=10, be_tol=1e-13):
+    """F A H y = F b, x = H y (Fact 4.1) with F drawn from subsequence 1 and H from subsequence 2 of the
+    seed's stream; kindF / kindH None for the identity.  Returns dict(X, LU, F, H, info, growth, berr, iters)."""
+    n, k = B.shape
+    ws = workspace_two_sided(n, k, kindF, kindH, prec)
+    F = make_multiplier(kindF, n, seed, 1, prec) if kindF is not None else None
+    H = make_multiplier(kindH, n, seed, 2, prec) if kindH is not None else None
+    M = apply_two_sided(kindF, F, kindH, H, A, prec, ws=ws)
+    info, growth = factor(M, prec, ws=ws)
+    X = solve_two_sided(kindF, F, kindH, H, M, B, prec, ws=ws)
+    berr, iters = refine_two_sided(kindF, F, kindH, H, A, M, B, X, prec, max_iters, be_tol, ws=ws)
+    return {"X": X, "LU": M, "F": F, "H": H, "info": info, "growth": growth, "berr": berr, "iters": iters}
 
 
 def gesv(kind, A, B, seed, prec="f64", max_iters=10, be_tol=1e-13, subsequence=1):
