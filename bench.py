@@ -250,7 +250,8 @@ def extra_workloads(W, rmge, peaks, which=("precision", "batch", "grad")):
 
 
 FORMS = {"f64x": ("gaussian", "f64x"), "circ_f64": ("circulant", "f64"), "circ_f64x": ("circulant", "f64x"),
-         "unitary_f64x": ("circulant_unitary", "f64x"), "toeplitz_f64x": ("toeplitz", "f64x")}
+         "unitary_f64x": ("circulant_unitary", "f64x"), "toeplitz_f64x": ("toeplitz", "f64x"),
+         "two_sided_circ_f64x": (("circulant", "circulant"), "f64x")}
 FORM_TEXT = {
     "f64x": "Gaussian G; A G and GENP's Schur updates as FP64 products emulated on the BF16 tensor cores (8 base-128 "
             "digits, 36 digit-pair MMAs, exact FP32 chunks, 64-bit fixed-point sums); pivot blocks, panels, solves, "
@@ -260,6 +261,8 @@ FORM_TEXT = {
                  "refinement in FP64",
     "unitary_f64x": "random unitary circulant G of Ex. 5.2 (real orthogonal, unit spectrum) applied by FFT; mixed form",
     "toeplitz_f64x": "Toeplitz G = leading block of a 2n Gaussian circulant, applied by 2n-point FFTs; mixed form",
+    "two_sided_circ_f64x": "random circulants on both sides (F A H y = F b, x = H y; Fact 4.1, Remark 5.1), "
+                           "applied by FFT; mixed form",
 }
 
 
@@ -269,21 +272,39 @@ def timed_form(rmge, A, Bm, M, X, kind, prec, args, stream, barrier, world, valu
     import torch
     import torch.distributed as dist
     n, k = A.shape[0], Bm.shape[1]
-    ws = rmge.workspace(n, k, kind, prec)
-    G = rmge.empty_multiplier(kind, n, prec)
+    two = isinstance(kind, tuple)
+    if two:
+        kF, kH = kind
+        ws = rmge.workspace_two_sided(n, k, kF, kH, prec)
+        F, H = rmge.empty_multiplier(kF, n, prec), rmge.empty_multiplier(kH, n, prec)
+        T = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    else:
+        ws = rmge.workspace(n, k, kind, prec)
+        G = rmge.empty_multiplier(kind, n, prec)
 
     def one(i, rec=None):
-        rmge.make_multiplier(kind, n, SEED + i, 1, prec, G=G)
+        if two:
+            rmge.make_multiplier(kF, n, SEED + i, 1, prec, G=F)
+            rmge.make_multiplier(kH, n, SEED + i, 2, prec, G=H)
+        else:
+            rmge.make_multiplier(kind, n, SEED + i, 1, prec, G=G)
         if rec is not None:
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a0.record(stream)
-        rmge.apply_multiplier(kind, A, G, prec, M=M, ws=ws)
+        if two:
+            rmge.apply_two_sided(kF, F, kH, H, A, prec, M=M, ws=ws, T=T)
+        else:
+            rmge.apply_multiplier(kind, A, G, prec, M=M, ws=ws)
         if rec is not None:
             a1.record(stream)
             rec.append((a0, a1))
         info, _ = rmge.factor(M, prec, ws=ws)
-        rmge.solve(kind, M, G, Bm, prec, X=X, ws=ws)
-        berr, it = rmge.refine(kind, A, M, G, Bm, X, prec, MAX_ITERS, BE_TOL, ws=ws)
+        if two:
+            rmge.solve_two_sided(kF, F, kH, H, M, Bm, prec, X=X, ws=ws)
+            berr, it = rmge.refine_two_sided(kF, F, kH, H, A, M, Bm, X, prec, MAX_ITERS, BE_TOL, ws=ws)
+        else:
+            rmge.solve(kind, M, G, Bm, prec, X=X, ws=ws)
+            berr, it = rmge.refine(kind, A, M, G, Bm, X, prec, MAX_ITERS, BE_TOL, ws=ws)
         return info, berr, it
 
     for i in range(args.warmup):
@@ -317,7 +338,7 @@ def timed_form(rmge, A, Bm, M, X, kind, prec, args, stream, barrier, world, valu
                            "unit": "TFLOP/s (BF16 MMA)", "frac": None,
                            "traffic": OZ_AG_TRAFFIC_BYTES if n == N_SYS else None,
                            "algorithmic_bytes": 3 * n * n * 8 + 2 * 8 * n * n * 2}
-    del ws, G
+    del ws
     return out
 
 
@@ -338,9 +359,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other measured workloads")
     ap.add_argument("--extras", default="precision,batch,grad",
                     help="comma list of the other workloads (precision, batch, grad)")
-    ap.add_argument("--forms", default="f64x,circ_f64,circ_f64x,unitary_f64x,toeplitz_f64x",
+    ap.add_argument("--forms", default="f64x,circ_f64,circ_f64x,unitary_f64x,toeplitz_f64x,two_sided_circ_f64x",
                     help="comma list of the other forms timed on the same inputs (f64x, circ_f64, circ_f64x, "
-                         "unitary_f64x, toeplitz_f64x; "
+                         "unitary_f64x, toeplitz_f64x, two_sided_circ_f64x; "
                          "'none' for the main line only)")
     args = ap.parse_args()
     if args.impl == "reference":

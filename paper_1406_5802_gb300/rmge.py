@@ -266,13 +266,16 @@ def workspace_two_sided(n, nrhs, kindF, kindH, prec, device="cuda") -> torch.Ten
     return torch.empty(nb, dtype=torch.uint8, device=device)
 
 
-def apply_two_sided(kindF, F, kindH, H, A, prec="f64", M=None, ws=None) -> torch.Tensor:
-    """M = F A H (F or H None for the identity)."""
+def apply_two_sided(kindF, F, kindH, H, A, prec="f64", M=None, ws=None, T=None) -> torch.Tensor:
+    """M = F A H (F or H None for the identity); T: n x n FP64 scratch for A H when both are given."""
     L = _cuda_lib()
     n = A.shape[0]
     if M is None:
         M = torch.empty(n, n, dtype=torch.float64, device=A.device)
-    T = torch.empty(n, n, dtype=torch.float64, device=A.device) if (F is not None and H is not None) else None
+    if F is None or H is None:
+        T = None
+    elif T is None:
+        T = torch.empty(n, n, dtype=torch.float64, device=A.device)
     if ws is None:
         ws = workspace_two_sided(n, 1, kindF, kindH, prec)
     _check("rmge_apply_two_sided", L.rmge_apply_two_sided(
