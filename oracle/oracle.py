@@ -67,6 +67,9 @@ def lib():
             "orc_solve_adjoint_gepp": (C.c_int, [_i64, _i64, _dp, _dp, _dp, _dp, _dp]),
             "orc_rmge_solve_two_sided": (C.c_int, [C.c_int, _dp, C.c_int, _dp, _i64, _i64, _dp, _dp, _dp, _dp,
                                                    C.c_int, C.c_double, _dp, C.POINTER(C.c_int)]),
+            "orc_qr": (None, [_i64, _i64, _dp, _dp, _dp]),
+            "orc_lowrank_multiplier_dense": (None, [C.c_int, _i64, _i64, _dp, _dp]),
+            "orc_lowrank": (None, [C.c_int, _i64, _i64, _i64, _dp, _dp, _dp, _dp]),
             "orc_genp_complex": (C.c_int, [_i64, _dp, _dp, _dp, _dp]),
         }
         for name, (res, args) in sig.items():
@@ -309,6 +312,40 @@ def rmge_solve_two_sided(kindF, F, kindH, H, A, B, max_iters=10, be_tol=1e-13):
                                           n, k, A, B, X, LU, int(max_iters), float(be_tol), berr, C.byref(iters))
     return {"X": X, "LU": LU, "info": info, "iters": iters.value,
             "berr": [float(v) for v in berr[: iters.value + 1]] if info == 0 else []}
+
+
+def qr(B):
+    """Thin Householder QR with diag(R) >= 0: (Q, R)."""
+    B = _f64(B)
+    m, l = B.shape
+    Q = np.empty((m, l), np.float64)
+    R = np.empty((l, l), np.float64)
+    lib().orc_qr(m, l, B, Q, R)
+    return Q, R
+
+
+def lowrank_multiplier(kind, n, l, seed, subseq=1):
+    """Algorithm 6.1's multiplier: a dense n x l Gaussian for kind 0 (the first n*l entries of the Gaussian
+    stream), else the first column c (n,) of the circulant whose n x l leading block is used."""
+    if kind == GAUSSIAN:
+        return gaussian(n * l, seed, subseq).reshape(n, l)
+    return make_multiplier(kind, n, seed, subseq)
+
+
+def lowrank_multiplier_dense(kind, n, l, H):
+    out = np.empty((int(n), int(l)), np.float64)
+    lib().orc_lowrank_multiplier_dense(int(kind), int(n), int(l), _f64(H), out)
+    return out
+
+
+def lowrank(kind, A, H, l):
+    """Algorithm 6.1: (Q, Z) with Q = Q(A H) and Z = Q^T A."""
+    A = _f64(A)
+    m, n = A.shape
+    Q = np.empty((m, int(l)), np.float64)
+    Z = np.empty((int(l), n), np.float64)
+    lib().orc_lowrank(int(kind), m, n, int(l), A, _f64(H), Q, Z)
+    return Q, Z
 
 
 def solve_adjoint_gepp(A, X, Wbar):

@@ -619,6 +619,104 @@ int orc_rmge_solve_two_sided(int kindF, const double* F, int kindH, const double
     return info;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Low-rank approximation (Sec. 6, Algorithm 6.1)                           */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Thin Householder QR of B (m x l, m >= l): B = Q R, Q (m x l) with orthonormal columns, R (l x l)
+ * upper triangular.  Column j is reflected by I - 2 v v^T / v^T v with v = x - alpha e_1,
+ * alpha = -sign(x_1) ||x||; Q is the product of the reflections applied to the first l columns of
+ * the identity.  Finally each j with R_jj < 0 has row j of R and column j of Q negated, so that
+ * diag(R) >= 0 and the factorization of a full-rank B is unique.
+ */
+void orc_qr(int64_t m, int64_t l, const double* B, double* Q, double* R) {
+    double* W = (double*)malloc(sizeof(double) * (size_t)(m * l));
+    double* V = (double*)malloc(sizeof(double) * (size_t)(m * l));  /* reflection j in column j, rows j.. */
+    memcpy(W, B, sizeof(double) * (size_t)(m * l));
+    memset(V, 0, sizeof(double) * (size_t)(m * l));
+    for (int64_t j = 0; j < l; ++j) {
+        double nx = 0.0;
+        for (int64_t i = j; i < m; ++i) nx += W[i * l + j] * W[i * l + j];
+        nx = sqrt(nx);
+        const double x1 = W[j * l + j];
+        const double alpha = (x1 >= 0.0) ? -nx : nx;
+        double vv = 0.0;
+        for (int64_t i = j; i < m; ++i) {
+            const double v = W[i * l + j] - ((i == j) ? alpha : 0.0);
+            V[i * l + j] = v;
+            vv += v * v;
+        }
+        if (vv > 0.0) {
+            for (int64_t c = j; c < l; ++c) {
+                double d = 0.0;
+                for (int64_t i = j; i < m; ++i) d += V[i * l + j] * W[i * l + c];
+                const double f = 2.0 * d / vv;
+                for (int64_t i = j; i < m; ++i) W[i * l + c] -= f * V[i * l + j];
+            }
+        }
+        /* keep v^T v with the reflection for forming Q */
+        V[j * l + j] = (vv > 0.0) ? V[j * l + j] : 0.0;
+        W[j * l + j] = (vv > 0.0) ? W[j * l + j] : x1;
+        for (int64_t c = 0; c < l; ++c) R[j * l + c] = (c >= j) ? W[j * l + c] : 0.0;
+    }
+    /* Q = H_0 H_1 ... H_{l-1} [I_l; 0]: apply the reflections in reverse order */
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t c = 0; c < l; ++c) Q[i * l + c] = (i == c) ? 1.0 : 0.0;
+    for (int64_t j = l - 1; j >= 0; --j) {
+        double vv = 0.0;
+        for (int64_t i = j; i < m; ++i) vv += V[i * l + j] * V[i * l + j];
+        if (vv == 0.0) continue;
+        for (int64_t c = 0; c < l; ++c) {
+            double d = 0.0;
+            for (int64_t i = j; i < m; ++i) d += V[i * l + j] * Q[i * l + c];
+            const double f = 2.0 * d / vv;
+            for (int64_t i = j; i < m; ++i) Q[i * l + c] -= f * V[i * l + j];
+        }
+    }
+    for (int64_t j = 0; j < l; ++j) {
+        if (R[j * l + j] < 0.0) {
+            for (int64_t c = 0; c < l; ++c) R[j * l + c] = -R[j * l + c];
+            for (int64_t i = 0; i < m; ++i) Q[i * l + j] = -Q[i * l + j];
+        }
+    }
+    free(W);
+    free(V);
+}
+
+/*
+ * The n x l multiplier of Algorithm 6.1 as a dense matrix: kind 0, H itself (n x l); kinds 1, 2, 3,
+ * the n x l leading block of the n x n circulant with first column c = H (Sec. 7.2's Toeplitz
+ * multipliers: the maximal leading submatrices of random circulants), D_ij = c_{(i - j) mod n}.
+ */
+void orc_lowrank_multiplier_dense(int kind, int64_t n, int64_t l, const double* H, double* D) {
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < l; ++j) D[i * l + j] = (kind == 0) ? H[i * l + j] : H[((i - j) % n + n) % n];
+}
+
+/*
+ * Algorithm 6.1 (low-rank approximation, after Halko, Martinsson and Tropp): B = A H (m x l),
+ * Q = Q(B) by orc_qr (orthonormal columns sharing B's range), Z = Q^T A (l x n); Q Z = Q Q^T A has
+ * rank at most l and approximates A.
+ */
+void orc_lowrank(int kind, int64_t m, int64_t n, int64_t l, const double* A, const double* H, double* Q, double* Z) {
+    double* D = (double*)malloc(sizeof(double) * (size_t)(n * l));
+    double* B = (double*)malloc(sizeof(double) * (size_t)(m * l));
+    double* R = (double*)malloc(sizeof(double) * (size_t)(l * l));
+    orc_lowrank_multiplier_dense(kind, n, l, H, D);
+    orc_matmul(m, n, l, A, D, B);
+    orc_qr(m, l, B, Q, R);
+    for (int64_t i = 0; i < l; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            double z = 0.0;
+            for (int64_t t = 0; t < m; ++t) z += Q[t * l + i] * A[t * n + j];
+            Z[i * n + j] = z;
+        }
+    free(D);
+    free(B);
+    free(R);
+}
+
 /*
  * Reference gradient of a loss L(X) with X = A^{-1} B, given Wbar = dL/dX:
  * dB = A^{-T} Wbar by GEPP on A^T (independent of the GENP factors),

@@ -59,6 +59,20 @@ def orthogonal_factor_system(n: int, k: int, sigma_min: float, seed: int):
     return A, B
 
 
+def lowrank_test_matrix(n: int, r: int, seed: int, tail: float = 1e-10):
+    """The low-rank test matrices of Sec. 7.2: A = S diag(sigma) T^T with S, T Haar-orthogonal n x n,
+    sigma_j = 1/j for j <= r and sigma_j = tail beyond (so ||A|| = 1 and the numerical rank is r).
+    Returns (A, S_r): S_r = the first r columns of S, a basis of A's leading r-dimensional left singular
+    space."""
+    g = rng(seed)
+    S = haar_orthogonal(n, g)
+    T = haar_orthogonal(n, g)
+    sigma = np.full(n, float(tail))
+    sigma[:r] = 1.0 / np.arange(1, r + 1)
+    A = (S * sigma[None, :]) @ T.T
+    return A, np.ascontiguousarray(S[:, :r])
+
+
 def orthogonal_factor_system_torch(n: int, k: int, sigma_min: float, seed: int, device: str):
     """Same recipe as orthogonal_factor_system, drawn with torch on ``device`` (used for the large
     workloads, whose host-side QR would take minutes).  Returns float64 torch tensors on ``device``."""
