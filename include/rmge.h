@@ -234,6 +234,33 @@ rmge_status rmge_refine_two_sided(rmge_mult_kind kindF, const void* F, rmge_mult
                                   size_t ws_bytes, rmge_stream_t stream);
 
 /*
+ * Randomized low-rank approximation (Sec. 6, Algorithm 6.1, after Halko, Martinsson and Tropp): for
+ * A (m x n, FP64 row-major) and an n x l multiplier H, Q (m x l) is an orthonormal basis of the range
+ * of A H and Z = Q^T A (l x n), so that A ~ Q Z = Q Q^T A (rank <= l).  The paper shows that l equal
+ * to the numerical rank r (no oversampling) suffices with Gaussian H.
+ * Multipliers: RMGE_GAUSSIAN, H is n x l FP64 (leading dimension l); the circulant kinds
+ * (RMGE_CIRCULANT_GAUSSIAN, _UNIFORM, _UNITARY; n a power of two <= 8192), H is the n x l leading block
+ * of the circulant stored as by rmge_make_multiplier (3n FP64; Sec. 7.2's Toeplitz multipliers),
+ * applied by FFT.  1 <= l <= 64, l <= m, l <= n.
+ * rmge_lowrank_multiplier draws H (the Gaussian entries are the first n l of the stream of
+ * rmge_make_multiplier's Gaussian kind).  rmge_lowrank_basis computes B = A H, then Q by CholeskyQR2
+ * (two passes of Q^T Q = R^T R, Q <- Q R^{-1}; R has a positive diagonal, so Q is the unique thin QR
+ * factor of a full-rank B); it needs B well-conditioned enough for the Cholesky of its Gram matrix
+ * (kappa(A H) well below 1e8).  *info (device int32, may be NULL) is 0, or j > 0 when the Cholesky met
+ * a non-positive pivot at column j (Q is then not orthonormal).  ws: rmge_lowrank_workspace_size bytes,
+ * 256-byte aligned.  rmge_lowrank_project computes Z = Q^T A.  Errors: RMGE_ERR_INVALID_ARG,
+ * RMGE_ERR_WORKSPACE; all calls are asynchronous on `stream`.
+ */
+size_t rmge_lowrank_workspace_size(rmge_mult_kind kind, int64_t m, int64_t n, int32_t l);
+rmge_status rmge_lowrank_multiplier(rmge_mult_kind kind, int64_t n, int32_t l, uint64_t seed, uint64_t subsequence,
+                                    double* H, rmge_stream_t stream);
+rmge_status rmge_lowrank_basis(rmge_mult_kind kind, int64_t m, int64_t n, int32_t l, const double* A, int64_t lda,
+                               const double* H, double* Q, int64_t ldq, int32_t* info, void* ws, size_t ws_bytes,
+                               rmge_stream_t stream);
+rmge_status rmge_lowrank_project(int64_t m, int64_t n, int32_t l, const double* Q, int64_t ldq, const double* A,
+                                 int64_t lda, double* Z, int64_t ldz, rmge_stream_t stream);
+
+/*
  * rmge_solve for callers that cannot allocate device memory.  The paper has no counterpart: this is
  * a deployment convenience.  Some callers must not call cudaMalloc at the point where they solve:
  * a serving loop with latency guarantees (a device allocation can synchronise the whole device),

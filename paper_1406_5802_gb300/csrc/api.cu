@@ -584,6 +584,46 @@ rmge_status rmge_refine_two_sided(rmge_mult_kind kindF, const void* F, rmge_mult
     return refine_finish(w.st, max_iters, berr, iters, s);
 }
 
+// ---- low-rank approximation (Sec. 6, Algorithm 6.1) ------------------------------------------------
+
+static bool lowrank_args_ok(rmge_mult_kind kind, int64_t m, int64_t n, int32_t l) {
+    if ((int)kind < (int)RMGE_GAUSSIAN || (int)kind > (int)RMGE_CIRCULANT_UNITARY) return false;
+    if (m < 1 || n < 1 || m > RMGE_MAX_N || n > RMGE_MAX_N || l < 1 || l > kLowRankMaxL || l > m || l > n) return false;
+    return kind == RMGE_GAUSSIAN || circ_ok(kind, n);
+}
+
+size_t rmge_lowrank_workspace_size(rmge_mult_kind kind, int64_t m, int64_t n, int32_t l) {
+    if (!lowrank_args_ok(kind, m, n, l)) return 0;
+    return lowrank_workspace_bytes(n, l, kind != RMGE_GAUSSIAN);
+}
+
+rmge_status rmge_lowrank_multiplier(rmge_mult_kind kind, int64_t n, int32_t l, uint64_t seed, uint64_t subsequence,
+                                    double* H, rmge_stream_t stream) {
+    if (!lowrank_args_ok(kind, n, n, l) || H == nullptr) return RMGE_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (kind == RMGE_GAUSSIAN) return launch_gaussian(n * (int64_t)l, seed, subsequence, H, s);
+    return rmge_make_multiplier(kind, n, seed, subsequence, RMGE_F64, H, stream);
+}
+
+rmge_status rmge_lowrank_basis(rmge_mult_kind kind, int64_t m, int64_t n, int32_t l, const double* A, int64_t lda,
+                               const double* H, double* Q, int64_t ldq, int32_t* info, void* ws, size_t ws_bytes,
+                               rmge_stream_t stream) {
+    if (!lowrank_args_ok(kind, m, n, l) || A == nullptr || H == nullptr || Q == nullptr || lda < n || ldq < l)
+        return RMGE_ERR_INVALID_ARG;
+    if (ws == nullptr || ((uintptr_t)ws & 255) != 0 || ws_bytes < lowrank_workspace_bytes(n, l, kind != RMGE_GAUSSIAN))
+        return RMGE_ERR_WORKSPACE;
+    if (kind != RMGE_GAUSSIAN && ((uintptr_t)H & 15) != 0) return RMGE_ERR_INVALID_ARG;
+    return lowrank_basis((int)kind, m, n, l, A, lda, H, Q, ldq, info, ws, reinterpret_cast<cudaStream_t>(stream));
+}
+
+rmge_status rmge_lowrank_project(int64_t m, int64_t n, int32_t l, const double* Q, int64_t ldq, const double* A,
+                                 int64_t lda, double* Z, int64_t ldz, rmge_stream_t stream) {
+    if (!lowrank_args_ok(RMGE_GAUSSIAN, m, n, l) || Q == nullptr || A == nullptr || Z == nullptr || ldq < l ||
+        lda < n || ldz < n)
+        return RMGE_ERR_INVALID_ARG;
+    return lowrank_project(m, n, l, Q, ldq, A, lda, Z, ldz, reinterpret_cast<cudaStream_t>(stream));
+}
+
 size_t rmge_batched_workspace_size(int64_t nmax, int32_t ctas) {
     if (nmax < 1 || nmax > 4096 || ctas < 1 || ctas > 65535) return 0;
     return batched_scratch_bytes(nmax, ctas);

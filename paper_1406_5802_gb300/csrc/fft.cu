@@ -229,6 +229,28 @@ rmge_status circulant_apply_rows(int64_t n, int64_t N, const double* A, int64_t 
     return launch_fft(a, (int)((n + 1) / 2), s);
 }
 
+rmge_status circulant_apply_rows_block(int64_t rows, int64_t n, int64_t nout, const double* A, int64_t lda,
+                                       const double* G, double2* tw, double* M, int64_t ldm, cudaStream_t s) {
+    twiddle_kernel<<<(unsigned)((n / 2 + 255) / 256), 256, 0, s>>>((int)n, tw);
+    RMGE_LAUNCH_CHECK();
+    FftArgs a{};
+    a.n = (int)n;
+    a.logn = ilog2(n);
+    a.count = (int)rows;
+    a.mode = 1;
+    a.nin = (int)n;
+    a.nout = (int)nout;
+    a.cols = false;
+    a.conj_spec = true;  // row of A C = cross-correlation of the row with c
+    a.src = A;
+    a.lds = lda;
+    a.spec = reinterpret_cast<const double2*>(G + n);
+    a.tw = tw;
+    a.dst = M;
+    a.ldd = ldm;
+    return launch_fft(a, (int)((rows + 1) / 2), s);
+}
+
 rmge_status circulant_apply_cols(int64_t n, int64_t N, int64_t k, const double* G, double2* tw, bool transpose,
                                  const double* Y, int64_t ldy, double* X, int64_t ldx, bool accumulate, const int* skip,
                                  cudaStream_t s) {

@@ -147,9 +147,20 @@ rmge_status circulant_from_spectrum(int64_t N, double* G, double2* tw, cudaStrea
 // M = A H (rows of A correlated with c), M in FP64 or FP32.
 rmge_status circulant_apply_rows(int64_t n, int64_t N, const double* A, int64_t lda, const double* G, double2* tw,
                                  void* M, int64_t ldm, bool out_f32, cudaStream_t s);
+// M (rows x nout) = the first nout columns of A C for an n x n circulant C (A: rows x n), FP64.
+rmge_status circulant_apply_rows_block(int64_t rows, int64_t n, int64_t nout, const double* A, int64_t lda,
+                                       const double* G, double2* tw, double* M, int64_t ldm, cudaStream_t s);
 // X (+)= H Y, or H^T Y when transpose, k columns, FP64; nothing when *skip != 0.
 rmge_status circulant_apply_cols(int64_t n, int64_t N, int64_t k, const double* G, double2* tw, bool transpose,
                                  const double* Y, int64_t ldy, double* X, int64_t ldx, bool accumulate,
                                  const int* skip, cudaStream_t s);
+
+// lowrank.cu: Algorithm 6.1 (B = A H, Q = Q(B) by CholeskyQR2, Z = Q^T A); kind 0 a dense n x l H, else
+// the n x l leading block of an n x n circulant (G storage); ws: lowrank_workspace_bytes.
+size_t lowrank_workspace_bytes(int64_t n, int l, bool fft);
+rmge_status lowrank_basis(int kind, int64_t m, int64_t n, int l, const double* A, int64_t lda, const double* H,
+                          double* Q, int64_t ldq, int32_t* info, void* ws, cudaStream_t s);
+rmge_status lowrank_project(int64_t m, int64_t n, int l, const double* Q, int64_t ldq, const double* A, int64_t lda,
+                            double* Z, int64_t ldz, cudaStream_t s);
 
 }  // namespace rmge

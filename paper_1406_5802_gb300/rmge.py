@@ -29,7 +29,8 @@ STATUS = {0: "RMGE_OK", 1: "RMGE_ERR_INVALID_ARG", 2: "RMGE_ERR_BREAKDOWN", 3: "
 EXPORTED = ["rmge_multiplier_bytes", "rmge_workspace_size", "rmge_make_multiplier", "rmge_apply_multiplier",
             "rmge_factor", "rmge_solve", "rmge_refine", "rmge_solve_backward", "rmge_status_string",
             "rmge_kernel_launches", "rmge_solve_workspace_size", "rmge_solve_noalloc", "rmge_noalloc_capacity",
-            "rmge_workspace_size_two_sided", "rmge_apply_two_sided", "rmge_solve_two_sided", "rmge_refine_two_sided"]
+            "rmge_workspace_size_two_sided", "rmge_apply_two_sided", "rmge_solve_two_sided", "rmge_refine_two_sided",
+            "rmge_lowrank_workspace_size", "rmge_lowrank_multiplier", "rmge_lowrank_basis", "rmge_lowrank_project"]
 
 
 class RmgeError(RuntimeError):
@@ -74,6 +75,11 @@ def load_library(path: str = LIB_PATH):
         "rmge_refine_two_sided": (C.c_int, [C.c_int, _vp, C.c_int, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp,
                                             _i64, _vp, _i64, C.c_int, C.c_int32, C.c_double, _vp, _vp, _vp, _sz,
                                             _vp]),
+        "rmge_lowrank_workspace_size": (_sz, [C.c_int, _i64, _i64, C.c_int32]),
+        "rmge_lowrank_multiplier": (C.c_int, [C.c_int, _i64, C.c_int32, _u64, _u64, _vp, _vp]),
+        "rmge_lowrank_basis": (C.c_int, [C.c_int, _i64, _i64, C.c_int32, _vp, _i64, _vp, _vp, _i64, _vp, _vp, _sz,
+                                         _vp]),
+        "rmge_lowrank_project": (C.c_int, [_i64, _i64, C.c_int32, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -322,6 +328,39 @@ def gesv_two_sided(kindF, kindH, A, B, seed, prec="f64", max_iters=10, be_tol=1e
     X = solve_two_sided(kindF, F, kindH, H, M, B, prec, ws=ws)
     berr, iters = refine_two_sided(kindF, F, kindH, H, A, M, B, X, prec, max_iters, be_tol, ws=ws)
     return {"X": X, "LU": M, "F": F, "H": H, "info": info, "growth": growth, "berr": berr, "iters": iters}
+
+
+def lowrank_multiplier(kind, n, l, seed, subsequence=1) -> torch.Tensor:
+    """Algorithm 6.1's multiplier: an n x l Gaussian, or a circulant (3n storage) whose n x l leading block
+    is used."""
+    L = _cuda_lib()
+    k = _kind(kind)
+    H = torch.empty((n, l) if k == GAUSSIAN else (3 * n,), dtype=torch.float64, device="cuda")
+    _check("rmge_lowrank_multiplier", L.rmge_lowrank_multiplier(k, int(n), int(l), int(seed), int(subsequence),
+                                                                _p(H), _stream()))
+    return H
+
+
+def lowrank(kind, A, H, l, Q=None, Z=None, ws=None):
+    """Algorithm 6.1 on a device matrix A (m x n): (Q, Z, info) with Q = Q(A H) (m x l) and Z = Q^T A."""
+    L = _cuda_lib()
+    m, n = A.shape
+    k = _kind(kind)
+    if Q is None:
+        Q = torch.empty(m, l, dtype=torch.float64, device=A.device)
+    if Z is None:
+        Z = torch.empty(l, n, dtype=torch.float64, device=A.device)
+    if ws is None:
+        nb = int(L.rmge_lowrank_workspace_size(k, int(m), int(n), int(l)))
+        if nb == 0:
+            raise ValueError("invalid low-rank request")
+        ws = torch.empty(nb, dtype=torch.uint8, device=A.device)
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check("rmge_lowrank_basis", L.rmge_lowrank_basis(k, int(m), int(n), int(l), _p(A), _ld(A), _p(H), _p(Q), _ld(Q),
+                                                      _p(info), _p(ws), ws.numel(), _stream()))
+    _check("rmge_lowrank_project", L.rmge_lowrank_project(int(m), int(n), int(l), _p(Q), _ld(Q), _p(A), _ld(A), _p(Z),
+                                                          _ld(Z), _stream()))
+    return Q, Z, info
 
 
 def gesv(kind, A, B, seed, prec="f64", max_iters=10, be_tol=1e-13, subsequence=1):
