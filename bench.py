@@ -118,7 +118,7 @@ def run_reference(args):
     return 0
 
 
-def extra_workloads(W, rmge, peaks, which=("precision", "batch", "grad")):
+def extra_workloads(W, rmge, peaks, which=("precision", "batch", "grad", "lowrank")):
     """The other measured workloads (one JSON object each, added to the main line): the n = 16384
     precision comparison (the FP64 form against the tensor-core forms with FP64 refinement: emulated FP64
     products (f64x), three-pass and one-pass BF16/FP16 splits), the batch of 4096 uneven systems in one
@@ -207,6 +207,57 @@ def extra_workloads(W, rmge, peaks, which=("precision", "batch", "grad")):
                              "tuned": {"config": tune["config"], "ctas": tune["ctas"]}}
     except Exception as e:
         out["batch_4096"] = {"error": repr(e)}
+
+    # -- low-rank approximation (Algorithm 6.1): n = 8192, r = l = 32, Sec. 7.2's test matrices -------------
+    try:
+        if "lowrank" not in which:
+            raise LookupError("not selected")
+        n, r = 8192, 32
+        g = torch.Generator(device="cuda")
+        g.manual_seed(W.SEED_BASE + 6)
+
+        def haar(m):
+            Qh, Rh = torch.linalg.qr(torch.randn(m, m, generator=g, dtype=torch.float64, device="cuda"))
+            return Qh * torch.sign(torch.diagonal(Rh))[None, :]
+
+        S, T = haar(n), haar(n)
+        sig = torch.full((n,), 1e-10, dtype=torch.float64, device="cuda")
+        sig[:r] = 1.0 / torch.arange(1, r + 1, dtype=torch.float64, device="cuda")
+        A = (S * sig[None, :]) @ T.T
+        Sr = S[:, :r].contiguous()
+        del S, T
+        res = {"workload": "n=8192, A = S diag(sigma) T^T with sigma_j = 1/j (j <= 32), 1e-10 beyond; l = r = 32 "
+                           "(no oversampling); Q = Q(A H) by CholeskyQR2 and Z = Q^T A"}
+        for kind in ("gaussian", "circulant_unitary"):
+            H = rmge.lowrank_multiplier(kind, n, r, W.SEED_BASE + 6, 1)
+            Q, Z, info = rmge.lowrank(kind, A, H, r)
+            torch.cuda.synchronize()
+            t0, t1 = ev(), ev()
+            reps = 5
+            t0.record()
+            for _ in range(reps):
+                rmge.lowrank(kind, A, H, r, Q=Q, Z=Z)
+            t1.record()
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1) / reps
+            # residual norms (checks, outside the timed region): rn1 = ||Q Q^T S_r - S_r||_2 exactly,
+            # rn2 = ||A - Q Z||_2 by 30 power iterations
+            rn1 = float(torch.linalg.matrix_norm(Q @ (Q.T @ Sr) - Sr, 2).item())
+            v = torch.randn(n, 1, generator=g, dtype=torch.float64, device="cuda")
+            for _ in range(30):
+                w = A @ v - Q @ (Z @ v)
+                v = A.T @ w - Z.T @ (Q.T @ w)
+                v = v / torch.linalg.vector_norm(v)
+            rn2 = float(torch.linalg.vector_norm(A @ v - Q @ (Z @ v)).item())
+            flops = 2.0 * n * n * r * (1 if kind == "gaussian" else 0) + 2.0 * n * n * r + 4.0 * n * r * r
+            res[kind] = {"ms": ms, "info": int(info.item()), "rn1": rn1, "rn2": rn2,
+                         "fp64_tflops_gemm_part": flops / (ms / 1e3) / 1e12,
+                         "note": "A H by FP64 GEMM" if kind == "gaussian" else "A H by FFT row correlation (8192-point)"}
+        out["lowrank_n8192"] = res
+        del A, Sr
+        torch.cuda.empty_cache()
+    except Exception as e:
+        out["lowrank_n8192"] = {"error": repr(e)}
 
     # -- differentiation: 64 systems, n = 2048, FP32, forward + backward --------------------------------
     # Two forms of the same batch: FP32 factors with FP64 FGMRES sweeps (at most 3 cycles per solve: every
@@ -357,8 +408,8 @@ def main():
     ap.add_argument("--impl", default="rmge", choices=["rmge", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other measured workloads")
-    ap.add_argument("--extras", default="precision,batch,grad",
-                    help="comma list of the other workloads (precision, batch, grad)")
+    ap.add_argument("--extras", default="precision,batch,grad,lowrank",
+                    help="comma list of the other workloads (precision, batch, grad, lowrank)")
     ap.add_argument("--forms", default="f64x,circ_f64,circ_f64x,unitary_f64x,toeplitz_f64x,two_sided_circ_f64x",
                     help="comma list of the other forms timed on the same inputs (f64x, circ_f64, circ_f64x, "
                          "unitary_f64x, toeplitz_f64x, two_sided_circ_f64x; "
