@@ -33,7 +33,7 @@ struct DevState {
 };
 
 // Triangular-solve tiling (rows per block, right-hand sides per block column).
-constexpr int kTrsvRows = 32;
+constexpr int kTrsvRows = 64;
 constexpr int kTrsvCols = 2;
 constexpr int kLowRankMaxL = 64;  // columns of the low-rank basis (Algorithm 6.1's l)
 // Refinement sweeps one rmge_refine call may run.

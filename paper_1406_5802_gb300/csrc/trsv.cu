@@ -45,8 +45,9 @@ template <typename T>
 __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t nrhs, const T* __restrict__ LU,
                                                   int64_t ld, T* B, int64_t ldb, DevState* st, int* flags,
                                                   int epoch, const int* skip) {
-    __shared__ T cs[TB][TB + 1];  // off-diagonal coefficient tile
-    __shared__ T cd[TB][TB + 1];  // diagonal block
+    extern __shared__ __align__(16) unsigned char trsv_smem[];
+    T (*cs)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(trsv_smem);  // off-diagonal coefficient tile
+    T (*cd)[TB + 1] = cs + TB;                                     // diagonal block
     __shared__ T ys[TB][KC];
     __shared__ T rd[TB];  // reciprocals of the diagonal (non-unit kinds)
     __shared__ int my_ticket;
@@ -163,7 +164,12 @@ rmge_status trsv(int kind, int64_t n, int64_t nrhs, const T* LU, int64_t ldlu, T
     const int64_t nblk = (n + TB - 1) / TB;
     const int64_t ncb = (nrhs + KC - 1) / KC;
     const int64_t grid = nblk * ncb;
-    trsv_kernel<T><<<(unsigned)grid, NT, 0, s>>>(kind, n, nrhs, LU, ldlu, B, ldb, st, flags, epoch, skip);
+    const size_t smem = 2 * (size_t)TB * (TB + 1) * sizeof(T);
+    if (cudaFuncSetAttribute(trsv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RMGE_ERR_CUDA;
+    }
+    trsv_kernel<T><<<(unsigned)grid, NT, smem, s>>>(kind, n, nrhs, LU, ldlu, B, ldb, st, flags, epoch, skip);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }
