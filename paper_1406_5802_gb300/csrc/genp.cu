@@ -15,6 +15,7 @@
 #include <climits>
 
 #include "kernels.cuh"
+#include "pivot_block.cuh"
 
 namespace rmge {
 namespace {
@@ -27,58 +28,32 @@ __device__ __forceinline__ bool finite_nonzero(T v) {
     return v != T(0) && isfinite(v);
 }
 
-// One CTA factors the pivot block in shared memory.  GB300 retires 2 FP64 operations per clock per
-// SM, so the kernel keeps every lane of every FP64 instruction busy: step s first scales column s of L
-// by the reciprocal of the pivot (one division per step, formed by the thread that finished the
-// pivot), then the (b-s-1)^2 trailing entries are spread evenly over the 256 threads, the entry index
-// e split into (row, column) by a multiply-shift reciprocal of the width instead of an integer division.
+// One CTA factors the pivot block in shared memory (pivot_block_genp, 256 threads).
+struct CtaSync {
+    __device__ void operator()() const { __syncthreads(); }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256) diag_factor_kernel(int64_t k, int b, T* __restrict__ M, int64_t ldm,
                                                           DevState* st) {
-    __shared__ T a[NB * LDS];
+    __shared__ T a[NB * kPivotLds];
     __shared__ T rp;
     if (*(volatile int*)&st->halt) return;
     const int tid = threadIdx.x;
     T* blk = M + k * ldm + k;
     for (int i = tid >> 6; i < b; i += 4)
-        if ((tid & 63) < b) a[i * LDS + (tid & 63)] = blk[i * ldm + (tid & 63)];
+        if ((tid & 63) < b) a[i * kPivotLds + (tid & 63)] = blk[i * ldm + (tid & 63)];
     __syncthreads();
-    if (tid == 0) rp = T(1) / a[0];
-    __syncthreads();
-
-    int s = 0;
-    bool broke = false;
-    for (; s < b; ++s) {
-        const T piv = a[s * LDS + s];
-        if (!finite_nonzero(piv)) {  // uniform: every thread read the same pivot
-            broke = true;
-            break;
-        }
-        const int w = b - s - 1;
-        if (w == 0) break;
-        if (tid < w) a[(s + 1 + tid) * LDS + s] *= rp;  // column s of L
-        __syncthreads();
-        // e < w^2 <= 63^2: floor(e / w) = (e * ceil(2^20 / w)) >> 20 exactly for e < 2^20 / w
-        const unsigned mw = ((1u << 20) + (unsigned)w - 1u) / (unsigned)w;
-        const T* us = a + s * LDS + s + 1;
-        for (int e = tid; e < w * w; e += 256) {
-            const int ii = (int)(((unsigned)e * mw) >> 20), jj = e - ii * w;
-            T* dst = a + (s + 1 + ii) * LDS + s + 1 + jj;
-            const T v = fma(-a[(s + 1 + ii) * LDS + s], us[jj], *dst);
-            *dst = v;
-            if (ii == 0 && jj == 0) rp = T(1) / v;  // the next pivot is final now
-        }
-        __syncthreads();
-    }
-    if (broke) {
+    const int broke = pivot_block_genp<T, 256>(a, b, &rp, tid, CtaSync{});
+    if (broke != 0) {
         if (tid == 0) {
-            atomicMin(&st->info, (int)(k + s + 1));
+            atomicMin(&st->info, (int)(k + broke));
             atomicExch(&st->halt, 1);
         }
         return;
     }
     for (int i = tid >> 6; i < b; i += 4)
-        if ((tid & 63) < b) blk[i * ldm + (tid & 63)] = a[i * LDS + (tid & 63)];
+        if ((tid & 63) < b) blk[i * ldm + (tid & 63)] = a[i * kPivotLds + (tid & 63)];
 }
 
 // Panel of pivot step k by substitution against the factored pivot block (in shared memory):
@@ -247,14 +222,18 @@ rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const
 // row k of U12 carries u_kk, so the pair is first balanced by an exact power of two per k (oz_kmax);
 // without it the per-row scaling of L21 and per-column scaling of U12 pair the large column of a small
 // pivot with the large rows of other pivots and the update loses most of its relative accuracy.
+// The update launch of step k also factors the pivot block of step k + 1 (CTA 0 takes the tile holding it
+// alone), so only the first pivot block has a launch of its own.
 rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s) {
     constexpr int PT = 16;
     RMGE_TRY(maxabs<double>(n, n, M, ldm, false, &st->maxabs_m, s));
     int64_t step = 0;
     for (int64_t k = 0; k < n; k += NB, ++step) {
         const int b = (int)((n - k) < NB ? (n - k) : NB);
-        diag_factor_kernel<double><<<1, 256, 0, s>>>(k, b, M, ldm, st);
-        RMGE_LAUNCH_CHECK();
+        if (k == 0) {  // every later pivot block is factored inside the previous step's update launch
+            diag_factor_kernel<double><<<1, 256, 0, s>>>(k, b, M, ldm, st);
+            RMGE_LAUNCH_CHECK();
+        }
         const int64_t rest = n - k - b;
         if (rest <= 0) break;
         const int tiles = (int)((rest + PT - 1) / PT);
@@ -262,10 +241,12 @@ rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, cons
         RMGE_LAUNCH_CHECK();
         const double* L21 = M + (k + b) * ldm + k;
         const double* U12 = M + k * ldm + k + b;
+        double* E = M + (k + b) * ldm + (k + b);
         unsigned long long* kmA = oz.kmax + 128 * step;
         RMGE_TRY(oz_kmax(rest, rest, b, L21, ldm, U12, ldm, kmA, kmA + 64, s));
-        RMGE_TRY(oz_gemm(rest, rest, b, kOzSlices, -1.0, L21, ldm, U12, ldm, 1.0, M + (k + b) * ldm + (k + b), ldm,
-                         oz.planesA, oz.planesB, oz.ea, oz.eb, kmA, kmA + 64, &st->error, &st->halt, s));
+        const OzFuse next{E, ldm, (int)(rest < NB ? rest : NB), k + b, &st->info, &st->halt};
+        RMGE_TRY(oz_gemm(rest, rest, b, kOzSlices, -1.0, L21, ldm, U12, ldm, 1.0, E, ldm, oz.planesA, oz.planesB,
+                         oz.ea, oz.eb, kmA, kmA + 64, &st->error, &st->halt, s, &next));
     }
     RMGE_TRY(maxabs<double>(n, n, M, ldm, true, &st->maxabs_u, s));
     return RMGE_OK;

@@ -48,10 +48,21 @@ constexpr int kOzSlices = 8;
 size_t oz_plane_bytes(int64_t rows, int64_t k, int s);
 rmge_status oz_kmax(int64_t M, int64_t N, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
                     unsigned long long* kmaxA, unsigned long long* kmaxB, cudaStream_t st);
+// The pivot block of the next GENP step, factored inside the update launch (K <= 64, 8 slices): the
+// b x b block at D (b <= 64, leading dimension ldd) must lie in the first 128 x 64 tile of C; a
+// breakdown at its step s records k + s in *info (atomicMin) and raises *halt.
+struct OzFuse {
+    double* D;
+    int64_t ldd;
+    int b;
+    int64_t k;
+    int* info;
+    int* halt;
+};
 rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* planesA, void* planesB,
                     int* ea, int* eb, const unsigned long long* kmaxA, const unsigned long long* kmaxB, int* err,
-                    const int* halt, cudaStream_t st);
+                    const int* halt, cudaStream_t st, const OzFuse* fuse = nullptr);
 struct OzUpdate {
     void* planesA;
     void* planesB;

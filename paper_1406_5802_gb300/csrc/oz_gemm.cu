@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <climits>
 
+#include "pivot_block.cuh"
 #include "tc_common.cuh"
 
 namespace rmge {
@@ -332,6 +333,19 @@ struct UpdParams {
     int64_t ldc;
     int* err;
     const int* halt;
+    // the next pivot block (GENP), factored by CTA 0 after its single tile, which contains the block;
+    // D == nullptr: no fused factorization
+    double* D;
+    int64_t ldd;
+    int bd;
+    int64_t dk;  // global offset of the block: a breakdown at its step s (1-based) is step dk + s
+    int* dinfo;
+    int* dhalt;
+};
+
+// Barrier over the 16 epilogue warps (named barrier 1).
+struct EpiSync {
+    __device__ void operator()() const { asm volatile("bar.sync 1, %0;" ::"r"(OEPI * 32) : "memory"); }
 };
 
 // Pass P streams B planes q = 0 .. upd_nq(P)-1 and pairs each with the A planes p in [upd_p0, upd_p1],
@@ -358,10 +372,19 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
     uint64_t* tempty = tfull + 2;      // [2]
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tempty + 2);
     __shared__ int aborted;
+    __shared__ double piv_rp;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t0 = (int)((long long)blockIdx.x * p.tiles / gridDim.x);
-    const int t1 = (int)((long long)(blockIdx.x + 1) * p.tiles / gridDim.x);
+    // With a fused pivot block, CTA 0 takes tile 0 (which holds the block) alone and the other CTAs
+    // share the remaining tiles evenly.
+    int t0, t1;
+    if (p.D != nullptr && gridDim.x > 1) {
+        t0 = (blockIdx.x == 0) ? 0 : 1 + (int)((long long)(blockIdx.x - 1) * (p.tiles - 1) / (gridDim.x - 1));
+        t1 = 1 + (int)((long long)blockIdx.x * (p.tiles - 1) / (gridDim.x - 1));
+    } else {
+        t0 = (int)((long long)blockIdx.x * p.tiles / gridDim.x);
+        t1 = (int)((long long)(blockIdx.x + 1) * p.tiles / gridDim.x);
+    }
 
     if (threadIdx.x == 0) {
         mbar_init(fullA, 1);
@@ -554,6 +577,28 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
                 }
             }
             asm volatile("bar.sync 1, %0;" ::"r"(OEPI * 32) : "memory");  // the staging area is reused
+            if (p.D != nullptr && t == 0) {
+                // tile 0, just written by these warps, holds the next pivot block: factor it in the staging
+                // area while the other CTAs finish the update.  The test is uniform over the 16 warps (the
+                // barriers inside must be met by all of them); after a timeout the factorization still
+                // runs, over whatever the tile holds, and the launch reports the timeout.
+                double* a = stg;
+                const int tid = threadIdx.x;
+                for (int i = tid >> 6; i < p.bd; i += (OEPI * 32) / 64)
+                    if ((tid & 63) < p.bd) a[i * kPivotLds + (tid & 63)] = p.D[i * p.ldd + (tid & 63)];
+                EpiSync{}();
+                const int broke = pivot_block_genp<double, OEPI * 32>(a, p.bd, &piv_rp, tid, EpiSync{});
+                if (broke != 0) {
+                    if (tid == 0) {
+                        atomicMin(p.dinfo, (int)(p.dk + broke));
+                        atomicExch(p.dhalt, 1);
+                    }
+                } else {
+                    for (int i = tid >> 6; i < p.bd; i += (OEPI * 32) / 64)
+                        if ((tid & 63) < p.bd) p.D[i * p.ldd + (tid & 63)] = a[i * kPivotLds + (tid & 63)];
+                }
+                EpiSync{}();  // the staging area is reused by the next tile
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -830,12 +875,16 @@ rmge_status oz_kmax(int64_t M, int64_t N, int K, const double* A, int64_t lda, c
 rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* planesA, void* planesB,
                     int* ea, int* eb, const unsigned long long* kmaxA, const unsigned long long* kmaxB, int* err,
-                    const int* halt, cudaStream_t st) {
+                    const int* halt, cudaStream_t st, const OzFuse* fuse) {
     if ((kmaxA == nullptr) != (kmaxB == nullptr)) return RMGE_ERR_INVALID_ARG;
     if (M <= 0 || N <= 0) return RMGE_OK;
     if (K <= 0 || s < 1 || s > 8 || M > INT32_MAX / 16 || N > INT32_MAX / 16 || K > INT32_MAX / 2)
         return RMGE_ERR_INVALID_ARG;
     const int64_t Mp = (M + 127) / 128 * 128, Np = (N + 127) / 128 * 128, Kp = (K + 63) / 64 * 64;
+    // the fused pivot block needs the persistent update kernel and must lie in its first tile
+    if (fuse != nullptr && (Kp != OBK || s != 8 || fuse->D == nullptr || fuse->b < 1 || fuse->b > UBN ||
+                            fuse->b > M || fuse->b > N || fuse->info == nullptr || fuse->halt == nullptr))
+        return RMGE_ERR_INVALID_ARG;
     __nv_bfloat16* pa = static_cast<__nv_bfloat16*>(planesA);
     __nv_bfloat16* pb = static_cast<__nv_bfloat16*>(planesB);
     if (Kp == OBK) {
@@ -886,6 +935,14 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
         u.ldc = ldc;
         u.err = err;
         u.halt = halt;
+        if (fuse != nullptr) {
+            u.D = fuse->D;
+            u.ldd = fuse->ldd;
+            u.bd = fuse->b;
+            u.dk = fuse->k;
+            u.dinfo = fuse->info;
+            u.dhalt = fuse->halt;
+        }
         // idesc: FP32 accumulate, BF16 A and B, both K-major, N = 64, M = 128
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UBN >> 3) << 17) |
                                ((uint32_t)(UBM >> 4) << 24);

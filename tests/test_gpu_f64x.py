@@ -68,6 +68,38 @@ def test_emulated_factor_backward_error(orc, n):
     assert abs(float(host(growth)[0]) - g) <= 1e-6 * g
 
 
+def _coupled(n, i):
+    """Identity with a 2 x 2 block of ones at rows / columns i, i + 1: pivot i + 1 (1-based) is 1 and the
+    Schur update leaves exactly 1 - 1 = 0 at step i + 2."""
+    M = np.eye(n)
+    M[i:i + 2, i:i + 2] = 1.0
+    return M
+
+
+@pytest.mark.parametrize("n,step", [(200, 70), (130, 64), (130, 65), (300, 300), (512, 200), (1000, 777)])
+def test_emulated_breakdown_steps(orc, n, step):
+    """Cor. 3.1 on the emulated path, where every pivot block after the first is factored inside the
+    previous step's update launch: info is the first zero pivot, also one that the update itself creates
+    across a block edge (rows 127 / 128) and inside a block."""
+    M = np.eye(n)
+    M[step - 1, step - 1] = 0.0
+    info, growth = rmge.factor(dev(M), "f64x")
+    assert int(host(info)[0]) == step == orc.genp(M)[1]
+    assert np.isnan(host(growth)[0])
+    for i in (126, 127, 99):
+        if i + 2 <= n:
+            C = _coupled(n, i)
+            info, _ = rmge.factor(dev(C), "f64x")
+            assert int(host(info)[0]) == i + 2 == orc.genp(C)[1]
+
+
+def test_emulated_breakdown_non_finite():
+    M = np.eye(150)
+    M[100, 100] = np.nan
+    info, _ = rmge.factor(dev(M), "f64x")
+    assert int(host(info)[0]) == 101
+
+
 @pytest.mark.parametrize("n,k", [(256, 1), (1000, 16)])
 def test_emulated_solve_reaches_fp64_target(orc, n, k):
     A, B = W.orthogonal_factor_system(n, k, 1e-6, seed=300 + n)
