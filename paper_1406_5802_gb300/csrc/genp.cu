@@ -60,10 +60,14 @@ __global__ void __launch_bounds__(256) diag_factor_kernel(int64_t k, int b, T* _
 //   row tiles (blockIdx.x < row_tiles):  L21 = A21 U11^{-1}, row by row (x U11 = a);
 //   column tiles:                         U12 = L11^{-1} A12, column by column (L11 x = a).
 // PT rows (columns) per CTA, 16 lanes per row (column); the substitution of one row (column) is
-// sequential over the b pivot columns and synchronises only its own warp.
+// sequential over the b pivot columns and synchronises only its own warp.  With kmax != NULL the
+// kernel also leaves, for the balancing of the emulated Schur update, max_i |L21_ik| in kmax[k] and
+// max_j |U12_kj| in kmax[64 + k] (FP64 bit patterns of the finite maxima, merged by atomicMax into
+// zeroed slots).
 template <typename T, int PT>
 __global__ void __launch_bounds__(256) panel_apply_kernel(int64_t k, int b, int64_t rest, int row_tiles,
-                                                          T* __restrict__ M, int64_t ldm, const DevState* st) {
+                                                          T* __restrict__ M, int64_t ldm, const DevState* st,
+                                                          unsigned long long* kmax) {
     static_assert(PT * 16 == 256, "16 lanes per row or column");
     __shared__ T dd[NB][LDS];
     __shared__ T tile[PT][LDS];  // row tile: tile[r][t]; column tile stored transposed: tile[c][t]
@@ -107,6 +111,14 @@ __global__ void __launch_bounds__(256) panel_apply_kernel(int64_t k, int b, int6
         }
     }
     __syncthreads();
+    if (kmax != nullptr && tid < b) {  // column tid of this tile's L21 rows, or row tid of its U12 columns
+        unsigned long long m = 0ull;
+        for (int r = 0; r < cnt; ++r) {
+            const unsigned long long v = abs_bits((double)tile[r][tid]);
+            if (v < 0x7ff0000000000000ull && v > m) m = v;  // finite entries only
+        }
+        if (m != 0ull) atomicMax(kmax + (is_row ? 0 : 64) + tid, m);
+    }
     if (is_row) {
         for (int e = tid; e < PT * NB; e += blockDim.x) {
             const int r = e / NB, jj = e % NB;
@@ -173,7 +185,7 @@ rmge_status genp_factor(int64_t n, T* M, int64_t ldm, DevState* st, cudaStream_t
         const int64_t rest = n - k - b;
         if (rest <= 0) break;
         const int tiles = (int)((rest + PT - 1) / PT);
-        panel_apply_kernel<T, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st);
+        panel_apply_kernel<T, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, nullptr);
         RMGE_LAUNCH_CHECK();
         RMGE_TRY(gemm<T>(false, rest, rest, b, T(-1), M + (k + b) * ldm + k, ldm, M + k * ldm + k + b, ldm, T(1),
                          M + (k + b) * ldm + (k + b), ldm, &st->halt, s));
@@ -197,7 +209,7 @@ rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const
         const int64_t rest = n - k - b;
         if (rest <= 0) break;
         const int tiles = (int)((rest + PT - 1) / PT);
-        panel_apply_kernel<float, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st);
+        panel_apply_kernel<float, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, nullptr);
         RMGE_LAUNCH_CHECK();
         const float* L21 = M + (k + b) * ldm + k;
         const float* U12 = M + k * ldm + k + b;
@@ -219,9 +231,10 @@ rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const
 }
 
 // The Schur update E <- E - L21 U12 as an emulated FP64 product.  Column k of L21 carries 1 / u_kk and
-// row k of U12 carries u_kk, so the pair is first balanced by an exact power of two per k (oz_kmax);
-// without it the per-row scaling of L21 and per-column scaling of U12 pair the large column of a small
-// pivot with the large rows of other pivots and the update loses most of its relative accuracy.
+// row k of U12 carries u_kk, so the pair is first balanced by an exact power of two per k, from the
+// per-k maxima that the panel kernel leaves; without it the per-row scaling of L21 and per-column
+// scaling of U12 pair the large column of a small pivot with the large rows of other pivots and the
+// update loses most of its relative accuracy.
 // The update launch of step k also factors the pivot block of step k + 1 (CTA 0 takes the tile holding it
 // alone), so only the first pivot block has a launch of its own.
 rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s) {
@@ -237,13 +250,12 @@ rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, cons
         const int64_t rest = n - k - b;
         if (rest <= 0) break;
         const int tiles = (int)((rest + PT - 1) / PT);
-        panel_apply_kernel<double, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st);
+        unsigned long long* kmA = oz.kmax + 128 * step;  // zeroed with the factorization's state
+        panel_apply_kernel<double, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, kmA);
         RMGE_LAUNCH_CHECK();
         const double* L21 = M + (k + b) * ldm + k;
         const double* U12 = M + k * ldm + k + b;
         double* E = M + (k + b) * ldm + (k + b);
-        unsigned long long* kmA = oz.kmax + 128 * step;
-        RMGE_TRY(oz_kmax(rest, rest, b, L21, ldm, U12, ldm, kmA, kmA + 64, s));
         const OzFuse next{E, ldm, (int)(rest < NB ? rest : NB), k + b, &st->info, &st->halt};
         RMGE_TRY(oz_gemm(rest, rest, b, kOzSlices, -1.0, L21, ldm, U12, ldm, 1.0, E, ldm, oz.planesA, oz.planesB,
                          oz.ea, oz.eb, kmA, kmA + 64, &st->error, &st->halt, s, &next));

@@ -42,12 +42,11 @@ uint32_t tc_idesc(bool bf16);
 // oz_gemm.cu: C (FP64) <- beta C + alpha A B with the product emulated on BF16 tensor cores from
 // s base-128 digit planes of A (rows) and B (columns).  planesA/planesB: oz_plane_bytes(M, K, s) and
 // oz_plane_bytes(N, K, s) bytes; ea[M], eb[N] ints of scratch.  kmaxA/kmaxB (both or neither): the
-// per-k maxima from oz_kmax, which balance column k of A against row k of B by an exact power of two.
+// per-k maxima max_i |A_ik| and max_j |B_kj| (FP64 bit patterns, K <= 64), which balance column k of A
+// against row k of B by an exact power of two.
 // *err <- RMGE_ERR_TIMEOUT if a bounded wait expires; nothing happens while *halt != 0 (halt may be NULL).
 constexpr int kOzSlices = 8;
 size_t oz_plane_bytes(int64_t rows, int64_t k, int s);
-rmge_status oz_kmax(int64_t M, int64_t N, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
-                    unsigned long long* kmaxA, unsigned long long* kmaxB, cudaStream_t st);
 // The pivot block of the next GENP step, factored inside the update launch (K <= 64, 8 slices): the
 // b x b block at D (b <= 64, leading dimension ldd) must lie in the first 128 x 64 tile of C; a
 // breakdown at its step s records k + s in *info (atomicMin) and raises *halt.

@@ -166,7 +166,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
                         const int ya = pa * p.Mp + m0, yb = (d - pa) * p.Np + n0;
                         for (int kb = 0; kb < nkb; ++kb, ++it) {
                             const int st = it % OSTAGES;
-                            if (!mbar_wait(empty + st, (uint32_t)(((it / OSTAGES) & 1) ^ 1), deadline)) {
+                            if (!mbar_wait_idle(empty + st, (uint32_t)(((it / OSTAGES) & 1) ^ 1), deadline)) {
                                 atomicExch(&aborted, 1);
                                 break;
                             }
@@ -208,11 +208,13 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
                                 break;
                             }
                             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                            const uint32_t a0 = smem_u32(sA + st * OA_BYTES), b0 = smem_u32(sB + st * OB_BYTES);
+                            // 32-byte K steps inside the swizzled tile advance the descriptors' address field by 2
+                            const uint64_t ad = smem_desc(smem_u32(sA + st * OA_BYTES)),
+                                           bd = smem_desc(smem_u32(sB + st * OB_BYTES));
 #pragma unroll
                             for (int kk = 0; kk < OBK / 16; ++kk)
-                                mma_f16(tmem + (uint32_t)(buf * 128), smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32),
-                                        idesc, (pa > 0 || kb > 0 || kk > 0) ? 1u : 0u);
+                                mma_f16(tmem + (uint32_t)(buf * 128), ad + 2 * kk, bd + 2 * kk, idesc,
+                                        (pa > 0 || kb > 0 || kk > 0) ? 1u : 0u);
                             mma_commit(empty + st);
                         }
                     }
@@ -240,7 +242,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
             const int lsh = sh > 0 ? sh : 0;
             for (int k0 = sc; k0 < se; k0 += kc, ++u) {
                 const int buf = u & 1;
-                if (!mbar_wait(tfull + buf, (uint32_t)((u >> 1) & 1), deadline)) {
+                if (!mbar_wait_idle(tfull + buf, (uint32_t)((u >> 1) & 1), deadline)) {
                     atomicExch(&aborted, 1);
                     ok = false;
                     break;
@@ -420,7 +422,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
             for (int t = t0; t < t1 && ok; ++t) {
                 const int mb = t / p.tiles_n, nb = t % p.tiles_n;
                 if (mb != cur) {
-                    if (na > 0 && !mbar_wait(doneA, (uint32_t)((na - 1) & 1), deadline)) {
+                    if (na > 0 && !mbar_wait_idle(doneA, (uint32_t)((na - 1) & 1), deadline)) {
                         ok = false;
                         break;
                     }
@@ -432,7 +434,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
                 for (int P = 0; P < 2 && ok; ++P)
                     for (int q = 0; q < upd_nq(P); ++q, ++it) {
                         const int st = it % URING;
-                        if (!mbar_wait(emptyB + st, (uint32_t)(((it / URING) & 1) ^ 1), deadline)) {
+                        if (!mbar_wait_idle(emptyB + st, (uint32_t)(((it / URING) & 1) ^ 1), deadline)) {
                             ok = false;
                             break;
                         }
@@ -475,14 +477,13 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
                             break;
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint32_t b0 = smem_u32(sB + st * UB_PLANE);
+                        const uint64_t bd = smem_desc(smem_u32(sB + st * UB_PLANE));
                         for (int pa = upd_p0(P, q); pa <= upd_p1(P, q); ++pa) {
-                            const uint32_t a0 = smem_u32(sA + pa * UA_PLANE);
+                            const uint64_t ad = smem_desc(smem_u32(sA + pa * UA_PLANE));
                             const uint32_t dcol = tmem + (uint32_t)(bank * 256 + (pa + q - 4 * P) * UBN);
 #pragma unroll
                             for (int kk = 0; kk < OBK / 16; ++kk)
-                                mma_f16(dcol, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
-                                        (q > 0 || kk > 0) ? 1u : 0u);
+                                mma_f16(dcol, ad + 2 * kk, bd + 2 * kk, idesc, (q > 0 || kk > 0) ? 1u : 0u);
                         }
                         mma_commit(emptyB + st);
                     }
@@ -508,7 +509,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
             for (int j = 0; j < 16; ++j) acc[j] = 0;
             for (int P = 0; P < 2; ++P, ++u) {
                 const int bank = u & 1;
-                if (!mbar_wait(tfull + bank, (uint32_t)((u >> 1) & 1), deadline)) {
+                if (!mbar_wait_idle(tfull + bank, (uint32_t)((u >> 1) & 1), deadline)) {
                     atomicExch(&aborted, 1);
                     ok = false;
                 }
@@ -665,50 +666,6 @@ __global__ void col_exponent_kernel(int64_t rows, int64_t cols, const double* __
     }
 }
 
-// kmaxA[k] = max_r |A_rk| (k < K <= 64) and kmaxB[k] = max_c |B_kc| as FP64 bit patterns, by atomicMax
-// into zeroed slots; non-finite entries are skipped.  blockIdx.y = 0: 32 rows of A per block, a warp
-// reading 32 consecutive entries of one row; blockIdx.y = 1: 64 columns of B per block, a warp per row.
-constexpr int kKmaxRows = 32, kKmaxCols = 64;
-__global__ void kmax_kernel(int64_t M, int64_t N, int K, const double* __restrict__ A, int64_t lda,
-                            const double* __restrict__ B, int64_t ldb, unsigned long long* __restrict__ kmaxA,
-                            unsigned long long* __restrict__ kmaxB) {
-    __shared__ unsigned long long part[64];
-    if (blockIdx.y == 0) {
-        if (threadIdx.x < 64) part[threadIdx.x] = 0ull;
-        __syncthreads();
-        const int c = threadIdx.x & 63, r = threadIdx.x >> 6;
-        const int64_t r0 = (int64_t)blockIdx.x * kKmaxRows;
-        double m = 0.0;
-        if (c < K)
-#pragma unroll
-            for (int i = r; i < kKmaxRows; i += 4) {
-                if (r0 + i >= M) break;
-                const double x = fabs(A[(r0 + i) * lda + c]);
-                if (isfinite(x)) m = fmax(m, x);
-            }
-        if (m > 0.0) atomicMax(&part[c], (unsigned long long)__double_as_longlong(m));
-        __syncthreads();
-        if (threadIdx.x < K && part[threadIdx.x] != 0ull) atomicMax(&kmaxA[threadIdx.x], part[threadIdx.x]);
-    } else {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int64_t c0 = (int64_t)blockIdx.x * kKmaxCols;
-        if (c0 >= N) return;
-        for (int k = warp; k < K; k += 8) {
-            double m = 0.0;
-#pragma unroll
-            for (int h = 0; h < kKmaxCols / 32; ++h) {
-                const int64_t c = c0 + h * 32 + lane;
-                if (c < N) {
-                    const double x = fabs(B[(int64_t)k * ldb + c]);
-                    if (isfinite(x)) m = fmax(m, x);
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (lane == 0 && m > 0.0) atomicMax(&kmaxB[k], (unsigned long long)__double_as_longlong(m));
-        }
-    }
-}
-
 // The 7s-bit magnitude |x| 2^(7s), x = v 2^-e, by integer shifts of the FP64 significand.
 __device__ __forceinline__ unsigned long long fixed_digits(double v, int e, int s) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
@@ -861,17 +818,6 @@ size_t oz_plane_bytes(int64_t rows, int64_t k, int s) {
     return (size_t)s * (size_t)rp * (size_t)kp * 2;
 }
 
-rmge_status oz_kmax(int64_t M, int64_t N, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
-                    unsigned long long* kmaxA, unsigned long long* kmaxB, cudaStream_t st) {
-    if (M <= 0 || N <= 0 || K <= 0) return RMGE_OK;
-    if (K > 64) return RMGE_ERR_INVALID_ARG;
-    const int64_t gx = std::max((M + kKmaxRows - 1) / kKmaxRows, (N + kKmaxCols - 1) / kKmaxCols);
-    if (gx > 65535 * 64) return RMGE_ERR_INVALID_ARG;
-    kmax_kernel<<<dim3((unsigned)gx, 2), 256, 0, st>>>(M, N, K, A, lda, B, ldb, kmaxA, kmaxB);
-    RMGE_LAUNCH_CHECK();
-    return RMGE_OK;
-}
-
 rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* planesA, void* planesB,
                     int* ea, int* eb, const unsigned long long* kmaxA, const unsigned long long* kmaxB, int* err,
@@ -957,6 +903,9 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
         return RMGE_OK;
     }
 
+    // |acc| < (chunks on diagonal 0 + 1) 2^(F + 10) must stay below 2^62
+    int ch0 = (int)((Kp + 1023) / 1024), lg = 0;
+    while ((1 << lg) < ch0 + 1) ++lg;
     CUtensorMap ta, tb;
     if (!tc_make_map(&ta, pa, true, (int64_t)s * Mp, Kp, Kp, OBM) || !tc_make_map(&tb, pb, true, (int64_t)s * Np, Kp, Kp, OBN))
         return RMGE_ERR_CUDA;
@@ -965,9 +914,6 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
     prm.N = (int)N;
     prm.K = (int)Kp;
     prm.s = s;
-    // |acc| < (chunks on diagonal 0 + 1) 2^(F + 10) must stay below 2^62
-    int ch0 = (int)((Kp + 1023) / 1024), lg = 0;
-    while ((1 << lg) < ch0 + 1) ++lg;
     prm.F = 52 - lg;
     prm.Mp = (int)Mp;
     prm.Np = (int)Np;

@@ -66,6 +66,16 @@ static __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
     return true;
 }
 
+// The same wait for warps that have nothing else to do meanwhile: between polls the warp sleeps, so
+// that it does not take issue slots from the TMA and MMA warps on its SM sub-partition.
+static __device__ __forceinline__ bool mbar_wait_idle(uint64_t* bar, uint32_t parity, unsigned long long deadline) {
+    while (!mbar_test(bar, parity)) {
+        if (now_ns() > deadline) return false;
+        __nanosleep(64);
+    }
+    return true;
+}
+
 static __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
