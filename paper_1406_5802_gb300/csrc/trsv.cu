@@ -12,11 +12,13 @@
 // (kSpinLimit polls); on expiry the CTA records RMGE_ERR_TIMEOUT in DevState::error and all
 // waiting CTAs return without writing.
 //
-// The factor is read once from HBM per column block; FP64 runs on the DFMA pipe.  GB300 retires 2 FP64
-// operations per clock per SM, so the chain of row blocks is bound by the FP64 work of each link (the
-// product with the block just solved plus the diagonal substitution): narrow column blocks (KC = 2)
-// give more independent chains with less FP64 work per link, and the diagonal substitution multiplies
-// by reciprocals formed before the CTA starts waiting, keeping FP64 divisions off the chain.
+// The factor is read once from HBM per column block; FP64 runs on the DFMA pipe (2 FP64 operations per
+// clock per SM on GB300).  The chain of row blocks is bound by the latency of each link (flag hand-off,
+// the product with the block just solved, the diagonal substitution) more than by its FP64 work: one
+// right-hand side takes nearly as long as sixteen.  So narrow column blocks (KC = 2) give more
+// independent chains, the substitution multiplies by reciprocals formed before the CTA starts waiting
+// and steps by warp shuffles (one warp per column) instead of block-wide barriers, and one thread
+// fences before the release.
 #include "kernels.cuh"
 
 namespace rmge {
@@ -136,21 +138,38 @@ __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t n
         __syncthreads();
     }
 
-    // diagonal block: column-oriented substitution inside the block
-    for (int step = 0; step < TB; ++step) {
-        const int p = forward ? step : TB - 1 - step;  // row finalised in this step
-        if (r == p) {
-            const T y = unit ? acc : acc * rd[p];
-            acc = y;
-            ys[p][c] = y;
+    // diagonal block: column-oriented substitution inside the block, one warp per column (lane l holds
+    // rows l and l + 32) stepping by warp shuffles instead of block-wide barriers; every row sees the
+    // same operations in the same order as a row-per-thread substitution
+    static_assert(TB == 64, "two rows per lane");
+    ys[r][c] = acc;
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    if (warp < KC) {
+        const int col = warp;
+        T x0 = ys[lane][col], x1 = ys[lane + 32][col];
+        for (int step = 0; step < TB; ++step) {
+            const int p = forward ? step : TB - 1 - step;  // row finalised in this step
+            const T xp = __shfl_sync(0xffffffffu, p < 32 ? x0 : x1, p & 31);
+            const T y = unit ? xp : xp * rd[p];
+            if (lane == (p & 31)) {
+                if (p < 32) x0 = y;
+                else x1 = y;
+            }
+            if (forward ? lane > p : lane < p) x0 = fma(-cd[lane][p], y, x0);
+            if (forward ? lane + 32 > p : lane + 32 < p) x1 = fma(-cd[lane + 32][p], y, x1);
         }
-        __syncthreads();
-        if ((forward && r > p) || (!forward && r < p)) acc = fma(-cd[r][p], ys[p][c], acc);
+        const int64_t gcol = c0 + col;
+        if (gcol < nrhs) {
+            if (r0 + lane < n) B[(r0 + lane) * ldb + gcol] = x0;
+            if (r0 + lane + 32 < n) B[(r0 + lane + 32) * ldb + gcol] = x1;
+        }
     }
-    if (live) B[gr * ldb + gc] = acc;
-    __threadfence();
+    // the block's results are published by one release after the barrier (the barrier orders the
+    // other threads' stores before thread 0's fence)
     __syncthreads();
     if (tid == 0) {
+        __threadfence();
         st_release(flags + rb * ncb + cb, epoch);
         finish_ticket(st);
     }
