@@ -16,9 +16,10 @@
 // clock per SM on GB300).  The chain of row blocks is bound by the latency of each link (flag hand-off,
 // the product with the block just solved, the diagonal substitution) more than by its FP64 work: one
 // right-hand side takes nearly as long as sixteen.  So narrow column blocks (KC = 2) give more
-// independent chains, the substitution multiplies by reciprocals formed before the CTA starts waiting
-// and steps by warp shuffles (one warp per column) instead of block-wide barriers, and one thread
-// fences before the release.
+// independent chains; a link's product runs as eight independent partial sums; the diagonal block is
+// row-scaled by reciprocals formed before the CTA starts waiting, so that the substitution is one
+// DFMA and one warp shuffle per step (one warp per column, no block-wide barriers); one thread fences
+// before the release.
 #include "kernels.cuh"
 
 namespace rmge {
@@ -86,6 +87,13 @@ __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t n
     __syncthreads();
     if (!unit && tid < TB) rd[tid] = T(1) / cd[tid][tid];
     __syncthreads();
+    // Non-unit kinds: row i of the block is divided by its diagonal entry, so the substitution below
+    // runs on a unit triangle and its chain of dependent steps carries no multiplication by 1 / u_ii.
+    if (!unit)
+        for (int e = tid; e < TB * TB; e += NT) {
+            const int i = e / TB, t = e % TB;
+            if (t != i) cd[i][t] *= rd[i];
+        }
 
     constexpr int CPT = TB * TB / NT;  // coefficients per thread per tile
     for (int64_t qq = 0; qq < q; ++qq) {
@@ -133,16 +141,23 @@ __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t n
             ys[r][c] = (gt < n && gc < nrhs) ? ldcg(B + gt * ldb + gc) : T(0);
         }
         __syncthreads();
-#pragma unroll 8
-        for (int t = 0; t < TB; ++t) acc = fma(-cs[r][t], ys[t][c], acc);
+        // eight independent partial sums: FP64 latency on GB300 is long, and one dependent chain of 64
+        // FMAs was the longest part of a link
+        T part[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) part[j] = T(0);
+#pragma unroll
+        for (int t = 0; t < TB; t += 8)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) part[j] = fma(-cs[r][t + j], ys[t + j][c], part[j]);
+        acc += ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
         __syncthreads();
     }
 
-    // diagonal block: column-oriented substitution inside the block, one warp per column (lane l holds
-    // rows l and l + 32) stepping by warp shuffles instead of block-wide barriers; every row sees the
-    // same operations in the same order as a row-per-thread substitution
+    // diagonal block: column-oriented substitution inside the (row-scaled, unit) block, one warp per
+    // column (lane l holds rows l and l + 32), stepping by warp shuffles instead of block-wide barriers
     static_assert(TB == 64, "two rows per lane");
-    ys[r][c] = acc;
+    ys[r][c] = unit ? acc : acc * rd[r];  // the row scaling of the right-hand side
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
     if (warp < KC) {
@@ -150,12 +165,7 @@ __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t n
         T x0 = ys[lane][col], x1 = ys[lane + 32][col];
         for (int step = 0; step < TB; ++step) {
             const int p = forward ? step : TB - 1 - step;  // row finalised in this step
-            const T xp = __shfl_sync(0xffffffffu, p < 32 ? x0 : x1, p & 31);
-            const T y = unit ? xp : xp * rd[p];
-            if (lane == (p & 31)) {
-                if (p < 32) x0 = y;
-                else x1 = y;
-            }
+            const T y = __shfl_sync(0xffffffffu, p < 32 ? x0 : x1, p & 31);  // final: unit diagonal
             if (forward ? lane > p : lane < p) x0 = fma(-cd[lane][p], y, x0);
             if (forward ? lane + 32 > p : lane + 32 < p) x1 = fma(-cd[lane + 32][p], y, x1);
         }
