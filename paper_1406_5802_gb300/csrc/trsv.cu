@@ -16,10 +16,14 @@
 // clock per SM on GB300).  The chain of row blocks is bound by the latency of each link (flag hand-off,
 // the product with the block just solved, the diagonal substitution) more than by its FP64 work: one
 // right-hand side takes nearly as long as sixteen.  So narrow column blocks (KC = 2) give more
-// independent chains; a link's product runs as eight independent partial sums; the diagonal block is
-// row-scaled by reciprocals formed before the CTA starts waiting, so that the substitution is one
-// DFMA and one warp shuffle per step (one warp per column, no block-wide barriers); one thread fences
-// before the release.
+// independent chains; the diagonal block is row-scaled by reciprocals formed before the CTA starts
+// waiting, so that the substitution is one DFMA and one warp shuffle per step (one warp per column, no
+// block-wide barriers); one thread fences before the release.  Measured per 64-row block at n = 4096:
+// flag hand-off 0.5 us, the product with the block just solved 2.8 us (64 x 64 x 2 FMAs: the FP64
+// throughput of one SM), the substitution 7.2 us (64 dependent DFMA + shuffle steps), release 0.5 us.
+// An explicit inverse of the diagonal block (formed off the chain) replaces the substitution by a
+// product but loses about u kappa of the block, which GENP's factors can make large; refined once
+// with its residual it is accurate again but three block products cost more than the substitution.
 #include "kernels.cuh"
 
 namespace rmge {
@@ -141,16 +145,8 @@ __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t n
             ys[r][c] = (gt < n && gc < nrhs) ? ldcg(B + gt * ldb + gc) : T(0);
         }
         __syncthreads();
-        // eight independent partial sums: FP64 latency on GB300 is long, and one dependent chain of 64
-        // FMAs was the longest part of a link
-        T part[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) part[j] = T(0);
-#pragma unroll
-        for (int t = 0; t < TB; t += 8)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) part[j] = fma(-cs[r][t + j], ys[t + j][c], part[j]);
-        acc += ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
+#pragma unroll 8
+        for (int t = 0; t < TB; ++t) acc = fma(-cs[r][t], ys[t][c], acc);
         __syncthreads();
     }
 
