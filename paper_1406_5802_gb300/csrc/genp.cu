@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) diag_factor_kernel(int64_t k, int b, T* _
 //   row tiles (blockIdx.x < row_tiles):  L21 = A21 U11^{-1}, row by row (x U11 = a);
 //   column tiles:                         U12 = L11^{-1} A12, column by column (L11 x = a).
 // PT rows (columns) per CTA, 16 lanes per row (column); the substitution of one row (column) is
-// sequential over the b pivot columns and synchronises only its own warp.  With kmax != NULL the
+// sequential over the b pivot columns, held in registers and stepped by 16-lane shuffles.  With kmax != NULL the
 // kernel also leaves, for the balancing of the emulated Schur update, max_i |L21_ik| in kmax[k] and
 // max_j |U12_kj| in kmax[64 + k] (FP64 bit patterns of the finite maxima, merged by atomicMax into
 // zeroed slots).
@@ -93,22 +93,39 @@ __global__ void __launch_bounds__(256) panel_apply_kernel(int64_t k, int b, int6
         }
     }
     __syncthreads();
+    // Row tiles solve x U11 = a as x U' = a D^{-1} with U11 = U' D (D its diagonal, U' unit): the
+    // columns of U11 and the entries of a are scaled first, so every step of the substitution below is
+    // a single DFMA on its dependency chain (GB300's FP64 latency is long).
+    if (is_row)
+        for (int e = tid; e < NB * NB; e += blockDim.x) {
+            const int j = e / NB, t = e % NB;
+            if (j < t && t < b) dd[j][t] *= rdiag[t];
+        }
     const int q = tid >> 4, lane = tid & 15;  // row (column) q of the tile, lane within it
-    T* x = tile[q];
-    if (is_row) {
-        for (int j = 0; j < b; ++j) {
-            const T xj = x[j] * rdiag[j];
-            __syncwarp();
-            if (lane == 0) x[j] = xj;
-            for (int t = j + 1 + lane; t < b; t += 16) x[t] = fma(-xj, dd[j][t], x[t]);
-            __syncwarp();
+    // lane holds entries lane + 16 kk of its row (column); entry j is broadcast by its owner lane
+    T x[NB / 16];
+#pragma unroll
+    for (int kk = 0; kk < NB / 16; ++kk) {
+        const int t = lane + 16 * kk;
+        x[kk] = (t < b) ? (is_row ? tile[q][t] * rdiag[t] : tile[q][t]) : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < NB / 16; ++jj)
+        for (int jl = 0; jl < 16; ++jl) {
+            const int j = 16 * jj + jl;
+            if (j >= b) break;  // uniform
+            const T xj = __shfl_sync(0xffffffffu, x[jj], jl, 16);
+#pragma unroll
+            for (int kk = jj; kk < NB / 16; ++kk) {
+                const int t = lane + 16 * kk;
+                if (t > j && t < b) x[kk] = fma(-xj, is_row ? dd[j][t] : dd[t][j], x[kk]);
+            }
         }
-    } else {
-        for (int i = 0; i < b; ++i) {
-            const T xi = x[i];
-            for (int t = i + 1 + lane; t < b; t += 16) x[t] = fma(-dd[t][i], xi, x[t]);
-            __syncwarp();
-        }
+#pragma unroll
+    for (int kk = 0; kk < NB / 16; ++kk) {
+        const int t = lane + 16 * kk;
+        if (t < b) tile[q][t] = x[kk];
     }
     __syncthreads();
     if (kmax != nullptr && tid < b) {  // column tid of this tile's L21 rows, or row tid of its U12 columns
