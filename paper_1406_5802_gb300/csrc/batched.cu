@@ -7,7 +7,8 @@
 //   x_i  = G_i U^{-1} L^{-1} b_i          (Fact 4.1)
 //   sweeps of r = b - A x (FP64), x += G U^{-1} L^{-1} r, until the normwise backward error is
 //   below tol (Sec. 1.2, Sec. 7.1); once a sweep fails to halve the error, the remaining sweeps are
-//   right-preconditioned GMRES cycles in FP64 (preconditioner G U^{-1} L^{-1} in FP32); when those
+//   right-preconditioned GMRES cycles (FP64 basis, FP32 products with A and the preconditioner
+//   G U^{-1} L^{-1}; the residual of every sweep stays FP64); when those
 //   stall too, a fresh multiplier is drawn (up to three draws), and a system that no FP32 draw can
 //   refine is factored in FP64 in the same CTA (its A G and GENP on the DFMA pipe)
 // CTAs are persistent: each takes the next system from a queue ordered by decreasing n (longest
@@ -319,6 +320,75 @@ __device__ double cta_sum(double v, double* red) {
 
 constexpr int GM = 16;  // restart length of the per-system GMRES cycles
 
+// CTA-wide maximum of one non-negative FP64 bit pattern per thread (integer compares: GB300's FP64
+// pipe is narrow and slow to answer); every thread gets the total.
+template <int T>
+__device__ unsigned long long cta_max_bits(unsigned long long v, unsigned long long* redb) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+    }
+    if ((threadIdx.x & 31) == 0) redb[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned long long t = 0ull;
+    for (int w = 0; w < T / 32; ++w) t = redb[w] > t ? redb[w] : t;
+    __syncthreads();
+    return t;
+}
+
+// r = b - A x in FP64 (the residual of every sweep) with its maximum, and, when with_norm, the largest
+// absolute row sum of A.  Each warp takes four rows at a time so that four independent FMA chains
+// hide the FP64 latency.
+template <int T>
+__device__ void cta_residual(int n, const double* A, const double* b, const double* x, double* r, bool with_norm,
+                             unsigned long long* rmax_bits, unsigned long long* amax_bits, unsigned long long* redb) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long rb = 0ull, ab = 0ull;
+    for (int i0 = warp * 4; i0 < n; i0 += (T / 32) * 4) {
+        double sacc[4], as[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            sacc[q] = (lane == 0 && i0 + q < n) ? b[i0 + q] : 0.0;  // b enters the warp sum once
+            as[q] = 0.0;
+        }
+        for (int j = lane; j < n; j += 32) {
+            const double xj = x[j];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (i0 + q < n) {
+                    const double aij = A[(int64_t)(i0 + q) * n + j];
+                    sacc[q] = fma(-aij, xj, sacc[q]);
+                    if (with_norm) as[q] += fabs(aij);
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            for (int o = 16; o > 0; o >>= 1) {
+                sacc[q] += __shfl_xor_sync(0xffffffffu, sacc[q], o);
+                if (with_norm) as[q] += __shfl_xor_sync(0xffffffffu, as[q], o);
+            }
+            if (i0 + q < n) {
+                if (lane == 0) r[i0 + q] = sacc[q];
+                const unsigned long long v = abs_bits(sacc[q]), w = abs_bits(as[q]);
+                rb = v > rb ? v : rb;
+                ab = w > ab ? w : ab;
+            }
+        }
+    }
+    *rmax_bits = cta_max_bits<T>(rb, redb);
+    *amax_bits = with_norm ? cta_max_bits<T>(ab, redb) : 0ull;
+}
+
+template <int T>
+__device__ double cta_max_abs(int n, const double* v, unsigned long long* redb) {
+    unsigned long long m = 0ull;
+    for (int i = threadIdx.x; i < n; i += T) {
+        const unsigned long long u = abs_bits(v[i]);
+        m = u > m ? u : m;
+    }
+    return __longlong_as_double((long long)cta_max_bits<T>(m, redb));
+}
+
 // z (FP64) = G U^{-1} L^{-1} v with the FP32 factors: the preconditioner P of Fact 4.1.
 template <int T>
 __device__ void cta_precond(int n, const float* M, const float* G, const double* v, float* y, double* z) {
@@ -328,12 +398,17 @@ __device__ void cta_precond(int n, const float* M, const float* G, const double*
     cta_gemv<T, float>(n, G, y, z, false);
 }
 
-// One right-preconditioned GMRES(GM) cycle in FP64 on A d = r (r in rz on entry), x += P V y.
-// V: (GM + 1) x n doubles of scratch; rz is reused as the preconditioned vector.
+// One right-preconditioned GMRES(GM) cycle on A d = r (r in rz on entry), x += P V y, with the
+// Krylov basis, orthogonalisation and rotations in FP64 and the products A z in FP32 against A32, an
+// FP32 copy of A: GMRES-based refinement only needs the correction to a modest relative accuracy
+// while the residual of every sweep stays in FP64 (a lower-precision Krylov product, as in the
+// five-precision GMRES-IR analysis of Amestoy, Buttari, Higham, L'Excellent, Mary and Vieuble).
+// V: (GM + 1) x n doubles of scratch; rz is reused as the preconditioned vector; z32: n floats.
 template <int T>
-__device__ void cta_gmres_cycle(int n, const double* A, const float* M, const float* G, double* x, double* rz,
-                                double* V, float* y, double* red) {
+__device__ void cta_gmres_cycle(int n, const float* A32, const float* M, const float* G, double* x, double* rz,
+                                double* V, float* y, float* z32, double* red) {
     __shared__ double H[(GM + 1) * GM], cs[GM], sn[GM], g[GM + 1], hs[GM + 1], ys[GM];
+    __shared__ double redm[T / 32][GM];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double acc = 0.0;
     for (int i = threadIdx.x; i < n; i += T) acc = fma(rz[i], rz[i], acc);
@@ -350,23 +425,50 @@ __device__ void cta_gmres_cycle(int n, const double* A, const float* M, const fl
     for (int j = 0; j < GM; ++j) {
         double* vj = V + (int64_t)j * n;
         double* w = V + (int64_t)(j + 1) * n;
-        cta_precond<T>(n, M, G, vj, y, rz);  // rz = P v_j
-        for (int i = warp; i < n; i += T / 32) {  // w = A z
-            double s = 0.0;
-            for (int k = lane; k < n; k += 32) s = fma(A[(int64_t)i * n + k], rz[k], s);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) w[i] = s;
+        cta_precond<T>(n, M, G, vj, y, rz);  // rz = P v_j (FP32 values held in doubles)
+        for (int i = threadIdx.x; i < n; i += T) z32[i] = (float)rz[i];
+        __syncthreads();
+        for (int i0 = warp * 4; i0 < n; i0 += (T / 32) * 4) {  // w = A z, four rows per warp at a time
+            float sv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int k = lane; k < n; k += 32) {
+                const float zk = z32[k];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (i0 + q < n) sv[q] = fmaf(A32[(int64_t)(i0 + q) * n + k], zk, sv[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                for (int o = 16; o > 0; o >>= 1) sv[q] += __shfl_xor_sync(0xffffffffu, sv[q], o);
+                if (lane == 0 && i0 + q < n) w[i0 + q] = (double)sv[q];
+            }
         }
         __syncthreads();
         for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-            for (int l = 0; l <= j; ++l) {
-                double d = 0.0;
-                for (int i = threadIdx.x; i < n; i += T) d = fma(V[(int64_t)l * n + i], w[i], d);
-                d = cta_sum<T>(d, red);
-                if (threadIdx.x == 0) {
-                    hs[l] = d;
-                    H[l * GM + j] += d;
+            // the j + 1 dot products in groups of LB: one reduction round per group instead of per product
+            constexpr int LB = (T >= 1024) ? 4 : GM;  // 1024-thread CTAs have 64 registers per thread
+            for (int l0 = 0; l0 <= j; l0 += LB) {
+                double d[LB];
+#pragma unroll
+                for (int l = 0; l < LB; ++l) d[l] = 0.0;
+                for (int i = threadIdx.x; i < n; i += T) {
+                    const double wi = w[i];
+#pragma unroll
+                    for (int l = 0; l < LB; ++l)
+                        if (l0 + l <= j) d[l] = fma(V[(int64_t)(l0 + l) * n + i], wi, d[l]);
                 }
+#pragma unroll
+                for (int l = 0; l < LB; ++l)
+                    if (l0 + l <= j) {
+                        for (int o = 16; o > 0; o >>= 1) d[l] += __shfl_xor_sync(0xffffffffu, d[l], o);
+                        if (lane == 0) redm[warp][l0 + l] = d[l];
+                    }
+            }
+            __syncthreads();
+            if (threadIdx.x <= j) {
+                double t = 0.0;
+                for (int w2 = 0; w2 < T / 32; ++w2) t += redm[w2][threadIdx.x];
+                hs[threadIdx.x] = t;
+                H[threadIdx.x * GM + j] += t;
             }
             __syncthreads();
             for (int i = threadIdx.x; i < n; i += T) {
@@ -423,20 +525,24 @@ __device__ void cta_gmres_cycle(int n, const double* A, const float* M, const fl
     __syncthreads();
 }
 
+// 256-thread CTAs are held to 80 registers so that three fit on an SM: the refinement's FP64 loops are
+// latency-bound and gain more from the third CTA than they lose to a few spilled registers (measured:
+// 178 against 215 ms for the 4096-system batch at two CTAs per SM).
 template <int T, int TILE>
-__global__ void __launch_bounds__(T) batched_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(T, T >= 1024 ? 1 : 3) batched_kernel(BatchArgs a) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int sys_s, flag, stop_s;
     __shared__ double red[T / 32];
-    __shared__ double red2[T / 32];
+    __shared__ unsigned long long redb[T / 32];
     // per CTA: G (nmax^2 floats), M (nmax^2 doubles: FP32 factors, or FP64 ones on the fallback), y
     float* G = a.scratch + (int64_t)blockIdx.x * (3 * a.nmax * a.nmax + 2 * a.nmax);
     float* M = G + a.nmax * a.nmax;
     double* M64 = reinterpret_cast<double*>(M);
     float* y = M + 2 * a.nmax * a.nmax;
+    float* z32 = y + a.nmax;
+    float* A32 = M + a.nmax * a.nmax;  // FP32 copy of A for the Krylov products (M's FP64 half is free then)
     double* r = a.dscratch + (int64_t)blockIdx.x * a.nmax * (GM + 2);
     double* V = r + a.nmax;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned int q = atomicAdd(&a.queue[0], 1u);
@@ -456,6 +562,8 @@ __global__ void __launch_bounds__(T) batched_kernel(BatchArgs a) {
         // subsequence -- the method's guarantees hold with probability close to 1 per draw (Sec. 4).
         constexpr int kDraws = 3;
         int info = 0, total_sweeps = 0;
+        for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += T) A32[e] = (float)A[e];
+        const double bmax = cta_max_abs<T>(n, b, redb);  // also orders the A32 stores before their use
         double eta = __longlong_as_double(0x7ff0000000000000LL);
         bool done = false;
         for (int draw = 0; draw < kDraws && !done; ++draw) {
@@ -475,38 +583,12 @@ __global__ void __launch_bounds__(T) batched_kernel(BatchArgs a) {
             double norm_a = 0.0, eta_prev = 0.0;
             bool krylov = false;
             for (int sw = 0;; ++sw, ++total_sweeps) {
-                double rmax = 0.0, amax = 0.0;
-                for (int i = warp; i < n; i += T / 32) {
-                    double sacc = (lane == 0) ? b[i] : 0.0, as = 0.0;  // b enters the warp sum once
-                    for (int j = lane; j < n; j += 32) {
-                        const double aij = A[(int64_t)i * n + j];
-                        sacc = fma(-aij, x[j], sacc);
-                        as += fabs(aij);
-                    }
-                    for (int o = 16; o > 0; o >>= 1) {
-                        sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-                        as += __shfl_xor_sync(0xffffffffu, as, o);
-                    }
-                    if (lane == 0) r[i] = sacc;
-                    rmax = fmax(rmax, fabs(sacc));
-                    amax = fmax(amax, as);
-                }
-                if (lane == 0) {
-                    red[warp] = rmax;
-                    red2[warp] = amax;
-                }
-                __syncthreads();
+                unsigned long long rbits, abits;
+                cta_residual<T>(n, A, b, x, r, sw == 0, &rbits, &abits, redb);
+                const double xmax = cta_max_abs<T>(n, x, redb);
                 if (threadIdx.x == 0) {
-                    double rm = 0.0, am = 0.0, xm = 0.0, bm = 0.0;
-                    for (int w = 0; w < T / 32; ++w) {
-                        rm = fmax(rm, red[w]);
-                        am = fmax(am, red2[w]);
-                    }
-                    for (int i = 0; i < n; ++i) {
-                        xm = fmax(xm, fabs(x[i]));
-                        bm = fmax(bm, fabs(b[i]));
-                    }
-                    if (sw == 0) norm_a = am;
+                    const double rm = __longlong_as_double((long long)rbits), xm = xmax, bm = bmax;
+                    if (sw == 0) norm_a = __longlong_as_double((long long)abits);
                     const double den = norm_a * xm + bm;
                     double e = den > 0.0 ? rm / den : 0.0;
                     if (!isfinite(e) || !isfinite(xm)) e = __longlong_as_double(0x7ff0000000000000LL);
@@ -532,7 +614,7 @@ __global__ void __launch_bounds__(T) batched_kernel(BatchArgs a) {
                 krylov = (st == 1);
                 eta_prev = e;
                 if (krylov) {
-                    cta_gmres_cycle<T>(n, A, M, G, x, r, V, y, red);
+                    cta_gmres_cycle<T>(n, A32, M, G, x, r, V, y, z32, red);
                 } else {
                     for (int i = threadIdx.x; i < n; i += T) y[i] = (float)r[i];
                     __syncthreads();
@@ -556,38 +638,12 @@ __global__ void __launch_bounds__(T) batched_kernel(BatchArgs a) {
                 cta_gemv<T, double>(n, G, y64, x, false);
                 double eta_prev = 0.0, norm_a = 0.0;
                 for (int sw = 0;; ++sw, ++total_sweeps) {
-                    double rmax = 0.0, amax = 0.0;
-                    for (int i = warp; i < n; i += T / 32) {
-                        double sacc = (lane == 0) ? b[i] : 0.0, as = 0.0;
-                        for (int j = lane; j < n; j += 32) {
-                            const double aij = A[(int64_t)i * n + j];
-                            sacc = fma(-aij, x[j], sacc);
-                            as += fabs(aij);
-                        }
-                        for (int o = 16; o > 0; o >>= 1) {
-                            sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-                            as += __shfl_xor_sync(0xffffffffu, as, o);
-                        }
-                        if (lane == 0) r[i] = sacc;
-                        rmax = fmax(rmax, fabs(sacc));
-                        amax = fmax(amax, as);
-                    }
-                    if (lane == 0) {
-                        red[warp] = rmax;
-                        red2[warp] = amax;
-                    }
-                    __syncthreads();
+                    unsigned long long rbits, abits;
+                    cta_residual<T>(n, A, b, x, r, sw == 0, &rbits, &abits, redb);
+                    const double xmax = cta_max_abs<T>(n, x, redb);
                     if (threadIdx.x == 0) {
-                        double rm = 0.0, am = 0.0, xm = 0.0, bm = 0.0;
-                        for (int w = 0; w < T / 32; ++w) {
-                            rm = fmax(rm, red[w]);
-                            am = fmax(am, red2[w]);
-                        }
-                        for (int i = 0; i < n; ++i) {
-                            xm = fmax(xm, fabs(x[i]));
-                            bm = fmax(bm, fabs(b[i]));
-                        }
-                        if (sw == 0) norm_a = am;
+                        const double rm = __longlong_as_double((long long)rbits), xm = xmax, bm = bmax;
+                        if (sw == 0) norm_a = __longlong_as_double((long long)abits);
                         const double den = norm_a * xm + bm;
                         double e = den > 0.0 ? rm / den : 0.0;
                         if (!isfinite(e) || !isfinite(xm)) e = __longlong_as_double(0x7ff0000000000000LL);
