@@ -251,16 +251,30 @@ __device__ int cta_genp(int n, E* M, E* smem, int* flag) {
 
 // In-place y <- U^{-1} L^{-1} y (FP32 vector, n), warp 0 solving 32-row diagonal blocks, all threads
 // updating the rows below (above) with the solved block.
+// FP32 factors: each lane first loads its row of the 32 x 32 diagonal block into registers, so the
+// dependent shuffle chain does not wait on a global load at every step.
 template <int T, typename E>
 __device__ void cta_lu_solve(int n, const E* M, E* y) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr bool kRegRow = sizeof(E) == 4;
     for (int k = 0; k < n; k += 32) {  // L z = y
         const int b = min(32, n - k);
         if (warp == 0) {
             E v = lane < b ? y[k + lane] : E(0);
-            for (int j = 0; j < b; ++j) {
-                const E zj = __shfl_sync(0xffffffffu, v, j);
-                if (lane > j && lane < b) v = fma(-M[(int64_t)(k + lane) * n + k + j], zj, v);
+            if constexpr (kRegRow) {
+                E row[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) row[j] = (lane < b && j < lane) ? M[(int64_t)(k + lane) * n + k + j] : E(0);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const E zj = __shfl_sync(0xffffffffu, v, j);
+                    v = fma(-row[j], zj, v);  // row[j] = 0 for j >= lane
+                }
+            } else {
+                for (int j = 0; j < b; ++j) {
+                    const E zj = __shfl_sync(0xffffffffu, v, j);
+                    if (lane > j && lane < b) v = fma(-M[(int64_t)(k + lane) * n + k + j], zj, v);
+                }
             }
             if (lane < b) y[k + lane] = v;
         }
@@ -276,10 +290,24 @@ __device__ void cta_lu_solve(int n, const E* M, E* y) {
         const int b = min(32, n - k);
         if (warp == 0) {
             E v = lane < b ? y[k + lane] : E(0);
-            for (int j = b - 1; j >= 0; --j) {
-                if (lane == j) v = v / M[(int64_t)(k + j) * n + k + j];
-                const E xj = __shfl_sync(0xffffffffu, v, j);
-                if (lane < j) v = fma(-M[(int64_t)(k + lane) * n + k + j], xj, v);
+            if constexpr (kRegRow) {
+                E row[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) row[j] = (lane < b && j >= lane && j < b) ? M[(int64_t)(k + lane) * n + k + j] : E(0);
+#pragma unroll
+                for (int j = 31; j >= 0; --j) {
+                    if (j < b) {  // uniform
+                        if (lane == j) v = v / row[j];
+                        const E xj = __shfl_sync(0xffffffffu, v, j);
+                        if (lane < j) v = fma(-row[j], xj, v);
+                    }
+                }
+            } else {
+                for (int j = b - 1; j >= 0; --j) {
+                    if (lane == j) v = v / M[(int64_t)(k + j) * n + k + j];
+                    const E xj = __shfl_sync(0xffffffffu, v, j);
+                    if (lane < j) v = fma(-M[(int64_t)(k + lane) * n + k + j], xj, v);
+                }
             }
             if (lane < b) y[k + lane] = v;
         }
