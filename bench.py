@@ -294,6 +294,32 @@ def extra_workloads(W, rmge, peaks, which=("precision", "batch", "grad", "lowran
             torch.cuda.synchronize()
             ms = t0.elapsed_time(t1)
             res[prec] = {"ms_per_batch": ms, "systems_per_s": count / (ms / 1e3), "max_iters": iters}
+            # The same step captured once in a CUDA graph and replayed, as a training loop with fixed
+            # shapes would run it: the eager step pays a host launch per kernel (hundreds per system).
+            try:
+                side = torch.cuda.Stream()
+                side.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.stream(side):
+                    step()
+                torch.cuda.current_stream().wait_stream(side)
+                torch.cuda.synchronize()
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph):
+                    step()
+                graph.replay()
+                torch.cuda.synchronize()
+                t0, t1 = ev(), ev()
+                t0.record()
+                for _ in range(3):
+                    graph.replay()
+                t1.record()
+                torch.cuda.synchronize()
+                gms = t0.elapsed_time(t1) / 3
+                res[prec]["graph_ms_per_batch"] = gms
+                res[prec]["graph_systems_per_s"] = count / (gms / 1e3)
+                del graph
+            except Exception as e:  # report, keep the eager number
+                res[prec]["graph_error"] = repr(e)[:200]
         out["grad_64x2048"] = res
     except Exception as e:
         out["grad_64x2048"] = {"error": repr(e)}

@@ -46,10 +46,22 @@ def rmge_solve(A, B, seed: int, kind: str = "gaussian", prec: str = "f64", max_i
     return RmgeSolve.apply(A, B, seed, kind, prec, max_iters, be_tol)
 
 
+_POOLS: dict = {}
+
+
+def _stream_pool(count: int, device) -> list:
+    """The same side streams on every call, so that a training step that uses them can be captured in a
+    CUDA graph (the streams fork from and join the capturing stream)."""
+    key = (torch.cuda.current_device() if device is None else device, count)
+    if key not in _POOLS:
+        _POOLS[key] = [torch.cuda.Stream() for _ in range(count)]
+    return _POOLS[key]
+
+
 def rmge_solve_batched(As, Bs, seeds, kind: str = "gaussian", prec: str = "f32", streams: int = 8, **kw):
     """A list of independent differentiable solves, spread round-robin over CUDA streams so that small
     systems overlap on the GPU.  Returns the list of X."""
-    pool = [torch.cuda.Stream() for _ in range(max(1, streams))]
+    pool = _stream_pool(max(1, streams), As[0].device.index if len(As) else None)
     cur = torch.cuda.current_stream()
     outs = []
     for i, (A, B, s) in enumerate(zip(As, Bs, seeds)):

@@ -202,15 +202,21 @@ rmge_status refine_loop(rmge_mult_kind kind, rmge_prec prec, bool trans, int64_t
         // R = B - op(A) X in FP64, then the backward error and the stopping test
         RMGE_TRY(copy_matrix<double, double>(n, nrhs, B, ldb, w.R, nrhs, stop, s));
         RMGE_TRY(gemm<double>(trans, n, nrhs, n, -1.0, A, lda, X, ldx, 1.0, w.R, nrhs, stop, s));
-        RMGE_TRY(backward_error(n, nrhs, w.R, nrhs, X, ldx, B, ldb, w.st, w.colred, it, be_tol, max_iters, berr, s));
+        const bool hybrid = prec != RMGE_F64;
+        RMGE_TRY(backward_error(n, nrhs, w.R, nrhs, X, ldx, B, ldb, w.st, w.colred, it, be_tol, max_iters, berr, s,
+                                hybrid));
         if (it == max_iters) break;
         const int epoch = epoch0 + 2 * kGmresM * it;
-        if (prec == RMGE_F64) {
+        if (!hybrid) {
             // X <- X + G U^{-1} L^{-1} R  (transposed: L^{-T} U^{-T} G^T R)
             RMGE_TRY(correction(kind, prec, n, nrhs, LU, ldlu, G, w.R, nrhs, X, ldx, true, w, epoch, stop, s, trans));
         } else {
-            // X <- X + d, op(A) d = R solved by one preconditioned FGMRES cycle in FP64
-            RMGE_TRY(gmres_cycle(n, nrhs, A, lda, trans, w.R, X, ldx, w.gm, pre, epoch, stop, s));
+            // the same classical correction with the reduced-precision factors while it halves the backward
+            // error; after that X <- X + d, op(A) d = R solved by one preconditioned FGMRES cycle in FP64.
+            // decide_kernel sets the two skip flags, so exactly one of the two runs.
+            RMGE_TRY(correction(kind, prec, n, nrhs, LU, ldlu, G, w.R, nrhs, X, ldx, true, w, epoch, &w.st->skip_cls,
+                                s, trans));
+            RMGE_TRY(gmres_cycle(n, nrhs, A, lda, trans, w.R, X, ldx, w.gm, pre, epoch, &w.st->skip_kry, s));
         }
     }
     return refine_finish(w.st, max_iters, berr, iters, s);

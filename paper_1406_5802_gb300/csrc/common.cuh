@@ -30,6 +30,12 @@ struct DevState {
     unsigned int ticket;           // dynamic block-order ticket of the running triangular solve
     unsigned int done;             // CTAs of the running triangular solve that have finished
     unsigned int pad1[2];
+    // reduced-precision refinement: classical sweeps until one fails to halve the backward error,
+    // then FGMRES cycles; the two corrections of a sweep read these as their skip flags
+    int krylov;        // nonzero once the sweeps have switched to FGMRES cycles
+    int krylov_start;  // the sweep at which they switched
+    int skip_cls;      // stop || krylov
+    int skip_kry;      // stop || !krylov
 };
 
 // Triangular-solve tiling (rows per block, right-hand sides per block column).

@@ -124,7 +124,7 @@ rmge_status add_update(int64_t rows, int64_t cols, const T* D, int64_t ldd, doub
 // backward error of (R, X, B) into berr_out[sweep] and the stop test; see rmge_refine.
 rmge_status backward_error(int64_t n, int64_t k, const double* R, int64_t ldr, const double* X, int64_t ldx,
                            const double* B, int64_t ldb, DevState* st, double* colred, int sweep,
-                           double be_tol, int max_iters, double* berr_out, cudaStream_t s);
+                           double be_tol, int max_iters, double* berr_out, cudaStream_t s, bool hybrid = false);
 rmge_status refine_finish(DevState* st, int max_iters, double* berr_out, int32_t* iters, cudaStream_t s);
 // dA = -dB X^T
 rmge_status outer_neg(int64_t n, int64_t k, const double* dB, int64_t lddb, const double* X, int64_t ldx,

@@ -23,6 +23,10 @@ __global__ void state_init_kernel(DevState* st, int* flags, int64_t nflags, doub
         st->norm_a = 0.0;
         st->berr_prev = __longlong_as_double(0x7ff0000000000000LL);
         st->berr_last = __longlong_as_double(0x7ff0000000000000LL);
+        st->krylov = 0;
+        st->krylov_start = 0;
+        st->skip_cls = 0;
+        st->skip_kry = 1;
     }
     if (tid == 0) {
         st->ticket = 0u;
@@ -90,8 +94,11 @@ __global__ void colmax_kernel(int64_t n, int64_t k, const double* __restrict__ R
 }
 
 // eta = max_c max|r_c| / (||A||_inf max|x_c| + max|b_c|); stopping test; clears colred.
+// hybrid (reduced-precision factors): the sweeps are classical corrections while each at least halves
+// eta, then FGMRES cycles, which stop once a cycle fails to halve eta against two sweeps back; without
+// hybrid that last test applies from the start.
 __global__ void decide_kernel(int64_t k, DevState* st, unsigned long long* colred, int sweep, double tol,
-                              int max_iters, double* berr_out) {
+                              int max_iters, double* berr_out, bool hybrid) {
     if (st->stop != 0) return;
     double eta = 0.0;
     bool bad = false;
@@ -108,8 +115,21 @@ __global__ void decide_kernel(int64_t k, DevState* st, unsigned long long* colre
     if (bad || !isfinite(st->norm_a)) eta = __longlong_as_double(0x7ff0000000000000LL);
     if (berr_out) berr_out[sweep] = eta;
     st->sweeps = sweep;
-    const bool stagnated = sweep >= 2 && !(eta <= 0.5 * st->berr_prev);
+    bool stagnated;
+    if (!hybrid) {
+        stagnated = sweep >= 2 && !(eta <= 0.5 * st->berr_prev);
+    } else if (st->krylov == 0) {
+        stagnated = false;
+        if (sweep >= 1 && !(eta <= 0.5 * st->berr_last)) {
+            st->krylov = 1;
+            st->krylov_start = sweep;
+        }
+    } else {
+        stagnated = sweep - st->krylov_start >= 2 && !(eta <= 0.5 * st->berr_prev);
+    }
     if (eta <= tol || sweep >= max_iters || stagnated || !isfinite(eta)) st->stop = 1;
+    st->skip_cls = (st->stop != 0 || st->krylov != 0) ? 1 : 0;
+    st->skip_kry = (st->stop != 0 || st->krylov == 0) ? 1 : 0;
     st->berr_prev = st->berr_last;
     st->berr_last = eta;
 }
@@ -194,11 +214,11 @@ rmge_status add_update(int64_t rows, int64_t cols, const T* D, int64_t ldd, doub
 
 rmge_status backward_error(int64_t n, int64_t k, const double* R, int64_t ldr, const double* X, int64_t ldx,
                            const double* B, int64_t ldb, DevState* st, double* colred, int sweep, double be_tol,
-                           int max_iters, double* berr_out, cudaStream_t s) {
+                           int max_iters, double* berr_out, cudaStream_t s, bool hybrid) {
     unsigned long long* cr = reinterpret_cast<unsigned long long*>(colred);
     colmax_kernel<<<grid_for(n * k, 256), 256, 0, s>>>(n, k, R, ldr, X, ldx, B, ldb, st, cr);
     RMGE_LAUNCH_CHECK();
-    decide_kernel<<<1, 1, 0, s>>>(k, st, cr, sweep, be_tol, max_iters, berr_out);
+    decide_kernel<<<1, 1, 0, s>>>(k, st, cr, sweep, be_tol, max_iters, berr_out, hybrid);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }
