@@ -11,24 +11,49 @@
 // E <- E - (D B^-1)(B^-1 C) of eq. (3.1) in the blocked GENP, X = G Y, R = B - A X and the
 // adjoint product G^T dX.
 #include "kernels.cuh"
+#include "pivot_block.cuh"
 
 namespace rmge {
 namespace {
 
+struct CtaBarrier {
+    __device__ void operator()() const { __syncthreads(); }
+};
+
 // Thread (tx, ty) owns rows ty + i*RY and columns tx + j*RX of the CTA tile (i < TM, j < TN), so
 // a warp's shared-memory reads are broadcasts (A) or consecutive words (B), and its global
 // stores are consecutive along a row.
-template <typename T, typename SA, typename SB, int BM, int BN, int BK, int TM, int TN, bool TA>
+//
+// FUSE (GENP's trailing update, 64 x 64 tiles): tile (0, 0) of C holds the whole pivot block of the
+// next step, and its CTA factors that block once the tile is written (pivot_block_genp in the tile
+// staging area), while the other CTAs finish the update; a breakdown records its global step in
+// fz.info and raises fz.halt.
+template <typename T>
+struct PivotFuse {
+    T* D;        // the next pivot block: C's top-left corner, C's leading dimension
+    int b;       // its order, <= 64
+    int64_t k;   // its global offset (a breakdown at its step s is step k + s)
+    int* info;
+    int* halt;
+};
+
+template <typename T, typename SA, typename SB, int BM, int BN, int BK, int TM, int TN, bool TA, bool FUSE>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const SA* __restrict__ A, int64_t lda,
-            const SB* __restrict__ B, int64_t ldb, T beta, T* __restrict__ C, int64_t ldc, const int* halt) {
+            const SB* __restrict__ B, int64_t ldb, T beta, T* __restrict__ C, int64_t ldc, const int* halt,
+            PivotFuse<T> fz) {
     constexpr int RX = BN / TN;  // threads along a row of the tile
     constexpr int RY = BM / TM;
     constexpr int NT = RX * RY;
     if (halt != nullptr && *(volatile const int*)halt != 0) return;
 
-    __shared__ T As[2][BK][BM + 1];
-    __shared__ T Bs[2][BK][BN];
+    // the two double-buffered tiles, carved from one array (the fused pivot block reuses it whole)
+    constexpr int kTileBytes = (int)sizeof(T) * (2 * BK * (BM + 1) + 2 * BK * BN);
+    __shared__ __align__(16) unsigned char tiles[kTileBytes];
+    T (*As)[BK][BM + 1] = reinterpret_cast<T (*)[BK][BM + 1]>(tiles);
+    T (*Bs)[BK][BN] = reinterpret_cast<T (*)[BK][BN]>(tiles + sizeof(T) * 2 * BK * (BM + 1));
+    static_assert(!FUSE || (BM == 64 && BN == 64 && NT == 256 && kTileBytes >= (int)sizeof(T) * 64 * 64),
+                  "the fused pivot block is one 64 x 64 tile, staged in the tile buffers");
 
     const int tid = threadIdx.x;
     const int tx = tid % RX, ty = tid / RX;
@@ -126,6 +151,30 @@ gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const SA* __restrict__ A, 
             *c = (beta == T(0)) ? v : fma(beta, *c, v);
         }
     }
+    if constexpr (FUSE) {
+        if (blockIdx.x == 0 && blockIdx.y == 0) {
+            __shared__ T piv_rp;
+            T* a = reinterpret_cast<T*>(tiles);  // 64 x 64 at row stride 64
+            __syncthreads();      // the tile's stores to C are visible to the whole CTA
+            for (int e = tid; e < 64 * 64; e += NT) {
+                const int i = e / 64, j = e % 64;
+                if (i < fz.b && j < fz.b) a[e] = fz.D[i * ldc + j];
+            }
+            __syncthreads();
+            const int broke = pivot_block_genp<T, NT, CtaBarrier, 64>(a, fz.b, &piv_rp, tid, CtaBarrier{});
+            if (broke != 0) {
+                if (tid == 0) {
+                    atomicMin(fz.info, (int)(fz.k + broke));
+                    atomicExch(fz.halt, 1);
+                }
+            } else {
+                for (int e = tid; e < 64 * 64; e += NT) {
+                    const int i = e / 64, j = e % 64;
+                    if (i < fz.b && j < fz.b) fz.D[i * ldc + j] = a[e];
+                }
+            }
+        }
+    }
 }
 
 template <typename T, typename SA, typename SB, int BM, int BN, int BK, int TM, int TN>
@@ -134,11 +183,11 @@ rmge_status launch(bool ta, int64_t M, int64_t N, int64_t K, T alpha, const SA* 
     const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
     const int threads = (BM / TM) * (BN / TN);
     if (ta)
-        gemm_kernel<T, SA, SB, BM, BN, BK, TM, TN, true><<<grid, threads, 0, s>>>(M, N, K, alpha, A, lda, B, ldb,
-                                                                                 beta, C, ldc, halt);
+        gemm_kernel<T, SA, SB, BM, BN, BK, TM, TN, true, false><<<grid, threads, 0, s>>>(
+            M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, PivotFuse<T>{});
     else
-        gemm_kernel<T, SA, SB, BM, BN, BK, TM, TN, false><<<grid, threads, 0, s>>>(M, N, K, alpha, A, lda, B, ldb,
-                                                                                  beta, C, ldc, halt);
+        gemm_kernel<T, SA, SB, BM, BN, BK, TM, TN, false, false><<<grid, threads, 0, s>>>(
+            M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, PivotFuse<T>{});
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }
@@ -174,6 +223,22 @@ rmge_status gemm(bool trans_a, int64_t M, int64_t N, int64_t K, T alpha, const T
                  int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s) {
     return gemm_any<T, T, T>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
 }
+
+template <typename T>
+rmge_status gemm_update_fused(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, const T* B, int64_t ldb, T* C,
+                              int64_t ldc, const int* halt, int b, int64_t k, int* info, int* halt_w, cudaStream_t s) {
+    if (b < 1 || b > 64 || b > M || b > N || info == nullptr || halt_w == nullptr) return RMGE_ERR_INVALID_ARG;
+    const dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
+    gemm_kernel<T, T, T, 64, 64, 16, 4, 4, false, true><<<grid, 256, 0, s>>>(
+        M, N, K, T(-1), A, lda, B, ldb, T(1), C, ldc, halt, PivotFuse<T>{C, b, k, info, halt_w});
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+template rmge_status gemm_update_fused<double>(int64_t, int64_t, int64_t, const double*, int64_t, const double*,
+                                               int64_t, double*, int64_t, const int*, int, int64_t, int*, int*,
+                                               cudaStream_t);
+template rmge_status gemm_update_fused<float>(int64_t, int64_t, int64_t, const float*, int64_t, const float*, int64_t,
+                                              float*, int64_t, const int*, int, int64_t, int*, int*, cudaStream_t);
 
 rmge_status gemm_f64a_f32(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const float* B, int64_t ldb,
                           float* C, int64_t ldc, cudaStream_t s) {

@@ -197,15 +197,18 @@ rmge_status genp_factor(int64_t n, T* M, int64_t ldm, DevState* st, cudaStream_t
     RMGE_TRY(maxabs<T>(n, n, M, ldm, false, &st->maxabs_m, s));
     for (int64_t k = 0; k < n; k += NB) {
         const int b = (int)((n - k) < NB ? (n - k) : NB);
-        diag_factor_kernel<T><<<1, 256, 0, s>>>(k, b, M, ldm, st);
-        RMGE_LAUNCH_CHECK();
+        if (k == 0) {  // every later pivot block is factored inside the previous step's update launch
+            diag_factor_kernel<T><<<1, 256, 0, s>>>(k, b, M, ldm, st);
+            RMGE_LAUNCH_CHECK();
+        }
         const int64_t rest = n - k - b;
         if (rest <= 0) break;
         const int tiles = (int)((rest + PT - 1) / PT);
         panel_apply_kernel<T, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, nullptr);
         RMGE_LAUNCH_CHECK();
-        RMGE_TRY(gemm<T>(false, rest, rest, b, T(-1), M + (k + b) * ldm + k, ldm, M + k * ldm + k + b, ldm, T(1),
-                         M + (k + b) * ldm + (k + b), ldm, &st->halt, s));
+        RMGE_TRY(gemm_update_fused<T>(rest, rest, b, M + (k + b) * ldm + k, ldm, M + k * ldm + k + b, ldm,
+                                      M + (k + b) * ldm + (k + b), ldm, &st->halt, (int)(rest < NB ? rest : NB),
+                                      k + b, &st->info, &st->halt, s));
     }
     RMGE_TRY(maxabs<T>(n, n, M, ldm, true, &st->maxabs_u, s));
     return RMGE_OK;

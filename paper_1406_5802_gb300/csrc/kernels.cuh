@@ -17,6 +17,12 @@ rmge_status launch_unitary_spectrum(int64_t N, uint64_t seed, uint64_t subseq, d
 template <typename T>
 rmge_status gemm(bool trans_a, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda, const T* B,
                  int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s);
+// E <- E - L21 U12 (M x N, K <= 64) for GENP, whose CTA on tile (0, 0) then factors the b x b pivot
+// block at E's top-left corner (pivot_block_genp); a breakdown at its step s records k + s in *info
+// (atomicMin) and raises *halt_w.  halt: as for gemm.
+template <typename T>
+rmge_status gemm_update_fused(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, const T* B, int64_t ldb, T* C,
+                              int64_t ldc, const int* halt, int b, int64_t k, int* info, int* halt_w, cudaStream_t s);
 
 // C (FP32) = A (FP64, rounded to FP32 on load) * B (FP32): M = A G for the FP32 working matrix.
 rmge_status gemm_f64a_f32(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const float* B, int64_t ldb,
