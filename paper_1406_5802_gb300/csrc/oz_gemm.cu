@@ -321,9 +321,14 @@ constexpr int URING = 4;
 constexpr size_t kUpdSmem = 1024 + (size_t)8 * UA_PLANE + (size_t)URING * UB_PLANE + (size_t)UBM * UBN * 8 + 256;
 static_assert(kUpdSmem <= 232448, "update kernel shared memory");
 
+// One chunk per diagonal, K <= 64: |acc| <= sum_d (d + 1) 127^2 64 2^(F - 7(d + 2)) < 0.99 2^62 at
+// F = 56, so the fixed-point sum keeps the 56 bits of the 8-digit operands.  F is a compile-time
+// constant here: the epilogue's shifts and scalings are then immediates (the epilogue is ALU-bound).
+constexpr int kUpdF = 56;
+
 struct UpdParams {
     int M, N;            // output rows, columns
-    int F;               // fractional bits of the fixed-point accumulator
+    int F;               // fractional bits of the fixed-point accumulator (kUpdF)
     int Mp, Np;          // rows per digit plane of A, of B
     int tiles_n, tiles;  // column tiles, all tiles
     const int* ea;
@@ -507,6 +512,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
             long long acc[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) acc[j] = 0;
+#pragma unroll  // P compile-time: the epilogue shifts become immediates
             for (int P = 0; P < 2; ++P, ++u) {
                 const int bank = u & 1;
                 if (!mbar_wait_idle(tfull + bank, (uint32_t)((u >> 1) & 1), deadline)) {
@@ -518,7 +524,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
                 if (ok) {
 #pragma unroll
                     for (int sl = 0; sl < 4; ++sl) {
-                        const int sh = p.F - 7 * (4 * P + sl + 2);
+                        const int sh = kUpdF - 7 * (4 * P + sl + 2);  // compile-time: constant shifts
                         const float rscale = __int_as_float((127 + (sh < 0 ? sh : 0)) << 23);
                         const int lsh = sh > 0 ? sh : 0;
                         float v[16];
@@ -538,7 +544,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
                 for (int j = 0; j < 16; ++j) {
                     const int c = cg * 16 + j, col = nb * UBN + c;
                     const int ec = (col < p.N) ? p.eb[col] : 0;
-                    stg[r * UBN + (c ^ (r & 15))] = fixed_to_double(p.alpha_sign * acc[j], er + ec - p.F);
+                    stg[r * UBN + (c ^ (r & 15))] = fixed_to_double(p.alpha_sign * acc[j], er + ec - kUpdF);
                 }
             }
             asm volatile("bar.sync 1, %0;" ::"r"(OEPI * 32) : "memory");
@@ -736,12 +742,11 @@ __global__ void col_digits_kernel(int64_t rows, int64_t cols, const double* __re
 
 // K <= 64 (one K block): the exponent and the digits of a row in one pass, one warp per padded row
 // (lanes hold k = lane and lane + 32).
-__global__ void row_prep64_kernel(int64_t rows, int cols, const double* __restrict__ src, int64_t lds,
-                                  const unsigned long long* __restrict__ kmaxA,
-                                  const unsigned long long* __restrict__ kmaxB, int s, int64_t rows_p,
-                                  int* __restrict__ e, __nv_bfloat16* __restrict__ planes) {
+__device__ void row_prep64(int64_t bid, int64_t rows, int cols, const double* __restrict__ src, int64_t lds,
+                           const unsigned long long* __restrict__ kmaxA, const unsigned long long* __restrict__ kmaxB,
+                           int s, int64_t rows_p, int* __restrict__ e, __nv_bfloat16* __restrict__ planes) {
     const int lane = threadIdx.x & 31;
-    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t r = (bid * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (r >= rows_p) return;
     const bool live = r < rows;
     const int k0 = lane, k1 = lane + 32;
@@ -760,15 +765,14 @@ __global__ void row_prep64_kernel(int64_t rows, int cols, const double* __restri
 
 // K <= 64: the exponent and the (transposed) digits of 32 columns per block; 256 threads = 32 columns x
 // 8 row groups for the exponent, then consecutive threads along k for the digit stores.
-__global__ void col_prep64_kernel(int rows, int64_t cols, const double* __restrict__ src, int64_t lds,
-                                  const unsigned long long* __restrict__ kmaxA,
-                                  const unsigned long long* __restrict__ kmaxB, int s, int64_t cols_p,
-                                  int* __restrict__ e, __nv_bfloat16* __restrict__ planes) {
+__device__ void col_prep64(int64_t bid, int rows, int64_t cols, const double* __restrict__ src, int64_t lds,
+                           const unsigned long long* __restrict__ kmaxA, const unsigned long long* __restrict__ kmaxB,
+                           int s, int64_t cols_p, int* __restrict__ e, __nv_bfloat16* __restrict__ planes) {
     __shared__ double t[64][33];
     __shared__ int part[8][32];
     __shared__ int tk[64];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int64_t c0 = (int64_t)blockIdx.x * 32, c = c0 + tx;
+    const int64_t c0 = bid * 32, c = c0 + tx;
     if (threadIdx.x < 64) tk[threadIdx.x] = ((int)threadIdx.x < rows) ? bal_shift(kmaxA, kmaxB, threadIdx.x) : 0;
     for (int i = ty; i < 64; i += 8) t[i][tx] = (i < rows && c < cols) ? src[(int64_t)i * lds + c] : 0.0;
     __syncthreads();
@@ -790,6 +794,20 @@ __global__ void col_prep64_kernel(int rows, int64_t cols, const double* __restri
             store_digits(t[k][cl], (c0 + cl < cols && k < rows) ? part[0][cl] + tk[k] : 0, s,
                          planes + (c0 + cl) * 64 + k, total);
     }
+}
+
+// Both operands of a K <= 64 product in one launch: blocks [0, row_blocks) prepare the rows of A, the
+// rest the columns of B (one launch less per GENP step).
+__global__ void prep64_kernel(int64_t row_blocks, int64_t M, int64_t N, int K, const double* __restrict__ A,
+                              int64_t lda, const double* __restrict__ B, int64_t ldb,
+                              const unsigned long long* __restrict__ kmaxA,
+                              const unsigned long long* __restrict__ kmaxB, int s, int64_t Mp, int64_t Np,
+                              int* __restrict__ ea, int* __restrict__ eb, __nv_bfloat16* __restrict__ pa,
+                              __nv_bfloat16* __restrict__ pb) {
+    if ((int64_t)blockIdx.x < row_blocks)
+        row_prep64(blockIdx.x, M, K, A, lda, kmaxA, kmaxB, s, Mp, ea, pa);
+    else
+        col_prep64((int64_t)blockIdx.x - row_blocks, K, N, B, ldb, kmaxA, kmaxB, s, Np, eb, pb);
 }
 
 unsigned grid_for(int64_t work) {
@@ -834,10 +852,9 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
     __nv_bfloat16* pa = static_cast<__nv_bfloat16*>(planesA);
     __nv_bfloat16* pb = static_cast<__nv_bfloat16*>(planesB);
     if (Kp == OBK) {
-        row_prep64_kernel<<<(unsigned)((Mp * 32 + 255) / 256), 256, 0, st>>>(M, (int)K, A, lda, kmaxA, kmaxB, s, Mp, ea,
-                                                                          pa);
-        RMGE_LAUNCH_CHECK();
-        col_prep64_kernel<<<(unsigned)(Np / 32), 256, 0, st>>>((int)K, N, B, ldb, kmaxA, kmaxB, s, Np, eb, pb);
+        const int64_t row_blocks = (Mp * 32 + 255) / 256, col_blocks = Np / 32;
+        prep64_kernel<<<(unsigned)(row_blocks + col_blocks), 256, 0, st>>>(row_blocks, M, N, (int)K, A, lda, B, ldb,
+                                                                           kmaxA, kmaxB, s, Mp, Np, ea, eb, pa, pb);
         RMGE_LAUNCH_CHECK();
     } else {
         row_exponent_kernel<<<(unsigned)((M * 32 + 255) / 256), 256, 0, st>>>(M, K, A, lda, kmaxA, kmaxB, ea);
@@ -864,9 +881,7 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
         UpdParams u{};
         u.M = (int)M;
         u.N = (int)N;
-        // one chunk per diagonal, K <= 64: |acc| <= sum_d (d + 1) 127^2 64 2^(F - 7(d + 2)) < 0.99 2^62 at
-        // F = 56, so the fixed-point sum keeps the 56 bits of the 8-digit operands
-        u.F = 56;
+        u.F = kUpdF;
         u.Mp = (int)Mp;
         u.Np = (int)Np;
         u.tiles_n = (int)((N + UBN - 1) / UBN);
