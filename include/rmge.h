@@ -53,7 +53,7 @@ typedef enum {
     RMGE_ERR_CUDA = 5,          /* a CUDA launch or copy failed */
     RMGE_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up (see rmge_refine) */
     RMGE_ERR_WORKSPACE = 7,     /* ws is NULL, too small or misaligned */
-    RMGE_ERR_UNSUPPORTED = 8    /* valid request this build does not implement (e.g. circulant n not 2^p) */
+    RMGE_ERR_UNSUPPORTED = 8    /* valid request the library does not implement (e.g. circulant n not 2^p) */
 } rmge_status;
 
 /* Random multiplier G (Sec. 4-5). */

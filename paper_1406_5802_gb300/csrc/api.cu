@@ -340,7 +340,7 @@ const char* rmge_status_string(rmge_status s) {
         case RMGE_ERR_CUDA: return "CUDA launch or copy failed";
         case RMGE_ERR_TIMEOUT: return "bounded device wait expired";
         case RMGE_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
-        case RMGE_ERR_UNSUPPORTED: return "unsupported in this build";
+        case RMGE_ERR_UNSUPPORTED: return "unsupported request (e.g. a circulant n that is not a power of two)";
     }
     return "unknown status";
 }

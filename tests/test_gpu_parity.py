@@ -148,7 +148,7 @@ def test_solve_matches_oracle(orc, n, k):
 @pytest.mark.parametrize("kind", ["gaussian", "circulant", "circulant_uniform"])
 @pytest.mark.parametrize("n,k", [(64, 1), (256, 1), (512, 16)])
 def test_end_to_end_backward_error(orc, kind, n, k):
-    """The whole method on the GPU reaches the FP64 target, judged by the oracle's own residual."""
+    """The whole method on the GPU reaches the FP64 target, checked with the oracle's own residual."""
     A, B = W.gaussian_system(n, k, seed=W.SEED_BASE + n, zero_leading_pivot=True)
     out = rmge.gesv(kind, dev(A), dev(B), seed=W.SEED_BASE + 1, prec="f64", max_iters=10, be_tol=1e-13)
     assert int(host(out["info"])[0]) == 0

@@ -84,7 +84,7 @@ def test_structured_apply_matches_dense_definition(orc, kind, n):
 @pytest.mark.parametrize("n,k", [(64, 1), (1000, 3), (2048, 8)])
 def test_structured_solve_reaches_fp64_target(orc, kind, prec, n, k):
     """Fact 4.1 with H structured: GENP of A H (A[0,0] = 0, so GENP of A itself breaks down), X = H Y,
-    refinement; judged by the oracle's residual and against GEPP.  n = 1000 is not a power of two and
+    refinement; checked with the oracle's residual and against GEPP.  n = 1000 is not a power of two and
     must be refused."""
     A, B = W.gaussian_system(n, k, seed=W.SEED_BASE + 17 + n, zero_leading_pivot=True)
     if n & (n - 1):
