@@ -280,7 +280,7 @@ def extra_workloads(W, rmge, peaks, which=("precision", "batch", "grad", "lowran
             def step():
                 for t in As + Bs:
                     t.grad = None
-                Xs = rmge_solve_batched(As, Bs, seeds=list(range(count)), prec=prec, streams=8, max_iters=iters)
+                Xs = rmge_solve_batched(As, Bs, seeds=list(range(count)), prec=prec, streams=16, max_iters=iters)
                 loss = sum((X * Wt).sum() for X, Wt in zip(Xs, Ws))
                 loss.backward()
                 return loss
