@@ -1,8 +1,11 @@
 // genp.cu -- blocked Gaussian elimination with no pivoting (Sec. 3).
 //
 // One step of eq. (3.1) with a pivot block B of nb = kNb columns at offset k:
-//   1. diag_factor: one CTA factors B = L11 U11 by unblocked GENP in shared memory (no pivot
-//      search: the only branch is the breakdown test of Cor. 3.1).
+//   1. one CTA factors B = L11 U11 by unblocked GENP in shared memory (no pivot search: the only
+//      branch is the breakdown test of Cor. 3.1).  In the FP64, FP32 and emulated-FP64 forms only
+//      the first block has a launch of its own (diag_factor): every later block is the top-left tile
+//      of the previous step's Schur update, and the CTA that computes that tile factors it in the same
+//      launch (gemm_update_fused, oz_update).  The 16-bit tensor-core forms launch diag_factor per step.
 //   2. panel_apply: row tiles of D become D B^{-1}-rows  L21 = A21 U11^{-1}  (each row of L21
 //      depends on its own row of A21 only -- the row-parallel elimination that GENP allows and
 //      partial pivoting does not), and column tiles of C become U12 = L11^{-1} A12, both by
