@@ -18,9 +18,11 @@
 // right-hand side takes nearly as long as sixteen.  So narrow column blocks (KC = 2) give more
 // independent chains; the diagonal block is row-scaled by reciprocals formed before the CTA starts
 // waiting, so that the substitution is one DFMA and one warp shuffle per step (one warp per column, no
-// block-wide barriers); one thread fences before the release.  Measured per 64-row block at n = 4096:
-// flag hand-off 0.5 us, the product with the block just solved 2.8 us (64 x 64 x 2 FMAs: the FP64
-// throughput of one SM), the substitution 7.2 us (64 dependent DFMA + shuffle steps), release 0.5 us.
+// block-wide barriers), in two phases of 32 steps so that no step issues a DFMA whose lanes are all
+// idle; one thread fences before the release.  Measured per 64-row block at n = 4096: flag hand-off
+// 0.5 us, the product with the block just solved 2.8 to 3 us (64 x 64 x 2 FMAs: the FP64 throughput of
+// one SM; two interleaved chains were no faster), the substitution 5.6 us (7.2 us before the two
+// phases; 64 dependent DFMA + shuffle steps), release 0.5 to 0.8 us.
 // An explicit inverse of the diagonal block (formed off the chain) replaces the substitution by a
 // product but loses about u kappa of the block, which GENP's factors can make large; refined once
 // with its residual it is accurate again but three block products cost more than the substitution.
@@ -159,11 +161,33 @@ __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t n
     if (warp < KC) {
         const int col = warp;
         T x0 = ys[lane][col], x1 = ys[lane + 32][col];
-        for (int step = 0; step < TB; ++step) {
-            const int p = forward ? step : TB - 1 - step;  // row finalised in this step
-            const T y = __shfl_sync(0xffffffffu, p < 32 ? x0 : x1, p & 31);  // final: unit diagonal
-            if (forward ? lane > p : lane < p) x0 = fma(-cd[lane][p], y, x0);
-            if (forward ? lane + 32 > p : lane + 32 < p) x1 = fma(-cd[lane + 32][p], y, x1);
+        // Two phases of 32 steps.  While the rows of one half are being finalised, every row of the other
+        // half is still pending (one unpredicated DFMA); once that half is done, the loop touches only the
+        // other register, so no step issues a DFMA with all lanes idle.
+        if (forward) {
+#pragma unroll 8
+            for (int p = 0; p < 32; ++p) {
+                const T y = __shfl_sync(0xffffffffu, x0, p);  // final: unit diagonal
+                if (lane > p) x0 = fma(-cd[lane][p], y, x0);
+                x1 = fma(-cd[lane + 32][p], y, x1);
+            }
+#pragma unroll 8
+            for (int p = 32; p < TB; ++p) {
+                const T y = __shfl_sync(0xffffffffu, x1, p - 32);
+                if (lane + 32 > p) x1 = fma(-cd[lane + 32][p], y, x1);
+            }
+        } else {
+#pragma unroll 8
+            for (int p = TB - 1; p >= 32; --p) {
+                const T y = __shfl_sync(0xffffffffu, x1, p - 32);
+                if (lane + 32 < p) x1 = fma(-cd[lane + 32][p], y, x1);
+                x0 = fma(-cd[lane][p], y, x0);
+            }
+#pragma unroll 8
+            for (int p = 31; p >= 0; --p) {
+                const T y = __shfl_sync(0xffffffffu, x0, p);
+                if (lane < p) x0 = fma(-cd[lane][p], y, x0);
+            }
         }
         const int64_t gcol = c0 + col;
         if (gcol < nrhs) {

@@ -135,7 +135,7 @@ def test_breakdown_steps(orc):
 
 # ----------------------------------------------------------------------------- solve / refine / end to end
 
-@pytest.mark.parametrize("n,k", [(1, 1), (33, 3), (100, 16), (256, 1), (300, 17)])
+@pytest.mark.parametrize("n,k", [(1, 1), (97, 2), (33, 3), (1000, 4), (100, 16), (256, 1), (300, 17)])
 def test_solve_matches_oracle(orc, n, k):
     A, B = W.gaussian_system(n, k, seed=40 + n)
     G = W.gaussian_multiplier(n, 41 + n)
