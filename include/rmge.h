@@ -296,7 +296,9 @@ size_t rmge_noalloc_capacity(void);
  * succeeds with probability close to 1 per draw).  max_sweeps bounds the sweeps of each draw; sweeps[i]
  * counts them over all draws.  Device arrays: n[count]; offA[count] element offsets of A_i (n_i x n_i, FP64,
  * row-major, ld n_i) in A; offv[count] element offsets of b_i, x_i in b, x (FP64); order[count] a
- * permutation of 0..count-1; outputs info[i] (0 or first breakdown step), berr[i], sweeps[i].
+ * permutation of 0..count-1; outputs info[i] (0, the first breakdown step, or -1 if the system's wait for
+ * other CTAs' share of its FP64 fallback product timed out, which does not happen in a healthy launch),
+ * berr[i], sweeps[i].
  * config selects the compiled tile shape (0: 256 threads, 32x32 tiles; 1: 256 threads, 64x64;
  * 2: 1024 threads, 64x64) and ctas the number of persistent CTAs -- both chosen by the autotuner of
  * the Python binding.  ws: rmge_batched_workspace_size(nmax, ctas) bytes, 256-byte aligned (per-CTA

@@ -10,7 +10,8 @@
 //   right-preconditioned GMRES cycles (FP64 basis, FP32 products with A and the preconditioner
 //   G U^{-1} L^{-1}; the residual of every sweep stays FP64); when those
 //   stall too, a fresh multiplier is drawn (up to three draws), and a system that no FP32 draw can
-//   refine is factored in FP64 in the same CTA (its A G and GENP on the DFMA pipe)
+//   refine is factored in FP64 in the same CTA (its A G and GENP on the DFMA pipe; the first such
+//   system of a launch shares the rows of its A G with the CTAs that pass between two systems)
 // CTAs are persistent: each takes the next system from a queue ordered by decreasing n (longest
 // first), so uneven sizes balance across the SMs.  The queue counter re-arms itself when the last
 // CTA finishes, so the launch can be captured once in a CUDA graph and replayed.  Per-CTA scratch
@@ -41,7 +42,23 @@ struct BatchArgs {
     float* scratch;            // per CTA: G (nmax^2), M (nmax^2), y, t (nmax each) floats
     double* dscratch;          // per CTA: r (nmax) doubles
     int64_t nmax;
-    unsigned int* queue;       // [0] next system, [1] finished CTAs
+    unsigned int* queue;       // [0] next system, [1] finished CTAs, [2] CTAs working on a system
+    struct HelpJob* help;      // the shared FP64 product of a fallback system (in the zeroed queue head)
+};
+
+// A system that falls back to FP64 factors posts its product M = A G here, split into blocks of TILE
+// rows.  CTAs between two systems (and CTAs whose queue ran dry, while others still work) take blocks
+// from `next` and count them in `done`; the owner takes blocks too, then waits for `done`.  One job per
+// launch: `claimed` is never released, so no CTA can mistake a later job's fields for this one's.
+struct HelpJob {
+    unsigned int claimed;  // set once by the owner (atomicCAS)
+    int ready;             // release-stored 1 once the fields below are valid
+    unsigned int next;     // next block to take (can run past `blocks`)
+    int done;              // finished blocks
+    int n, blocks;
+    const double* A;
+    const float* G;
+    double* M;
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -553,13 +570,39 @@ __device__ void cta_gmres_cycle(int n, const float* A32, const float* M, const f
     __syncthreads();
 }
 
+// Take blocks of the posted FP64 product while any remain: rows [TILE blk, TILE blk + TILE) of M = A G.
+// Every thread of the CTA calls this; blk_s is a shared slot.  Nothing in here waits on another CTA.
+template <int T, int TILE>
+__device__ void help_pass(HelpJob* h, double* smem_d, int* blk_s) {
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int blk = -1;
+            if (ld_acquire(&h->ready) == 1 && *(volatile unsigned int*)&h->next < (unsigned int)h->blocks) {
+                const unsigned int q = atomicAdd(&h->next, 1u);
+                if (q < (unsigned int)h->blocks) blk = (int)q;
+            }
+            *blk_s = blk;
+        }
+        __syncthreads();
+        const int blk = *blk_s;
+        __syncthreads();
+        if (blk < 0) return;
+        const int n = h->n, r0 = blk * TILE, rows = min(TILE, n - r0);
+        cta_gemm<T, TILE, double, double>(rows, n, n, h->A + (int64_t)r0 * n, n, h->G, n, h->M + (int64_t)r0 * n, n,
+                                          1.0, 0.0, smem_d);
+        __threadfence();  // every thread's rows of M before the count (cta_gemm ends with a barrier)
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(&h->done, 1);
+    }
+}
+
 // 256-thread CTAs are held to 80 registers so that three fit on an SM: the refinement's FP64 loops are
 // latency-bound and gain more from the third CTA than they lose to a few spilled registers (measured:
 // 178 against 215 ms for the 4096-system batch at two CTAs per SM).
 template <int T, int TILE>
 __global__ void __launch_bounds__(T, T >= 1024 ? 1 : 3) batched_kernel(BatchArgs a) {
     extern __shared__ __align__(16) float smem[];
-    __shared__ int sys_s, flag, stop_s;
+    __shared__ int sys_s, flag, stop_s, blk_s, job_s;
     __shared__ double red[T / 32];
     __shared__ unsigned long long redb[T / 32];
     // per CTA: G (nmax^2 floats), M (nmax^2 doubles: FP32 factors, or FP64 ones on the fallback), y
@@ -571,15 +614,32 @@ __global__ void __launch_bounds__(T, T >= 1024 ? 1 : 3) batched_kernel(BatchArgs
     float* A32 = M + a.nmax * a.nmax;  // FP32 copy of A for the Krylov products (M's FP64 half is free then)
     double* r = a.dscratch + (int64_t)blockIdx.x * a.nmax * (GM + 2);
     double* V = r + a.nmax;
+    double* smem_d = reinterpret_cast<double*>(smem);
+    bool stranded = false;  // a helper CTA timed out on this CTA's product: its scratch may still be written
     for (;;) {
+        help_pass<T, TILE>(a.help, smem_d, &blk_s);  // a fallback system's FP64 product comes first
         if (threadIdx.x == 0) {
             const unsigned int q = atomicAdd(&a.queue[0], 1u);
             sys_s = (q < (unsigned int)a.count) ? a.order[q] : -1;
+            if (sys_s >= 0) atomicAdd(&a.queue[2], 1u);
         }
         __syncthreads();
         const int sys = sys_s;
         __syncthreads();
-        if (sys < 0) break;
+        if (sys < 0) {
+            // The queue is empty: keep taking blocks while other CTAs still work on systems (one of them
+            // may yet post its product).  Bounded: past kSpinLimit polls the CTA simply leaves.
+            for (long long polls = 0; polls < kSpinLimit; ++polls) {
+                help_pass<T, TILE>(a.help, smem_d, &blk_s);
+                if (threadIdx.x == 0) stop_s = (*(volatile unsigned int*)&a.queue[2] == 0u) ? 1 : 0;
+                __syncthreads();
+                const int quit = stop_s;
+                __syncthreads();
+                if (quit) break;
+                __nanosleep(1000);
+            }
+            break;
+        }
         const int n = a.n[sys];
         const double* A = a.A + a.offA[sys];
         const double* b = a.b + a.offv[sys];
@@ -652,13 +712,46 @@ __global__ void __launch_bounds__(T, T >= 1024 ? 1 : 3) batched_kernel(BatchArgs
             }
         }
         if (!done) {
-            // FP64 fallback: M = A G and its GENP in FP64 (first multiplier), classical FP64 sweeps.
-            double* smem_d = reinterpret_cast<double*>(smem);
+            // FP64 fallback: M = A G and its GENP in FP64 (first multiplier), classical FP64 sweeps.  The
+            // product (n^3 FMAs on the DFMA pipe) is posted as row blocks for the other CTAs to share,
+            // unless another system already holds this launch's job slot.
             double* y64 = V;
             gen_gaussian_f32<T>((int64_t)n * n, a.seed, (uint64_t)sys, G);
+            __threadfence();  // G before the job is published
             __syncthreads();
-            cta_gemm<T, TILE, double, double>(n, n, n, A, n, G, n, M64, n, 1.0, 0.0, smem_d);
-            info = cta_genp<T, TILE, double>(n, M64, smem_d, &flag);
+            HelpJob* h = a.help;
+            if (threadIdx.x == 0) {
+                job_s = 0;
+                if (n > TILE && atomicCAS(&h->claimed, 0u, 1u) == 0u) {
+                    h->n = n;
+                    h->blocks = (n + TILE - 1) / TILE;
+                    h->A = A;
+                    h->G = G;
+                    h->M = M64;
+                    __threadfence();
+                    st_release(&h->ready, 1);
+                    job_s = 1;
+                }
+            }
+            __syncthreads();
+            const bool shared = job_s != 0;
+            if (shared) {
+                help_pass<T, TILE>(h, smem_d, &blk_s);
+                if (threadIdx.x == 0) {
+                    long long spins = 0;
+                    stop_s = 0;
+                    while (ld_acquire(&h->done) < h->blocks) {
+                        if (++spins > kSpinLimit) { stop_s = 1; break; }
+                        __nanosleep(128);
+                    }
+                }
+                __syncthreads();
+                stranded = stop_s != 0;
+                __threadfence();  // the helpers' rows of M are read below
+            } else {
+                cta_gemm<T, TILE, double, double>(n, n, n, A, n, G, n, M64, n, 1.0, 0.0, smem_d);
+            }
+            info = stranded ? -1 : cta_genp<T, TILE, double>(n, M64, smem_d, &flag);
             if (info == 0) {
                 for (int i = threadIdx.x; i < n; i += T) y64[i] = b[i];
                 __syncthreads();
@@ -701,8 +794,10 @@ __global__ void __launch_bounds__(T, T >= 1024 ? 1 : 3) batched_kernel(BatchArgs
             a.info[sys] = done ? 0 : info;
             a.berr[sys] = (!done && info != 0) ? __longlong_as_double(0x7ff8000000000000LL) : eta;
             a.sweeps[sys] = total_sweeps;
+            atomicSub(&a.queue[2], 1u);
         }
         __syncthreads();
+        if (stranded) break;  // never reached in practice: leave the scratch to the late helper
     }
     // the last CTA to leave re-arms the queue for the next launch (or graph replay)
     if (threadIdx.x == 0) {
@@ -710,6 +805,11 @@ __global__ void __launch_bounds__(T, T >= 1024 ? 1 : 3) batched_kernel(BatchArgs
         if (atomicAdd(&a.queue[1], 1u) == gridDim.x - 1) {
             a.queue[0] = 0u;
             a.queue[1] = 0u;
+            a.queue[2] = 0u;
+            a.help->claimed = 0u;
+            a.help->ready = 0;
+            a.help->next = 0u;
+            a.help->done = 0;
             __threadfence();
         }
     }
@@ -729,6 +829,8 @@ rmge_status launch_batched(const BatchArgs& a, int ctas, cudaStream_t s) {
 }
 
 }  // namespace
+
+static_assert(64 + sizeof(HelpJob) <= 256, "the job slot lives in the zeroed queue head");
 
 size_t batched_scratch_bytes(int64_t nmax, int ctas) {
     return align256((size_t)ctas * (size_t)(3 * nmax * nmax + 2 * nmax) * sizeof(float)) +
@@ -757,6 +859,7 @@ rmge_status batched_solve(int64_t count, const int32_t* n, const int64_t* offA, 
     a.tol = tol;
     a.nmax = nmax;
     a.queue = reinterpret_cast<unsigned int*>(base);
+    a.help = reinterpret_cast<HelpJob*>(base + 64);  // inside the 256 bytes the caller zeroes per launch
     a.scratch = reinterpret_cast<float*>(base + 256);
     a.dscratch = reinterpret_cast<double*>(base + 256 +
                                            align256((size_t)ctas * (size_t)(3 * nmax * nmax + 2 * nmax) * sizeof(float)));

@@ -71,3 +71,31 @@ def test_uneven_batch_all_systems_reach_target(orc):
     for i in range(0, 120, 7):
         x = s.solution(i).cpu().numpy().reshape(-1, 1)
         assert orc.backward_error(As[i], x, bs[i]) <= 1e-13
+
+
+def test_fp64_fallback_shares_its_product(orc):
+    """Systems with kappa(A) = 1e12 defeat every FP32 draw (kappa u_32 >> 1) and end in the FP64 fallback.
+    The first of them in a launch posts its FP64 product A G as row blocks that the other CTAs take
+    between systems; the second finds the launch's job slot taken and computes its product alone.  Both
+    reach the FP64 target, and a second launch (the slot re-armed) repeats them."""
+    As, bs = [], []
+    for i, n in enumerate([300, 257, 40, 100, 64, 129, 200, 33]):
+        if i < 2:
+            A, B = W.orthogonal_factor_system(n, 1, 1e-12, seed=71 + i)
+        else:
+            A, B = W.gaussian_system(n, 1, seed=80 + i)
+        As.append(A)
+        bs.append(B)
+    for config in sorted(CONFIGS):
+        s = BatchedSolver(As, bs, seed=5, max_sweeps=40, be_tol=1e-13)
+        for _ in range(2):
+            s.x.zero_()
+            s.launch(config, 2 * 152)
+            torch.cuda.synchronize()
+            info = s.info.cpu().numpy()
+            berr = s.berr.cpu().numpy()
+            assert np.all(info == 0), (config, info)
+            assert np.all(berr <= 1e-13), (config, berr)
+            for i in range(len(As)):
+                x = s.solution(i).cpu().numpy().reshape(-1, 1)
+                assert orc.backward_error(As[i], x, bs[i]) <= 1e-13, (config, i)
