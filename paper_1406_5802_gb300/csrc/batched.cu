@@ -738,11 +738,13 @@ __global__ void __launch_bounds__(T, T >= 1024 ? 1 : 3) batched_kernel(BatchArgs
             if (shared) {
                 help_pass<T, TILE>(h, smem_d, &blk_s);
                 if (threadIdx.x == 0) {
+                    // A block is at most TILE n^2 FMAs (under a second at n = 4096 with three CTAs on the
+                    // SM's DFMA pipe); the bound, about a minute of 1 us polls, only ends a real fault.
                     long long spins = 0;
                     stop_s = 0;
                     while (ld_acquire(&h->done) < h->blocks) {
-                        if (++spins > kSpinLimit) { stop_s = 1; break; }
-                        __nanosleep(128);
+                        if (++spins > 16 * kSpinLimit) { stop_s = 1; break; }
+                        __nanosleep(1000);
                     }
                 }
                 __syncthreads();
