@@ -347,7 +347,8 @@ def timed_form(rmge, A, Bm, M, X, kind, prec, args, stream, barrier, world, valu
     """Whole solves (multiplier, A G, GENP, solve, refinement to the target) in one form, timed like the main
     line; the apply step is also timed on its own for the roofline of its kernel."""
     import torch
-    import torch.distributed as dist
+
+    from paper_1406_5802_gb300 import ranks
     n, k = A.shape[0], Bm.shape[1]
     two = isinstance(kind, tuple)
     if two:
@@ -395,15 +396,12 @@ def timed_form(rmge, A, Bm, M, X, kind, prec, args, stream, barrier, world, valu
         res.append(one(args.warmup + i, ev))
     m1.record(stream)
     torch.cuda.synchronize()
-    mt = torch.tensor([m0.elapsed_time(m1)], device="cuda")
-    if world > 1:
-        dist.all_reduce(mt, op=dist.ReduceOp.MAX)
-    ms = float(mt.item())
+    ms = ranks.max_over_ranks(m0.elapsed_time(m1), world, "cuda")
     sw = [int(r[2].item()) for r in res]
     be = [float(r[1][q].item()) for r, q in zip(res, sw)]
     ok = all(int(r[0].item()) == 0 for r in res) and all(b <= BE_TOL for b in be)
     apply_ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
-    val = args.steps * world / (ms / 1e3)
+    val = ranks.whole_job_rate(args.steps, world, ms / 1e3)
     out = {"form": FORM_TEXT[args_form_key(kind, prec)], "value": val, "unit": "solves/s",
            "ms_per_step": ms / args.steps, "all_steps_be_le_1e-13": ok, "max_berr": max(be),
            "mean_sweeps": sum(sw) / len(sw), "apply_ms": apply_ms, "speedup_vs_f64": val / value_f64,
@@ -448,6 +446,7 @@ def main():
     import torch
     import torch.distributed as dist
 
+    from paper_1406_5802_gb300 import ranks
     from paper_1406_5802_gb300 import rmge
     from paper_1406_5802_gb300 import workloads as W
 
@@ -469,7 +468,7 @@ def main():
     rmge.load_library()
 
     n, k = N_SYS, K_RHS
-    A_np, B_np = W.orthogonal_factor_system(n, k, SIGMA_MIN, seed=SEED + 7919 * rank)
+    A_np, B_np = W.orthogonal_factor_system(n, k, SIGMA_MIN, seed=ranks.system_seed(SEED, rank))
     A = torch.as_tensor(A_np).cuda()
     Bm = torch.as_tensor(B_np).cuda()
     kind, prec = "gaussian", "f64"
@@ -519,10 +518,7 @@ def main():
     th.join(timeout=2)
     barrier()
     ms = t0.elapsed_time(t1)
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = ranks.max_over_ranks(ms, world, "cuda")  # the whole job lasts as long as its slowest rank
 
     # every timed solve must have met the accuracy target
     infos = [int(r[0].item()) for r in results]
@@ -536,8 +532,7 @@ def main():
         orc.set_threads(os.cpu_count() or 1)
         be_oracle = orc.backward_error(A.cpu().numpy(), X.cpu().numpy(), Bm.cpu().numpy())
 
-    solves = args.steps * world
-    value = solves / (ms_max / 1e3)
+    value = ranks.whole_job_rate(args.steps, world, ms_max / 1e3)
     mean_sweeps = sum(sweeps) / len(sweeps)
     flops = flops_per_solve(n, k, mean_sweeps)
     apply_ms = sum(a.elapsed_time(b) for a, b in ev_apply) / len(ev_apply)
@@ -577,10 +572,7 @@ def main():
         be_h.copy_(berr, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - te
-    e2e_t = torch.tensor([e2e_s], device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = solves / float(e2e_t.item())
+    e2e_value = ranks.whole_job_rate(args.steps, world, ranks.max_over_ranks(e2e_s, world, "cuda"))
 
     if rank == 0:
         peaks = {}
