@@ -33,42 +33,34 @@ def _lib():
     return L
 
 
+def pack_layout(sizes):
+    """Packing of uneven systems: element offsets of A_i (n_i x n_i, back to back) and of b_i, x_i, and the
+    processing order (decreasing n, ties in index order), as the persistent kernel's queue takes them."""
+    sizes = np.asarray(sizes, dtype=np.int32)
+    if sizes.ndim != 1 or sizes.size == 0 or sizes.min() < 1:
+        raise ValueError("sizes must be a non-empty list of positive orders")
+    sq = sizes.astype(np.int64) ** 2
+    offA = np.zeros(sizes.size, np.int64)
+    offv = np.zeros(sizes.size, np.int64)
+    offA[1:] = np.cumsum(sq)[:-1]
+    offv[1:] = np.cumsum(sizes.astype(np.int64))[:-1]
+    order = np.argsort(-sizes, kind="stable").astype(np.int32)  # longest first
+    return offA, offv, order
+
+
 class BatchedSolver:
     """Holds one packed batch (A_i, b_i) on the device and solves it with one persistent launch."""
 
     def __init__(self, As, bs, seed: int, max_sweeps: int = 10, be_tol: float = 1e-13, device="cuda"):
         sizes = np.array([a.shape[0] for a in As], dtype=np.int32)
-        self.count = len(As)
-        self.nmax = int(sizes.max())
-        offA = np.zeros(self.count, np.int64)
-        offv = np.zeros(self.count, np.int64)
-        offA[1:] = np.cumsum(sizes.astype(np.int64) ** 2)[:-1]
-        offv[1:] = np.cumsum(sizes.astype(np.int64))[:-1]
-        order = np.argsort(-sizes, kind="stable").astype(np.int32)  # longest first
-        tot_a = int((sizes.astype(np.int64) ** 2).sum())
-        tot_v = int(sizes.sum())
-        A_h = torch.empty(tot_a, dtype=torch.float64)
-        b_h = torch.empty(tot_v, dtype=torch.float64)
+        offA, offv, _ = pack_layout(sizes)
+        A_h = torch.empty(int((sizes.astype(np.int64) ** 2).sum()), dtype=torch.float64)
+        b_h = torch.empty(int(sizes.sum()), dtype=torch.float64)
         for i, (a, b) in enumerate(zip(As, bs)):
             n = sizes[i]
             A_h[offA[i]:offA[i] + n * n] = torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).reshape(-1)
             b_h[offv[i]:offv[i] + n] = torch.as_tensor(np.ascontiguousarray(b, dtype=np.float64)).reshape(-1)
-        self.sizes = sizes
-        self.offA, self.offv = offA, offv
-        self.d_n = torch.as_tensor(sizes).to(device)
-        self.d_offA = torch.as_tensor(offA).to(device)
-        self.d_offv = torch.as_tensor(offv).to(device)
-        self.d_order = torch.as_tensor(order).to(device)
-        self.A = A_h.to(device)
-        self.b = b_h.to(device)
-        self.x = torch.empty(tot_v, dtype=torch.float64, device=device)
-        self.info = torch.empty(self.count, dtype=torch.int32, device=device)
-        self.berr = torch.empty(self.count, dtype=torch.float64, device=device)
-        self.sweeps = torch.empty(self.count, dtype=torch.int32, device=device)
-        self.seed, self.max_sweeps, self.be_tol = int(seed), int(max_sweeps), float(be_tol)
-        self.config, self.ctas = 1, torch.cuda.get_device_properties(device).multi_processor_count
-        self.ws = None
-        self.graph = None
+        self._init_packed(sizes, offA, offv, A_h.to(device), b_h.to(device), seed, max_sweeps, be_tol)
 
     @classmethod
     def synthetic(cls, sizes, seed: int, leading_scale: float = 1e-10, **kw):
@@ -78,10 +70,7 @@ class BatchedSolver:
         sizes = np.asarray(sizes, dtype=np.int32)
         g = torch.Generator(device="cuda")
         g.manual_seed(int(seed))
-        offA = np.zeros(len(sizes), np.int64)
-        offv = np.zeros(len(sizes), np.int64)
-        offA[1:] = np.cumsum(sizes.astype(np.int64) ** 2)[:-1]
-        offv[1:] = np.cumsum(sizes.astype(np.int64))[:-1]
+        offA, offv, _ = pack_layout(sizes)
         A = torch.randn(int((sizes.astype(np.int64) ** 2).sum()), generator=g, dtype=torch.float64, device="cuda")
         A[torch.as_tensor(offA, device="cuda")] *= leading_scale
         b = torch.randn(int(sizes.sum()), generator=g, dtype=torch.float64, device="cuda")
@@ -93,7 +82,7 @@ class BatchedSolver:
         self.count = len(sizes)
         self.nmax = int(sizes.max())
         self.sizes, self.offA, self.offv = sizes, offA, offv
-        order = np.argsort(-sizes, kind="stable").astype(np.int32)
+        order = pack_layout(sizes)[2]
         self.d_n = torch.as_tensor(sizes).to(device)
         self.d_offA = torch.as_tensor(offA).to(device)
         self.d_offv = torch.as_tensor(offv).to(device)
