@@ -1,0 +1,60 @@
+"""The benchmark's output contract, checked on the source (no GPU): the JSON line of each arm carries
+every key its consumers read, and the timed region's rate comes from the slowest rank."""
+import ast
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MAIN_KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+             "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks", "cpu_baseline"}
+ROOFLINE_KEYS = {"bound", "achieved", "peak", "unit", "frac", "traffic"}
+E2E_KEYS = {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+CPU_KEYS = {"value", "unit", "cores", "kind", "sample"}
+
+
+def _dict_assigned(fn, name):
+    for node in ast.walk(fn):
+        if isinstance(node, ast.Assign) and any(isinstance(t, ast.Name) and t.id == name for t in node.targets):
+            if isinstance(node.value, ast.Dict):
+                return node.value
+    raise AssertionError(f"no dict literal assigned to {name!r} in {fn.name}")
+
+
+def _keys(d):
+    return {k.value for k in d.keys if isinstance(k, ast.Constant)}
+
+
+def _sub(d, key):
+    for k, v in zip(d.keys, d.values):
+        if isinstance(k, ast.Constant) and k.value == key:
+            return v
+    raise AssertionError(key)
+
+
+def _functions():
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    return {n.name: n for n in tree.body if isinstance(n, ast.FunctionDef)}
+
+
+def test_main_line_keys():
+    fns = _functions()
+    line = _dict_assigned(fns["main"], "line")
+    assert MAIN_KEYS <= _keys(line)
+    assert ROOFLINE_KEYS <= _keys(_sub(line, "roofline"))
+    assert E2E_KEYS <= _keys(_sub(line, "e2e"))
+    assert "workload" in _keys(_sub(line, "config"))
+    assert CPU_KEYS <= _keys(_dict_assigned(fns["main"], "cpu"))
+
+
+def test_reference_line_keys():
+    line = _dict_assigned(_functions()["run_reference"], "line")
+    assert (MAIN_KEYS - {"roofline", "gpu_launches", "clocks"}) | {"impl"} <= _keys(line)
+    assert CPU_KEYS <= _keys(_sub(line, "cpu_baseline"))
+    assert E2E_KEYS <= _keys(_sub(line, "e2e"))
+
+
+def test_rates_use_the_slowest_rank():
+    src = ast.unparse(_functions()["main"])  # literals are normalised: 1e3 reads back as 1000.0
+    assert "ms_max = ranks.max_over_ranks(ms, world, 'cuda')" in src
+    assert "value = ranks.whole_job_rate(args.steps, world, ms_max / 1000.0)" in src
+    assert "ranks.whole_job_rate(args.steps, world, ranks.max_over_ranks(e2e_s, world, 'cuda'))" in src
