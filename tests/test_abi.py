@@ -70,3 +70,12 @@ def test_bad_arguments_are_rejected_without_gpu_work(lib):
     assert lib.rmge_refine(0, 8, 1, p, 8, p, 8, p, p, 1, p, 1, 0, 99, 1e-13, None, None, p, 1 << 20, None) == INVALID
     assert lib.rmge_refine(0, 8, 1, p, 8, p, 8, p, p, 1, p, 1, 0, 3, -1.0, None, None, p, 1 << 20, None) == INVALID
     assert lib.rmge_status_string(6) == b"bounded device wait expired"
+    # empty inputs: no right-hand sides, an empty batch
+    assert lib.rmge_solve(0, 8, 0, p, 8, p, p, 1, p, 1, 0, p, 1 << 20, None) == INVALID
+    assert lib.rmge_workspace_size(8, 0, 0, 0) == 0
+    lib.rmge_solve_batched.restype = C.c_int
+    lib.rmge_solve_batched.argtypes = [C.c_int64] + [C.c_void_p] * 10 + [C.c_uint64, C.c_int32, C.c_double,
+                                                                          C.c_int64, C.c_int32, C.c_int32,
+                                                                          C.c_void_p, C.c_size_t, C.c_void_p]
+    assert lib.rmge_solve_batched(0, p, p, p, p, p, p, p, p, p, p, 1, 10, 1e-13, 8, 1, 152, p, 1 << 20,
+                                  None) == INVALID
