@@ -48,6 +48,7 @@ def lib():
                                                                                flags="C_CONTIGUOUS")]),
             "orc_matmul": (None, [_i64, _i64, _i64, _dp, _dp, _dp]),
             "orc_circulant_dense": (None, [_i64, _dp, _dp]),
+            "orc_circulant_rows": (None, [_i64, _i64, _i64, _dp, _dp, _dp]),
             "orc_dft": (None, [_i64, _dp, _dp, _dp, _dp, C.c_int]),
             "orc_genp": (C.c_int, [_i64, _dp]),
             "orc_genp_blocked": (C.c_int, [_i64, _i64, _dp]),
@@ -190,6 +191,18 @@ def circulant_dense(c):
     n = c.shape[0]
     out = np.empty((n, n), np.float64)
     lib().orc_circulant_dense(n, c, out)
+    return out
+
+
+def circulant_rows(A_rows, c, N=None):
+    """Rows of A H, H the leading n x n block of the N x N circulant with first column c (N = n by
+    default), from the definition; A_rows is r x n."""
+    A_rows, c = _f64(np.atleast_2d(A_rows)), _f64(c)
+    r, n = A_rows.shape
+    N = n if N is None else int(N)
+    assert c.shape[0] >= N
+    out = np.empty((r, n), np.float64)
+    lib().orc_circulant_rows(n, N, r, A_rows, c, out)
     return out
 
 

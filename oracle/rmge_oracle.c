@@ -205,6 +205,22 @@ void orc_toeplitz_dense(int64_t n, const double* c2, double* T) {
 }
 
 /*
+ * Selected rows of A H for a multiplier that is the leading n x n block of an N x N circulant with first
+ * column c (N = n: the circulant of Sec. 5; N = 2n: the Toeplitz multiplier above), straight from the
+ * entries H_kj = c[(k - j) mod N]:  out_ij = sum_{k < n} a_ik c[(k - j) mod N], for the r rows of A given
+ * (r x n).  For checking A H at sizes where the dense H does not fit in memory.
+ */
+void orc_circulant_rows(int64_t n, int64_t N, int64_t r, const double* A, const double* c, double* out) {
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
+    for (int64_t i = 0; i < r; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int64_t k = 0; k < n; ++k) s += A[i * n + k] * c[((k - j) % N + N) % N];
+            out[i * n + j] = s;
+        }
+}
+
+/*
  * Plain O(n^2) DFT y_f = sum_t x_t w^{f t}, w = exp(sign * 2 pi i / n).
  * With sign = +1 this is the matrix Omega of Sec. 5 applied to x.
  */

@@ -112,3 +112,32 @@ def test_structured_multiplier_solve(orc, kind, n):
     kappa = np.linalg.cond(A, np.inf)
     be_p = orc.backward_error(A, Xp, B)
     assert np.max(np.abs(out["X"] - Xp)) / np.max(np.abs(Xp)) <= 10 * kappa * (be + be_p)
+
+
+@pytest.mark.parametrize("n,N", [(5, 5), (16, 16), (64, 128), (33, 66)])
+def test_circulant_rows_is_the_product_with_the_dense_multiplier(orc, n, N):
+    """orc_circulant_rows (rows of A H straight from H_kj = c[(k - j) mod N]) against the dense circulant or
+    Toeplitz block times A by the plain product: same terms in the same order, so bit for bit."""
+    rng = np.random.default_rng(n + N)
+    A = rng.standard_normal((7, n))
+    c = rng.standard_normal(N)
+    D = orc.circulant_dense(c) if N == n else orc.toeplitz_dense(n, c)
+    assert np.array_equal(orc.circulant_rows(A, c, N), orc.matmul(A, D))
+
+
+def test_circulant_rows_exact_on_integers_and_by_the_dft(orc):
+    """Integer inputs: the exact product by Python integers (brute force).  Real inputs: Theorem 5.1's
+    diagonalisation, a row of A C is F^{-1}(F(a) conj(F(c))) for real c."""
+    rng = np.random.default_rng(3)
+    n = 12
+    A = rng.integers(-9, 10, (3, n)).astype(np.float64)
+    c = rng.integers(-9, 10, n).astype(np.float64)
+    got = orc.circulant_rows(A, c)
+    for i in range(3):
+        for j in range(n):
+            assert got[i, j] == sum(int(A[i, k]) * int(c[(k - j) % n]) for k in range(n))
+    n = 1024
+    A = rng.standard_normal((4, n))
+    c = rng.standard_normal(n)
+    ref = np.real(np.fft.ifft(np.fft.fft(A, axis=1) * np.conj(np.fft.fft(c))[None, :], axis=1))
+    assert np.max(np.abs(orc.circulant_rows(A, c) - ref)) <= 1e-12 * np.max(np.abs(ref))
