@@ -23,8 +23,8 @@
  *   cudaStream_t; NULL = legacy default stream).  It returns RMGE_OK when all launches were
  *   accepted.  Numerical outcomes (breakdown step, growth, backward errors, sweep count)
  *   are written by the kernels to caller memory and are valid once the stream has been
- *   synchronised; none of them changes the return value.  rmge_refine is the one exception
- *   to "enqueue only": see its comment.
+ *   synchronised; none of them changes the return value.  The one exception is an _ex call
+ *   with rmge_options.sync set, which synchronises the stream and returns the outcome.
  * - No call prints, aborts, throws, or traps on the device.  Argument errors return
  *   RMGE_ERR_INVALID_ARG and enqueue nothing; a failed launch returns RMGE_ERR_CUDA.
  * - n >= 1, nrhs >= 1; n <= RMGE_MAX_N.
@@ -47,13 +47,14 @@ typedef struct CUstream_st* rmge_stream_t;
 typedef enum {
     RMGE_OK = 0,
     RMGE_ERR_INVALID_ARG = 1,   /* bad size, leading dimension, pointer or enum; nothing enqueued */
-    RMGE_ERR_BREAKDOWN = 2,     /* a zero or non-finite pivot (Cor. 3.1); only from rmge_refine */
-    RMGE_ERR_GROWTH = 3,        /* reserved */
-    RMGE_ERR_NOT_CONVERGED = 4, /* rmge_refine stopped above be_tol */
+    RMGE_ERR_BREAKDOWN = 2,     /* a zero or non-finite pivot (Cor. 3.1) */
+    RMGE_ERR_GROWTH = 3,        /* pivot growth above rmge_options.growth_tol (Thm 3.2, Remark 3.2) */
+    RMGE_ERR_NOT_CONVERGED = 4, /* refinement stopped above be_tol */
     RMGE_ERR_CUDA = 5,          /* a CUDA launch or copy failed */
-    RMGE_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up (see rmge_refine) */
+    RMGE_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
     RMGE_ERR_WORKSPACE = 7,     /* ws is NULL, too small or misaligned */
-    RMGE_ERR_UNSUPPORTED = 8    /* valid request the library does not implement (e.g. circulant n not 2^p) */
+    RMGE_ERR_UNSUPPORTED = 8,   /* valid request the library does not implement (e.g. circulant n not 2^p) */
+    RMGE_ERR_NONFINITE = 9      /* a result (factors, X) holds an Inf or NaN */
 } rmge_status;
 
 /* Random multiplier G (Sec. 4-5). */
@@ -87,14 +88,47 @@ typedef enum {
 } rmge_prec;
 
 /*
+ * Options of the _ex entry points.  rmge_options_init fills the defaults, which are what the calls
+ * without _ex use; a NULL options pointer means the defaults too.
+ * - growth_tol (default 0 = no gate): rmge_factor_ex reports RMGE_ERR_GROWTH when the pivot growth
+ *   max|U_ij| / max|M_ij| exceeds it.  Thm 3.2 bounds the pivots of GENP on a Gaussian-multiplied
+ *   matrix and Remark 3.2 ties the stability of GENP to that growth; growth near 1/u of the factor
+ *   precision means the factors carry no correct digits.
+ * - spin_limit (default 2^22, about a second): polls of each bounded device-side wait of the
+ *   triangular solves (a row block waits for the blocks it depends on) and of the batched solve (a
+ *   system waits for the CTAs that share its FP64 fallback product) before the wait gives up: the
+ *   solve then records RMGE_ERR_TIMEOUT and its CTAs return without writing; the batched system gets
+ *   info -1.  0 gives up at the first unmet poll.  The tensor-core kernels keep their own
+ *   time-based limit.
+ * - gmres_m (default 16, at most 256): restart length of the FGMRES cycles that refinement runs
+ *   with reduced-precision factors (see rmge_refine).  The workspace grows with it
+ *   (rmge_workspace_size_ex).  A cycle also ends once every column's residual estimate has fallen by
+ *   a factor 1e-6.
+ * - status (device int32, may be NULL): receives the call's outcome, RMGE_OK or the first of
+ *   RMGE_ERR_TIMEOUT, RMGE_ERR_BREAKDOWN, RMGE_ERR_NONFINITE, then RMGE_ERR_GROWTH (factor) or
+ *   RMGE_ERR_NOT_CONVERGED (refine) that applies; valid once the stream is synchronised.
+ * - sync (default 0): nonzero makes the call synchronise `stream` after enqueuing its work and return
+ *   that outcome instead of RMGE_OK (not for use inside stream capture).
+ */
+typedef struct rmge_options {
+    double growth_tol;
+    int64_t spin_limit;
+    int32_t gmres_m;
+    int32_t sync;
+    int32_t* status;
+} rmge_options;
+
+void rmge_options_init(rmge_options* opts);
+
+/*
  * Multiplier storage (what `G` points to in every call below):
  * - RMGE_GAUSSIAN: n x n row-major, leading dimension n; FP64 for RMGE_F64 and RMGE_F64X_TC, FP32
  *   for the other precisions.
  * - circulant kinds: 3n FP64 values: the first column c[0..n-1], then its DFT u = Omega c
  *   (Theorem 5.1; Omega = (w^{ij}), w = exp(2 pi sqrt(-1) / n)) stored as n interleaved
- *   (re, im) pairs.  n must be a power of two, 2 <= n <= 8192.
+ *   (re, im) pairs.  n must be a power of two, 4 <= n <= 16384.
  * - Toeplitz kinds: 6n FP64 values, the same for the 2n x 2n circulant whose leading n x n block
- *   is the multiplier: c2[0..2n-1], then its 2n-point DFT.  n a power of two, 2 <= n <= 4096.
+ *   is the multiplier: c2[0..2n-1], then its 2n-point DFT.  n a power of two, 2 <= n <= 8192.
  *   (No square Toeplitz multiplier is cut from a unitary circulant: that block is singular exactly
  *   when u_0 u_n = -1.)
  * rmge_multiplier_bytes returns the size (0 for an invalid request).
@@ -106,6 +140,9 @@ size_t rmge_multiplier_bytes(rmge_mult_kind kind, int64_t n, rmge_prec prec);
  * this size serves all of them.  0 for an invalid request.
  */
 size_t rmge_workspace_size(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec);
+
+/* rmge_workspace_size for the _ex calls with these options (the FGMRES basis grows with gmres_m). */
+size_t rmge_workspace_size_ex(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec, const rmge_options* opts);
 
 /*
  * The smaller scratch size that rmge_solve, and rmge_solve_backward without refinement, need
@@ -147,6 +184,9 @@ rmge_status rmge_apply_multiplier(rmge_mult_kind kind, int64_t n, const double* 
  */
 rmge_status rmge_factor(int64_t n, void* M, int64_t ldm, rmge_prec prec, int32_t* info, double* growth,
                         void* ws, size_t ws_bytes, rmge_stream_t stream);
+/* rmge_factor with options: growth gate (RMGE_ERR_GROWTH), status and sync as described there. */
+rmge_status rmge_factor_ex(int64_t n, void* M, int64_t ldm, rmge_prec prec, int32_t* info, double* growth,
+                           const rmge_options* opts, void* ws, size_t ws_bytes, rmge_stream_t stream);
 
 /*
  * X = G U^{-1} L^{-1} B (Fact 4.1: x = H y with (A H) y = b), nrhs right-hand sides.
@@ -157,6 +197,11 @@ rmge_status rmge_factor(int64_t n, void* M, int64_t ldm, rmge_prec prec, int32_t
 rmge_status rmge_solve(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void* LU, int64_t ldlu,
                        const void* G, const double* B, int64_t ldb, double* X, int64_t ldx, rmge_prec prec,
                        void* ws, size_t ws_bytes, rmge_stream_t stream);
+/* rmge_solve with options: the spin limit of the triangular solves' waits, and a status of RMGE_ERR_TIMEOUT
+ * or RMGE_ERR_NONFINITE (X holds an Inf or NaN, e.g. from factors that broke down). */
+rmge_status rmge_solve_ex(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void* LU, int64_t ldlu,
+                          const void* G, const double* B, int64_t ldb, double* X, int64_t ldx, rmge_prec prec,
+                          const rmge_options* opts, void* ws, size_t ws_bytes, rmge_stream_t stream);
 
 /*
  * Iterative refinement of X (Sec. 1.2 and Sec. 7.1: one or more sweeps of residual
@@ -181,6 +226,14 @@ rmge_status rmge_refine(rmge_mult_kind kind, int64_t n, int64_t nrhs, const doub
                         const void* LU, int64_t ldlu, const void* G, const double* B, int64_t ldb,
                         double* X, int64_t ldx, rmge_prec prec, int32_t max_iters, double be_tol,
                         double* berr, int32_t* iters, void* ws, size_t ws_bytes, rmge_stream_t stream);
+/* rmge_refine with options: FGMRES restart length, spin limit, and a status of RMGE_ERR_TIMEOUT,
+ * RMGE_ERR_NONFINITE (the last backward error is not finite) or RMGE_ERR_NOT_CONVERGED (it is above be_tol).
+ * ws: rmge_workspace_size_ex bytes for these options. */
+rmge_status rmge_refine_ex(rmge_mult_kind kind, int64_t n, int64_t nrhs, const double* A, int64_t lda,
+                           const void* LU, int64_t ldlu, const void* G, const double* B, int64_t ldb,
+                           double* X, int64_t ldx, rmge_prec prec, int32_t max_iters, double be_tol,
+                           double* berr, int32_t* iters, const rmge_options* opts, void* ws, size_t ws_bytes,
+                           rmge_stream_t stream);
 
 /*
  * Adjoint of X = A^{-1} B for a loss L with dX = dL/dX given (n x nrhs): reusing the factors of
@@ -239,7 +292,7 @@ rmge_status rmge_refine_two_sided(rmge_mult_kind kindF, const void* F, rmge_mult
  * of A H and Z = Q^T A (l x n), so that A ~ Q Z = Q Q^T A (rank <= l).  The paper shows that l equal
  * to the numerical rank r (no oversampling) suffices with Gaussian H.
  * Multipliers: RMGE_GAUSSIAN, H is n x l FP64 (leading dimension l); the circulant kinds
- * (RMGE_CIRCULANT_GAUSSIAN, _UNIFORM, _UNITARY; n a power of two <= 8192), H is the n x l leading block
+ * (RMGE_CIRCULANT_GAUSSIAN, _UNIFORM, _UNITARY; n a power of two, 4 <= n <= 16384), H is the n x l leading block
  * of the circulant stored as by rmge_make_multiplier (3n FP64; Sec. 7.2's Toeplitz multipliers),
  * applied by FFT.  1 <= l <= 64, l <= m, l <= n.
  * rmge_lowrank_multiplier draws H (the Gaussian entries are the first n l of the stream of
@@ -266,15 +319,17 @@ rmge_status rmge_lowrank_project(int64_t m, int64_t n, int32_t l, const double* 
  * a serving loop with latency guarantees (a device allocation can synchronise the whole device),
  * or a plugin whose host process owns all device memory and passes it only inputs and outputs.
  * This call takes the same inputs and outputs as rmge_solve but no workspace: its scratch is one
- * file-scope device array of rmge_noalloc_capacity() bytes (16 MiB), which every GPU that loads the
- * library holds until the process exits.  The call allocates nothing (no cudaMalloc, cudaFree or
- * allocating library routine).  On the first call on a device it looks up the array's device
- * address with cudaGetSymbolAddress (that device must be current) and caches it; make that first
- * call before any stream capture.  Requests whose rmge_solve_workspace_size exceeds the capacity
- * return RMGE_ERR_WORKSPACE and enqueue nothing (FP64 with nrhs = 16 fits n up to about 43 000).  Every call
- * shares the array and leaves its contents behind; each call clears what must start at zero (the
- * control block and the solve flags) on its stream before use, so calls that follow one another on
- * a stream are safe, but calls that overlap on the GPU (other streams, other host threads) race.
+ * file-scope device array of rmge_noalloc_capacity() bytes (16 MiB).  The call itself allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library routine); it looks up the array's device
+ * address with cudaGetSymbolAddress on the current device at every call.  The module that holds the
+ * array loads lazily: the first call on each device loads it, which places the array in device
+ * memory (held until the process exits) and may synchronise the device, so make one call per device
+ * at start-up, before any stream capture or latency-bound loop.  Requests whose
+ * rmge_solve_workspace_size exceeds the capacity return RMGE_ERR_WORKSPACE and enqueue nothing (FP64
+ * with nrhs = 16 fits n up to about 43 000).  Every call shares the array and leaves its contents
+ * behind; each call clears what must start at zero (the control block and the solve flags) on its
+ * stream before use, so calls that follow one another on a stream are safe, but calls that overlap
+ * on the GPU (other streams, other host threads) race.
  */
 rmge_status rmge_solve_noalloc(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void* LU, int64_t ldlu,
                                const void* G, const double* B, int64_t ldb, double* X, int64_t ldx, rmge_prec prec,
@@ -303,7 +358,10 @@ size_t rmge_noalloc_capacity(void);
  * 2: 1024 threads, 64x64) and ctas the number of persistent CTAs -- both chosen by the autotuner of
  * the Python binding.  ws: rmge_batched_workspace_size(nmax, ctas) bytes, 256-byte aligned (per-CTA
  * scratch for G_i, M_i and vectors).  The launch (one memset of the queue head + one kernel) can be
- * captured in a CUDA graph and replayed.
+ * captured in a CUDA graph and replayed.  rmge_solve_batched_ex takes options: spin_limit bounds the
+ * waits of the shared fallback product (its owner's wait for the other CTAs' blocks is 16 spin_limit
+ * polls of 1 us; an idle CTA offers help for spin_limit polls); status and sync report
+ * RMGE_ERR_TIMEOUT if any system's wait gave up (info -1).
  */
 size_t rmge_batched_workspace_size(int64_t nmax, int32_t ctas);
 rmge_status rmge_solve_batched(int64_t count, const int32_t* n, const int64_t* offA, const int64_t* offv,
@@ -311,6 +369,11 @@ rmge_status rmge_solve_batched(int64_t count, const int32_t* n, const int64_t* o
                                double* berr, int32_t* sweeps, uint64_t seed, int32_t max_sweeps, double be_tol,
                                int64_t nmax, int32_t config, int32_t ctas, void* ws, size_t ws_bytes,
                                rmge_stream_t stream);
+rmge_status rmge_solve_batched_ex(int64_t count, const int32_t* n, const int64_t* offA, const int64_t* offv,
+                                  const int32_t* order, const double* A, const double* b, double* x, int32_t* info,
+                                  double* berr, int32_t* sweeps, uint64_t seed, int32_t max_sweeps, double be_tol,
+                                  int64_t nmax, int32_t config, int32_t ctas, const rmge_options* opts, void* ws,
+                                  size_t ws_bytes, rmge_stream_t stream);
 
 /* Number of kernel launches this process has enqueued through the library so far (host-side
  * counter; lets a caller count the kernels of a timed region). */

@@ -21,16 +21,7 @@ TUNE_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "
 
 
 def _lib():
-    L = rmge._cuda_lib()
-    if not hasattr(L, "_batched_sig"):
-        L.rmge_batched_workspace_size.restype = C.c_size_t
-        L.rmge_batched_workspace_size.argtypes = [C.c_int64, C.c_int32]
-        L.rmge_solve_batched.restype = C.c_int
-        vp = C.c_void_p
-        L.rmge_solve_batched.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_uint64, C.c_int32,
-                                         C.c_double, C.c_int64, C.c_int32, C.c_int32, vp, C.c_size_t, vp]
-        L._batched_sig = True
-    return L
+    return rmge._cuda_lib()
 
 
 def pack_layout(sizes):
@@ -109,17 +100,23 @@ class BatchedSolver:
         if self.ws is None or self.ws.numel() < need:
             self.ws = torch.empty(need, dtype=torch.uint8, device=self.A.device)
 
-    def launch(self, config=None, ctas=None):
+    def launch(self, config=None, ctas=None, opts=None):
+        """One launch of rmge_solve_batched (rmge_solve_batched_ex with opts, an rmge.Options); returns the
+        call's return value (its outcome when opts.sync is set)."""
         config = self.config if config is None else config
         ctas = self.ctas if ctas is None else ctas
         self._ensure_ws(ctas)
         p = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
-        st = _lib().rmge_solve_batched(self.count, p(self.d_n), p(self.d_offA), p(self.d_offv), p(self.d_order),
-                                       p(self.A), p(self.b), p(self.x), p(self.info), p(self.berr), p(self.sweeps),
-                                       self.seed, self.max_sweeps, self.be_tol, self.nmax, int(config), int(ctas),
-                                       p(self.ws), self.ws.numel(), C.c_void_p(torch.cuda.current_stream().cuda_stream))
-        if st != 0:
-            raise rmge.RmgeError("rmge_solve_batched", st)
+        args = (self.count, p(self.d_n), p(self.d_offA), p(self.d_offv), p(self.d_order), p(self.A), p(self.b),
+                p(self.x), p(self.info), p(self.berr), p(self.sweeps), self.seed, self.max_sweeps, self.be_tol,
+                self.nmax, int(config), int(ctas))
+        tail = (p(self.ws), self.ws.numel(), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        if opts is None:
+            st = _lib().rmge_solve_batched(*args, *tail)
+            rmge._check("rmge_solve_batched", st)
+            return st
+        st = _lib().rmge_solve_batched_ex(*args, C.byref(opts), *tail)
+        return rmge._check_ex("rmge_solve_batched_ex", st, opts)
 
     def tune(self, reps: int = 2, use_cache: bool = True):
         """Time every compiled variant at 1..3 persistent CTAs per SM on this batch; keep the fastest.

@@ -27,7 +27,8 @@ bool is_circ(rmge_mult_kind k) { return k != RMGE_GAUSSIAN; }
 bool is_toeplitz(rmge_mult_kind k) { return k == RMGE_TOEPLITZ_GAUSSIAN || k == RMGE_TOEPLITZ_UNIFORM; }
 int64_t fft_len(rmge_mult_kind k, int64_t n) { return is_toeplitz(k) ? 2 * n : n; }
 bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
-bool circ_ok(rmge_mult_kind k, int64_t n) { return pow2(n) && n >= 2 && fft_len(k, n) <= 8192; }
+// one real transform of length N = 2^p, 4 <= N <= 16384, per CTA (fft.cu)
+bool circ_ok(rmge_mult_kind k, int64_t n) { return pow2(n) && fft_len(k, n) >= 4 && fft_len(k, n) <= 16384; }
 size_t elem(rmge_prec p) { return data_prec(p) == RMGE_F64 ? 8 : 4; }
 
 int64_t nflags_for(int64_t n, int64_t nrhs) {
@@ -46,14 +47,40 @@ struct Ws {
     double* gm;                // FGMRES work
     unsigned long long* tcmx;  // FP16 scaling slots
     char* oz;                  // digit planes and exponents of the emulated FP64 products
+    long long spin;            // spin limit of the bounded waits (rmge_options.spin_limit)
+    int gm_m;                  // FGMRES restart length (rmge_options.gmres_m)
 };
+
+// rmge_options with the defaults filled in (the calls without _ex use these).
+struct Opts {
+    double growth_tol = 0.0;
+    long long spin = kSpinLimit;
+    int gm_m = kGmresM;
+    bool sync = false;
+    int32_t* status = nullptr;
+    bool report() const { return sync || status != nullptr; }
+};
+
+bool opts_of(const rmge_options* o, Opts* out) {
+    *out = Opts{};
+    if (o == nullptr) return true;
+    if (!(o->growth_tol >= 0.0) || o->spin_limit < 0 || o->gmres_m < 1 || o->gmres_m > kMaxGmresM) return false;
+    out->growth_tol = o->growth_tol;
+    out->spin = o->spin_limit;
+    out->gm_m = o->gmres_m;
+    out->sync = o->sync != 0;
+    out->status = o->status;
+    return true;
+}
 
 // full = false: the call needs no tensor-core operand buffers and no FGMRES work (solves, adjoint),
 // which sit at the end of the layout.
 rmge_status carve(void* ws, size_t ws_bytes, int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec, Ws* out,
-                  bool full = true) {
+                  bool full = true, const Opts& o = Opts{}) {
     if (ws == nullptr || ((uintptr_t)ws & 255) != 0) return RMGE_ERR_WORKSPACE;
-    const WsLayout L = ws_layout(n, nrhs, kind, prec);
+    const WsLayout L = ws_layout(n, nrhs, kind, prec, o.gm_m);
+    out->spin = o.spin;
+    out->gm_m = o.gm_m;
     if (ws_bytes < (full ? L.total : L.tcmx)) return RMGE_ERR_WORKSPACE;
     char* b = static_cast<char*>(ws);
     out->st = reinterpret_cast<DevState*>(b + L.state);
@@ -69,6 +96,20 @@ rmge_status carve(void* ws, size_t ws_bytes, int64_t n, int64_t nrhs, rmge_mult_
     out->oz = (full && prec == RMGE_F64X_TC) ? b + L.oz : nullptr;
     if (!full) out->tc = nullptr;
     return RMGE_OK;
+}
+
+// The call's outcome into o.status and, with o.sync, synchronise and return it (rmge_options).
+rmge_status finish_call(const Ws& w, int what, const Opts& o, double be_tol, cudaStream_t s) {
+    if (!o.report()) return RMGE_OK;
+    RMGE_TRY(write_status(w.st, what, o.growth_tol, be_tol, o.status, s));
+    if (!o.sync) return RMGE_OK;
+    int h = RMGE_OK;
+    if (cudaMemcpyAsync(&h, &w.st->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RMGE_ERR_CUDA;
+    }
+    return (rmge_status)h;
 }
 
 // Digit planes (A side, B side) and line exponents of the emulated FP64 products, in w.oz.
@@ -193,7 +234,8 @@ rmge_status refine_loop(rmge_mult_kind kind, rmge_prec prec, bool trans, int64_t
                         int64_t lda, const void* LU, int64_t ldlu, const void* G, const double* B, int64_t ldb,
                         double* X, int64_t ldx, int32_t max_iters, double be_tol, double* berr, int32_t* iters,
                         const Ws& w, int epoch0, cudaStream_t s) {
-    RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, (int)(3 * nrhs), berr, max_iters + 1, s));
+    RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, (int)(3 * nrhs), berr, max_iters + 1, s,
+                        w.spin));
     RMGE_TRY(abs_sums_max(n, A, lda, trans, w.st, s));
     const int* stop = &w.st->stop;
     const PrecondCtx pctx{kind, prec, n, nrhs, LU, ldlu, G, &w, trans};
@@ -206,7 +248,7 @@ rmge_status refine_loop(rmge_mult_kind kind, rmge_prec prec, bool trans, int64_t
         RMGE_TRY(backward_error(n, nrhs, w.R, nrhs, X, ldx, B, ldb, w.st, w.colred, it, be_tol, max_iters, berr, s,
                                 hybrid));
         if (it == max_iters) break;
-        const int epoch = epoch0 + 2 * kGmresM * it;
+        const int epoch = epoch0 + 2 * w.gm_m * it;
         if (!hybrid) {
             // X <- X + G U^{-1} L^{-1} R  (transposed: L^{-T} U^{-T} G^T R)
             RMGE_TRY(correction(kind, prec, n, nrhs, LU, ldlu, G, w.R, nrhs, X, ldx, true, w, epoch, stop, s, trans));
@@ -216,7 +258,8 @@ rmge_status refine_loop(rmge_mult_kind kind, rmge_prec prec, bool trans, int64_t
             // decide_kernel sets the two skip flags, so exactly one of the two runs.
             RMGE_TRY(correction(kind, prec, n, nrhs, LU, ldlu, G, w.R, nrhs, X, ldx, true, w, epoch, &w.st->skip_cls,
                                 s, trans));
-            RMGE_TRY(gmres_cycle(n, nrhs, A, lda, trans, w.R, X, ldx, w.gm, pre, epoch, &w.st->skip_kry, s));
+            RMGE_TRY(gmres_cycle(n, nrhs, w.gm_m, A, lda, trans, w.R, X, ldx, w.gm, pre, epoch, &w.st->skip_kry,
+                                 s));
         }
     }
     return refine_finish(w.st, max_iters, berr, iters, s);
@@ -290,7 +333,7 @@ bool two_sided_ok(rmge_mult_kind kF, const void* F, rmge_mult_kind kH, const voi
 
 }  // namespace
 
-WsLayout ws_layout(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec) {
+WsLayout ws_layout(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec, int gmres_m) {
     WsLayout L{};
     size_t off = 0;
     L.state = off;
@@ -313,7 +356,7 @@ WsLayout ws_layout(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec)
     L.tc = off;
     if (is_tc(prec)) off = align256(off + 4 * 2 * (size_t)n * (size_t)tc_ldk(n));
     L.gm = off;
-    if (data_prec(prec) != RMGE_F64) off = align256(off + gmres_bytes(n, nrhs));
+    if (data_prec(prec) != RMGE_F64) off = align256(off + gmres_bytes(n, nrhs, gmres_m));
     L.oz = off;
     if (prec == RMGE_F64X_TC)
         off = align256(off + 2 * oz_plane_bytes(n, n, kOzSlices) + 2 * sizeof(int) * (size_t)(n + 128) +
@@ -341,6 +384,7 @@ const char* rmge_status_string(rmge_status s) {
         case RMGE_ERR_TIMEOUT: return "bounded device wait expired";
         case RMGE_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
         case RMGE_ERR_UNSUPPORTED: return "unsupported request (e.g. a circulant n that is not a power of two)";
+        case RMGE_ERR_NONFINITE: return "non-finite values in the result";
     }
     return "unknown status";
 }
@@ -358,9 +402,24 @@ size_t rmge_solve_workspace_size(int64_t n, int64_t nrhs, rmge_mult_kind kind, r
 }
 
 size_t rmge_workspace_size(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec) {
-    if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs)) return 0;
+    return rmge_workspace_size_ex(n, nrhs, kind, prec, nullptr);
+}
+
+void rmge_options_init(rmge_options* opts) {
+    if (opts == nullptr) return;
+    const Opts d{};
+    opts->growth_tol = d.growth_tol;
+    opts->spin_limit = d.spin;
+    opts->gmres_m = d.gm_m;
+    opts->sync = 0;
+    opts->status = nullptr;
+}
+
+size_t rmge_workspace_size_ex(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec, const rmge_options* opts) {
+    Opts o;
+    if (!opts_of(opts, &o) || !valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs)) return 0;
     if (is_circ(kind) && !circ_ok(kind, n)) return 0;
-    return ws_layout(n, nrhs, kind, prec).total;
+    return ws_layout(n, nrhs, kind, prec, o.gm_m).total;
 }
 
 rmge_status rmge_make_multiplier(rmge_mult_kind kind, int64_t n, uint64_t seed, uint64_t subsequence, rmge_prec prec,
@@ -436,16 +495,24 @@ rmge_status rmge_apply_multiplier(rmge_mult_kind kind, int64_t n, const double* 
 
 rmge_status rmge_factor(int64_t n, void* M, int64_t ldm, rmge_prec prec, int32_t* info, double* growth, void* ws,
                         size_t ws_bytes, rmge_stream_t stream) {
-    if (!valid_prec(prec) || !check_dims(n, 1) || M == nullptr || ldm < n) return RMGE_ERR_INVALID_ARG;
+    return rmge_factor_ex(n, M, ldm, prec, info, growth, nullptr, ws, ws_bytes, stream);
+}
+
+rmge_status rmge_factor_ex(int64_t n, void* M, int64_t ldm, rmge_prec prec, int32_t* info, double* growth,
+                           const rmge_options* opts, void* ws, size_t ws_bytes, rmge_stream_t stream) {
+    Opts o;
+    if (!opts_of(opts, &o) || !valid_prec(prec) || !check_dims(n, 1) || M == nullptr || ldm < n)
+        return RMGE_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Ws w{};
-    RMGE_TRY(carve(ws, ws_bytes, n, 1, RMGE_GAUSSIAN, prec, &w));
-    RMGE_TRY(state_init(w.st, w.flags, 0, w.colred, 0, nullptr, 0, s));
+    RMGE_TRY(carve(ws, ws_bytes, n, 1, RMGE_GAUSSIAN, prec, &w, true, o));
+    RMGE_TRY(state_init(w.st, w.flags, 0, w.colred, 0, nullptr, 0, s, w.spin));
     if (prec == RMGE_F64)
         RMGE_TRY(genp_factor<double>(n, static_cast<double*>(M), ldm, w.st, s));
     else if (prec == RMGE_F64X_TC) {
         const OzUpdate oz = oz_buffers(w, n);
-        RMGE_TRY(state_init(w.st, w.flags, 0, reinterpret_cast<double*>(oz.kmax), (int)oz_kmax_slots(n), nullptr, 0, s));
+        RMGE_TRY(state_init(w.st, w.flags, 0, reinterpret_cast<double*>(oz.kmax), (int)oz_kmax_slots(n), nullptr, 0, s,
+                            w.spin));
         RMGE_TRY(genp_factor_oz(n, static_cast<double*>(M), ldm, w.st, oz, s));
     }
     else if (prec == RMGE_F32)
@@ -458,40 +525,60 @@ rmge_status rmge_factor(int64_t n, void* M, int64_t ldm, rmge_prec prec, int32_t
                     buf + 3 * plane, ldk, w.tcmx};
         if (tc.scale)
             RMGE_TRY(state_init(w.st, w.flags, 0, reinterpret_cast<double*>(w.tcmx), (int)(2 * (n / kNb + 2)),
-                                nullptr, 0, s));
+                                nullptr, 0, s, w.spin));
         RMGE_TRY(genp_factor_tc(n, static_cast<float*>(M), ldm, w.st, tc, s));
     }
-    return genp_finish(w.st, info, growth, s);
+    RMGE_TRY(genp_finish(w.st, info, growth, s));
+    return finish_call(w, kStatusFactor, o, 0.0, s);
 }
 
 rmge_status rmge_solve(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void* LU, int64_t ldlu, const void* G,
                        const double* B, int64_t ldb, double* X, int64_t ldx, rmge_prec prec, void* ws, size_t ws_bytes,
                        rmge_stream_t stream) {
-    if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs) || LU == nullptr || G == nullptr ||
-        B == nullptr || X == nullptr || ldlu < n || ldb < nrhs || ldx < nrhs)
+    return rmge_solve_ex(kind, n, nrhs, LU, ldlu, G, B, ldb, X, ldx, prec, nullptr, ws, ws_bytes, stream);
+}
+
+rmge_status rmge_solve_ex(rmge_mult_kind kind, int64_t n, int64_t nrhs, const void* LU, int64_t ldlu, const void* G,
+                          const double* B, int64_t ldb, double* X, int64_t ldx, rmge_prec prec,
+                          const rmge_options* opts, void* ws, size_t ws_bytes, rmge_stream_t stream) {
+    Opts o;
+    if (!opts_of(opts, &o) || !valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs) || LU == nullptr ||
+        G == nullptr || B == nullptr || X == nullptr || ldlu < n || ldb < nrhs || ldx < nrhs)
         return RMGE_ERR_INVALID_ARG;
     if (is_circ(kind) && !circ_ok(kind, n)) return RMGE_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Ws w{};
-    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w, false));
-    RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, 0, nullptr, 0, s));
-    return correction(kind, data_prec(prec), n, nrhs, LU, ldlu, G, B, ldb, X, ldx, false, w, 1, nullptr, s);
+    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w, false, o));
+    RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, 0, nullptr, 0, s, w.spin));
+    RMGE_TRY(correction(kind, data_prec(prec), n, nrhs, LU, ldlu, G, B, ldb, X, ldx, false, w, 1, nullptr, s));
+    if (o.report()) RMGE_TRY(nonfinite_scan<double>(n, nrhs, X, ldx, w.st, s));
+    return finish_call(w, kStatusSolve, o, 0.0, s);
 }
 
 rmge_status rmge_refine(rmge_mult_kind kind, int64_t n, int64_t nrhs, const double* A, int64_t lda, const void* LU,
                         int64_t ldlu, const void* G, const double* B, int64_t ldb, double* X, int64_t ldx,
                         rmge_prec prec, int32_t max_iters, double be_tol, double* berr, int32_t* iters, void* ws,
                         size_t ws_bytes, rmge_stream_t stream) {
-    if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs) || A == nullptr || LU == nullptr ||
-        G == nullptr || B == nullptr || X == nullptr || lda < n || ldlu < n || ldb < nrhs || ldx < nrhs ||
-        max_iters < 0 || max_iters > kMaxSweeps || !(be_tol >= 0.0))
+    return rmge_refine_ex(kind, n, nrhs, A, lda, LU, ldlu, G, B, ldb, X, ldx, prec, max_iters, be_tol, berr, iters,
+                          nullptr, ws, ws_bytes, stream);
+}
+
+rmge_status rmge_refine_ex(rmge_mult_kind kind, int64_t n, int64_t nrhs, const double* A, int64_t lda, const void* LU,
+                           int64_t ldlu, const void* G, const double* B, int64_t ldb, double* X, int64_t ldx,
+                           rmge_prec prec, int32_t max_iters, double be_tol, double* berr, int32_t* iters,
+                           const rmge_options* opts, void* ws, size_t ws_bytes, rmge_stream_t stream) {
+    Opts o;
+    if (!opts_of(opts, &o) || !valid_kind(kind) || !valid_prec(prec) || !check_dims(n, nrhs) || A == nullptr ||
+        LU == nullptr || G == nullptr || B == nullptr || X == nullptr || lda < n || ldlu < n || ldb < nrhs ||
+        ldx < nrhs || max_iters < 0 || max_iters > kMaxSweeps || !(be_tol >= 0.0))
         return RMGE_ERR_INVALID_ARG;
     if (is_circ(kind) && !circ_ok(kind, n)) return RMGE_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Ws w{};
-    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w));
-    return refine_loop(kind, data_prec(prec), false, n, nrhs, A, lda, LU, ldlu, G, B, ldb, X, ldx, max_iters, be_tol,
-                       berr, iters, w, 1, s);
+    RMGE_TRY(carve(ws, ws_bytes, n, nrhs, kind, prec, &w, true, o));
+    RMGE_TRY(refine_loop(kind, data_prec(prec), false, n, nrhs, A, lda, LU, ldlu, G, B, ldb, X, ldx, max_iters, be_tol,
+                         berr, iters, w, 1, s));
+    return finish_call(w, kStatusRefine, o, be_tol, s);
 }
 
 rmge_status rmge_solve_backward(rmge_mult_kind kind, int64_t n, int64_t nrhs, const double* A, int64_t lda,
@@ -640,9 +727,20 @@ rmge_status rmge_solve_batched(int64_t count, const int32_t* n, const int64_t* o
                                double* berr, int32_t* sweeps, uint64_t seed, int32_t max_sweeps, double be_tol,
                                int64_t nmax, int32_t config, int32_t ctas, void* ws, size_t ws_bytes,
                                rmge_stream_t stream) {
-    if (count < 1 || count > INT32_MAX || n == nullptr || offA == nullptr || offv == nullptr || order == nullptr ||
-        A == nullptr || b == nullptr || x == nullptr || info == nullptr || berr == nullptr || sweeps == nullptr ||
-        max_sweeps < 0 || max_sweeps > kMaxSweeps || !(be_tol >= 0.0) || config < 0 || config > 2)
+    return rmge_solve_batched_ex(count, n, offA, offv, order, A, b, x, info, berr, sweeps, seed, max_sweeps, be_tol,
+                                 nmax, config, ctas, nullptr, ws, ws_bytes, stream);
+}
+
+rmge_status rmge_solve_batched_ex(int64_t count, const int32_t* n, const int64_t* offA, const int64_t* offv,
+                                  const int32_t* order, const double* A, const double* b, double* x, int32_t* info,
+                                  double* berr, int32_t* sweeps, uint64_t seed, int32_t max_sweeps, double be_tol,
+                                  int64_t nmax, int32_t config, int32_t ctas, const rmge_options* opts, void* ws,
+                                  size_t ws_bytes, rmge_stream_t stream) {
+    Opts o;
+    if (!opts_of(opts, &o) || count < 1 || count > INT32_MAX || n == nullptr || offA == nullptr || offv == nullptr ||
+        order == nullptr || A == nullptr || b == nullptr || x == nullptr || info == nullptr || berr == nullptr ||
+        sweeps == nullptr || max_sweeps < 0 || max_sweeps > kMaxSweeps || !(be_tol >= 0.0) || config < 0 ||
+        config > 2)
         return RMGE_ERR_INVALID_ARG;
     const size_t need = rmge_batched_workspace_size(nmax, ctas);
     if (need == 0) return RMGE_ERR_INVALID_ARG;
@@ -652,8 +750,18 @@ rmge_status rmge_solve_batched(int64_t count, const int32_t* n, const int64_t* o
         (void)cudaGetLastError();
         return RMGE_ERR_CUDA;
     }
-    return batched_solve(count, n, offA, offv, order, A, b, x, info, berr, sweeps, seed, max_sweeps, be_tol, nmax,
-                         config, ctas, ws, s);
+    RMGE_TRY(batched_solve(count, n, offA, offv, order, A, b, x, info, berr, sweeps, seed, max_sweeps, be_tol, nmax,
+                           config, ctas, o.spin, ws, s));
+    if (!o.report()) return RMGE_OK;
+    RMGE_TRY(batched_status(count, info, ws, o.status, s));
+    if (!o.sync) return RMGE_OK;
+    int h = RMGE_OK;
+    if (cudaMemcpyAsync(&h, static_cast<char*>(ws) + 32, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RMGE_ERR_CUDA;
+    }
+    return (rmge_status)h;
 }
 
 }  // extern "C"

@@ -44,6 +44,7 @@ struct BatchArgs {
     int64_t nmax;
     unsigned int* queue;       // [0] next system, [1] finished CTAs, [2] CTAs working on a system
     struct HelpJob* help;      // the shared FP64 product of a fallback system (in the zeroed queue head)
+    long long spin_limit;      // polls of the bounded waits around the shared product
 };
 
 // A system that falls back to FP64 factors posts its product M = A G here, split into blocks of TILE
@@ -628,8 +629,8 @@ __global__ void __launch_bounds__(T, T >= 1024 ? 1 : 3) batched_kernel(BatchArgs
         __syncthreads();
         if (sys < 0) {
             // The queue is empty: keep taking blocks while other CTAs still work on systems (one of them
-            // may yet post its product).  Bounded: past kSpinLimit polls the CTA simply leaves.
-            for (long long polls = 0; polls < kSpinLimit; ++polls) {
+            // may yet post its product).  Bounded: past spin_limit polls the CTA simply leaves.
+            for (long long polls = 0; polls < a.spin_limit; ++polls) {
                 help_pass<T, TILE>(a.help, smem_d, &blk_s);
                 if (threadIdx.x == 0) stop_s = (*(volatile unsigned int*)&a.queue[2] == 0u) ? 1 : 0;
                 __syncthreads();
@@ -739,11 +740,11 @@ __global__ void __launch_bounds__(T, T >= 1024 ? 1 : 3) batched_kernel(BatchArgs
                 help_pass<T, TILE>(h, smem_d, &blk_s);
                 if (threadIdx.x == 0) {
                     // A block is at most TILE n^2 FMAs (under a second at n = 4096 with three CTAs on the
-                    // SM's DFMA pipe); the bound, about a minute of 1 us polls, only ends a real fault.
+                    // SM's DFMA pipe); the default bound, about a minute of 1 us polls, only ends a real fault.
                     long long spins = 0;
                     stop_s = 0;
                     while (ld_acquire(&h->done) < h->blocks) {
-                        if (++spins > 16 * kSpinLimit) { stop_s = 1; break; }
+                        if (++spins > 16 * a.spin_limit) { stop_s = 1; break; }
                         __nanosleep(1000);
                     }
                 }
@@ -833,6 +834,23 @@ rmge_status launch_batched(const BatchArgs& a, int ctas, cudaStream_t s) {
 }  // namespace
 
 static_assert(64 + sizeof(HelpJob) <= 256, "the job slot lives in the zeroed queue head");
+// queue words 0..2 at bytes 0..11, the status word at byte 32, the job slot from byte 64
+
+// RMGE_ERR_TIMEOUT if a system's wait for its shared product gave up (info -1), else RMGE_OK, into *slot
+// (the queue head) and *out (may be NULL).
+__global__ void batched_status_kernel(int64_t count, const int32_t* info, int* slot, int32_t* out) {
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < count; i += blockDim.x)
+        if (info[i] == -1) bad = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int st = bad ? (int)RMGE_ERR_TIMEOUT : (int)RMGE_OK;
+        *slot = st;
+        if (out != nullptr) *out = st;
+    }
+}
 
 size_t batched_scratch_bytes(int64_t nmax, int ctas) {
     return align256((size_t)ctas * (size_t)(3 * nmax * nmax + 2 * nmax) * sizeof(float)) +
@@ -842,9 +860,10 @@ size_t batched_scratch_bytes(int64_t nmax, int ctas) {
 rmge_status batched_solve(int64_t count, const int32_t* n, const int64_t* offA, const int64_t* offv,
                           const int32_t* order, const double* A, const double* b, double* x, int32_t* info,
                           double* berr, int32_t* sweeps, uint64_t seed, int max_sweeps, double tol, int64_t nmax,
-                          int config, int ctas, void* ws, cudaStream_t s) {
+                          int config, int ctas, long long spin_limit, void* ws, cudaStream_t s) {
     char* base = static_cast<char*>(ws);
     BatchArgs a{};
+    a.spin_limit = spin_limit;
     a.count = count;
     a.n = n;
     a.offA = offA;
@@ -871,6 +890,12 @@ rmge_status batched_solve(int64_t count, const int32_t* n, const int64_t* offA, 
         case 2: return launch_batched<1024, 64>(a, ctas, s);
         default: return RMGE_ERR_INVALID_ARG;
     }
+}
+
+rmge_status batched_status(int64_t count, const int32_t* info, void* ws, int32_t* out, cudaStream_t s) {
+    batched_status_kernel<<<1, 256, 0, s>>>(count, info, reinterpret_cast<int*>(static_cast<char*>(ws) + 32), out);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
 }
 
 }  // namespace rmge

@@ -29,14 +29,17 @@ struct DevState {
     double berr_last;              // latest backward error
     unsigned int ticket;           // dynamic block-order ticket of the running triangular solve
     unsigned int done;             // CTAs of the running triangular solve that have finished
-    unsigned int pad1[2];
+    long long spin_limit;          // polls of a bounded wait before it gives up (set by state_init)
     // reduced-precision refinement: classical sweeps until one fails to halve the backward error,
     // then FGMRES cycles; the two corrections of a sweep read these as their skip flags
     int krylov;        // nonzero once the sweeps have switched to FGMRES cycles
     int krylov_start;  // the sweep at which they switched
     int skip_cls;      // stop || krylov
     int skip_kry;      // stop || !krylov
+    int nonfinite;     // nonzero once a scanned result held an Inf or NaN
+    int status;        // the call's outcome as an rmge_status, written by its last kernel
 };
+static_assert(sizeof(DevState) <= 256, "the control block fits its 256-byte slot");
 
 // Triangular-solve tiling (rows per block, right-hand sides per block column).
 constexpr int kTrsvRows = 64;
@@ -44,9 +47,12 @@ constexpr int kTrsvCols = 2;
 constexpr int kLowRankMaxL = 64;  // columns of the low-rank basis (Algorithm 6.1's l)
 // Refinement sweeps one rmge_refine call may run.
 constexpr int kMaxSweeps = 64;
-// Restart length of the FGMRES cycles used as refinement sweeps for reduced-precision factors.
+// Restart length of the FGMRES cycles used as refinement sweeps for reduced-precision factors
+// (default; rmge_options.gmres_m chooses another, up to kMaxGmresM).
 constexpr int kGmresM = 16;
-// Spin limit of every bounded device wait (about a second at the default back-off).
+constexpr int kMaxGmresM = 256;
+// Default spin limit of the bounded device waits of the triangular solves and the batched solve (about
+// a second at their back-off); rmge_options.spin_limit overrides it.
 constexpr long long kSpinLimit = 1LL << 22;
 
 // Pivot block width of the blocked GENP.
@@ -71,7 +77,7 @@ struct WsLayout {
     size_t total;
 };
 
-WsLayout ws_layout(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec);
+WsLayout ws_layout(int64_t n, int64_t nrhs, rmge_mult_kind kind, rmge_prec prec, int gmres_m = kGmresM);
 
 // ------------------------------------------------------------------------------------------
 // Small device helpers

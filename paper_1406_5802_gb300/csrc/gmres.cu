@@ -9,13 +9,17 @@
 // side by side, each with its own Krylov basis (V, Z: vector v, row r, column c at
 // [v][r * k + c]), its own Hessenberg matrix H[c][i][j] (i <= m, j < m) and Givens rotations.
 // Orthogonalisation is classical Gram-Schmidt applied twice.  Every kernel skips its work once
-// DevState::stop is set.
+// DevState::stop is set; the steps of a cycle also stop once its residual estimate has fallen by
+// kInnerTol for every column, and the correction uses the steps taken.
 #include "kernels.cuh"
 
 namespace rmge {
 namespace {
 
 constexpr int RT = 1024;  // threads of the per-column reduction kernels
+// A cycle ends early once every column's FGMRES residual estimate has fallen by this factor: the outer
+// sweep then recomputes the residual in FP64 and starts a new cycle if the target is not met.
+constexpr double kInnerTol = 1e-6;
 
 __device__ __forceinline__ bool stopped(const int* skip) { return skip != nullptr && *(volatile const int*)skip != 0; }
 
@@ -43,7 +47,7 @@ __device__ double block_sum(double v, double* red) {
 __global__ void __launch_bounds__(RT) norm_scale_kernel(int64_t n, int64_t k, int m, const double* __restrict__ src,
                                                         double* __restrict__ dst, bool start, int j,
                                                         double* __restrict__ H, double* __restrict__ g,
-                                                        const int* skip) {
+                                                        double* __restrict__ beta, const int* skip) {
     __shared__ double red[RT / 32];
     if (stopped(skip)) return;
     const int64_t c = blockIdx.x;
@@ -59,6 +63,7 @@ __global__ void __launch_bounds__(RT) norm_scale_kernel(int64_t n, int64_t k, in
         if (start) {
             g[c * (m + 1)] = nrm;
             for (int i = 1; i <= m; ++i) g[c * (m + 1) + i] = 0.0;
+            beta[c] = nrm;
         } else {
             H[(c * (m + 1) + (j + 1)) * m + j] = nrm;
         }
@@ -97,63 +102,85 @@ __global__ void axpy_kernel(int64_t n, int64_t k, int m, int j, const double* __
     }
 }
 
-// One thread per column: rotate column j of H by the previous rotations, form rotation j so that
-// H[j+1][j] becomes 0, and rotate g.
-__global__ void givens_kernel(int64_t k, int m, int j, double* __restrict__ H, double* __restrict__ cs,
-                              double* __restrict__ sn, double* __restrict__ g, const int* skip) {
-    if (stopped(skip)) return;
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= k) return;
-    double* h = H + c * (m + 1) * m;
-    for (int i = 0; i < j; ++i) {
-        const double a = h[i * m + j], b = h[(i + 1) * m + j];
-        const double cc = cs[c * m + i], ss = sn[c * m + i];
-        h[i * m + j] = cc * a + ss * b;
-        h[(i + 1) * m + j] = -ss * a + cc * b;
+// Columns strided over one CTA: rotate column j of H by the previous rotations, form rotation j so that
+// H[j+1][j] becomes 0, and rotate g.  ctl[1] <- j + 1 (steps taken); once every column's residual
+// estimate |g_{j+1}| is within kInnerTol of its starting norm, ctl[0] <- 1 ends the cycle early.
+__global__ void __launch_bounds__(128) givens_kernel(int64_t k, int m, int j, double* __restrict__ H,
+                                                     double* __restrict__ cs, double* __restrict__ sn,
+                                                     double* __restrict__ g, const double* __restrict__ beta,
+                                                     int* ctl) {
+    __shared__ int open_cols;
+    if (stopped(ctl)) return;
+    if (threadIdx.x == 0) open_cols = 0;
+    __syncthreads();
+    for (int64_t c = threadIdx.x; c < k; c += blockDim.x) {
+        double* h = H + c * (m + 1) * m;
+        for (int i = 0; i < j; ++i) {
+            const double a = h[i * m + j], b = h[(i + 1) * m + j];
+            const double cc = cs[c * m + i], ss = sn[c * m + i];
+            h[i * m + j] = cc * a + ss * b;
+            h[(i + 1) * m + j] = -ss * a + cc * b;
+        }
+        const double a = h[j * m + j], b = h[(j + 1) * m + j];
+        const double r = hypot(a, b);
+        double cc = 1.0, ss = 0.0;
+        if (r > 0.0) {
+            cc = a / r;
+            ss = b / r;
+        }
+        cs[c * m + j] = cc;
+        sn[c * m + j] = ss;
+        h[j * m + j] = r;
+        h[(j + 1) * m + j] = 0.0;
+        double* gc = g + c * (m + 1);
+        const double g0 = gc[j];
+        gc[j] = cc * g0;
+        gc[j + 1] = -ss * g0;
+        if (!(fabs(gc[j + 1]) <= kInnerTol * beta[c])) atomicAdd(&open_cols, 1);
     }
-    const double a = h[j * m + j], b = h[(j + 1) * m + j];
-    const double r = hypot(a, b);
-    double cc = 1.0, ss = 0.0;
-    if (r > 0.0) {
-        cc = a / r;
-        ss = b / r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl[1] = j + 1;
+        if (open_cols == 0) ctl[0] = 1;
     }
-    cs[c * m + j] = cc;
-    sn[c * m + j] = ss;
-    h[j * m + j] = r;
-    h[(j + 1) * m + j] = 0.0;
-    double* gc = g + c * (m + 1);
-    const double g0 = gc[j];
-    gc[j] = cc * g0;
-    gc[j + 1] = -ss * g0;
 }
 
-// One thread per column: y = H(0:m, 0:m)^{-1} g(0:m) by back substitution (zero pivot -> 0).
+// One thread per column: y = H(0:j, 0:j)^{-1} g(0:j) by back substitution (zero pivot -> 0), j = ctl[1]
+// the steps the cycle took.
 __global__ void backsolve_kernel(int64_t k, int m, const double* __restrict__ H, const double* __restrict__ g,
-                                 double* __restrict__ y, const int* skip) {
+                                 double* __restrict__ y, const int* ctl, const int* skip) {
     if (stopped(skip)) return;
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= k) return;
+    const int steps = ctl[1];
     const double* h = H + c * (m + 1) * m;
-    for (int i = m - 1; i >= 0; --i) {
+    for (int i = steps - 1; i >= 0; --i) {
         double s = g[c * (m + 1) + i];
-        for (int t = i + 1; t < m; ++t) s = fma(-h[i * m + t], y[c * m + t], s);
+        for (int t = i + 1; t < steps; ++t) s = fma(-h[i * m + t], y[c * m + t], s);
         const double d = h[i * m + i];
         y[c * m + i] = d != 0.0 ? s / d : 0.0;
     }
 }
 
-// X[r][c] += sum_i Z_i[r][c] y[c][i]
+// X[r][c] += sum_{i < ctl[1]} Z_i[r][c] y[c][i]
 __global__ void update_kernel(int64_t n, int64_t k, int m, const double* __restrict__ Z, const double* __restrict__ y,
-                              double* __restrict__ X, int64_t ldx, const int* skip) {
+                              double* __restrict__ X, int64_t ldx, const int* ctl, const int* skip) {
     if (stopped(skip)) return;
+    const int steps = ctl[1];
     const int64_t total = n * k;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / k, c = e % k;
         double s = 0.0;
-        for (int i = 0; i < m; ++i) s = fma(Z[(int64_t)i * total + e], y[c * m + i], s);
+        for (int i = 0; i < steps; ++i) s = fma(Z[(int64_t)i * total + e], y[c * m + i], s);
         X[r * ldx + c] += s;
     }
+}
+
+// The cycle's own skip flag starts as the sweep's (stop || not in the Krylov phase); givens_kernel raises it
+// once the cycle has converged.
+__global__ void cycle_begin_kernel(const int* skip, int* ctl) {
+    ctl[0] = (skip != nullptr && *(volatile const int*)skip != 0) ? 1 : 0;
+    ctl[1] = 0;
 }
 
 unsigned grid_for(int64_t work) {
@@ -164,16 +191,15 @@ unsigned grid_for(int64_t work) {
 
 }  // namespace
 
-size_t gmres_bytes(int64_t n, int64_t k) {
-    const int m = kGmresM;
+size_t gmres_bytes(int64_t n, int64_t k, int m) {
     const size_t vec = (size_t)n * (size_t)k * sizeof(double);
-    const size_t small = (size_t)k * (size_t)((m + 1) * m + 3 * m + 3 * (m + 1) + 8) * sizeof(double);
-    return (size_t)(2 * m + 2) * vec + small;
+    const size_t small = (size_t)k * (size_t)((m + 1) * m + 3 * m + 3 * (m + 1) + 1) * sizeof(double);
+    return (size_t)(2 * m + 2) * vec + small + 256;
 }
 
-rmge_status gmres_cycle(int64_t n, int64_t k, const double* A, int64_t lda, bool trans_a, const double* R, double* X,
-                        int64_t ldx, double* buf, const GmresPrecond& P, int epoch0, const int* skip, cudaStream_t s) {
-    const int m = kGmresM;
+rmge_status gmres_cycle(int64_t n, int64_t k, int m, const double* A, int64_t lda, bool trans_a, const double* R,
+                        double* X, int64_t ldx, double* buf, const GmresPrecond& P, int epoch0, const int* skip,
+                        cudaStream_t s) {
     const int64_t vec = n * k;
     double* V = buf;                          // (m + 1) vectors
     double* Z = V + (int64_t)(m + 1) * vec;   // m vectors
@@ -184,32 +210,37 @@ rmge_status gmres_cycle(int64_t n, int64_t k, const double* A, int64_t lda, bool
     double* sn = cs + k * m;                  // k m
     double* g = sn + k * m;                   // k (m + 1)
     double* y = g + k * (m + 1);              // k m
+    double* beta = y + k * m;                 // k
+    int* ctl = reinterpret_cast<int*>(beta + k);  // the cycle's skip flag, steps taken
 
-    norm_scale_kernel<<<(unsigned)k, RT, 0, s>>>(n, k, m, R, V, true, 0, H, g, skip);
+    cycle_begin_kernel<<<1, 1, 0, s>>>(skip, ctl);
+    RMGE_LAUNCH_CHECK();
+    norm_scale_kernel<<<(unsigned)k, RT, 0, s>>>(n, k, m, R, V, true, 0, H, g, beta, ctl);
     RMGE_LAUNCH_CHECK();
     for (int j = 0; j < m; ++j) {
         double* vj = V + (int64_t)j * vec;
         double* zj = Z + (int64_t)j * vec;
         // z_j = P v_j in the factor precision, widened to FP64
-        RMGE_TRY(P.apply(P.ctx, vj, zj, epoch0 + 2 * j, skip, s));
+        RMGE_TRY(P.apply(P.ctx, vj, zj, epoch0 + 2 * j, ctl, s));
         // w = op(A) z_j in FP64
-        RMGE_TRY(gemm<double>(trans_a, n, k, n, 1.0, A, lda, zj, k, 0.0, W, k, skip, s));
+        RMGE_TRY(gemm<double>(trans_a, n, k, n, 1.0, A, lda, zj, k, 0.0, W, k, ctl, s));
         // classical Gram-Schmidt, twice
         for (int pass = 0; pass < 2; ++pass) {
             dots_kernel<<<dim3((unsigned)(j + 1), (unsigned)k), RT, 0, s>>>(n, k, m, j, V, W, hc, H, pass == 1,
-                                                                           skip);
+                                                                           ctl);
             RMGE_LAUNCH_CHECK();
-            axpy_kernel<<<grid_for(vec), 256, 0, s>>>(n, k, m, j, V, hc, W, skip);
+            axpy_kernel<<<grid_for(vec), 256, 0, s>>>(n, k, m, j, V, hc, W, ctl);
             RMGE_LAUNCH_CHECK();
         }
-        norm_scale_kernel<<<(unsigned)k, RT, 0, s>>>(n, k, m, W, V + (int64_t)(j + 1) * vec, false, j, H, g, skip);
+        norm_scale_kernel<<<(unsigned)k, RT, 0, s>>>(n, k, m, W, V + (int64_t)(j + 1) * vec, false, j, H, g, beta,
+                                                     ctl);
         RMGE_LAUNCH_CHECK();
-        givens_kernel<<<(unsigned)((k + 127) / 128), 128, 0, s>>>(k, m, j, H, cs, sn, g, skip);
+        givens_kernel<<<1, 128, 0, s>>>(k, m, j, H, cs, sn, g, beta, ctl);
         RMGE_LAUNCH_CHECK();
     }
-    backsolve_kernel<<<(unsigned)((k + 127) / 128), 128, 0, s>>>(k, m, H, g, y, skip);
+    backsolve_kernel<<<(unsigned)((k + 127) / 128), 128, 0, s>>>(k, m, H, g, y, ctl, skip);
     RMGE_LAUNCH_CHECK();
-    update_kernel<<<grid_for(vec), 256, 0, s>>>(n, k, m, Z, y, X, ldx, skip);
+    update_kernel<<<grid_for(vec), 256, 0, s>>>(n, k, m, Z, y, X, ldx, ctl, skip);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }

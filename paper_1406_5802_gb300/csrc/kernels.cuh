@@ -113,10 +113,10 @@ rmge_status trsv(int kind, int64_t n, int64_t nrhs, const T* LU, int64_t ldlu, T
                  DevState* st, int* flags, int epoch, const int* skip, cudaStream_t s);
 
 // refine.cu
-// Resets the control block, zeroes nflags solve flags and ncolred reduction slots, sets
-// berr_out[0..nberr) to -1 (berr_out may be NULL).
+// Resets the control block (with the spin limit of the call's bounded waits), zeroes nflags solve flags and
+// ncolred reduction slots, sets berr_out[0..nberr) to -1 (berr_out may be NULL).
 rmge_status state_init(DevState* st, int* flags, int64_t nflags, double* colred, int ncolred, double* berr_out,
-                       int nberr, cudaStream_t s);
+                       int nberr, cudaStream_t s, long long spin_limit = kSpinLimit);
 // st->norm_a = ||A||_inf (transposed: ||A^T||_inf)
 rmge_status abs_sums_max(int64_t n, const double* A, int64_t lda, bool transposed, DevState* st, cudaStream_t s);
 // R = B (copy, n x k)
@@ -132,27 +132,38 @@ rmge_status backward_error(int64_t n, int64_t k, const double* R, int64_t ldr, c
                            const double* B, int64_t ldb, DevState* st, double* colred, int sweep,
                            double be_tol, int max_iters, double* berr_out, cudaStream_t s, bool hybrid = false);
 rmge_status refine_finish(DevState* st, int max_iters, double* berr_out, int32_t* iters, cudaStream_t s);
+// st->nonfinite <- 1 if P (rows x cols) holds an Inf or NaN.
+template <typename T>
+rmge_status nonfinite_scan(int64_t rows, int64_t cols, const T* P, int64_t ldp, DevState* st, cudaStream_t s);
+// The call's rmge_status from the control block into st->status and *out (out may be NULL): what is
+// kStatusFactor (breakdown, non-finite values, growth above growth_tol > 0), kStatusSolve (non-finite
+// result) or kStatusRefine (non-finite result, backward error above be_tol); a timeout comes first.
+constexpr int kStatusFactor = 0, kStatusSolve = 1, kStatusRefine = 2;
+rmge_status write_status(DevState* st, int what, double growth_tol, double be_tol, int32_t* out, cudaStream_t s);
 // dA = -dB X^T
 rmge_status outer_neg(int64_t n, int64_t k, const double* dB, int64_t lddb, const double* X, int64_t ldx,
                       double* dA, int64_t ldda, cudaStream_t s);
 
-// gmres.cu: one FGMRES(kGmresM) cycle on op(A) d = R (op(A) = A^T when trans_a) for all k columns, right-preconditioned by P
-// (z = P v applied in the factor precision), X += d.  buf: gmres_bytes(n, k) bytes.  Uses epochs
-// epoch0 .. epoch0 + 2 kGmresM - 1 for P's triangular solves.
+// gmres.cu: one FGMRES(m) cycle on op(A) d = R (op(A) = A^T when trans_a) for all k columns, right-preconditioned by P
+// (z = P v applied in the factor precision), X += d.  buf: gmres_bytes(n, k, m) bytes.  Uses epochs
+// epoch0 .. epoch0 + 2 m - 1 for P's triangular solves.
 struct GmresPrecond {
     rmge_status (*apply)(const void* ctx, const double* v, double* z, int epoch, const int* skip, cudaStream_t s);
     const void* ctx;
 };
-size_t gmres_bytes(int64_t n, int64_t k);
-rmge_status gmres_cycle(int64_t n, int64_t k, const double* A, int64_t lda, bool trans_a, const double* R, double* X,
-                        int64_t ldx, double* buf, const GmresPrecond& P, int epoch0, const int* skip, cudaStream_t s);
+size_t gmres_bytes(int64_t n, int64_t k, int m);
+rmge_status gmres_cycle(int64_t n, int64_t k, int m, const double* A, int64_t lda, bool trans_a, const double* R,
+                        double* X, int64_t ldx, double* buf, const GmresPrecond& P, int epoch0, const int* skip,
+                        cudaStream_t s);
 
 // batched.cu: persistent one-CTA-per-system solves (see rmge_solve_batched).
 size_t batched_scratch_bytes(int64_t nmax, int ctas);
 rmge_status batched_solve(int64_t count, const int32_t* n, const int64_t* offA, const int64_t* offv,
                           const int32_t* order, const double* A, const double* b, double* x, int32_t* info,
                           double* berr, int32_t* sweeps, uint64_t seed, int max_sweeps, double tol, int64_t nmax,
-                          int config, int ctas, void* ws, cudaStream_t s);
+                          int config, int ctas, long long spin_limit, void* ws, cudaStream_t s);
+// RMGE_ERR_TIMEOUT if some info[i] is -1, else RMGE_OK, into the int at byte 32 of ws and *out (may be NULL).
+rmge_status batched_status(int64_t count, const int32_t* info, void* ws, int32_t* out, cudaStream_t s);
 
 // fft.cu: circulant multiplier (Theorem 5.1).  G = [c (n doubles) | u = F(c) (n double2)];
 // FFT kinds (fft.cu), N the transform length (n for a circulant, 2n for a Toeplitz multiplier, the

@@ -4,17 +4,19 @@
 // touch the device allocator after start-up (a latency-bound serving loop, where cudaMalloc can
 // synchronise the device), or a plugin whose host process owns every allocation and hands it
 // only the inputs and outputs.  This entry point serves them: the workspace rmge_solve needs comes
-// from a file-scope __device__ array of RMGE_NOALLOC_WS_BYTES, which every GPU that loads the
-// library holds until the process exits.  The entry point itself calls no cudaMalloc, cudaFree
+// from a file-scope __device__ array of RMGE_NOALLOC_WS_BYTES, which every GPU that has made a call
+// holds until the process exits.  The entry point itself calls no cudaMalloc, cudaFree
 // or other allocating routine.
 //
-// The array's name is, in host code, only a host-side stand-in for the symbol; its device
-// address is looked up once per device with cudaGetSymbolAddress (with that device current) and
-// cached.  All calls share the one array: rmge_solve clears the parts that must start at zero
-// (the control block and the solve flags) at the start of each call, in stream order, and
-// calls that overlap on the GPU (different streams, or different host threads) race on it.
-#include <mutex>
-
+// The array's name is, in host code, only a host-side stand-in for the symbol; its device address is
+// looked up with cudaGetSymbolAddress, with the calling device current, on every call (a cheap lookup
+// once the module is loaded, and never stale: a cached address would outlive a cudaDeviceReset or a
+// re-created primary context).  The module holding the array loads lazily (CUDA's default module
+// loading): the first call on each device loads it, which allocates the array and may synchronise the
+// device, so callers make one call at start-up, before any stream capture or latency-bound loop.  All
+// calls share the one array: rmge_solve clears the parts that must start at zero (the control block and
+// the solve flags) at the start of each call, in stream order, and calls that overlap on the GPU
+// (different streams, or different host threads) race on it.
 #include "kernels.cuh"
 
 #define RMGE_NOALLOC_WS_BYTES ((size_t)16 << 20)
@@ -23,27 +25,14 @@ namespace {
 
 __device__ __align__(256) unsigned char g_noalloc_ws[RMGE_NOALLOC_WS_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
 // Device address of g_noalloc_ws on the current device; NULL on failure.
 void* noalloc_ws_address() {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_ws) != cudaSuccess) {
         (void)cudaGetLastError();
         return nullptr;
     }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (g_addr[dev] == nullptr) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_ws) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return nullptr;
-        }
-        g_addr[dev] = p;
-    }
-    return g_addr[dev];
+    return p;
 }
 
 }  // namespace

@@ -9,7 +9,7 @@ namespace rmge {
 namespace {
 
 __global__ void state_init_kernel(DevState* st, int* flags, int64_t nflags, double* colred, int ncolred,
-                                  double* berr_out, int nberr) {
+                                  double* berr_out, int nberr, long long spin_limit) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (tid == 0) {
@@ -27,6 +27,9 @@ __global__ void state_init_kernel(DevState* st, int* flags, int64_t nflags, doub
         st->krylov_start = 0;
         st->skip_cls = 0;
         st->skip_kry = 1;
+        st->nonfinite = 0;
+        st->status = 0;
+        st->spin_limit = spin_limit;
     }
     if (tid == 0) {
         st->ticket = 0u;
@@ -138,6 +141,40 @@ __global__ void refine_finish_kernel(const DevState* st, int32_t* iters) {
     if (iters) *iters = st->sweeps;
 }
 
+// Flags an Inf or NaN anywhere in P (rows x cols).
+template <typename T>
+__global__ void nonfinite_scan_kernel(int64_t rows, int64_t cols, const T* __restrict__ P, int64_t ldp, DevState* st) {
+    bool bad = false;
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(P[(e / cols) * ldp + e % cols])) bad = true;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(&st->nonfinite, 1);
+}
+
+// The call's outcome (rmge_options.status): a bounded wait that gave up first, then a breakdown, then a
+// non-finite result, then growth above growth_tol (factorizations) or a backward error above be_tol
+// (refinement).
+__global__ void status_kernel(DevState* st, int what, double growth_tol, double be_tol, int32_t* out) {
+    int s = RMGE_OK;
+    if (st->error != 0) {
+        s = st->error;
+    } else if (what == kStatusFactor) {
+        const double mu = __longlong_as_double((long long)st->maxabs_u);
+        const double mm = __longlong_as_double((long long)st->maxabs_m);
+        const double growth = mu / mm;
+        if (st->info != INT_MAX) s = RMGE_ERR_BREAKDOWN;
+        else if (!isfinite(mu) || !isfinite(mm)) s = RMGE_ERR_NONFINITE;
+        else if (growth_tol > 0.0 && !(growth <= growth_tol)) s = RMGE_ERR_GROWTH;
+    } else if (what == kStatusSolve) {
+        if (st->nonfinite != 0) s = RMGE_ERR_NONFINITE;
+    } else {
+        if (!isfinite(st->berr_last)) s = RMGE_ERR_NONFINITE;
+        else if (!(st->berr_last <= be_tol)) s = RMGE_ERR_NOT_CONVERGED;
+    }
+    st->status = s;
+    if (out != nullptr) *out = s;
+}
+
 __global__ void outer_neg_kernel(int64_t n, int64_t k, const double* __restrict__ dB, int64_t lddb,
                                  const double* __restrict__ X, int64_t ldx, double* __restrict__ dA, int64_t ldda) {
     // one CTA per row of dA; the row's dB entries are broadcast from registers
@@ -178,11 +215,11 @@ unsigned grid_for(int64_t work, int threads) {
 }  // namespace
 
 rmge_status state_init(DevState* st, int* flags, int64_t nflags, double* colred, int ncolred, double* berr_out,
-                       int nberr, cudaStream_t s) {
+                       int nberr, cudaStream_t s, long long spin_limit) {
     int64_t work = nflags > ncolred ? nflags : ncolred;
     if (work < 64) work = 64;
     state_init_kernel<<<grid_for(work, 256), 256, 0, s>>>(st, flags, nflags, colred, ncolred, berr_out,
-                                                          berr_out ? nberr : 0);
+                                                          berr_out ? nberr : 0, spin_limit);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }
@@ -231,6 +268,19 @@ rmge_status refine_finish(DevState* st, int max_iters, double* berr_out, int32_t
     return RMGE_OK;
 }
 
+template <typename T>
+rmge_status nonfinite_scan(int64_t rows, int64_t cols, const T* P, int64_t ldp, DevState* st, cudaStream_t s) {
+    nonfinite_scan_kernel<T><<<grid_for(rows * cols, 256), 256, 0, s>>>(rows, cols, P, ldp, st);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
+rmge_status write_status(DevState* st, int what, double growth_tol, double be_tol, int32_t* out, cudaStream_t s) {
+    status_kernel<<<1, 1, 0, s>>>(st, what, growth_tol, be_tol, out);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
 rmge_status outer_neg(int64_t n, int64_t k, const double* dB, int64_t lddb, const double* X, int64_t ldx, double* dA,
                       int64_t ldda, cudaStream_t s) {
     outer_neg_kernel<<<(unsigned)n, 256, 0, s>>>(n, k, dB, lddb, X, ldx, dA, ldda);
@@ -246,6 +296,8 @@ template rmge_status copy_matrix<float, double>(int64_t, int64_t, const float*, 
                                                 cudaStream_t);
 template rmge_status add_update<double>(int64_t, int64_t, const double*, int64_t, double*, int64_t, const int*,
                                         cudaStream_t);
+template rmge_status nonfinite_scan<double>(int64_t, int64_t, const double*, int64_t, DevState*, cudaStream_t);
+template rmge_status nonfinite_scan<float>(int64_t, int64_t, const float*, int64_t, DevState*, cudaStream_t);
 template rmge_status add_update<float>(int64_t, int64_t, const float*, int64_t, double*, int64_t, const int*,
                                        cudaStream_t);
 

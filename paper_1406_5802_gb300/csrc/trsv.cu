@@ -9,8 +9,8 @@
 // block from it, so a CTA only ever waits for CTAs that took earlier tickets and are therefore
 // already running: no co-residency assumption, no deadlock.  The last CTA to finish resets the
 // counter, so consecutive solves on one stream need no re-initialisation.  Every wait is bounded
-// (kSpinLimit polls); on expiry the CTA records RMGE_ERR_TIMEOUT in DevState::error and all
-// waiting CTAs return without writing.
+// (DevState::spin_limit polls, set per call); on expiry the CTA records RMGE_ERR_TIMEOUT in
+// DevState::error and all waiting CTAs return without writing.
 //
 // The factor is read once from HBM per column block; FP64 runs on the DFMA pipe (2 FP64 operations per
 // clock per SM on GB300).  The chain of row blocks is bound by the latency of each link (flag hand-off,
@@ -118,10 +118,11 @@ __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t n
         }
         if (tid == 0) {
             const int* f = flags + sb * ncb + cb;
+            const long long limit = *(volatile const long long*)&st->spin_limit;
             long long spins = 0;
             while (ld_acquire(f) != epoch) {
                 if (*(volatile int*)&st->error != 0) { failed = 1; break; }
-                if (++spins > kSpinLimit) {
+                if (++spins > limit) {
                     atomicExch(&st->error, (int)RMGE_ERR_TIMEOUT);
                     failed = 1;
                     break;

@@ -24,13 +24,24 @@ KINDS = {"gaussian": GAUSSIAN, "circulant": CIRCULANT_GAUSSIAN, "circulant_unifo
 PRECS = {"f64": F64, "f32": F32, "bf16": BF16_TC, "f16": F16_TC, "bf16x3": 4, "f16x3": 5, "f64x": 6}
 STATUS = {0: "RMGE_OK", 1: "RMGE_ERR_INVALID_ARG", 2: "RMGE_ERR_BREAKDOWN", 3: "RMGE_ERR_GROWTH",
           4: "RMGE_ERR_NOT_CONVERGED", 5: "RMGE_ERR_CUDA", 6: "RMGE_ERR_TIMEOUT", 7: "RMGE_ERR_WORKSPACE",
-          8: "RMGE_ERR_UNSUPPORTED"}
+          8: "RMGE_ERR_UNSUPPORTED", 9: "RMGE_ERR_NONFINITE"}
+CODES = {v: k for k, v in STATUS.items()}
+# outcomes a synchronising _ex call returns (numerical results, not errors of the call)
+OUTCOMES = {0, 2, 3, 4, 6, 9}
 
 EXPORTED = ["rmge_multiplier_bytes", "rmge_workspace_size", "rmge_make_multiplier", "rmge_apply_multiplier",
             "rmge_factor", "rmge_solve", "rmge_refine", "rmge_solve_backward", "rmge_status_string",
             "rmge_kernel_launches", "rmge_solve_workspace_size", "rmge_solve_noalloc", "rmge_noalloc_capacity",
             "rmge_workspace_size_two_sided", "rmge_apply_two_sided", "rmge_solve_two_sided", "rmge_refine_two_sided",
-            "rmge_lowrank_workspace_size", "rmge_lowrank_multiplier", "rmge_lowrank_basis", "rmge_lowrank_project"]
+            "rmge_lowrank_workspace_size", "rmge_lowrank_multiplier", "rmge_lowrank_basis", "rmge_lowrank_project",
+            "rmge_options_init", "rmge_workspace_size_ex", "rmge_factor_ex", "rmge_solve_ex", "rmge_refine_ex",
+            "rmge_solve_batched", "rmge_solve_batched_ex", "rmge_batched_workspace_size"]
+
+
+class Options(C.Structure):
+    """rmge_options (include/rmge.h)."""
+    _fields_ = [("growth_tol", C.c_double), ("spin_limit", C.c_int64), ("gmres_m", C.c_int32), ("sync", C.c_int32),
+                ("status", C.c_void_p)]
 
 
 class RmgeError(RuntimeError):
@@ -80,6 +91,19 @@ def load_library(path: str = LIB_PATH):
         "rmge_lowrank_basis": (C.c_int, [C.c_int, _i64, _i64, C.c_int32, _vp, _i64, _vp, _vp, _i64, _vp, _vp, _sz,
                                          _vp]),
         "rmge_lowrank_project": (C.c_int, [_i64, _i64, C.c_int32, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
+        "rmge_options_init": (None, [C.POINTER(Options)]),
+        "rmge_workspace_size_ex": (_sz, [_i64, _i64, C.c_int, C.c_int, C.POINTER(Options)]),
+        "rmge_factor_ex": (C.c_int, [_i64, _vp, _i64, C.c_int, _vp, _vp, C.POINTER(Options), _vp, _sz, _vp]),
+        "rmge_solve_ex": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, C.c_int,
+                                    C.POINTER(Options), _vp, _sz, _vp]),
+        "rmge_refine_ex": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, C.c_int,
+                                     C.c_int32, C.c_double, _vp, _vp, C.POINTER(Options), _vp, _sz, _vp]),
+        "rmge_batched_workspace_size": (_sz, [_i64, C.c_int32]),
+        "rmge_solve_batched": (C.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u64, C.c_int32,
+                                         C.c_double, _i64, C.c_int32, C.c_int32, _vp, _sz, _vp]),
+        "rmge_solve_batched_ex": (C.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u64, C.c_int32,
+                                            C.c_double, _i64, C.c_int32, C.c_int32, C.POINTER(Options), _vp, _sz,
+                                            _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -212,6 +236,83 @@ def solve(kind, LU, G, B, prec="f64", X=None, ws=None) -> torch.Tensor:
     _check("rmge_solve", L.rmge_solve(_kind(kind), n, k, _p(LU), _ld(LU), _p(G), _p(B), _ld(B), _p(X), _ld(X),
                                       _prec(prec), _p(ws), ws.numel(), _stream()))
     return X
+
+
+def options(growth_tol=0.0, spin_limit=None, gmres_m=None, sync=False, status=None) -> Options:
+    """rmge_options with the library's defaults (rmge_options_init) and the given fields replaced; status is
+    a device int32 tensor or None."""
+    o = Options()
+    load_library().rmge_options_init(C.byref(o))
+    o.growth_tol = float(growth_tol)
+    if spin_limit is not None:
+        o.spin_limit = int(spin_limit)
+    if gmres_m is not None:
+        o.gmres_m = int(gmres_m)
+    o.sync = 1 if sync else 0
+    o.status = None if status is None else status.data_ptr()
+    return o
+
+
+def _check_ex(fn, code, opts):
+    # a synchronising call returns its numerical outcome, which is not an error of the call
+    if opts is not None and opts.sync and code in OUTCOMES:
+        return code
+    _check(fn, code)
+    return code
+
+
+def workspace_size_ex(n, nrhs, kind, prec, opts) -> int:
+    return int(load_library().rmge_workspace_size_ex(int(n), int(nrhs), _kind(kind), _prec(prec), C.byref(opts)))
+
+
+def workspace_ex(n, nrhs, kind, prec, opts, device="cuda") -> torch.Tensor:
+    nb = workspace_size_ex(n, nrhs, kind, prec, opts)
+    if nb == 0:
+        raise ValueError("invalid workspace request")
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def factor_ex(M, prec, opts, ws=None):
+    """rmge_factor_ex: (info, growth, code); code is the call's return value (its outcome when opts.sync)."""
+    L = _cuda_lib()
+    _need(M, factor_dtype(prec), "M")
+    n = M.shape[0]
+    info = torch.empty(1, dtype=torch.int32, device=M.device)
+    growth = torch.empty(1, dtype=torch.float64, device=M.device)
+    if ws is None:
+        ws = workspace_ex(n, 1, GAUSSIAN, prec, opts)
+    code = L.rmge_factor_ex(n, _p(M), _ld(M), _prec(prec), _p(info), _p(growth), C.byref(opts), _p(ws), ws.numel(),
+                            _stream())
+    return info, growth, _check_ex("rmge_factor_ex", code, opts)
+
+
+def solve_ex(kind, LU, G, B, prec, opts, X=None, ws=None):
+    """rmge_solve_ex: (X, code)."""
+    L = _cuda_lib()
+    _need(B, torch.float64, "B")
+    n, k = B.shape
+    if X is None:
+        X = torch.empty(n, k, dtype=torch.float64, device=B.device)
+    _need(X, torch.float64, "X")
+    if ws is None:
+        ws = workspace_ex(n, k, kind, prec, opts)
+    code = L.rmge_solve_ex(_kind(kind), n, k, _p(LU), _ld(LU), _p(G), _p(B), _ld(B), _p(X), _ld(X), _prec(prec),
+                           C.byref(opts), _p(ws), ws.numel(), _stream())
+    return X, _check_ex("rmge_solve_ex", code, opts)
+
+
+def refine_ex(kind, A, LU, G, B, X, prec, max_iters, be_tol, opts, ws=None):
+    """rmge_refine_ex: (berr, iters, code)."""
+    L = _cuda_lib()
+    n, k = B.shape
+    berr = torch.empty(max_iters + 1, dtype=torch.float64, device=B.device)
+    iters = torch.empty(1, dtype=torch.int32, device=B.device)
+    if ws is None:
+        ws = workspace_ex(n, k, kind, prec, opts)
+    code = L.rmge_refine_ex(_kind(kind), n, k, _p(A), _ld(A), _p(LU), _ld(LU), _p(G), _p(B), _ld(B), _p(X), _ld(X),
+                            _prec(prec), int(max_iters), float(be_tol), _p(berr), _p(iters), C.byref(opts), _p(ws),
+                            ws.numel(), _stream())
+    return berr, iters, _check_ex("rmge_refine_ex", code, opts)
 
 
 def solve_noalloc(kind, LU, G, B, prec="f64", X=None) -> torch.Tensor:

@@ -44,12 +44,17 @@ def test_workspace_and_multiplier_sizes(lib):
     assert rmge.multiplier_bytes("gaussian", 256, "f64") == 256 * 256 * 8
     assert rmge.multiplier_bytes("gaussian", 256, "f32") == 256 * 256 * 4
     assert rmge.multiplier_bytes("circulant", 256, "f64") == 3 * 256 * 8
-    assert rmge.multiplier_bytes("circulant", 16384, "f64") == 0
+    # one real transform of length 4 .. 16384 per CTA
+    assert rmge.multiplier_bytes("circulant", 16384, "f64") == 3 * 16384 * 8
+    assert rmge.multiplier_bytes("circulant", 32768, "f64") == 0
+    assert rmge.multiplier_bytes("circulant", 2, "f64") == 0
     # the unitary circulant stores like the others; a Toeplitz multiplier stores its 2n circulant
-    assert rmge.multiplier_bytes("circulant_unitary", 8192, "f64") == 3 * 8192 * 8
+    assert rmge.multiplier_bytes("circulant_unitary", 16384, "f64") == 3 * 16384 * 8
     assert rmge.multiplier_bytes("toeplitz", 4096, "f64") == 6 * 4096 * 8
     assert rmge.multiplier_bytes("toeplitz_uniform", 64, "f32") == 6 * 64 * 8
-    assert rmge.multiplier_bytes("toeplitz", 8192, "f64") == 0  # its 16384-point transform is too long
+    assert rmge.multiplier_bytes("toeplitz", 8192, "f64") == 6 * 8192 * 8
+    assert rmge.multiplier_bytes("toeplitz", 16384, "f64") == 0  # its 32768-point transform is too long
+    assert rmge.multiplier_bytes("toeplitz", 2, "f64") == 6 * 2 * 8
     assert rmge.multiplier_bytes("toeplitz", 1000, "f64") == 0  # not a power of two
     assert rmge.workspace_size(1000, 1, "toeplitz", "f64") == 0
 
@@ -79,3 +84,29 @@ def test_bad_arguments_are_rejected_without_gpu_work(lib):
                                                                           C.c_void_p, C.c_size_t, C.c_void_p]
     assert lib.rmge_solve_batched(0, p, p, p, p, p, p, p, p, p, p, 1, 10, 1e-13, 8, 1, 152, p, 1 << 20,
                                   None) == INVALID
+
+
+def test_options_defaults_and_validation(lib):
+    INVALID = 1
+    o = rmge.options()
+    assert o.growth_tol == 0.0 and o.gmres_m == 16 and o.spin_limit == 1 << 22 and o.sync == 0 and not o.status
+    # the FGMRES basis grows with the restart length; out-of-range options make every size request invalid
+    base = rmge.workspace_size_ex(4096, 8, "gaussian", "bf16x3", o)
+    assert base == rmge.workspace_size(4096, 8, "gaussian", "bf16x3")
+    assert rmge.workspace_size_ex(4096, 8, "gaussian", "bf16x3", rmge.options(gmres_m=64)) > base
+    assert rmge.workspace_size_ex(4096, 8, "gaussian", "f64", rmge.options(gmres_m=64)) == \
+        rmge.workspace_size(4096, 8, "gaussian", "f64")  # FP64 factors refine classically: no basis
+    assert rmge.workspace_size_ex(4096, 8, "gaussian", "bf16x3", rmge.options(gmres_m=257)) == 0
+    assert rmge.workspace_size_ex(4096, 8, "gaussian", "bf16x3", rmge.options(gmres_m=0)) == 0
+    assert rmge.workspace_size_ex(64, 1, "gaussian", "f64", rmge.options(growth_tol=-1.0)) == 0
+    assert rmge.workspace_size_ex(64, 1, "gaussian", "f64", rmge.options(spin_limit=-1)) == 0
+    p = C.c_void_p(256)
+    bad = rmge.options(gmres_m=1000)
+    assert lib.rmge_factor_ex(8, p, 8, 0, None, None, C.byref(bad), p, 1 << 20, None) == INVALID
+    assert lib.rmge_solve_ex(0, 8, 1, p, 8, p, p, 1, p, 1, 0, C.byref(bad), p, 1 << 20, None) == INVALID
+    assert lib.rmge_refine_ex(0, 8, 1, p, 8, p, 8, p, p, 1, p, 1, 0, 3, 1e-13, None, None, C.byref(bad), p, 1 << 20,
+                              None) == INVALID
+    assert lib.rmge_solve_batched_ex(4, p, p, p, p, p, p, p, p, p, p, 1, 10, 1e-13, 8, 1, 152, C.byref(bad), p,
+                                     1 << 20, None) == INVALID
+    assert lib.rmge_status_string(9) == b"non-finite values in the result"
+    assert lib.rmge_status_string(3) == b"growth above threshold"

@@ -1,5 +1,7 @@
 """The FP64 products emulated on the BF16 tensor cores (RMGE_F64X_TC): exactness on integer inputs, accuracy
 on random FP64 inputs, the GENP factors it produces, and the whole solve at the FP64 target."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -26,21 +28,24 @@ def _lib():
     rmge.load_library()
 
 
-@pytest.mark.parametrize("n", [5, 128, 200, 1100])
+@pytest.mark.parametrize("n", [5, 128, 200, 1100, 3000, 4096])
 def test_emulated_product_is_exact_on_small_integers(orc, n):
     """Entries below 128 in magnitude are a single base-128 digit, and 1024-deep chunks of their products stay
     below 2^24: every step is exact, so the product must equal the integer product bit for bit (n = 1100
-    spans two K chunks)."""
+    spans two K chunks; n = 3000 and 4096 span several bands of 12 row blocks of 128, a ragged last band, and
+    three and four 1024-deep K super-chunks, as at the bench sizes)."""
     r = W.rng(n)
     A = r.integers(-127, 128, (n, n)).astype(np.float64)
     G = r.integers(-127, 128, (n, n)).astype(np.float64)
     M = host(rmge.apply_multiplier("gaussian", dev(A), dev(G), "f64x"))
-    ref = (A.astype(np.int64) @ G.astype(np.int64)).astype(np.float64)
+    # every partial sum is an integer below 127^2 n < 2^53, so the FP64 product is exact in any order
+    ref = A @ G
     assert np.array_equal(M, ref)
 
 
-@pytest.mark.parametrize("n", [64, 300, 1500])
+@pytest.mark.parametrize("n", [64, 300, 1500, 3000, 4096])
 def test_emulated_product_accuracy(orc, n):
+    orc.set_threads(os.cpu_count() or 1)  # the oracle's product is the same in any thread count
     A, _ = W.orthogonal_factor_system(n, 1, 1e-6, seed=n)
     G = W.gaussian_multiplier(n, n + 1)
     M = host(rmge.apply_multiplier("gaussian", dev(A), dev(G), "f64x"))
@@ -66,6 +71,31 @@ def test_emulated_factor_backward_error(orc, n):
     ref, _ = orc.genp(M)
     g = orc.growth(M, ref)
     assert abs(float(host(growth)[0]) - g) <= 1e-6 * g
+
+
+def test_emulated_factor_matches_oracle_at_bench_size(orc):
+    """n = 4096, the bench's size: 64 pivot-block steps whose Schur updates run on the emulated path over many
+    row bands, against the oracle's unblocked GENP of the same M (Sec. 3: every blocking reaches the same
+    Schur complements), entry by entry to rounding x growth, plus the factor backward error."""
+    orc.set_threads(os.cpu_count() or 1)
+    n = 4096
+    A, _ = W.gaussian_system(n, 1, seed=4096 + 90)
+    G = W.gaussian_multiplier(n, 4096 + 91)
+    M = orc.matmul(A, G)
+    Md = dev(M)
+    info, growth = rmge.factor(Md, "f64x")
+    LU = host(Md)
+    ref, rinfo = orc.genp(M.copy())
+    assert int(host(info)[0]) == rinfo == 0
+    g = orc.growth(M, ref)
+    assert abs(float(host(growth)[0]) - g) <= 1e-6 * g
+    # each emulated update keeps 2^-49 of the line maxima per term (16 u), against u for the oracle
+    err = np.max(np.abs(LU - ref)) / np.max(np.abs(ref))
+    assert err <= 16e3 * n * 2.0**-53 * g, err
+    L = np.tril(LU, -1) + np.eye(n)
+    U = np.triu(LU)
+    be = np.max(np.abs(L @ U - M)) / np.max(np.abs(L) @ np.abs(U))
+    assert be <= 1e-13, be
 
 
 def _coupled(n, i):

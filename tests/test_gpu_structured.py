@@ -11,7 +11,7 @@ from paper_1406_5802_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 U64 = 2.0**-53
-KIND = {"circulant_unitary": 3, "toeplitz": 4, "toeplitz_uniform": 5}
+KIND = {"circulant": 1, "circulant_uniform": 2, "circulant_unitary": 3, "toeplitz": 4, "toeplitz_uniform": 5}
 
 
 def dev(a, dtype=torch.float64):
@@ -35,7 +35,7 @@ def column_and_spectrum(G, N):
     return G[:N], u[:, 0] + 1j * u[:, 1]
 
 
-@pytest.mark.parametrize("n", [2, 8, 256, 8192])
+@pytest.mark.parametrize("n", [4, 8, 256, 8192, 16384])
 def test_unitary_circulant_matches_oracle(orc, n):
     G = host(rmge.make_multiplier("circulant_unitary", n, seed=31, subsequence=2, prec="f64"))
     assert G.shape == (3 * n,)
@@ -51,7 +51,7 @@ def test_unitary_circulant_matches_oracle(orc, n):
 
 
 @pytest.mark.parametrize("kind", ["toeplitz", "toeplitz_uniform"])
-@pytest.mark.parametrize("n", [2, 64, 4096])
+@pytest.mark.parametrize("n", [2, 64, 4096, 8192])
 def test_toeplitz_multiplier_matches_oracle(orc, kind, n):
     G = host(rmge.make_multiplier(kind, n, seed=8, subsequence=3, prec="f64"))
     assert G.shape == (6 * n,)
@@ -66,7 +66,7 @@ def test_toeplitz_multiplier_matches_oracle(orc, kind, n):
 
 
 @pytest.mark.parametrize("kind", ["circulant_unitary", "toeplitz", "toeplitz_uniform"])
-@pytest.mark.parametrize("n", [2, 64, 512, 4096])
+@pytest.mark.parametrize("n", [4, 64, 512, 4096])
 def test_structured_apply_matches_dense_definition(orc, kind, n):
     A, _ = W.gaussian_system(n, 1, seed=5 * n + KIND[kind])
     Gd = rmge.make_multiplier(kind, n, seed=13, subsequence=1, prec="f64")
@@ -77,6 +77,26 @@ def test_structured_apply_matches_dense_definition(orc, kind, n):
     ref = orc.matmul(A, D) if n <= 512 else A @ D
     scale = np.max(np.abs(A)) * np.max(np.sum(np.abs(D), axis=0))
     assert np.max(np.abs(M - ref)) <= 1e-14 * np.log2(4 * n) * np.sqrt(n) * scale
+
+
+@pytest.mark.parametrize("kind,n", [("circulant", 16384), ("circulant_unitary", 16384), ("circulant_uniform", 8192),
+                                    ("toeplitz", 8192)])
+def test_structured_apply_at_the_largest_transforms(orc, kind, n):
+    """A H by 16384-point real transforms (one per CTA, 192 KB of shared memory), against the oracle's rows of
+    A H from the definition H_kj = c[(k - j) mod N]: the first and last rows, and rows in between."""
+    A, _ = W.gaussian_system(n, 1, seed=11 * n + KIND.get(kind, 1))
+    Gd = rmge.make_multiplier(kind, n, seed=17, subsequence=1, prec="f64")
+    M = rmge.apply_multiplier(kind, dev(A), Gd, "f64")
+    G = host(Gd)
+    N = 2 * n if kind.startswith("toeplitz") else n
+    rows = np.array([0, 1, 977, n // 2 + 3, n - 2, n - 1])
+    got = host(M[torch.as_tensor(rows, device="cuda")])
+    ref = orc.circulant_rows(A[rows], G[:N], N)
+    scale = np.max(np.abs(A)) * np.sum(np.abs(G[:N]))
+    assert np.max(np.abs(got - ref)) <= 1e-14 * np.log2(4 * N) * np.sqrt(n) * scale
+    # the FP32 working matrix of the reduced precisions is the same product rounded once
+    M32 = host(rmge.apply_multiplier(kind, dev(A), Gd, "bf16x3")[torch.as_tensor(rows, device="cuda")])
+    assert np.max(np.abs(M32 - ref)) <= 2.0**-24 * np.max(np.abs(ref)) + 1e-13 * scale
 
 
 @pytest.mark.parametrize("kind", ["circulant_unitary", "toeplitz", "toeplitz_uniform"])

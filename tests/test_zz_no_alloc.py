@@ -59,6 +59,31 @@ def test_noalloc_solve_matches_workspace_solve(orc, lib, prec, code, dtype):
             assert np.max(np.abs(Xh - ref_h)) <= 1e-9 * np.max(np.abs(ref_h))
 
 
+@pytest.mark.parametrize("kind,prec", [("circulant", "f64"), ("circulant_unitary", "f64"), ("gaussian", "bf16")])
+def test_noalloc_binding_matches_workspace_solve(orc, lib, kind, prec):
+    """The Python binding of the entry point, with the multipliers whose FFT twiddle table sits in the shared
+    array, and with a tensor-core precision (FP32 factors)."""
+    n, k = 256, 3
+    A, B = W.gaussian_system(n, k, seed=700 + len(kind))
+    f32 = rmge.factor_dtype(prec) == torch.float32
+    G = rmge.make_multiplier(kind, n, seed=701, subsequence=1, prec=prec)
+    torch.cuda.synchronize()
+    Gh = G.cpu().numpy().astype(np.float64)
+    H = Gh.reshape(n, n) if kind == "gaussian" else orc.circulant_dense(Gh[:n])
+    LU, info = orc.genp(orc.matmul(A, H))
+    assert info == 0
+    LUd, Bd = _dev(LU, torch.float32 if f32 else torch.float64), _dev(B)
+    ref = rmge.solve(kind, LUd, G, Bd, prec)
+    torch.cuda.synchronize()
+    ref_h = ref.cpu().numpy()
+    for _ in range(2):
+        X = rmge.solve_noalloc(kind, LUd, G, Bd, prec)
+        torch.cuda.synchronize()
+        Xh = X.cpu().numpy()
+        assert np.all(np.isfinite(Xh))
+        assert np.max(np.abs(Xh - ref_h)) <= 1e-9 * np.max(np.abs(ref_h))
+
+
 def test_noalloc_rejects_requests_beyond_its_array(lib):
     n, k = 60000, 16
     assert lib.rmge_solve_workspace_size(n, k, 0, 0) > lib.rmge_noalloc_capacity()
