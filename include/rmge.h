@@ -81,10 +81,10 @@ typedef enum {
                            product formed as x_hi y_hi + x_hi y_lo + x_lo y_hi (three tensor-core passes) */
     RMGE_F16X3_TC = 5,  /* the three-pass split with FP16 terms */
     RMGE_F64X_TC = 6    /* FP64 working matrix, factors and refinement; M = A G and GENP's Schur-complement
-                           updates are FP64 products emulated on the BF16 tensor cores (8 base-128 digits per
-                           entry, 36 digit-pair products in exact FP32 chunks, 64-bit fixed-point sums; the
-                           updates first balance column k of L21 against row k of U12 by a power of two);
-                           pivot blocks, panels, solves and residuals run on the FP64 pipe */
+                           updates are FP64 products emulated on the BF16 tensor cores (7 balanced base-256
+                           digits per entry, 28 digit-pair products in exact FP32 chunks, 64-bit fixed-point
+                           sums; the updates first balance column k of L21 against row k of U12 by a power
+                           of two); pivot blocks, panels, solves and residuals run on the FP64 pipe */
 } rmge_prec;
 
 /*
@@ -104,6 +104,13 @@ typedef enum {
  *   with reduced-precision factors (see rmge_refine).  The workspace grows with it
  *   (rmge_workspace_size_ex).  A cycle also ends once every column's residual estimate has fallen by
  *   a factor 1e-6.
+ * - apply_digits (default 7, from 1 to 7): balanced base-256 digits per entry that
+ *   rmge_apply_multiplier_ex keeps for RMGE_F64X_TC with a Gaussian multiplier.  7 digit planes (28
+ *   digit-pair products, 55 bits per operand) reproduce FP64 rounding; d digits keep d (d + 1) / 2
+ *   products and 8 d - 1 bits, which is M = A G with a relative error near (d + 5) 2^(-8 d) of the row
+ *   and column maxima per term.  Refinement with FP64 residuals wins that back while kappa(A G) times
+ *   that error stays well below 1 (a sweep more for each factor of about 1e4 lost); the factorization
+ *   itself is unchanged.
  * - status (device int32, may be NULL): receives the call's outcome, RMGE_OK or the first of
  *   RMGE_ERR_TIMEOUT, RMGE_ERR_BREAKDOWN, RMGE_ERR_NONFINITE, then RMGE_ERR_GROWTH (factor) or
  *   RMGE_ERR_NOT_CONVERGED (refine) that applies; valid once the stream is synchronised.
@@ -113,9 +120,10 @@ typedef enum {
 typedef struct rmge_options {
     double growth_tol;
     int64_t spin_limit;
-    int32_t gmres_m;
-    int32_t sync;
     int32_t* status;
+    int32_t gmres_m;
+    int32_t apply_digits;
+    int32_t sync;
 } rmge_options;
 
 void rmge_options_init(rmge_options* opts);
@@ -171,6 +179,10 @@ rmge_status rmge_make_multiplier(rmge_mult_kind kind, int64_t n, uint64_t seed, 
 rmge_status rmge_apply_multiplier(rmge_mult_kind kind, int64_t n, const double* A, int64_t lda,
                                   const void* G, void* M, int64_t ldm, rmge_prec prec,
                                   void* ws, size_t ws_bytes, rmge_stream_t stream);
+/* rmge_apply_multiplier with options (apply_digits for RMGE_F64X_TC; the other fields do not apply). */
+rmge_status rmge_apply_multiplier_ex(rmge_mult_kind kind, int64_t n, const double* A, int64_t lda,
+                                     const void* G, void* M, int64_t ldm, rmge_prec prec, const rmge_options* opts,
+                                     void* ws, size_t ws_bytes, rmge_stream_t stream);
 
 /*
  * In-place blocked GENP of M (eq. (3.1) with pivot blocks of nb columns; by Sec. 3 every

@@ -58,13 +58,17 @@ struct Opts {
     int gm_m = kGmresM;
     bool sync = false;
     int32_t* status = nullptr;
+    int digits = kOzSlices;  // balanced base-256 digits of the emulated A G
     bool report() const { return sync || status != nullptr; }
 };
 
 bool opts_of(const rmge_options* o, Opts* out) {
     *out = Opts{};
     if (o == nullptr) return true;
-    if (!(o->growth_tol >= 0.0) || o->spin_limit < 0 || o->gmres_m < 1 || o->gmres_m > kMaxGmresM) return false;
+    if (!(o->growth_tol >= 0.0) || o->spin_limit < 0 || o->gmres_m < 1 || o->gmres_m > kMaxGmresM ||
+        o->apply_digits < 1 || o->apply_digits > kOzSlices)
+        return false;
+    out->digits = o->apply_digits;
     out->growth_tol = o->growth_tol;
     out->spin = o->spin_limit;
     out->gm_m = o->gmres_m;
@@ -411,6 +415,7 @@ void rmge_options_init(rmge_options* opts) {
     opts->growth_tol = d.growth_tol;
     opts->spin_limit = d.spin;
     opts->gmres_m = d.gm_m;
+    opts->apply_digits = d.digits;
     opts->sync = 0;
     opts->status = nullptr;
 }
@@ -453,8 +458,15 @@ rmge_status rmge_make_multiplier(rmge_mult_kind kind, int64_t n, uint64_t seed, 
 
 rmge_status rmge_apply_multiplier(rmge_mult_kind kind, int64_t n, const double* A, int64_t lda, const void* G, void* M,
                                   int64_t ldm, rmge_prec prec, void* ws, size_t ws_bytes, rmge_stream_t stream) {
-    if (!valid_kind(kind) || !valid_prec(prec) || !check_dims(n, 1) || A == nullptr || G == nullptr || M == nullptr ||
-        lda < n || ldm < n)
+    return rmge_apply_multiplier_ex(kind, n, A, lda, G, M, ldm, prec, nullptr, ws, ws_bytes, stream);
+}
+
+rmge_status rmge_apply_multiplier_ex(rmge_mult_kind kind, int64_t n, const double* A, int64_t lda, const void* G,
+                                     void* M, int64_t ldm, rmge_prec prec, const rmge_options* opts, void* ws,
+                                     size_t ws_bytes, rmge_stream_t stream) {
+    Opts o;
+    if (!opts_of(opts, &o) || !valid_kind(kind) || !valid_prec(prec) || !check_dims(n, 1) || A == nullptr ||
+        G == nullptr || M == nullptr || lda < n || ldm < n)
         return RMGE_ERR_INVALID_ARG;
     if (is_circ(kind) && !circ_ok(kind, n)) return RMGE_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -465,7 +477,7 @@ rmge_status rmge_apply_multiplier(rmge_mult_kind kind, int64_t n, const double* 
                                     data_prec(prec) != RMGE_F64, s);
     if (prec == RMGE_F64X_TC) {
         const OzUpdate oz = oz_buffers(w, n);
-        return oz_gemm(n, n, n, kOzSlices, 1.0, A, lda, static_cast<const double*>(G), n, 0.0, static_cast<double*>(M),
+        return oz_gemm(n, n, n, o.digits, 1.0, A, lda, static_cast<const double*>(G), n, 0.0, static_cast<double*>(M),
                        ldm, oz.planesA, oz.planesB, oz.ea, oz.eb, nullptr, nullptr, &w.st->error, nullptr, s);
     }
     if (prec == RMGE_F64)

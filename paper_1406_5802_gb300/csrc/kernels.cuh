@@ -46,14 +46,14 @@ rmge_status tc_split(int64_t rows, int64_t cols, const S* src, int64_t lds, bool
 uint32_t tc_idesc(bool bf16);
 
 // oz_gemm.cu: C (FP64) <- beta C + alpha A B with the product emulated on BF16 tensor cores from
-// s base-128 digit planes of A (rows) and B (columns).  planesA/planesB: oz_plane_bytes(M, K, s) and
+// s balanced base-256 digit planes of A (rows) and B (columns); s = kOzSlices reproduces FP64.  planesA/planesB: oz_plane_bytes(M, K, s) and
 // oz_plane_bytes(N, K, s) bytes; ea[M], eb[N] ints of scratch.  kmaxA/kmaxB (both or neither): the
 // per-k maxima max_i |A_ik| and max_j |B_kj| (FP64 bit patterns, K <= 64), which balance column k of A
 // against row k of B by an exact power of two.
 // *err <- RMGE_ERR_TIMEOUT if a bounded wait expires; nothing happens while *halt != 0 (halt may be NULL).
-constexpr int kOzSlices = 8;
+constexpr int kOzSlices = 7;
 size_t oz_plane_bytes(int64_t rows, int64_t k, int s);
-// The pivot block of the next GENP step, factored inside the update launch (K <= 64, 8 slices): the
+// The pivot block of the next GENP step, factored inside the update launch (K <= 64, kOzSlices digits): the
 // b x b block at D (b <= 64, leading dimension ldd) must lie in the first 128 x 64 tile of C; a
 // breakdown at its step s records k + s in *info (atomicMin) and raises *halt.
 struct OzFuse {

@@ -3,17 +3,23 @@
 // GB300 executes FP64 only on its DFMA pipe (about 1.2 TFLOP/s) while its BF16 tensor cores run
 // about 1.9 PFLOP/s.  An FP64 product C = alpha A B + beta C is rebuilt from exact integer products:
 //   - every row i of A gets an exponent ea_i with max_k |A_ik| < 2^ea_i, every column j of B an eb_j;
-//   - x = A_ik 2^-ea_i (|x| < 1) is truncated to s base-128 digits, x ~ sign * sum_p d_p 128^-(p+1),
-//     0 <= d_p <= 127, and digit plane p is stored as BF16 (exact: integers below 256);
-//   - digit products d_p e_q are below 2^14; the d + 1 digit pairs of one diagonal d = p + q share a
-//     TMEM accumulator over a K chunk short enough that (d + 1) 127^2 kc < 2^24, so the tensor core's
-//     FP32 accumulation of every chunk is exact (kc = 1024, 512, ..., 128 for d = 0 .. 7);
-//   - each chunk result (an exact integer) is added, shifted to its weight 128^-(d+2), into a 64-bit
+//   - x = A_ik 2^-ea_i (|x| < 1) is truncated to 8s - 1 bits, X = |x| 2^(8s-1) < 2^(8s-1), and X is
+//     written in s balanced base-256 digits, X = sum_p D_p 256^(s-1-p) with -128 <= D_p <= 128 (carries
+//     from the low digits keep each digit within half a base; the top digit stays at most 128 because
+//     X < 2^(8s-1)), so x ~ sign * sum_p D_p 2^(1 - 8(p+1)); digit plane p holds sign * D_p as BF16
+//     (exact: BF16 carries every integer up to 256 in magnitude);
+//   - digit products are at most 2^14 in magnitude; the d + 1 digit pairs of one diagonal d = p + q
+//     share a TMEM accumulator over a K chunk short enough that (d + 1) 2^14 kc <= 2^24, so the tensor
+//     core's FP32 accumulation of every chunk is exact (kc = 1024, 512, 256, 256, 128, 128, 128 for
+//     d = 0 .. 6);
+//   - each chunk result (an exact integer) is added, shifted to its weight 2^(2 - 8(d+2)), into a 64-bit
 //     fixed-point accumulator per output element (integer work, not FP64): F fractional bits of
 //     max|A_i.| max|B_.j| with F = 52 - log2(chunks on diagonal 0 + 1), i.e. 51 bits up to K = 1024;
 //   - C_ij = 2^(ea_i + eb_j - F) acc, combined with beta C in FP64 once per element.
 // Digit pairs with p + q <= s - 1 are kept.  The first dropped diagonal (p + q = s) is worth about
-// (s + 1) 2^(-7s) of max|A_i.| max|B_.j| per term, so s = 8 (36 digit pairs) matches FP64 rounding.
+// (s + 1) 2^(-8s) of max|A_i.| max|B_.j| per term, so s = 7 (28 digit pairs, 55 bits per operand)
+// matches FP64 rounding.  Balanced digits use all eight bits that BF16 holds exactly; unsigned base-128
+// digits needed 8 digits and 36 pairs for the same accuracy.
 //
 // Kernel: one 128 x 128 output tile per CTA, 18 warps.  Warp 16 (one lane) streams 128x64 BF16 tiles
 // of A-digit and B-digit planes by TMA into a 6-stage ring; warp 17 (one lane) issues
@@ -68,7 +74,7 @@ struct OzParams {
 // in L2 (a diagonal-major order re-fetched plane q from DRAM for every diagonal d >= q).
 constexpr int kSuper = 1024;
 __device__ __forceinline__ int diag_kc(int d) {
-    constexpr int kc[8] = {1024, 512, 256, 256, 128, 128, 128, 128};
+    constexpr int kc[kOzSlices] = {1024, 512, 256, 256, 128, 128, 128};
     return kc[d];
 }
 
@@ -233,11 +239,11 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
         for (int sc = 0; sc < p.K && ok; sc += kSuper)
         for (int d = 0; d < p.s && ok; ++d) {
             const int kc = diag_kc(d), se = (p.K - sc < kSuper) ? p.K : sc + kSuper;
-            // chunk value v weighs 2^-(7(d+2)) = 2^(sh - F).  v is an integer below 2^24, converted to int32
-            // (the FP32 -> int64 conversion runs on GB300's narrow FP64 pipe; this one does not).
-            // Right shifts (sh < 0) are done exactly in FP32 (a power-of-two scaling of an integer below
-            // 2^24) and rounded to the nearest integer by the conversion; left shifts in 64-bit integers.
-            const int sh = p.F - 7 * (d + 2);
+            // chunk value v weighs 2^(2 - 8(d+2)) = 2^(sh - F).  v is an integer of magnitude at most 2^24,
+            // converted to int32 (the FP32 -> int64 conversion runs on GB300's narrow FP64 pipe; this one
+            // does not).  Right shifts (sh < 0) are done exactly in FP32 (a power-of-two scaling of an
+            // integer) and rounded to the nearest integer by the conversion; left shifts in 64-bit integers.
+            const int sh = p.F - 8 * d - 14;
             const float rscale = __int_as_float((127 + (sh < 0 ? sh : 0)) << 23);
             const int lsh = sh > 0 ? sh : 0;
             for (int k0 = sc; k0 < se; k0 += kc, ++u) {
@@ -307,23 +313,25 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
 
 // ---------------------------------------------------------------------------------------------
 // Products with K <= 64 (GENP's Schur updates: one 64-deep K block).  A persistent CTA walks its
-// share of 128 x 64 output tiles in row-major order, so the 8 A digit planes of a row block (128 KB)
+// share of 128 x 64 output tiles in row-major order, so the 7 A digit planes of a row block (112 KB)
 // are loaded once and stay in shared memory; the B digit planes of each tile stream through a 4-stage
-// ring.  The 36 digit pairs run in two passes of four diagonals (d = 0-3, then 4-7), each diagonal in
+// ring.  The 28 digit pairs run in two passes, diagonals d = 0-3 then 4-6, each diagonal in
 // its own 64-column TMEM accumulator; the two passes use the two halves of TMEM, so one pass's MMAs
-// overlap the drain of the other and the tile's final store.  Per tile the TMA moves 12 B planes (96 KB)
-// instead of 36 A and 36 B tiles.  (d + 1) 127^2 64 < 2^24 keeps every accumulator exact.
+// overlap the drain of the other and the tile's final store.  Per tile the TMA moves 11 B planes (88 KB)
+// instead of 28 A and 28 B tiles.  (d + 1) 2^14 64 < 2^24 keeps every accumulator exact.
 // ---------------------------------------------------------------------------------------------
 constexpr int UBM = 128, UBN = 64;
 constexpr int UA_PLANE = UBM * OBK * 2;  // 16 KB
 constexpr int UB_PLANE = UBN * OBK * 2;  // 8 KB
 constexpr int URING = 4;
-constexpr size_t kUpdSmem = 1024 + (size_t)8 * UA_PLANE + (size_t)URING * UB_PLANE + (size_t)UBM * UBN * 8 + 256;
+constexpr size_t kUpdSmem =
+    1024 + (size_t)kOzSlices * UA_PLANE + (size_t)URING * UB_PLANE + (size_t)UBM * UBN * 8 + 256;
 static_assert(kUpdSmem <= 232448, "update kernel shared memory");
 
-// One chunk per diagonal, K <= 64: |acc| <= sum_d (d + 1) 127^2 64 2^(F - 7(d + 2)) < 0.99 2^62 at
-// F = 56, so the fixed-point sum keeps the 56 bits of the 8-digit operands.  F is a compile-time
-// constant here: the epilogue's shifts and scalings are then immediates (the epilogue is ALU-bound).
+// One chunk per diagonal, K <= 64: |acc| <= sum_d (d + 1) 2^14 64 2^(F + 2 - 8(d + 2)) < 1.01 2^62 at F = 56,
+// within a signed 64-bit integer, so the fixed-point sum keeps the 55 bits of the 7-digit operands.  F is
+// a compile-time constant here: the epilogue's shifts and scalings are then immediates (the epilogue is
+// ALU-bound).
 constexpr int kUpdF = 56;
 
 struct UpdParams {
@@ -356,10 +364,13 @@ struct EpiSync {
 };
 
 // Pass P streams B planes q = 0 .. upd_nq(P)-1 and pairs each with the A planes p in [upd_p0, upd_p1],
-// so that p + q covers the diagonals 4P .. 4P + 3; q = 0 opens every diagonal of the pass.
-__device__ __forceinline__ int upd_nq(int P) { return P == 0 ? 4 : 8; }
+// so that p + q covers the diagonals 4P .. 4P + upd_nd(P) - 1 (0-3, then 4-6); q = 0 opens every diagonal
+// of the pass.
+constexpr int kDiagLast = kOzSlices - 1;  // the last kept diagonal, 6
+__device__ __forceinline__ constexpr int upd_nd(int P) { return P == 0 ? 4 : kOzSlices - 4; }
+__device__ __forceinline__ int upd_nq(int P) { return P == 0 ? 4 : kOzSlices; }
 __device__ __forceinline__ int upd_p0(int P, int q) { return P == 0 ? 0 : (q < 4 ? 4 - q : 0); }
-__device__ __forceinline__ int upd_p1(int P, int q) { return P == 0 ? 3 - q : 7 - q; }
+__device__ __forceinline__ int upd_p1(int P, int q) { return P == 0 ? 3 - q : kDiagLast - q; }
 
 __global__ void __launch_bounds__(OTHREADS, 1)
 oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, UpdParams p,
@@ -368,7 +379,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = base;
-    uint8_t* sB = sA + 8 * UA_PLANE;
+    uint8_t* sB = sA + kOzSlices * UA_PLANE;
     double* stg = reinterpret_cast<double*>(sB + URING * UB_PLANE);  // 128 x 64, columns XOR-swizzled by row
     uint64_t* fullA = reinterpret_cast<uint64_t*>(stg + UBM * UBN);
     uint64_t* doneA = fullA + 1;   // the MMAs reading the resident A planes have completed
@@ -431,8 +442,9 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(fullA, 8 * UA_PLANE);
-                    for (int pl = 0; pl < 8; ++pl) tma_load_2d(sA + pl * UA_PLANE, &tA, 0, pl * p.Mp + mb * UBM, fullA);
+                    mbar_expect_tx(fullA, kOzSlices * UA_PLANE);
+                    for (int pl = 0; pl < kOzSlices; ++pl)
+                        tma_load_2d(sA + pl * UA_PLANE, &tA, 0, pl * p.Mp + mb * UBM, fullA);
                     ++na;
                     cur = mb;
                 }
@@ -523,8 +535,8 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
                 __syncwarp();
                 if (ok) {
 #pragma unroll
-                    for (int sl = 0; sl < 4; ++sl) {
-                        const int sh = kUpdF - 7 * (4 * P + sl + 2);  // compile-time: constant shifts
+                    for (int sl = 0; sl < upd_nd(P); ++sl) {
+                        const int sh = kUpdF - 8 * (4 * P + sl) - 14;  // compile-time: constant shifts
                         const float rscale = __int_as_float((127 + (sh < 0 ? sh : 0)) << 23);
                         const int lsh = sh > 0 ? sh : 0;
                         float v[16];
@@ -672,7 +684,7 @@ __global__ void col_exponent_kernel(int64_t rows, int64_t cols, const double* __
     }
 }
 
-// The 7s-bit magnitude |x| 2^(7s), x = v 2^-e, by integer shifts of the FP64 significand.
+// The (8s - 1)-bit magnitude |x| 2^(8s-1), x = v 2^-e (|x| < 1), by integer shifts of the FP64 significand.
 __device__ __forceinline__ unsigned long long fixed_digits(double v, int e, int s) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
     const int be = (int)((bits >> 52) & 0x7FF);
@@ -685,11 +697,13 @@ __device__ __forceinline__ unsigned long long fixed_digits(double v, int e, int 
         m |= 1ull << 52;
         ex = be - 1023 - 52;
     }
-    const int sh = ex - e + 7 * s;  // |v| 2^(7s - e) = m 2^sh
-    if (sh >= 0) return m << sh;  // |x| < 1 keeps this below 2^(7s) <= 2^56: sh <= 3
+    const int sh = ex - e + 8 * s - 1;  // |v| 2^(8s - 1 - e) = m 2^sh
+    if (sh >= 0) return m << sh;  // |x| < 1 keeps this below 2^(8s-1) <= 2^55: sh <= 2
     return (-sh >= 64) ? 0ull : (m >> (-sh));
 }
 
+// The s balanced base-256 digits of X < 2^(8s-1), most significant first: the low digits are brought
+// into [-128, 127] by carrying into the next digit up, which leaves the top digit in [0, 128].
 __device__ __forceinline__ void store_digits(double v, int er, int s, __nv_bfloat16* dst, int64_t plane) {
     if (!isfinite(v)) {  // a NaN in the leading plane makes every product it enters NaN
         dst[0] = __float2bfloat16_rn(__int_as_float(0x7fc00000));
@@ -698,8 +712,14 @@ __device__ __forceinline__ void store_digits(double v, int er, int s, __nv_bfloa
     }
     const unsigned long long X = fixed_digits(v, er, s);
     const float sg = (v < 0.0) ? -1.0f : 1.0f;
-    for (int q = 0; q < s; ++q) {
-        const unsigned d = (unsigned)((X >> (7 * (s - 1 - q))) & 127ull);
+    int carry = 0;
+    for (int q = s - 1; q >= 0; --q) {
+        int d = (int)((X >> (8 * (s - 1 - q))) & 255ull) + carry;
+        carry = 0;
+        if (q > 0 && d >= 128) {
+            d -= 256;
+            carry = 1;
+        }
         dst[(int64_t)q * plane] = __float2bfloat16_rn(sg * (float)d);
     }
 }
@@ -842,11 +862,11 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
                     const int* halt, cudaStream_t st, const OzFuse* fuse) {
     if ((kmaxA == nullptr) != (kmaxB == nullptr)) return RMGE_ERR_INVALID_ARG;
     if (M <= 0 || N <= 0) return RMGE_OK;
-    if (K <= 0 || s < 1 || s > 8 || M > INT32_MAX / 16 || N > INT32_MAX / 16 || K > INT32_MAX / 2)
+    if (K <= 0 || s < 1 || s > kOzSlices || M > INT32_MAX / 16 || N > INT32_MAX / 16 || K > INT32_MAX / 2)
         return RMGE_ERR_INVALID_ARG;
     const int64_t Mp = (M + 127) / 128 * 128, Np = (N + 127) / 128 * 128, Kp = (K + 63) / 64 * 64;
     // the fused pivot block needs the persistent update kernel and must lie in its first tile
-    if (fuse != nullptr && (Kp != OBK || s != 8 || fuse->D == nullptr || fuse->b < 1 || fuse->b > UBN ||
+    if (fuse != nullptr && (Kp != OBK || s != kOzSlices || fuse->D == nullptr || fuse->b < 1 || fuse->b > UBN ||
                             fuse->b > M || fuse->b > N || fuse->info == nullptr || fuse->halt == nullptr))
         return RMGE_ERR_INVALID_ARG;
     __nv_bfloat16* pa = static_cast<__nv_bfloat16*>(planesA);
@@ -873,7 +893,7 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
     const long long alpha_sign = (mode < 2 && alpha < 0.0) ? -1 : 1;
     const double alpha_g = (mode < 2) ? 1.0 : alpha;
 
-    if (Kp == OBK && s == 8) {  // one K block: the persistent update kernel
+    if (Kp == OBK && s == kOzSlices) {  // one K block: the persistent update kernel
         CUtensorMap ta, tb;
         if (!tc_make_map(&ta, pa, true, (int64_t)s * Mp, Kp, Kp, UBM) ||
             !tc_make_map(&tb, pb, true, (int64_t)s * Np, Kp, Kp, UBN))

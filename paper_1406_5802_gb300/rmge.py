@@ -35,13 +35,14 @@ EXPORTED = ["rmge_multiplier_bytes", "rmge_workspace_size", "rmge_make_multiplie
             "rmge_workspace_size_two_sided", "rmge_apply_two_sided", "rmge_solve_two_sided", "rmge_refine_two_sided",
             "rmge_lowrank_workspace_size", "rmge_lowrank_multiplier", "rmge_lowrank_basis", "rmge_lowrank_project",
             "rmge_options_init", "rmge_workspace_size_ex", "rmge_factor_ex", "rmge_solve_ex", "rmge_refine_ex",
+            "rmge_apply_multiplier_ex",
             "rmge_solve_batched", "rmge_solve_batched_ex", "rmge_batched_workspace_size"]
 
 
 class Options(C.Structure):
     """rmge_options (include/rmge.h)."""
-    _fields_ = [("growth_tol", C.c_double), ("spin_limit", C.c_int64), ("gmres_m", C.c_int32), ("sync", C.c_int32),
-                ("status", C.c_void_p)]
+    _fields_ = [("growth_tol", C.c_double), ("spin_limit", C.c_int64), ("status", C.c_void_p), ("gmres_m", C.c_int32),
+                ("apply_digits", C.c_int32), ("sync", C.c_int32)]
 
 
 class RmgeError(RuntimeError):
@@ -94,6 +95,8 @@ def load_library(path: str = LIB_PATH):
         "rmge_options_init": (None, [C.POINTER(Options)]),
         "rmge_workspace_size_ex": (_sz, [_i64, _i64, C.c_int, C.c_int, C.POINTER(Options)]),
         "rmge_factor_ex": (C.c_int, [_i64, _vp, _i64, C.c_int, _vp, _vp, C.POINTER(Options), _vp, _sz, _vp]),
+        "rmge_apply_multiplier_ex": (C.c_int, [C.c_int, _i64, _vp, _i64, _vp, _vp, _i64, C.c_int, C.POINTER(Options),
+                                               _vp, _sz, _vp]),
         "rmge_solve_ex": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, C.c_int,
                                     C.POINTER(Options), _vp, _sz, _vp]),
         "rmge_refine_ex": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, C.c_int,
@@ -238,7 +241,7 @@ def solve(kind, LU, G, B, prec="f64", X=None, ws=None) -> torch.Tensor:
     return X
 
 
-def options(growth_tol=0.0, spin_limit=None, gmres_m=None, sync=False, status=None) -> Options:
+def options(growth_tol=0.0, spin_limit=None, gmres_m=None, sync=False, status=None, apply_digits=None) -> Options:
     """rmge_options with the library's defaults (rmge_options_init) and the given fields replaced; status is
     a device int32 tensor or None."""
     o = Options()
@@ -248,6 +251,8 @@ def options(growth_tol=0.0, spin_limit=None, gmres_m=None, sync=False, status=No
         o.spin_limit = int(spin_limit)
     if gmres_m is not None:
         o.gmres_m = int(gmres_m)
+    if apply_digits is not None:
+        o.apply_digits = int(apply_digits)
     o.sync = 1 if sync else 0
     o.status = None if status is None else status.data_ptr()
     return o
@@ -270,6 +275,22 @@ def workspace_ex(n, nrhs, kind, prec, opts, device="cuda") -> torch.Tensor:
     if nb == 0:
         raise ValueError("invalid workspace request")
     return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def apply_multiplier_ex(kind, A, G, prec, opts, M=None, ws=None) -> torch.Tensor:
+    """rmge_apply_multiplier_ex: M = A G with options (apply_digits for the emulated FP64 product)."""
+    L = _cuda_lib()
+    _need(A, torch.float64, "A")
+    n = A.shape[0]
+    if M is None:
+        M = torch.empty(n, n, dtype=factor_dtype(prec), device=A.device)
+    _need(M, factor_dtype(prec), "M")
+    if ws is None:
+        ws = workspace_ex(n, 1, kind, prec, opts)
+    _check("rmge_apply_multiplier_ex", L.rmge_apply_multiplier_ex(_kind(kind), n, _p(A), _ld(A), _p(G), _p(M), _ld(M),
+                                                                  _prec(prec), C.byref(opts), _p(ws), ws.numel(),
+                                                                  _stream()))
+    return M
 
 
 def factor_ex(M, prec, opts, ws=None):

@@ -36,21 +36,46 @@ def _functions():
     return {n.name: n for n in tree.body if isinstance(n, ast.FunctionDef)}
 
 
+def _returned_dict(fn):
+    for node in ast.walk(fn):
+        if isinstance(node, ast.Return) and isinstance(node.value, ast.Dict):
+            return node.value
+    raise AssertionError(f"{fn.name} returns no dict literal")
+
+
+def _config_call(line):
+    c = _sub(line, "config")
+    assert isinstance(c, ast.Call) and isinstance(c.func, ast.Name), "config comes from one helper"
+    return c
+
+
 def test_main_line_keys():
     fns = _functions()
     line = _dict_assigned(fns["main"], "line")
     assert MAIN_KEYS <= _keys(line)
-    assert ROOFLINE_KEYS <= _keys(_sub(line, "roofline"))
     assert E2E_KEYS <= _keys(_sub(line, "e2e"))
-    assert "workload" in _keys(_sub(line, "config"))
     assert CPU_KEYS <= _keys(_dict_assigned(fns["main"], "cpu"))
+    # the roofline object is built by oz_roofline (the headline's dominant kernel)
+    assert ROOFLINE_KEYS <= _keys(_returned_dict(fns["oz_roofline"]))
+    assert ROOFLINE_KEYS <= _keys(_returned_dict(fns["fp64_roofline"]))
+    assert "workload" in _keys(_returned_dict(fns["workload_config"]))
 
 
 def test_reference_line_keys():
-    line = _dict_assigned(_functions()["run_reference"], "line")
+    fns = _functions()
+    line = _dict_assigned(fns["run_reference"], "line")
     assert (MAIN_KEYS - {"roofline", "gpu_launches", "clocks"}) | {"impl"} <= _keys(line)
     assert CPU_KEYS <= _keys(_sub(line, "cpu_baseline"))
     assert E2E_KEYS <= _keys(_sub(line, "e2e"))
+
+
+def test_both_arms_name_the_same_workload():
+    """Identical config dicts: both arms build theirs with the same helper and the same arguments."""
+    fns = _functions()
+    main_cfg = _config_call(_dict_assigned(fns["main"], "line"))
+    ref_cfg = _config_call(_dict_assigned(fns["run_reference"], "line"))
+    assert main_cfg.func.id == ref_cfg.func.id == "workload_config"
+    assert [ast.unparse(a) for a in main_cfg.args] == [ast.unparse(a) for a in ref_cfg.args]
 
 
 def test_rates_use_the_slowest_rank():
