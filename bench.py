@@ -35,8 +35,8 @@ N2, K2, SIGMA2 = 4096, 16, 1e-6       # the FP64 workload with its multiplier fo
 BE_TOL, MAX_ITERS = 1e-13, 10
 HEADLINE = ("gaussian", "f64x")       # multiplier kind, precision of the headline form
 # FP64 on GB300 runs on the DFMA pipe: 2 DFMA per clock per SM; at the 2070 MHz maximum SM clock that is
-# 152 SMs x 2 DFMA x 2 flop x 2.070 GHz = 1.2586 TFLOP/s (an FMA-chain microbenchmark measured 1.195,
-# profiles/fp64_dfma_peak_microbench.md).
+# 152 SMs x 2 DFMA x 2 flop x 2.070 GHz = 1.2586 TFLOP/s.  The measured FP64 GEMM rate (cuBLAS DGEMM) is
+# taken live by dgemm_peak_tflops() and reported beside it (profiles/fp64_peak_cublas_dgemm_n8192.md).
 FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) per launch of the two A G kernels from ncu captures, per n^3 (the tiled
 # products re-read their panels, so the traffic scales with n^3 once the panels exceed L2); None until
@@ -246,13 +246,33 @@ def oz_roofline(n, apply_ms, digits, peaks):
             "note": "apply_ms brackets the apply call: the digit-plane kernels and oz_gemm_kernel"}
 
 
-def fp64_roofline(n, apply_ms):
+def dgemm_peak_tflops(n=8192, reps=5):
+    """The measured FP64 GEMM rate of this GPU: cuBLAS DGEMM (torch.matmul in float64) on n x n operands, best
+    of `reps` (MEASURED_PEAKS.json has no FP64 entry)."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2.0 * n**3 / (best / 1e3) / 1e12
+
+
+def fp64_roofline(n, apply_ms, dgemm_tflops=None):
     achieved = (2 * n**3 - n**2) / (apply_ms / 1e3) / 1e12
     return {"kernel": "gemm_kernel (M = A G, FP64 DFMA)", "bound": "alu", "achieved": achieved,
             "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_ALU_PEAK_TFLOPS,
             "traffic": AG_TRAFFIC_PER_N3 * n**3, "algorithmic_bytes": 3 * n * n * 8,
-            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (FP64 is not in MEASURED_PEAKS.json; "
-                           "measured DFMA microbenchmark 1.195 TFLOP/s)",
+            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (FP64 is not in MEASURED_PEAKS.json)",
+            "measured_dgemm_tflops": dgemm_tflops,
+            "frac_of_measured_dgemm": achieved / dgemm_tflops if dgemm_tflops else None,
             "apply_ms": apply_ms}
 
 
@@ -510,8 +530,10 @@ def main():
     t0.record(stream)
     results = []
     launches0 = rmge.kernel_launches()
+    torch.cuda.nvtx.range_push("headline_timed")  # lets a profiler select the timed region's launches
     for i in range(args.steps):
         results.append(head.step(seed + args.warmup + i, record=True))
+    torch.cuda.nvtx.range_pop()
     launches = rmge.kernel_launches() - launches0
     t1.record(stream)
     torch.cuda.synchronize()
@@ -539,10 +561,12 @@ def main():
     # the plain FP64 form on the same inputs: the comparison the metric names
     fp64 = None
     try:
+        if args.fp64_steps < 1:
+            raise LookupError("not selected")
         f64 = Form(rmge, A, Bm, "gaussian", "f64")
         fp64 = timed_form(f64, args.fp64_steps, 1, seed + 100, barrier, world)
         fp64["form"] = "Gaussian G; A G, GENP's Schur updates, solves and refinement on the FP64 DFMA pipe"
-        fp64["roofline"] = fp64_roofline(n, fp64["apply_ms"])
+        fp64["roofline"] = fp64_roofline(n, fp64["apply_ms"], dgemm_peak_tflops())
         del f64
         torch.cuda.empty_cache()
     except Exception as e:

@@ -40,9 +40,14 @@ namespace {
 
 using namespace tc;
 
-constexpr int OBM = 128, OBN = 128, OBK = 64, OSTAGES = 6;
-constexpr int OA_BYTES = OBM * OBK * 2;
-constexpr int OB_BYTES = OBN * OBK * 2;
+// OBK: the K extent of one TMA box (64 BF16 = one 128-byte swizzle span, also the planes' K padding and
+// the update kernel's whole K); OKS: the K depth of one ring stage of the general kernel, two boxes per
+// operand, so that each stage feeds 8 MMAs and the per-stage waits and commits are paid half as often.
+constexpr int OBM = 128, OBN = 128, OBK = 64, OKS = 128, OSTAGES = 3;
+constexpr int OBOX_A = OBM * OBK * 2;   // one 128 x 64 BF16 box, 16 KB
+constexpr int OBOX_B = OBN * OBK * 2;
+constexpr int OA_BYTES = OBM * OKS * 2;
+constexpr int OB_BYTES = OBN * OKS * 2;
 constexpr int OSTAGE_BYTES = OA_BYTES + OB_BYTES;
 constexpr int OEPI = 16;                    // epilogue warps: 4 TMEM lane quadrants x 4 column groups of 32
 constexpr int OTHREADS = (OEPI + 2) * 32;   // + the TMA producer warp and the MMA warp
@@ -167,7 +172,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
             for (int d = 0; d < p.s && !*(volatile int*)&aborted; ++d) {
                 const int kc = diag_kc(d), se = (p.K - sc < kSuper) ? p.K : sc + kSuper;
                 for (int k0 = sc; k0 < se && !*(volatile int*)&aborted; k0 += kc) {
-                    const int nkb = ((se - k0 < kc ? se - k0 : kc) + OBK - 1) / OBK;
+                    const int nkb = ((se - k0 < kc ? se - k0 : kc) + OKS - 1) / OKS;
                     for (int pa = 0; pa <= d; ++pa) {
                         const int ya = pa * p.Mp + m0, yb = (d - pa) * p.Np + n0;
                         for (int kb = 0; kb < nkb; ++kb, ++it) {
@@ -176,9 +181,13 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
                                 atomicExch(&aborted, 1);
                                 break;
                             }
+                            // two 64-deep boxes per operand; a box past the padded K reads zeros
+                            const int kx = k0 + kb * OKS;
                             mbar_expect_tx(full + st, OSTAGE_BYTES);
-                            tma_load_2d(sA + st * OA_BYTES, &tA, k0 + kb * OBK, ya, full + st);
-                            tma_load_2d(sB + st * OB_BYTES, &tB, k0 + kb * OBK, yb, full + st);
+                            tma_load_2d(sA + st * OA_BYTES, &tA, kx, ya, full + st);
+                            tma_load_2d(sA + st * OA_BYTES + OBOX_A, &tA, kx + OBK, ya, full + st);
+                            tma_load_2d(sB + st * OB_BYTES, &tB, kx, yb, full + st);
+                            tma_load_2d(sB + st * OB_BYTES + OBOX_B, &tB, kx + OBK, yb, full + st);
                         }
                         if (*(volatile int*)&aborted) break;
                     }
@@ -204,7 +213,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const int nkb = ((se - k0 < kc ? se - k0 : kc) + OBK - 1) / OBK;
+                    const int nkb = ((se - k0 < kc ? se - k0 : kc) + OKS - 1) / OKS;
                     for (int pa = 0; pa <= d && ok; ++pa) {
                         for (int kb = 0; kb < nkb; ++kb, ++it) {
                             const int st = it % OSTAGES;
@@ -214,13 +223,16 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
                                 break;
                             }
                             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                            // 32-byte K steps inside the swizzled tile advance the descriptors' address field by 2
-                            const uint64_t ad = smem_desc(smem_u32(sA + st * OA_BYTES)),
-                                           bd = smem_desc(smem_u32(sB + st * OB_BYTES));
+                            // 32-byte K steps inside a swizzled box advance the descriptors' address field by 2
 #pragma unroll
-                            for (int kk = 0; kk < OBK / 16; ++kk)
-                                mma_f16(tmem + (uint32_t)(buf * 128), ad + 2 * kk, bd + 2 * kk, idesc,
-                                        (pa > 0 || kb > 0 || kk > 0) ? 1u : 0u);
+                            for (int h = 0; h < OKS / OBK; ++h) {
+                                const uint64_t ad = smem_desc(smem_u32(sA + st * OA_BYTES + h * OBOX_A)),
+                                               bd = smem_desc(smem_u32(sB + st * OB_BYTES + h * OBOX_B));
+#pragma unroll
+                                for (int kk = 0; kk < OBK / 16; ++kk)
+                                    mma_f16(tmem + (uint32_t)(buf * 128), ad + 2 * kk, bd + 2 * kk, idesc,
+                                            (pa > 0 || kb > 0 || h > 0 || kk > 0) ? 1u : 0u);
+                            }
                             mma_commit(empty + st);
                         }
                     }
