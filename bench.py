@@ -43,7 +43,7 @@ FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # captured for the kernel as built.  Sources: profiles/gemm_kernel_fp64_AG_n4096.md and
 # profiles/oz_gemm_kernel_f64x_AG_n8192.md.
 AG_TRAFFIC_PER_N3 = (3.730475e9 + 0.134292e9) / 4096**3
-OZ_AG_TRAFFIC_PER_N3 = None
+OZ_AG_TRAFFIC_PER_N3 = (14.101759e9 + 0.810690e9) / 8192**3
 
 
 def flops_per_solve(n, k, sweeps):
