@@ -387,6 +387,64 @@ rmge_status rmge_solve_batched_ex(int64_t count, const int32_t* n, const int64_t
                                   int64_t nmax, int32_t config, int32_t ctas, const rmge_options* opts, void* ws,
                                   size_t ws_bytes, rmge_stream_t stream);
 
+/*
+ * Uniform batches: count independent systems of one order n, each with its own dense Gaussian multiplier
+ * G_i (Def. 4.1; drawn per system, e.g. by rmge_make_multiplier), solved by the same method as the calls
+ * above -- M_i = A_i G_i (Fact 4.1), blocked GENP of M_i (eq. (3.1), Sec. 3) -- with one launch per kernel
+ * and per pivot-block step covering all of them, so that the short latency-bound steps of many small
+ * systems run side by side instead of one system after another.  The triangular solves, X_i = G_i Y_i and
+ * the refinement then use rmge_solve / rmge_refine per system on the factors left in M_i.
+ * Precision RMGE_F64X_TC only (the emulated-FP64 products; other precisions return RMGE_ERR_UNSUPPORTED).
+ * Matrices are row-major with leading dimensions lda, ldm >= n; system i's A, G and M start strideA,
+ * strideG (G has leading dimension n) and strideM elements after system i-1's, and must not overlap
+ * (stride >= (n - 1) ld + n).  1 <= count <= 65535.
+ * rmge_batched_uniform_workspace_size: scratch bytes for both calls (count control blocks, per-system digit
+ * planes of A and G, exponents and per-step maxima); 0 for an invalid request.
+ * rmge_apply_multiplier_batched: M_i = A_i G_i; opts may be NULL (apply_digits applies as for
+ * rmge_apply_multiplier_ex).
+ * rmge_factor_batched: in-place GENP of every M_i, as rmge_factor; info[i] and growth[i] (device arrays of
+ * count entries; growth may be NULL) as rmge_factor reports them.  A breakdown of one system does not stop
+ * the others.
+ */
+size_t rmge_batched_uniform_workspace_size(int64_t count, int64_t n, rmge_prec prec);
+rmge_status rmge_apply_multiplier_batched(int64_t count, int64_t n, const double* A, int64_t lda, int64_t strideA,
+                                          const double* G, int64_t strideG, double* M, int64_t ldm, int64_t strideM,
+                                          rmge_prec prec, const rmge_options* opts, void* ws, size_t ws_bytes,
+                                          rmge_stream_t stream);
+rmge_status rmge_factor_batched(int64_t count, int64_t n, double* M, int64_t ldm, int64_t strideM, rmge_prec prec,
+                                int32_t* info, double* growth, void* ws, size_t ws_bytes, rmge_stream_t stream);
+
+/*
+ * The rest of a uniform batch, with the FP64 factors that rmge_factor_batched leaves (RMGE_F64 or
+ * RMGE_F64X_TC; other precisions return RMGE_ERR_UNSUPPORTED) and dense Gaussian multipliers (leading
+ * dimension n): the calls rmge_solve, rmge_refine and rmge_solve_backward make for one system, for all
+ * count systems at once, each kernel launched once for all of them.  System i's LU, G, A, B, X, dX, dB and
+ * dA start stride* elements after system i-1's (leading dimensions as the single calls take them); berr
+ * holds count consecutive arrays of max_iters + 1 entries and iters count entries, as rmge_refine fills
+ * them per system.  The refinement is the classical FP64 correction of FP64 factors; each system stops on
+ * its own test.  ws: rmge_uniform_solve_workspace_size bytes, 256-byte aligned (one single-system block
+ * per system).  Errors as for the single calls.
+ */
+size_t rmge_uniform_solve_workspace_size(int64_t count, int64_t n, int64_t nrhs, rmge_prec prec);
+rmge_status rmge_solve_uniform_batched(int64_t count, int64_t n, int64_t nrhs, const double* LU, int64_t ldlu,
+                                       int64_t strideLU, const double* G, int64_t strideG, const double* B,
+                                       int64_t ldb, int64_t strideB, double* X, int64_t ldx, int64_t strideX,
+                                       rmge_prec prec, void* ws, size_t ws_bytes, rmge_stream_t stream);
+rmge_status rmge_refine_uniform_batched(int64_t count, int64_t n, int64_t nrhs, const double* A, int64_t lda,
+                                        int64_t strideA, const double* LU, int64_t ldlu, int64_t strideLU,
+                                        const double* G, int64_t strideG, const double* B, int64_t ldb,
+                                        int64_t strideB, double* X, int64_t ldx, int64_t strideX, rmge_prec prec,
+                                        int32_t max_iters, double be_tol, double* berr, int32_t* iters, void* ws,
+                                        size_t ws_bytes, rmge_stream_t stream);
+rmge_status rmge_solve_backward_uniform_batched(int64_t count, int64_t n, int64_t nrhs, const double* A, int64_t lda,
+                                                int64_t strideA, const double* LU, int64_t ldlu, int64_t strideLU,
+                                                const double* G, int64_t strideG, const double* X, int64_t ldx,
+                                                int64_t strideX, const double* dX, int64_t lddx, int64_t stridedX,
+                                                double* dB, int64_t lddb, int64_t stridedB, double* dA, int64_t ldda,
+                                                int64_t stridedA, rmge_prec prec, int32_t max_iters, double be_tol,
+                                                double* berr, int32_t* iters, void* ws, size_t ws_bytes,
+                                                rmge_stream_t stream);
+
 /* Number of kernel launches this process has enqueued through the library so far (host-side
  * counter; lets a caller count the kernels of a timed region). */
 unsigned long long rmge_kernel_launches(void);

@@ -58,9 +58,57 @@ def _stream_pool(count: int, device) -> list:
     return _POOLS[key]
 
 
+class RmgeSolveUniform(torch.autograd.Function):
+    """count systems of one order n in one autograd node: the multipliers' products M_i = A_i G_i and the
+    GENP factorizations run as uniform batches (one launch per kernel and step for all systems,
+    rmge_apply_multiplier_batched / rmge_factor_batched), and so do the triangular solves, X_i = G_i Y_i,
+    the refinement and the adjoint (rmge_solve_uniform_batched, rmge_refine_uniform_batched,
+    rmge_solve_backward_uniform_batched)."""
+
+    @staticmethod
+    def forward(ctx, A, B, seeds, prec, max_iters, be_tol, streams):
+        count, n, _ = A.shape
+        A64 = A.detach().to(torch.float64).contiguous()
+        B64 = B.detach().to(torch.float64).contiguous()
+        G = torch.empty(count, n, n, dtype=torch.float64, device=A.device)
+        for i, s in enumerate(seeds):
+            rmge.make_multiplier("gaussian", n, int(s), 1, prec, G=G[i])
+        ws = rmge.uniform_workspace(count, n, prec)
+        M = rmge.apply_multiplier_batched(A64, G, prec, ws=ws)
+        info, _ = rmge.factor_batched(M, prec, ws=ws)
+        del ws
+        # the solves and sweeps with FP64 factors are uniform batches too: one launch per kernel for all
+        # systems, each system stopping its refinement on its own test
+        ws = rmge.uniform_solve_workspace(count, n, B64.shape[2], prec)
+        X = rmge.solve_uniform_batched(M, G, B64, prec, ws=ws)
+        rmge.refine_uniform_batched(A64, M, G, B64, X, prec, max_iters, be_tol, ws=ws)
+        ctx.save_for_backward(M, G, X, A64)
+        ctx.prec, ctx.max_iters, ctx.be_tol, ctx.streams, ctx.info = prec, max_iters, be_tol, streams, info
+        return X.to(B.dtype)
+
+    @staticmethod
+    def backward(ctx, dX):
+        M, G, X, A64 = ctx.saved_tensors
+        count, n, _ = M.shape
+        dX64 = dX.detach().to(torch.float64).contiguous()
+        dB, dA, _, _ = rmge.solve_backward_uniform_batched(A64, M, G, X, dX64, ctx.prec,
+                                                           want_dA=ctx.needs_input_grad[0],
+                                                           max_iters=ctx.max_iters, be_tol=ctx.be_tol)
+        gA = dA.to(dX.dtype) if dA is not None else None
+        gB = dB.to(dX.dtype) if ctx.needs_input_grad[1] else None
+        return gA, gB, None, None, None, None, None
+
+
 def rmge_solve_batched(As, Bs, seeds, kind: str = "gaussian", prec: str = "f32", streams: int = 8, **kw):
-    """A list of independent differentiable solves, spread round-robin over CUDA streams so that small
-    systems overlap on the GPU.  Returns the list of X."""
+    """A list of independent differentiable solves.  Systems of one order with the emulated-FP64 precision
+    ("f64x") and dense Gaussian multipliers go through the uniform batched path (one autograd node;
+    products and factorizations batched); otherwise each solve is its own node and the solves are spread
+    round-robin over CUDA streams so that small systems overlap on the GPU.  Returns the list of X."""
+    if (prec == "f64x" and kind == "gaussian" and len(As) > 1 and len({tuple(a.shape) for a in As}) == 1
+            and len({tuple(b.shape) for b in Bs}) == 1):
+        X = RmgeSolveUniform.apply(torch.stack(As), torch.stack(Bs), list(seeds), prec, kw.get("max_iters", 10),
+                                   kw.get("be_tol", 1e-13), streams)
+        return list(X.unbind(0))
     pool = _stream_pool(max(1, streams), As[0].device.index if len(As) else None)
     cur = torch.cuda.current_stream()
     outs = []

@@ -269,6 +269,90 @@ rmge_status refine_loop(rmge_mult_kind kind, rmge_prec prec, bool trans, int64_t
     return refine_finish(w.st, max_iters, berr, iters, s);
 }
 
+// ---- uniform batches of the solve, the refinement and the adjoint (FP64 factors, dense Gaussian G) ---------
+// Every system has its own workspace block (the single-system layout), ws bytes after the previous one, so
+// each workspace array advances by ws / sizeof(element); user arrays advance by their own strides.
+
+struct Bt {
+    int count;
+    int64_t ws;  // bytes between the systems' workspace blocks
+    int64_t lu, g;
+    int64_t wd() const { return ws / (int64_t)sizeof(double); }
+};
+
+Zb zb3(const Bt& bt, int64_t m0, int64_t m1, int64_t m2 = 0, int64_t m3 = 0) {
+    Zb z;
+    z.count = bt.count;
+    z.m0 = m0;
+    z.m1 = m1;
+    z.m2 = m2;
+    z.m3 = m3;
+    z.ws = bt.ws;
+    return z;
+}
+
+// X (+)= G U^{-1} L^{-1} V (trans: X (+)= L^{-T} U^{-T} G^T V) for every system; V and X advance by sV, sX.
+rmge_status correction_z(const Bt& bt, int64_t n, int64_t k, const double* LU, int64_t ldlu, const double* G,
+                         const double* V, int64_t ldv, int64_t sV, double* X, int64_t ldx, int64_t sX,
+                         bool accumulate, const Ws& w, int epoch, const int* skip, cudaStream_t s, bool trans) {
+    const int64_t wd = bt.wd();
+    if (trans) {
+        RMGE_TRY(gemm<double>(true, n, k, n, 1.0, G, n, V, ldv, 0.0, w.Y, k, skip, s, zb3(bt, bt.g, sV, wd)));
+        RMGE_TRY(trsv<double>(2, n, k, LU, ldlu, w.Y, k, w.st, w.flags, epoch, skip, s, zb3(bt, bt.lu, wd)));
+        RMGE_TRY(trsv<double>(3, n, k, LU, ldlu, w.Y, k, w.st, w.flags, epoch + 1, skip, s, zb3(bt, bt.lu, wd)));
+        if (accumulate) return add_update<double>(n, k, w.Y, k, X, ldx, skip, s, zb3(bt, wd, sX));
+        return copy_matrix<double, double>(n, k, w.Y, k, X, ldx, skip, s, zb3(bt, wd, sX));
+    }
+    RMGE_TRY(copy_matrix<double, double>(n, k, V, ldv, w.Y, k, skip, s, zb3(bt, sV, wd)));
+    RMGE_TRY(trsv<double>(0, n, k, LU, ldlu, w.Y, k, w.st, w.flags, epoch, skip, s, zb3(bt, bt.lu, wd)));
+    RMGE_TRY(trsv<double>(1, n, k, LU, ldlu, w.Y, k, w.st, w.flags, epoch + 1, skip, s, zb3(bt, bt.lu, wd)));
+    return gemm<double>(false, n, k, n, 1.0, G, n, w.Y, k, accumulate ? 1.0 : 0.0, X, ldx, skip, s,
+                        zb3(bt, bt.g, wd, sX));
+}
+
+// Classical FP64 refinement sweeps of every system (see rmge_refine); berr and iters advance by
+// max_iters + 1 and 1 entries.
+rmge_status refine_loop_z(const Bt& bt, bool trans, int64_t n, int64_t nrhs, const double* A, int64_t lda,
+                          int64_t sA, const double* LU, int64_t ldlu, const double* G, const double* B, int64_t ldb,
+                          int64_t sB, double* X, int64_t ldx, int64_t sX, int32_t max_iters, double be_tol,
+                          double* berr, int32_t* iters, const Ws& w, int epoch0, cudaStream_t s) {
+    const int64_t wd = bt.wd(), sb = max_iters + 1;
+    RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, (int)(3 * nrhs), berr, max_iters + 1, s,
+                        w.spin, zb3(bt, sb, 0)));
+    RMGE_TRY(abs_sums_max(n, A, lda, trans, w.st, s, zb3(bt, sA, 0)));
+    const int* stop = &w.st->stop;
+    for (int it = 0; it <= max_iters; ++it) {
+        RMGE_TRY(copy_matrix<double, double>(n, nrhs, B, ldb, w.R, nrhs, stop, s, zb3(bt, sB, wd)));
+        RMGE_TRY(gemm<double>(trans, n, nrhs, n, -1.0, A, lda, X, ldx, 1.0, w.R, nrhs, stop, s, zb3(bt, sA, sX, wd)));
+        RMGE_TRY(backward_error(n, nrhs, w.R, nrhs, X, ldx, B, ldb, w.st, w.colred, it, be_tol, max_iters, berr, s,
+                                false, zb3(bt, wd, sX, sB, sb)));
+        if (it == max_iters) break;
+        RMGE_TRY(correction_z(bt, n, nrhs, LU, ldlu, G, w.R, nrhs, wd, X, ldx, sX, true, w, epoch0 + 2 * it, stop, s,
+                              trans));
+    }
+    return refine_finish(w.st, max_iters, berr, iters, s, zb3(bt, 1, 0));
+}
+
+// The common argument checks of the three uniform-batch calls; fills bt and carves system 0's workspace.
+rmge_status uniform_setup(int64_t count, int64_t n, int64_t nrhs, rmge_prec prec, const void* LU, int64_t ldlu,
+                          int64_t sLU, const void* G, int64_t sG, void* ws, size_t ws_bytes, Bt* bt, Ws* w) {
+    if (count < 1 || count > 65535 || !check_dims(n, nrhs) || !valid_prec(prec) || LU == nullptr || G == nullptr ||
+        ldlu < n || sLU < (n - 1) * ldlu + n || sG < n * n)
+        return RMGE_ERR_INVALID_ARG;
+    if (data_prec(prec) != RMGE_F64) return RMGE_ERR_UNSUPPORTED;
+    const size_t per = ws_layout(n, nrhs, RMGE_GAUSSIAN, RMGE_F64).total;
+    if (ws == nullptr || ((uintptr_t)ws & 255) != 0 || ws_bytes / (size_t)count < per) return RMGE_ERR_WORKSPACE;
+    bt->count = (int)count;
+    bt->ws = (int64_t)per;
+    bt->lu = sLU;
+    bt->g = sG;
+    return carve(ws, per, n, nrhs, RMGE_GAUSSIAN, RMGE_F64, w);
+}
+
+bool mat_ok(const void* P, int64_t n, int64_t cols, int64_t ld, int64_t stride) {
+    return P != nullptr && ld >= cols && stride >= (n - 1) * ld + cols;
+}
+
 // ---- two-sided forms (Fact 4.1: A^{-1} = H (F A H)^{-1} F), FP64 data ------------------------------------
 
 // The layout kind whose workspace serves both multipliers: the longer FFT wins.
@@ -727,6 +811,161 @@ rmge_status rmge_lowrank_project(int64_t m, int64_t n, int32_t l, const double* 
         lda < n || ldz < n)
         return RMGE_ERR_INVALID_ARG;
     return lowrank_project(m, n, l, Q, ldq, A, lda, Z, ldz, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ---- uniform batches (emulated FP64): count systems of order n, one launch per kernel and step -------------
+
+struct UniLayout {
+    size_t states, kmax, ea, eb, planesA, planesB, total;
+    int64_t Mp, Kp, steps;
+};
+
+static UniLayout uni_layout(int64_t count, int64_t n) {
+    UniLayout L{};
+    L.Mp = (n + 127) / 128 * 128;
+    L.Kp = (n + 63) / 64 * 64;
+    L.steps = (n + kNb - 1) / kNb;
+    size_t off = 0;
+    L.states = off;
+    off = align256(off + sizeof(DevState) * (size_t)count);
+    L.kmax = off;
+    off = align256(off + sizeof(unsigned long long) * 128 * (size_t)L.steps * (size_t)count);
+    L.ea = off;
+    off = align256(off + sizeof(int) * (size_t)L.Mp * (size_t)count);
+    L.eb = off;
+    off = align256(off + sizeof(int) * (size_t)L.Mp * (size_t)count);
+    const size_t plane = (size_t)kOzSlices * (size_t)L.Mp * (size_t)L.Kp * 2 * (size_t)count;
+    L.planesA = off;
+    off = align256(off + plane);
+    L.planesB = off;
+    off = align256(off + plane);
+    L.total = off;
+    return L;
+}
+
+static bool uni_args_ok(int64_t count, int64_t n) {
+    return count >= 1 && count <= 65535 && n >= 1 && n <= RMGE_MAX_N;
+}
+
+static bool uni_stride_ok(int64_t n, int64_t ld, int64_t stride) {
+    return ld >= n && stride >= (n - 1) * ld + n;
+}
+
+size_t rmge_batched_uniform_workspace_size(int64_t count, int64_t n, rmge_prec prec) {
+    if (!uni_args_ok(count, n) || prec != RMGE_F64X_TC) return 0;
+    return uni_layout(count, n).total;
+}
+
+rmge_status rmge_apply_multiplier_batched(int64_t count, int64_t n, const double* A, int64_t lda, int64_t strideA,
+                                          const double* G, int64_t strideG, double* M, int64_t ldm, int64_t strideM,
+                                          rmge_prec prec, const rmge_options* opts, void* ws, size_t ws_bytes,
+                                          rmge_stream_t stream) {
+    Opts o;
+    if (!opts_of(opts, &o) || !uni_args_ok(count, n) || !valid_prec(prec) || A == nullptr || G == nullptr ||
+        M == nullptr || !uni_stride_ok(n, lda, strideA) || !uni_stride_ok(n, n, strideG) ||
+        !uni_stride_ok(n, ldm, strideM))
+        return RMGE_ERR_INVALID_ARG;
+    if (prec != RMGE_F64X_TC) return RMGE_ERR_UNSUPPORTED;
+    const UniLayout L = uni_layout(count, n);
+    if (ws == nullptr || ((uintptr_t)ws & 255) != 0 || ws_bytes < L.total) return RMGE_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char* b = static_cast<char*>(ws);
+    DevState* st = reinterpret_cast<DevState*>(b + L.states);
+    RMGE_TRY(states_init(st, (int)count, nullptr, 0, s, o.spin));
+    OzBatch bt;
+    bt.count = (int)count;
+    bt.sA = strideA;
+    bt.sB = strideG;
+    bt.sC = strideM;
+    return oz_gemm(n, n, n, o.digits, 1.0, A, lda, G, n, 0.0, M, ldm, b + L.planesA, b + L.planesB,
+                   reinterpret_cast<int*>(b + L.ea), reinterpret_cast<int*>(b + L.eb), nullptr, nullptr, &st->error,
+                   nullptr, s, nullptr, bt);
+}
+
+rmge_status rmge_factor_batched(int64_t count, int64_t n, double* M, int64_t ldm, int64_t strideM, rmge_prec prec,
+                                int32_t* info, double* growth, void* ws, size_t ws_bytes, rmge_stream_t stream) {
+    if (!uni_args_ok(count, n) || !valid_prec(prec) || M == nullptr || info == nullptr ||
+        !uni_stride_ok(n, ldm, strideM))
+        return RMGE_ERR_INVALID_ARG;
+    if (prec != RMGE_F64X_TC) return RMGE_ERR_UNSUPPORTED;
+    const UniLayout L = uni_layout(count, n);
+    if (ws == nullptr || ((uintptr_t)ws & 255) != 0 || ws_bytes < L.total) return RMGE_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char* b = static_cast<char*>(ws);
+    DevState* st = reinterpret_cast<DevState*>(b + L.states);
+    OzUpdate oz{};
+    oz.planesA = b + L.planesA;
+    oz.planesB = b + L.planesB;
+    oz.ea = reinterpret_cast<int*>(b + L.ea);
+    oz.eb = reinterpret_cast<int*>(b + L.eb);
+    oz.kmax = reinterpret_cast<unsigned long long*>(b + L.kmax);
+    RMGE_TRY(states_init(st, (int)count, oz.kmax, 128 * L.steps * count, s));
+    RMGE_TRY(genp_factor_oz(n, M, ldm, st, oz, s, (int)count, strideM));
+    return genp_finish(st, info, growth, s, (int)count);
+}
+
+size_t rmge_uniform_solve_workspace_size(int64_t count, int64_t n, int64_t nrhs, rmge_prec prec) {
+    if (count < 1 || count > 65535 || !check_dims(n, nrhs) || !valid_prec(prec) || data_prec(prec) != RMGE_F64)
+        return 0;
+    return (size_t)count * ws_layout(n, nrhs, RMGE_GAUSSIAN, RMGE_F64).total;
+}
+
+rmge_status rmge_solve_uniform_batched(int64_t count, int64_t n, int64_t nrhs, const double* LU, int64_t ldlu,
+                                       int64_t strideLU, const double* G, int64_t strideG, const double* B,
+                                       int64_t ldb, int64_t strideB, double* X, int64_t ldx, int64_t strideX,
+                                       rmge_prec prec, void* ws, size_t ws_bytes, rmge_stream_t stream) {
+    Bt bt{};
+    Ws w{};
+    if (!mat_ok(B, n, nrhs, ldb, strideB) || !mat_ok(X, n, nrhs, ldx, strideX)) return RMGE_ERR_INVALID_ARG;
+    RMGE_TRY(uniform_setup(count, n, nrhs, prec, LU, ldlu, strideLU, G, strideG, ws, ws_bytes, &bt, &w));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, 0, nullptr, 0, s, w.spin, zb3(bt, 0, 0)));
+    return correction_z(bt, n, nrhs, LU, ldlu, G, B, ldb, strideB, X, ldx, strideX, false, w, 1, nullptr, s, false);
+}
+
+rmge_status rmge_refine_uniform_batched(int64_t count, int64_t n, int64_t nrhs, const double* A, int64_t lda,
+                                        int64_t strideA, const double* LU, int64_t ldlu, int64_t strideLU,
+                                        const double* G, int64_t strideG, const double* B, int64_t ldb,
+                                        int64_t strideB, double* X, int64_t ldx, int64_t strideX, rmge_prec prec,
+                                        int32_t max_iters, double be_tol, double* berr, int32_t* iters, void* ws,
+                                        size_t ws_bytes, rmge_stream_t stream) {
+    Bt bt{};
+    Ws w{};
+    if (!mat_ok(A, n, n, lda, strideA) || !mat_ok(B, n, nrhs, ldb, strideB) || !mat_ok(X, n, nrhs, ldx, strideX) ||
+        max_iters < 0 || max_iters > kMaxSweeps || !(be_tol >= 0.0))
+        return RMGE_ERR_INVALID_ARG;
+    RMGE_TRY(uniform_setup(count, n, nrhs, prec, LU, ldlu, strideLU, G, strideG, ws, ws_bytes, &bt, &w));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return refine_loop_z(bt, false, n, nrhs, A, lda, strideA, LU, ldlu, G, B, ldb, strideB, X, ldx, strideX,
+                         max_iters, be_tol, berr, iters, w, 1, s);
+}
+
+rmge_status rmge_solve_backward_uniform_batched(int64_t count, int64_t n, int64_t nrhs, const double* A, int64_t lda,
+                                                int64_t strideA, const double* LU, int64_t ldlu, int64_t strideLU,
+                                                const double* G, int64_t strideG, const double* X, int64_t ldx,
+                                                int64_t strideX, const double* dX, int64_t lddx, int64_t stridedX,
+                                                double* dB, int64_t lddb, int64_t stridedB, double* dA, int64_t ldda,
+                                                int64_t stridedA, rmge_prec prec, int32_t max_iters, double be_tol,
+                                                double* berr, int32_t* iters, void* ws, size_t ws_bytes,
+                                                rmge_stream_t stream) {
+    Bt bt{};
+    Ws w{};
+    if (!mat_ok(dX, n, nrhs, lddx, stridedX) || !mat_ok(dB, n, nrhs, lddb, stridedB) ||
+        (dA != nullptr && (!mat_ok(dA, n, n, ldda, stridedA) || !mat_ok(X, n, nrhs, ldx, strideX))) ||
+        max_iters < 0 || max_iters > kMaxSweeps || (max_iters > 0 && !mat_ok(A, n, n, lda, strideA)) ||
+        !(be_tol >= 0.0))
+        return RMGE_ERR_INVALID_ARG;
+    RMGE_TRY(uniform_setup(count, n, nrhs, prec, LU, ldlu, strideLU, G, strideG, ws, ws_bytes, &bt, &w));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    RMGE_TRY(state_init(w.st, w.flags, nflags_for(n, nrhs), w.colred, 0, nullptr, 0, s, w.spin, zb3(bt, 0, 0)));
+    // dB = A^{-T} dX ~= L^{-T} U^{-T} G^T dX, refined on A^T dB = dX, then dA = -dB X^T
+    RMGE_TRY(correction_z(bt, n, nrhs, LU, ldlu, G, dX, lddx, stridedX, dB, lddb, stridedB, false, w, 1, nullptr, s,
+                          true));
+    if (max_iters > 0)
+        RMGE_TRY(refine_loop_z(bt, true, n, nrhs, A, lda, strideA, LU, ldlu, G, dX, lddx, stridedX, dB, lddb,
+                               stridedB, max_iters, be_tol, berr, iters, w, 3, s));
+    if (dA != nullptr) return outer_neg(n, nrhs, dB, lddb, X, ldx, dA, ldda, s, zb3(bt, stridedB, strideX, stridedA));
+    return RMGE_OK;
 }
 
 size_t rmge_batched_workspace_size(int64_t nmax, int32_t ctas) {

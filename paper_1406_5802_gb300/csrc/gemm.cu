@@ -41,11 +41,15 @@ template <typename T, typename SA, typename SB, int BM, int BN, int BK, int TM, 
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const SA* __restrict__ A, int64_t lda,
             const SB* __restrict__ B, int64_t ldb, T beta, T* __restrict__ C, int64_t ldc, const int* halt,
-            PivotFuse<T> fz) {
+            PivotFuse<T> fz, Zb zb) {
     constexpr int RX = BN / TN;  // threads along a row of the tile
     constexpr int RY = BM / TM;
     constexpr int NT = RX * RY;
+    halt = zws(halt, zb.ws);
     if (halt != nullptr && *(volatile const int*)halt != 0) return;
+    A = zmat(A, zb.m0);
+    B = zmat(B, zb.m1);
+    C = zmat(C, zb.m2);
 
     // the two double-buffered tiles, carved from one array (the fused pivot block reuses it whole)
     constexpr int kTileBytes = (int)sizeof(T) * (2 * BK * (BM + 1) + 2 * BK * BN);
@@ -184,8 +188,12 @@ gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const SA* __restrict__ A, 
 template <typename T, typename SA, typename SB, int NC>
 __global__ void __launch_bounds__(256) gemv_kernel(int64_t M, int64_t K, T alpha, const SA* __restrict__ A,
                                                    int64_t lda, const SB* __restrict__ B, int64_t ldb, T beta,
-                                                   T* __restrict__ C, int64_t ldc, const int* halt) {
+                                                   T* __restrict__ C, int64_t ldc, const int* halt, Zb zb) {
+    halt = zws(halt, zb.ws);
     if (halt != nullptr && *(volatile const int*)halt != 0) return;
+    A = zmat(A, zb.m0);
+    B = zmat(B, zb.m1);
+    C = zmat(C, zb.m2);
     const int lane = threadIdx.x & 31;
     const int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;  // one row per warp: uniform
     if (m >= M) return;
@@ -226,24 +234,25 @@ __global__ void __launch_bounds__(256) gemv_kernel(int64_t M, int64_t K, T alpha
 
 template <typename T, typename SA, typename SB, int NC>
 rmge_status launch_gemv(int64_t M, int64_t K, T alpha, const SA* A, int64_t lda, const SB* B, int64_t ldb, T beta,
-                        T* C, int64_t ldc, const int* halt, cudaStream_t s) {
+                        T* C, int64_t ldc, const int* halt, cudaStream_t s, const Zb& zb) {
     const int64_t blocks = (M + 7) / 8;  // 8 warps (rows) per block
-    gemv_kernel<T, SA, SB, NC><<<(unsigned)blocks, 256, 0, s>>>(M, K, alpha, A, lda, B, ldb, beta, C, ldc, halt);
+    gemv_kernel<T, SA, SB, NC><<<dim3((unsigned)blocks, 1, zb.count), 256, 0, s>>>(M, K, alpha, A, lda, B, ldb, beta,
+                                                                                  C, ldc, halt, zb);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }
 
 template <typename T, typename SA, typename SB, int BM, int BN, int BK, int TM, int TN>
 rmge_status launch(bool ta, int64_t M, int64_t N, int64_t K, T alpha, const SA* A, int64_t lda, const SB* B,
-                   int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s) {
-    const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
+                   int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s, const Zb& zb) {
+    const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)zb.count);
     const int threads = (BM / TM) * (BN / TN);
     if (ta)
         gemm_kernel<T, SA, SB, BM, BN, BK, TM, TN, true, false><<<grid, threads, 0, s>>>(
-            M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, PivotFuse<T>{});
+            M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, PivotFuse<T>{}, zb);
     else
         gemm_kernel<T, SA, SB, BM, BN, BK, TM, TN, false, false><<<grid, threads, 0, s>>>(
-            M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, PivotFuse<T>{});
+            M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, PivotFuse<T>{}, zb);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }
@@ -252,41 +261,41 @@ constexpr int64_t kSMs = 152;
 
 template <typename T, typename SA, typename SB>
 rmge_status gemm_any(bool trans_a, int64_t M, int64_t N, int64_t K, T alpha, const SA* A, int64_t lda, const SB* B,
-                     int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s) {
+                     int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s, const Zb& zb = Zb{}) {
     if (M <= 0 || N <= 0) return RMGE_OK;
     if (!trans_a && N <= 4) {
         switch (N) {
-            case 1: return launch_gemv<T, SA, SB, 1>(M, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
-            case 2: return launch_gemv<T, SA, SB, 2>(M, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
-            case 3: return launch_gemv<T, SA, SB, 3>(M, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
-            default: return launch_gemv<T, SA, SB, 4>(M, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
+            case 1: return launch_gemv<T, SA, SB, 1>(M, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s, zb);
+            case 2: return launch_gemv<T, SA, SB, 2>(M, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s, zb);
+            case 3: return launch_gemv<T, SA, SB, 3>(M, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s, zb);
+            default: return launch_gemv<T, SA, SB, 4>(M, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s, zb);
         }
     }
     // One output per thread: the FMA pipe, not shared memory, bounds these on GB300.  (4-row tiles, which
     // spread M = 4096 x 16 columns more evenly over the 152 SMs than 256 tiles of 16 rows, measured slower.)
     if (N <= 8)
-        return launch<T, SA, SB, 16, 8, 64, 1, 1>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
+        return launch<T, SA, SB, 16, 8, 64, 1, 1>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s, zb);
     if (N <= 16)
-        return launch<T, SA, SB, 16, 16, 32, 1, 1>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
+        return launch<T, SA, SB, 16, 16, 32, 1, 1>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s, zb);
     // Square-ish: the largest tile that still gives every SM several tiles.
     if constexpr (sizeof(T) == 4) {
         const int64_t t128 = ((M + 127) / 128) * ((N + 127) / 128);
         if (t128 >= 4 * kSMs)
             return launch<T, SA, SB, 128, 128, 16, 8, 8>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt,
-                                                         s);
+                                                         s, zb);
     }
     const int64_t t64 = ((M + 63) / 64) * ((N + 63) / 64);
     if (t64 >= 2 * kSMs)
-        return launch<T, SA, SB, 64, 64, 16, 4, 4>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
-    return launch<T, SA, SB, 32, 32, 16, 2, 2>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
+        return launch<T, SA, SB, 64, 64, 16, 4, 4>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s, zb);
+    return launch<T, SA, SB, 32, 32, 16, 2, 2>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s, zb);
 }
 
 }  // namespace
 
 template <typename T>
 rmge_status gemm(bool trans_a, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda, const T* B,
-                 int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s) {
-    return gemm_any<T, T, T>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s);
+                 int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s, const Zb& zb) {
+    return gemm_any<T, T, T>(trans_a, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s, zb);
 }
 
 template <typename T>
@@ -295,7 +304,7 @@ rmge_status gemm_update_fused(int64_t M, int64_t N, int64_t K, const T* A, int64
     if (b < 1 || b > 64 || b > M || b > N || info == nullptr || halt_w == nullptr) return RMGE_ERR_INVALID_ARG;
     const dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
     gemm_kernel<T, T, T, 64, 64, 16, 4, 4, false, true><<<grid, 256, 0, s>>>(
-        M, N, K, T(-1), A, lda, B, ldb, T(1), C, ldc, halt, PivotFuse<T>{C, b, k, info, halt_w});
+        M, N, K, T(-1), A, lda, B, ldb, T(1), C, ldc, halt, PivotFuse<T>{C, b, k, info, halt_w}, Zb{});
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }
@@ -311,8 +320,8 @@ rmge_status gemm_f64a_f32(int64_t M, int64_t N, int64_t K, const double* A, int6
 }
 
 template rmge_status gemm<double>(bool, int64_t, int64_t, int64_t, double, const double*, int64_t, const double*,
-                                  int64_t, double, double*, int64_t, const int*, cudaStream_t);
+                                  int64_t, double, double*, int64_t, const int*, cudaStream_t, const Zb&);
 template rmge_status gemm<float>(bool, int64_t, int64_t, int64_t, float, const float*, int64_t, const float*,
-                                 int64_t, float, float*, int64_t, const int*, cudaStream_t);
+                                 int64_t, float, float*, int64_t, const int*, cudaStream_t, const Zb&);
 
 }  // namespace rmge

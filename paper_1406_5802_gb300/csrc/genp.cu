@@ -36,11 +36,15 @@ struct CtaSync {
     __device__ void operator()() const { __syncthreads(); }
 };
 
+// blockIdx.y (here and in the kernels below): the system of a batch of equal-size factorizations, whose
+// matrices lie sM elements apart and whose control blocks follow one another.
 template <typename T>
 __global__ void __launch_bounds__(256) diag_factor_kernel(int64_t k, int b, T* __restrict__ M, int64_t ldm,
-                                                          DevState* st) {
+                                                          DevState* st, int64_t sM) {
     __shared__ T a[NB * kPivotLds];
     __shared__ T rp;
+    M += blockIdx.y * sM;
+    st += blockIdx.y;
     if (*(volatile int*)&st->halt) return;
     const int tid = threadIdx.x;
     T* blk = M + k * ldm + k;
@@ -70,11 +74,14 @@ __global__ void __launch_bounds__(256) diag_factor_kernel(int64_t k, int b, T* _
 template <typename T, int PT>
 __global__ void __launch_bounds__(256) panel_apply_kernel(int64_t k, int b, int64_t rest, int row_tiles,
                                                           T* __restrict__ M, int64_t ldm, const DevState* st,
-                                                          unsigned long long* kmax) {
+                                                          unsigned long long* kmax, int64_t sM, int64_t sK) {
     static_assert(PT * 16 == 256, "16 lanes per row or column");
     __shared__ T dd[NB][LDS];
     __shared__ T tile[PT][LDS];  // row tile: tile[r][t]; column tile stored transposed: tile[c][t]
     __shared__ T rdiag[NB];      // 1 / u_jj, once per CTA (FP64 division is costly on GB300's FP64 pipe)
+    M += blockIdx.y * sM;
+    st += blockIdx.y;
+    if (kmax != nullptr) kmax += blockIdx.y * sK;
     if (*(volatile const int*)&st->halt) return;
     const int tid = threadIdx.x;
     const bool is_row = (int)blockIdx.x < row_tiles;
@@ -154,8 +161,10 @@ __global__ void __launch_bounds__(256) panel_apply_kernel(int64_t k, int b, int6
 
 template <typename T>
 __global__ void maxabs_kernel(int64_t rows, int64_t cols, const T* __restrict__ P, int64_t ldp, bool upper_only,
-                              unsigned long long* out) {
+                              unsigned long long* out, int64_t sP, int64_t sOut) {
     unsigned long long best = 0;
+    P += blockIdx.y * sP;
+    out += blockIdx.y * sOut;
     const int64_t total = rows * cols;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e / cols, j = e % cols;
@@ -171,6 +180,9 @@ __global__ void maxabs_kernel(int64_t rows, int64_t cols, const T* __restrict__ 
 }
 
 __global__ void finish_kernel(DevState* st, int32_t* info, double* growth) {
+    st += blockIdx.x;
+    if (info) info += blockIdx.x;
+    if (growth) growth += blockIdx.x;
     const int v = st->info;
     if (info) *info = (v == INT_MAX) ? 0 : v;
     if (growth) {
@@ -189,7 +201,7 @@ rmge_status maxabs(int64_t rows, int64_t cols, const T* P, int64_t ldp, bool upp
     int64_t g = (total + 255) / 256;
     if (g > 152 * 8) g = 152 * 8;
     if (g < 1) g = 1;
-    maxabs_kernel<T><<<(unsigned)g, 256, 0, s>>>(rows, cols, P, ldp, upper_only, out_bits);
+    maxabs_kernel<T><<<(unsigned)g, 256, 0, s>>>(rows, cols, P, ldp, upper_only, out_bits, 0, 0);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }
@@ -201,13 +213,13 @@ rmge_status genp_factor(int64_t n, T* M, int64_t ldm, DevState* st, cudaStream_t
     for (int64_t k = 0; k < n; k += NB) {
         const int b = (int)((n - k) < NB ? (n - k) : NB);
         if (k == 0) {  // every later pivot block is factored inside the previous step's update launch
-            diag_factor_kernel<T><<<1, 256, 0, s>>>(k, b, M, ldm, st);
+            diag_factor_kernel<T><<<1, 256, 0, s>>>(k, b, M, ldm, st, 0);
             RMGE_LAUNCH_CHECK();
         }
         const int64_t rest = n - k - b;
         if (rest <= 0) break;
         const int tiles = (int)((rest + PT - 1) / PT);
-        panel_apply_kernel<T, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, nullptr);
+        panel_apply_kernel<T, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, nullptr, 0, 0);
         RMGE_LAUNCH_CHECK();
         RMGE_TRY(gemm_update_fused<T>(rest, rest, b, M + (k + b) * ldm + k, ldm, M + k * ldm + k + b, ldm,
                                       M + (k + b) * ldm + (k + b), ldm, &st->halt, (int)(rest < NB ? rest : NB),
@@ -227,12 +239,12 @@ rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const
     int64_t step = 0;
     for (int64_t k = 0; k < n; k += NB, ++step) {
         const int b = (int)((n - k) < NB ? (n - k) : NB);
-        diag_factor_kernel<float><<<1, 256, 0, s>>>(k, b, M, ldm, st);
+        diag_factor_kernel<float><<<1, 256, 0, s>>>(k, b, M, ldm, st, 0);
         RMGE_LAUNCH_CHECK();
         const int64_t rest = n - k - b;
         if (rest <= 0) break;
         const int tiles = (int)((rest + PT - 1) / PT);
-        panel_apply_kernel<float, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, nullptr);
+        panel_apply_kernel<float, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, nullptr, 0, 0);
         RMGE_LAUNCH_CHECK();
         const float* L21 = M + (k + b) * ldm + k;
         const float* U12 = M + k * ldm + k + b;
@@ -260,35 +272,57 @@ rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const
 // update loses most of its relative accuracy.
 // The update launch of step k also factors the pivot block of step k + 1 (CTA 0 takes the tile holding it
 // alone), so only the first pivot block has a launch of its own.
-rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s) {
+rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s,
+                           int count, int64_t sM) {
     constexpr int PT = 16;
-    RMGE_TRY(maxabs<double>(n, n, M, ldm, false, &st->maxabs_m, s));
+    const unsigned nz = (unsigned)count;
+    const int64_t steps = (n + NB - 1) / NB;
+    constexpr int64_t kStateUll = sizeof(DevState) / sizeof(unsigned long long);
+    constexpr int64_t kStateInt = sizeof(DevState) / sizeof(int);
+    // growth numerator and denominator go to each system's control block
+    {
+        int64_t g = (n * n + 255) / 256;
+        if (g > 152 * 8) g = 152 * 8;
+        maxabs_kernel<double><<<dim3((unsigned)g, nz), 256, 0, s>>>(n, n, M, ldm, false, &st->maxabs_m, sM, kStateUll);
+        RMGE_LAUNCH_CHECK();
+    }
     int64_t step = 0;
     for (int64_t k = 0; k < n; k += NB, ++step) {
         const int b = (int)((n - k) < NB ? (n - k) : NB);
         if (k == 0) {  // every later pivot block is factored inside the previous step's update launch
-            diag_factor_kernel<double><<<1, 256, 0, s>>>(k, b, M, ldm, st);
+            diag_factor_kernel<double><<<dim3(1, nz), 256, 0, s>>>(k, b, M, ldm, st, sM);
             RMGE_LAUNCH_CHECK();
         }
         const int64_t rest = n - k - b;
         if (rest <= 0) break;
         const int tiles = (int)((rest + PT - 1) / PT);
         unsigned long long* kmA = oz.kmax + 128 * step;  // zeroed with the factorization's state
-        panel_apply_kernel<double, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, kmA);
+        panel_apply_kernel<double, PT><<<dim3(2 * tiles, nz), 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, kmA, sM,
+                                                                           128 * steps);
         RMGE_LAUNCH_CHECK();
         const double* L21 = M + (k + b) * ldm + k;
         const double* U12 = M + k * ldm + k + b;
         double* E = M + (k + b) * ldm + (k + b);
         const OzFuse next{E, ldm, (int)(rest < NB ? rest : NB), k + b, &st->info, &st->halt};
+        OzBatch bt;
+        bt.count = count;
+        bt.sA = bt.sB = bt.sC = sM;
+        bt.sK = 128 * steps;
+        bt.sFlag = kStateInt;
         RMGE_TRY(oz_gemm(rest, rest, b, kOzSlices, -1.0, L21, ldm, U12, ldm, 1.0, E, ldm, oz.planesA, oz.planesB,
-                         oz.ea, oz.eb, kmA, kmA + 64, &st->error, &st->halt, s, &next));
+                         oz.ea, oz.eb, kmA, kmA + 64, &st->error, &st->halt, s, &next, bt));
     }
-    RMGE_TRY(maxabs<double>(n, n, M, ldm, true, &st->maxabs_u, s));
+    {
+        int64_t g = (n * n + 255) / 256;
+        if (g > 152 * 8) g = 152 * 8;
+        maxabs_kernel<double><<<dim3((unsigned)g, nz), 256, 0, s>>>(n, n, M, ldm, true, &st->maxabs_u, sM, kStateUll);
+        RMGE_LAUNCH_CHECK();
+    }
     return RMGE_OK;
 }
 
-rmge_status genp_finish(DevState* st, int32_t* info, double* growth, cudaStream_t s) {
-    finish_kernel<<<1, 1, 0, s>>>(st, info, growth);
+rmge_status genp_finish(DevState* st, int32_t* info, double* growth, cudaStream_t s, int count) {
+    finish_kernel<<<count, 1, 0, s>>>(st, info, growth);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }

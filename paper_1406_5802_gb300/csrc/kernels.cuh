@@ -5,6 +5,28 @@
 
 namespace rmge {
 
+// A uniform batch for the solve-path kernels: `count` systems, blockIdx.z picks one.  m0 .. m3 are the
+// element strides between the systems' copies of the launcher's first to fourth array argument (in the
+// order of its parameter list, control-block pointers not counted), ws the byte stride between their
+// workspace blocks, where every control-block pointer (DevState, skip and halt flags, solve flags,
+// reductions) lives.  The default is a single system.
+struct Zb {
+    int count = 1;
+    int64_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+    int64_t ws = 0;
+};
+
+template <typename T>
+__device__ __forceinline__ T* zmat(T* p, int64_t stride) {
+    return p == nullptr ? p : p + (int64_t)blockIdx.z * stride;
+}
+template <typename T>
+__device__ __forceinline__ T* zws(T* p, int64_t bytes) {
+    return p == nullptr ? p
+                        : reinterpret_cast<T*>(reinterpret_cast<char*>(const_cast<void*>(static_cast<const void*>(p))) +
+                                               (int64_t)blockIdx.z * bytes);
+}
+
 // gen.cu: the multiplier draws (Def. 4.1, Ex. 5.1) from Philox4x32-10.
 rmge_status launch_gaussian(int64_t count, uint64_t seed, uint64_t subseq, double* out, cudaStream_t s);
 rmge_status launch_gaussian(int64_t count, uint64_t seed, uint64_t subseq, float* out, cudaStream_t s);
@@ -16,7 +38,7 @@ rmge_status launch_unitary_spectrum(int64_t N, uint64_t seed, uint64_t subseq, d
 // reads C.  When halt is non-NULL and *halt != 0 at kernel start the kernel does nothing.
 template <typename T>
 rmge_status gemm(bool trans_a, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda, const T* B,
-                 int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s);
+                 int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s, const Zb& zb = Zb{});
 // E <- E - L21 U12 (M x N, K <= 64) for GENP, whose CTA on tile (0, 0) then factors the b x b pivot
 // block at E's top-left corner (pivot_block_genp); a breakdown at its step s records k + s in *info
 // (atomicMin) and raises *halt_w.  halt: as for gemm.
@@ -64,10 +86,21 @@ struct OzFuse {
     int* info;
     int* halt;
 };
+// A batch of `count` products of one shape (the systems of a uniform batched solve): the element strides
+// between the systems' A, B and C, the slots between their per-k maxima (kmaxA and kmaxB move together),
+// and the ints between their fused-pivot info / halt words; count = 1 is a single product.  planesA,
+// planesB, ea and eb then hold count consecutive per-system blocks of the single sizes (planes of
+// Mp x Kp and Np x Kp per digit, Mp and Np exponents).  With count > 1 a set halt word does not skip work.
+struct OzBatch {
+    int count = 1;
+    int64_t sA = 0, sB = 0, sC = 0;
+    int64_t sK = 0;
+    int64_t sFlag = 0;
+};
 rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* planesA, void* planesB,
                     int* ea, int* eb, const unsigned long long* kmaxA, const unsigned long long* kmaxB, int* err,
-                    const int* halt, cudaStream_t st, const OzFuse* fuse = nullptr);
+                    const int* halt, cudaStream_t st, const OzFuse* fuse = nullptr, const OzBatch& bt = OzBatch{});
 struct OzUpdate {
     void* planesA;
     void* planesB;
@@ -96,9 +129,14 @@ rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const
                            cudaStream_t s);
 // FP64 working matrix with the Schur-complement updates as balanced FP64 products emulated on the
 // tensor cores (oz_gemm); pivot blocks and panels on the FP64 pipe.
-rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s);
-// growth = max|U| / max|M| and info from the DevState (writes the caller's outputs).
-rmge_status genp_finish(DevState* st, int32_t* info, double* growth, cudaStream_t s);
+// count > 1: a batch of count equal-size systems, matrices sM elements apart, control blocks st[0..count),
+// per-system blocks of digit planes, exponents and per-k maxima in oz (OzBatch); one launch per kernel
+// and step covers every system.
+rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s,
+                           int count = 1, int64_t sM = 0);
+// growth = max|U| / max|M| and info from the DevState (writes the caller's outputs); count consecutive
+// control blocks to count outputs.
+rmge_status genp_finish(DevState* st, int32_t* info, double* growth, cudaStream_t s, int count = 1);
 template <typename T>
 rmge_status maxabs(int64_t rows, int64_t cols, const T* P, int64_t ldp, bool upper_only,
                    unsigned long long* out_bits, cudaStream_t s);
@@ -110,28 +148,34 @@ rmge_status maxabs(int64_t rows, int64_t cols, const T* P, int64_t ldp, bool upp
 // st must be zero at launch (state_init, and each solve re-arms them).  skip: as for gemm's halt.
 template <typename T>
 rmge_status trsv(int kind, int64_t n, int64_t nrhs, const T* LU, int64_t ldlu, T* B, int64_t ldb,
-                 DevState* st, int* flags, int epoch, const int* skip, cudaStream_t s);
+                 DevState* st, int* flags, int epoch, const int* skip, cudaStream_t s, const Zb& zb = Zb{});
 
 // refine.cu
 // Resets the control block (with the spin limit of the call's bounded waits), zeroes nflags solve flags and
 // ncolred reduction slots, sets berr_out[0..nberr) to -1 (berr_out may be NULL).
 rmge_status state_init(DevState* st, int* flags, int64_t nflags, double* colred, int ncolred, double* berr_out,
-                       int nberr, cudaStream_t s, long long spin_limit = kSpinLimit);
+                       int nberr, cudaStream_t s, long long spin_limit = kSpinLimit, const Zb& zb = Zb{});
+// count consecutive control blocks reset (as state_init does for one) and nzero 64-bit words cleared.
+rmge_status states_init(DevState* st, int count, unsigned long long* zero, int64_t nzero, cudaStream_t s,
+                        long long spin_limit = kSpinLimit);
 // st->norm_a = ||A||_inf (transposed: ||A^T||_inf)
-rmge_status abs_sums_max(int64_t n, const double* A, int64_t lda, bool transposed, DevState* st, cudaStream_t s);
+rmge_status abs_sums_max(int64_t n, const double* A, int64_t lda, bool transposed, DevState* st, cudaStream_t s,
+                         const Zb& zb = Zb{});
 // R = B (copy, n x k)
 template <typename Tin, typename Tout>
 rmge_status copy_matrix(int64_t rows, int64_t cols, const Tin* src, int64_t lds, Tout* dst, int64_t ldd,
-                        const int* skip, cudaStream_t s);
+                        const int* skip, cudaStream_t s, const Zb& zb = Zb{});
 // X += D (FP64 X, D of type T), skipped when *skip != 0
 template <typename T>
 rmge_status add_update(int64_t rows, int64_t cols, const T* D, int64_t ldd, double* X, int64_t ldx,
-                       const int* skip, cudaStream_t s);
+                       const int* skip, cudaStream_t s, const Zb& zb = Zb{});
 // backward error of (R, X, B) into berr_out[sweep] and the stop test; see rmge_refine.
 rmge_status backward_error(int64_t n, int64_t k, const double* R, int64_t ldr, const double* X, int64_t ldx,
                            const double* B, int64_t ldb, DevState* st, double* colred, int sweep,
-                           double be_tol, int max_iters, double* berr_out, cudaStream_t s, bool hybrid = false);
-rmge_status refine_finish(DevState* st, int max_iters, double* berr_out, int32_t* iters, cudaStream_t s);
+                           double be_tol, int max_iters, double* berr_out, cudaStream_t s, bool hybrid = false,
+                           const Zb& zb = Zb{});
+rmge_status refine_finish(DevState* st, int max_iters, double* berr_out, int32_t* iters, cudaStream_t s,
+                          const Zb& zb = Zb{});
 // st->nonfinite <- 1 if P (rows x cols) holds an Inf or NaN.
 template <typename T>
 rmge_status nonfinite_scan(int64_t rows, int64_t cols, const T* P, int64_t ldp, DevState* st, cudaStream_t s);
@@ -142,7 +186,7 @@ constexpr int kStatusFactor = 0, kStatusSolve = 1, kStatusRefine = 2;
 rmge_status write_status(DevState* st, int what, double growth_tol, double be_tol, int32_t* out, cudaStream_t s);
 // dA = -dB X^T
 rmge_status outer_neg(int64_t n, int64_t k, const double* dB, int64_t lddb, const double* X, int64_t ldx,
-                      double* dA, int64_t ldda, cudaStream_t s);
+                      double* dA, int64_t ldda, cudaStream_t s, const Zb& zb = Zb{});
 
 // gmres.cu: one FGMRES(m) cycle on op(A) d = R (op(A) = A^T when trans_a) for all k columns, right-preconditioned by P
 // (z = P v applied in the factor precision), X += d.  buf: gmres_bytes(n, k, m) bytes.  Uses epochs

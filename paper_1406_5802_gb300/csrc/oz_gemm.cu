@@ -61,6 +61,8 @@ struct OzParams {
     int M, N, K, s;
     int F;  // fractional bits of the fixed-point accumulator
     int Mp, Np;  // rows per digit plane of A, of B
+    int64_t sC;  // elements between the C of successive systems (blockIdx.y); their planes and exponents
+                 // follow one another in blocks of s Mp (s Np) plane rows and Mp (Np) exponents
     const int* ea;
     const int* eb;
     double alpha, beta;  // general combine (mode 2): C = beta C + alpha v
@@ -140,6 +142,11 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
     int tmb, tnb;
     tile_of((int)blockIdx.x, p.Mp / OBM, p.Np / OBN, tmb, tnb);
     const int m0 = tmb * OBM, n0 = tnb * OBN;
+    // the system of a batched product: its plane rows start at z s Mp (A) and z s Np (B)
+    const int z = (int)blockIdx.y, zra = z * p.s * p.Mp, zrb = z * p.s * p.Np;
+    double* const Cz = p.C + (int64_t)z * p.sC;
+    const int* const eaz = p.ea + (int64_t)z * p.Mp;
+    const int* const ebz = p.eb + (int64_t)z * p.Np;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OSTAGES; ++s) {
@@ -174,7 +181,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
                 for (int k0 = sc; k0 < se && !*(volatile int*)&aborted; k0 += kc) {
                     const int nkb = ((se - k0 < kc ? se - k0 : kc) + OKS - 1) / OKS;
                     for (int pa = 0; pa <= d; ++pa) {
-                        const int ya = pa * p.Mp + m0, yb = (d - pa) * p.Np + n0;
+                        const int ya = zra + pa * p.Mp + m0, yb = zrb + (d - pa) * p.Np + n0;
                         for (int kb = 0; kb < nkb; ++kb, ++it) {
                             const int st = it % OSTAGES;
                             if (!mbar_wait_idle(empty + st, (uint32_t)(((it / OSTAGES) & 1) ^ 1), deadline)) {
@@ -286,11 +293,11 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
         double* stg = reinterpret_cast<double*>(base);
         if (ok && !*(volatile int*)&aborted) {
             const int r = quad * 32 + lane;
-            const int er = (m0 + r < p.M) ? p.ea[m0 + r] : 0;
+            const int er = (m0 + r < p.M) ? eaz[m0 + r] : 0;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int c = cg * 32 + j;
-                const int ec = (n0 + c < p.N) ? p.eb[n0 + c] : 0;
+                const int ec = (n0 + c < p.N) ? ebz[n0 + c] : 0;
                 stg[r * OSTG + c] = fixed_to_double(p.alpha_sign * acc[j], er + ec - p.F);
             }
         }
@@ -299,7 +306,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
             for (int r = warp; r < OBM; r += OEPI) {
                 const int row = m0 + r;
                 if (row >= p.M) break;
-                double* crow = p.C + (int64_t)row * p.ldc;
+                double* crow = Cz + (int64_t)row * p.ldc;
 #pragma unroll
                 for (int q = 0; q < OBN / 32; ++q) {
                     const int c = q * 32 + lane, col = n0 + c;
@@ -348,6 +355,9 @@ constexpr int kUpdF = 56;
 
 struct UpdParams {
     int M, N;            // output rows, columns
+    int count;           // systems of a batched update: tile t belongs to system t / tiles
+    int64_t sC;          // elements between the systems' C (and pivot blocks D)
+    int64_t sFlag;       // ints between the systems' info / halt words
     int F;               // fractional bits of the fixed-point accumulator (kUpdF)
     int Mp, Np;          // rows per digit plane of A, of B
     int tiles_n, tiles;  // column tiles, all tiles
@@ -408,12 +418,16 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
     // With a fused pivot block, CTA 0 takes tile 0 (which holds the block) alone and the other CTAs
     // share the remaining tiles evenly.
     int t0, t1;
-    if (p.D != nullptr && gridDim.x > 1) {
+    // A batch of systems shares the tiles evenly; the CTA that writes a system's tile 0 then factors that
+    // system's pivot block (every pivot block must be done when the launch ends, which is all the next step
+    // waits for).
+    const int tiles_all = p.tiles * p.count;
+    if (p.D != nullptr && gridDim.x > 1 && p.count == 1) {
         t0 = (blockIdx.x == 0) ? 0 : 1 + (int)((long long)(blockIdx.x - 1) * (p.tiles - 1) / (gridDim.x - 1));
         t1 = 1 + (int)((long long)blockIdx.x * (p.tiles - 1) / (gridDim.x - 1));
     } else {
-        t0 = (int)((long long)blockIdx.x * p.tiles / gridDim.x);
-        t1 = (int)((long long)(blockIdx.x + 1) * p.tiles / gridDim.x);
+        t0 = (int)((long long)blockIdx.x * tiles_all / gridDim.x);
+        t1 = (int)((long long)(blockIdx.x + 1) * tiles_all / gridDim.x);
     }
 
     if (threadIdx.x == 0) {
@@ -448,7 +462,9 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
             int it = 0, na = 0, cur = -1;
             bool ok = true;
             for (int t = t0; t < t1 && ok; ++t) {
-                const int mb = t / p.tiles_n, nb = t % p.tiles_n;
+                // row blocks are numbered across the systems (t / tiles_n), so a new system reloads A too
+                const int z = t / p.tiles, tl = t - z * p.tiles;
+                const int mb = t / p.tiles_n, nb = tl % p.tiles_n, mbz = tl / p.tiles_n;
                 if (mb != cur) {
                     if (na > 0 && !mbar_wait_idle(doneA, (uint32_t)((na - 1) & 1), deadline)) {
                         ok = false;
@@ -456,7 +472,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
                     }
                     mbar_expect_tx(fullA, kOzSlices * UA_PLANE);
                     for (int pl = 0; pl < kOzSlices; ++pl)
-                        tma_load_2d(sA + pl * UA_PLANE, &tA, 0, pl * p.Mp + mb * UBM, fullA);
+                        tma_load_2d(sA + pl * UA_PLANE, &tA, 0, (z * kOzSlices + pl) * p.Mp + mbz * UBM, fullA);
                     ++na;
                     cur = mb;
                 }
@@ -468,7 +484,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
                             break;
                         }
                         mbar_expect_tx(fullB + st, UB_PLANE);
-                        tma_load_2d(sB + st * UB_PLANE, &tB, 0, q * p.Np + nb * UBN, fullB + st);
+                        tma_load_2d(sB + st * UB_PLANE, &tB, 0, (z * kOzSlices + q) * p.Np + nb * UBN, fullB + st);
                     }
             }
             if (!ok) atomicExch(&aborted, 1);
@@ -532,7 +548,11 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
         int u = 0;
         bool ok = true;
         for (int t = t0; t < t1; ++t) {
-            const int mb = t / p.tiles_n, nb = t % p.tiles_n;
+            const int z = t / p.tiles, tl = t - z * p.tiles;
+            const int mb = tl / p.tiles_n, nb = tl % p.tiles_n;
+            double* const C = p.C + (int64_t)z * p.sC;
+            const int* const ea = p.ea + (int64_t)z * p.Mp;
+            const int* const eb = p.eb + (int64_t)z * p.Np;
             long long acc[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) acc[j] = 0;
@@ -563,11 +583,11 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
             }
             if (ok) {
                 const int row = mb * UBM + r;
-                const int er = (row < p.M) ? p.ea[row] : 0;
+                const int er = (row < p.M) ? ea[row] : 0;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int c = cg * 16 + j, col = nb * UBN + c;
-                    const int ec = (col < p.N) ? p.eb[col] : 0;
+                    const int ec = (col < p.N) ? eb[col] : 0;
                     stg[r * UBN + (c ^ (r & 15))] = fixed_to_double(p.alpha_sign * acc[j], er + ec - kUpdF);
                 }
             }
@@ -585,7 +605,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
 #pragma unroll
                         for (int h = 0; h < NH; ++h) {
                             const int row = mb * UBM + warp + OEPI * (g0 + i), col = nb * UBN + h * 32 + lane;
-                            cv[i][h] = (need_c && row < p.M && col < p.N) ? p.C[(int64_t)row * p.ldc + col] : 0.0;
+                            cv[i][h] = (need_c && row < p.M && col < p.N) ? C[(int64_t)row * p.ldc + col] : 0.0;
                         }
 #pragma unroll
                     for (int i = 0; i < NG; ++i)
@@ -602,31 +622,32 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
                                     out = cv[i][h] + v;
                                 else
                                     out = (p.beta == 0.0) ? p.alpha * v : fma(p.beta, cv[i][h], p.alpha * v);
-                                p.C[(int64_t)row * p.ldc + col] = out;
+                                C[(int64_t)row * p.ldc + col] = out;
                             }
                         }
                 }
             }
             asm volatile("bar.sync 1, %0;" ::"r"(OEPI * 32) : "memory");  // the staging area is reused
-            if (p.D != nullptr && t == 0) {
+            if (p.D != nullptr && tl == 0) {
                 // tile 0, just written by these warps, holds the next pivot block: factor it in the staging
                 // area while the other CTAs finish the update.  The test is uniform over the 16 warps (the
                 // barriers inside must be met by all of them); after a timeout the factorization still
                 // runs, over whatever the tile holds, and the launch reports the timeout.
                 double* a = stg;
+                double* const D = p.D + (int64_t)z * p.sC;
                 const int tid = threadIdx.x;
                 for (int i = tid >> 6; i < p.bd; i += (OEPI * 32) / 64)
-                    if ((tid & 63) < p.bd) a[i * kPivotLds + (tid & 63)] = p.D[i * p.ldd + (tid & 63)];
+                    if ((tid & 63) < p.bd) a[i * kPivotLds + (tid & 63)] = D[i * p.ldd + (tid & 63)];
                 EpiSync{}();
                 const int broke = pivot_block_genp<double, OEPI * 32>(a, p.bd, &piv_rp, tid, EpiSync{});
                 if (broke != 0) {
                     if (tid == 0) {
-                        atomicMin(p.dinfo, (int)(p.dk + broke));
-                        atomicExch(p.dhalt, 1);
+                        atomicMin(p.dinfo + (int64_t)z * p.sFlag, (int)(p.dk + broke));
+                        atomicExch(p.dhalt + (int64_t)z * p.sFlag, 1);
                     }
                 } else {
                     for (int i = tid >> 6; i < p.bd; i += (OEPI * 32) / 64)
-                        if ((tid & 63) < p.bd) p.D[i * p.ldd + (tid & 63)] = a[i * kPivotLds + (tid & 63)];
+                        if ((tid & 63) < p.bd) D[i * p.ldd + (tid & 63)] = a[i * kPivotLds + (tid & 63)];
                 }
                 EpiSync{}();  // the staging area is reused by the next tile
             }
@@ -664,12 +685,26 @@ __device__ __forceinline__ int entry_exp(double x, int t) {
 }
 
 // e[r] = smallest integer with max_k |A_rk 2^t_k| < 2^e (0 for an all-zero row): one warp per row.
+// blockIdx.y: the system of a batch (BatchOff strides); the same below for every digit kernel.
+struct BatchOff {
+    int64_t src;   // elements between the systems' source matrices
+    int64_t kmax;  // slots between their per-k maxima
+    int64_t e;     // ints between their exponent vectors
+    int64_t pl;    // elements between their digit-plane blocks
+};
+
 __global__ void row_exponent_kernel(int64_t rows, int64_t cols, const double* __restrict__ src, int64_t lds,
                                     const unsigned long long* __restrict__ kmaxA,
-                                    const unsigned long long* __restrict__ kmaxB, int* __restrict__ e) {
+                                    const unsigned long long* __restrict__ kmaxB, int* __restrict__ e, BatchOff bo) {
     const int lane = threadIdx.x & 31;
     const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (r >= rows) return;
+    src += blockIdx.y * bo.src;
+    e += blockIdx.y * bo.e;
+    if (kmaxA != nullptr) {
+        kmaxA += blockIdx.y * bo.kmax;
+        kmaxB += blockIdx.y * bo.kmax;
+    }
     int m = INT_MIN;
     for (int64_t k = lane; k < cols; k += 32) m = max(m, entry_exp(src[r * lds + k], bal_shift(kmaxA, kmaxB, k)));
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -680,8 +715,14 @@ __global__ void row_exponent_kernel(int64_t rows, int64_t cols, const double* __
 // columns), rows split over 8 thread groups and reduced in shared memory.
 __global__ void col_exponent_kernel(int64_t rows, int64_t cols, const double* __restrict__ src, int64_t lds,
                                     const unsigned long long* __restrict__ kmaxA,
-                                    const unsigned long long* __restrict__ kmaxB, int* __restrict__ e) {
+                                    const unsigned long long* __restrict__ kmaxB, int* __restrict__ e, BatchOff bo) {
     __shared__ int part[8][32];
+    src += blockIdx.y * bo.src;
+    e += blockIdx.y * bo.e;
+    if (kmaxA != nullptr) {
+        kmaxA += blockIdx.y * bo.kmax;
+        kmaxB += blockIdx.y * bo.kmax;
+    }
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * 32 + tx;
     int m = INT_MIN;
@@ -740,8 +781,15 @@ __device__ __forceinline__ void store_digits(double v, int er, int s, __nv_bfloa
 __global__ void row_digits_kernel(int64_t rows, int64_t cols, const double* __restrict__ src, int64_t lds,
                                   const int* __restrict__ e, const unsigned long long* __restrict__ kmaxA,
                                   const unsigned long long* __restrict__ kmaxB, int s, int64_t rows_p, int64_t kp,
-                                  __nv_bfloat16* __restrict__ planes) {
+                                  __nv_bfloat16* __restrict__ planes, BatchOff bo) {
     const int64_t total = rows_p * kp;
+    src += blockIdx.y * bo.src;
+    e += blockIdx.y * bo.e;
+    planes += blockIdx.y * bo.pl;
+    if (kmaxA != nullptr) {
+        kmaxA += blockIdx.y * bo.kmax;
+        kmaxB += blockIdx.y * bo.kmax;
+    }
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = idx / kp, k = idx % kp;
@@ -754,9 +802,16 @@ __global__ void row_digits_kernel(int64_t rows, int64_t cols, const double* __re
 __global__ void col_digits_kernel(int64_t rows, int64_t cols, const double* __restrict__ src, int64_t lds,
                                   const int* __restrict__ e, const unsigned long long* __restrict__ kmaxA,
                                   const unsigned long long* __restrict__ kmaxB, int s, int64_t cols_p, int64_t kp,
-                                  __nv_bfloat16* __restrict__ planes) {
+                                  __nv_bfloat16* __restrict__ planes, BatchOff bo) {
     __shared__ double t[32][33];
     const int64_t k0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    src += blockIdx.z * bo.src;  // the system index is blockIdx.z here (y runs over k blocks)
+    e += blockIdx.z * bo.e;
+    planes += blockIdx.z * bo.pl;
+    if (kmaxA != nullptr) {
+        kmaxA += blockIdx.z * bo.kmax;
+        kmaxB += blockIdx.z * bo.kmax;
+    }
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
     for (int i = ty; i < 32; i += 8) {
         const int64_t k = k0 + i, c = c0 + tx;
@@ -835,7 +890,18 @@ __global__ void prep64_kernel(int64_t row_blocks, int64_t M, int64_t N, int K, c
                               const unsigned long long* __restrict__ kmaxA,
                               const unsigned long long* __restrict__ kmaxB, int s, int64_t Mp, int64_t Np,
                               int* __restrict__ ea, int* __restrict__ eb, __nv_bfloat16* __restrict__ pa,
-                              __nv_bfloat16* __restrict__ pb) {
+                              __nv_bfloat16* __restrict__ pb, BatchOff boA, BatchOff boB) {
+    const int64_t z = blockIdx.y;
+    A += z * boA.src;
+    B += z * boB.src;
+    ea += z * boA.e;
+    eb += z * boB.e;
+    pa += z * boA.pl;
+    pb += z * boB.pl;
+    if (kmaxA != nullptr) {
+        kmaxA += z * boA.kmax;
+        kmaxB += z * boA.kmax;
+    }
     if ((int64_t)blockIdx.x < row_blocks)
         row_prep64(blockIdx.x, M, K, A, lda, kmaxA, kmaxB, s, Mp, ea, pa);
     else
@@ -871,8 +937,9 @@ size_t oz_plane_bytes(int64_t rows, int64_t k, int s) {
 rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* planesA, void* planesB,
                     int* ea, int* eb, const unsigned long long* kmaxA, const unsigned long long* kmaxB, int* err,
-                    const int* halt, cudaStream_t st, const OzFuse* fuse) {
+                    const int* halt, cudaStream_t st, const OzFuse* fuse, const OzBatch& bt) {
     if ((kmaxA == nullptr) != (kmaxB == nullptr)) return RMGE_ERR_INVALID_ARG;
+    if (bt.count < 1 || bt.count > 65535) return RMGE_ERR_INVALID_ARG;
     if (M <= 0 || N <= 0) return RMGE_OK;
     if (K <= 0 || s < 1 || s > kOzSlices || M > INT32_MAX / 16 || N > INT32_MAX / 16 || K > INT32_MAX / 2)
         return RMGE_ERR_INVALID_ARG;
@@ -883,20 +950,25 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
         return RMGE_ERR_INVALID_ARG;
     __nv_bfloat16* pa = static_cast<__nv_bfloat16*>(planesA);
     __nv_bfloat16* pb = static_cast<__nv_bfloat16*>(planesB);
+    // per-system offsets of a batch: sources, per-k maxima, exponents, digit-plane blocks
+    const unsigned nz = (unsigned)bt.count;
+    const BatchOff boA{bt.sA, bt.sK, Mp, (int64_t)s * Mp * Kp}, boB{bt.sB, bt.sK, Np, (int64_t)s * Np * Kp};
     if (Kp == OBK) {
         const int64_t row_blocks = (Mp * 32 + 255) / 256, col_blocks = Np / 32;
-        prep64_kernel<<<(unsigned)(row_blocks + col_blocks), 256, 0, st>>>(row_blocks, M, N, (int)K, A, lda, B, ldb,
-                                                                           kmaxA, kmaxB, s, Mp, Np, ea, eb, pa, pb);
+        prep64_kernel<<<dim3((unsigned)(row_blocks + col_blocks), nz), 256, 0, st>>>(
+            row_blocks, M, N, (int)K, A, lda, B, ldb, kmaxA, kmaxB, s, Mp, Np, ea, eb, pa, pb, boA, boB);
         RMGE_LAUNCH_CHECK();
     } else {
-        row_exponent_kernel<<<(unsigned)((M * 32 + 255) / 256), 256, 0, st>>>(M, K, A, lda, kmaxA, kmaxB, ea);
+        row_exponent_kernel<<<dim3((unsigned)((M * 32 + 255) / 256), nz), 256, 0, st>>>(M, K, A, lda, kmaxA, kmaxB,
+                                                                                       ea, boA);
         RMGE_LAUNCH_CHECK();
-        col_exponent_kernel<<<(unsigned)((N + 31) / 32), 256, 0, st>>>(K, N, B, ldb, kmaxA, kmaxB, eb);
+        col_exponent_kernel<<<dim3((unsigned)((N + 31) / 32), nz), 256, 0, st>>>(K, N, B, ldb, kmaxA, kmaxB, eb, boB);
         RMGE_LAUNCH_CHECK();
-        row_digits_kernel<<<grid_for(Mp * Kp), 256, 0, st>>>(M, K, A, lda, ea, kmaxA, kmaxB, s, Mp, Kp, pa);
+        row_digits_kernel<<<dim3(grid_for(Mp * Kp), nz), 256, 0, st>>>(M, K, A, lda, ea, kmaxA, kmaxB, s, Mp, Kp, pa,
+                                                                       boA);
         RMGE_LAUNCH_CHECK();
-        col_digits_kernel<<<dim3((unsigned)(Np / 32), (unsigned)(Kp / 32)), 256, 0, st>>>(K, N, B, ldb, eb, kmaxA,
-                                                                                          kmaxB, s, Np, Kp, pb);
+        col_digits_kernel<<<dim3((unsigned)(Np / 32), (unsigned)(Kp / 32), nz), 256, 0, st>>>(
+            K, N, B, ldb, eb, kmaxA, kmaxB, s, Np, Kp, pb, boB);
         RMGE_LAUNCH_CHECK();
     }
 
@@ -907,12 +979,15 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
 
     if (Kp == OBK && s == kOzSlices) {  // one K block: the persistent update kernel
         CUtensorMap ta, tb;
-        if (!tc_make_map(&ta, pa, true, (int64_t)s * Mp, Kp, Kp, UBM) ||
-            !tc_make_map(&tb, pb, true, (int64_t)s * Np, Kp, Kp, UBN))
+        if (!tc_make_map(&ta, pa, true, (int64_t)bt.count * s * Mp, Kp, Kp, UBM) ||
+            !tc_make_map(&tb, pb, true, (int64_t)bt.count * s * Np, Kp, Kp, UBN))
             return RMGE_ERR_CUDA;
         UpdParams u{};
         u.M = (int)M;
         u.N = (int)N;
+        u.count = bt.count;
+        u.sC = bt.sC;
+        u.sFlag = bt.sFlag;
         u.F = kUpdF;
         u.Mp = (int)Mp;
         u.Np = (int)Np;
@@ -927,7 +1002,7 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
         u.C = C;
         u.ldc = ldc;
         u.err = err;
-        u.halt = halt;
+        u.halt = bt.count == 1 ? halt : nullptr;  // a batch keeps going past one system's breakdown
         if (fuse != nullptr) {
             u.D = fuse->D;
             u.ldd = fuse->ldd;
@@ -944,7 +1019,8 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
             (void)cudaGetLastError();
             return RMGE_ERR_CUDA;
         }
-        const int grid = u.tiles < sm_count() ? u.tiles : sm_count();
+        const int64_t all = (int64_t)u.tiles * bt.count;
+        const int grid = all < sm_count() ? (int)all : sm_count();
         oz_update_kernel<<<grid, OTHREADS, kUpdSmem, st>>>(ta, tb, u, idesc);
         RMGE_LAUNCH_CHECK();
         return RMGE_OK;
@@ -954,7 +1030,8 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
     int ch0 = (int)((Kp + 1023) / 1024), lg = 0;
     while ((1 << lg) < ch0 + 1) ++lg;
     CUtensorMap ta, tb;
-    if (!tc_make_map(&ta, pa, true, (int64_t)s * Mp, Kp, Kp, OBM) || !tc_make_map(&tb, pb, true, (int64_t)s * Np, Kp, Kp, OBN))
+    if (!tc_make_map(&ta, pa, true, (int64_t)bt.count * s * Mp, Kp, Kp, OBM) ||
+        !tc_make_map(&tb, pb, true, (int64_t)bt.count * s * Np, Kp, Kp, OBN))
         return RMGE_ERR_CUDA;
     OzParams prm{};
     prm.M = (int)M;
@@ -972,8 +1049,9 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
     prm.beta = beta;
     prm.C = C;
     prm.ldc = ldc;
+    prm.sC = bt.sC;
     prm.err = err;
-    prm.halt = halt;
+    prm.halt = bt.count == 1 ? halt : nullptr;
     // idesc: FP32 accumulate, BF16 A and B, both K-major, N = 128, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OBN >> 3) << 17) |
                            ((uint32_t)(OBM >> 4) << 24);
@@ -981,7 +1059,7 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
         (void)cudaGetLastError();
         return RMGE_ERR_CUDA;
     }
-    oz_gemm_kernel<<<(unsigned)((Np / OBN) * (Mp / OBM)), OTHREADS, kOzSmem, st>>>(ta, tb, prm, idesc);
+    oz_gemm_kernel<<<dim3((unsigned)((Np / OBN) * (Mp / OBM)), nz), OTHREADS, kOzSmem, st>>>(ta, tb, prm, idesc);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }

@@ -53,8 +53,14 @@ __device__ __forceinline__ void finish_ticket(DevState* st) {
 template <typename T>
 __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t nrhs, const T* __restrict__ LU,
                                                   int64_t ld, T* B, int64_t ldb, DevState* st, int* flags,
-                                                  int epoch, const int* skip) {
+                                                  int epoch, const int* skip, Zb zb) {
     extern __shared__ __align__(16) unsigned char trsv_smem[];
+    // a batch's systems (blockIdx.z) each have their own factors, right-hand sides, ticket counter and flags
+    skip = zws(skip, zb.ws);
+    st = zws(st, zb.ws);
+    flags = zws(flags, zb.ws);
+    LU = zmat(LU, zb.m0);
+    B = zmat(B, zb.m1);
     T (*cs)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(trsv_smem);  // off-diagonal coefficient tile
     T (*cd)[TB + 1] = cs + TB;                                     // diagonal block
     __shared__ T ys[TB][KC];
@@ -210,7 +216,7 @@ __global__ void __launch_bounds__(NT) trsv_kernel(int kind, int64_t n, int64_t n
 
 template <typename T>
 rmge_status trsv(int kind, int64_t n, int64_t nrhs, const T* LU, int64_t ldlu, T* B, int64_t ldb, DevState* st,
-                 int* flags, int epoch, const int* skip, cudaStream_t s) {
+                 int* flags, int epoch, const int* skip, cudaStream_t s, const Zb& zb) {
     const int64_t nblk = (n + TB - 1) / TB;
     const int64_t ncb = (nrhs + KC - 1) / KC;
     const int64_t grid = nblk * ncb;
@@ -219,14 +225,17 @@ rmge_status trsv(int kind, int64_t n, int64_t nrhs, const T* LU, int64_t ldlu, T
         (void)cudaGetLastError();
         return RMGE_ERR_CUDA;
     }
-    trsv_kernel<T><<<(unsigned)grid, NT, smem, s>>>(kind, n, nrhs, LU, ldlu, B, ldb, st, flags, epoch, skip);
+    // CTAs of a batch take tickets from their own system's counter and wait only for that system's earlier
+    // tickets, which are running already: systems do not wait for one another
+    trsv_kernel<T><<<dim3((unsigned)grid, 1, (unsigned)zb.count), NT, smem, s>>>(kind, n, nrhs, LU, ldlu, B, ldb, st,
+                                                                               flags, epoch, skip, zb);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }
 
 template rmge_status trsv<double>(int, int64_t, int64_t, const double*, int64_t, double*, int64_t, DevState*, int*,
-                                  int, const int*, cudaStream_t);
+                                  int, const int*, cudaStream_t, const Zb&);
 template rmge_status trsv<float>(int, int64_t, int64_t, const float*, int64_t, float*, int64_t, DevState*, int*, int,
-                                 const int*, cudaStream_t);
+                                 const int*, cudaStream_t, const Zb&);
 
 }  // namespace rmge

@@ -35,7 +35,9 @@ EXPORTED = ["rmge_multiplier_bytes", "rmge_workspace_size", "rmge_make_multiplie
             "rmge_workspace_size_two_sided", "rmge_apply_two_sided", "rmge_solve_two_sided", "rmge_refine_two_sided",
             "rmge_lowrank_workspace_size", "rmge_lowrank_multiplier", "rmge_lowrank_basis", "rmge_lowrank_project",
             "rmge_options_init", "rmge_workspace_size_ex", "rmge_factor_ex", "rmge_solve_ex", "rmge_refine_ex",
-            "rmge_apply_multiplier_ex",
+            "rmge_apply_multiplier_ex", "rmge_batched_uniform_workspace_size", "rmge_apply_multiplier_batched",
+            "rmge_factor_batched", "rmge_uniform_solve_workspace_size", "rmge_solve_uniform_batched",
+            "rmge_refine_uniform_batched", "rmge_solve_backward_uniform_batched",
             "rmge_solve_batched", "rmge_solve_batched_ex", "rmge_batched_workspace_size"]
 
 
@@ -102,6 +104,20 @@ def load_library(path: str = LIB_PATH):
         "rmge_refine_ex": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, C.c_int,
                                      C.c_int32, C.c_double, _vp, _vp, C.POINTER(Options), _vp, _sz, _vp]),
         "rmge_batched_workspace_size": (_sz, [_i64, C.c_int32]),
+        "rmge_batched_uniform_workspace_size": (_sz, [_i64, _i64, C.c_int]),
+        "rmge_apply_multiplier_batched": (C.c_int, [_i64, _i64, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _i64, C.c_int,
+                                                    C.POINTER(Options), _vp, _sz, _vp]),
+        "rmge_factor_batched": (C.c_int, [_i64, _i64, _vp, _i64, _i64, C.c_int, _vp, _vp, _vp, _sz, _vp]),
+        "rmge_uniform_solve_workspace_size": (_sz, [_i64, _i64, _i64, C.c_int]),
+        "rmge_solve_uniform_batched": (C.c_int, [_i64, _i64, _i64, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _i64, _vp,
+                                                 _i64, _i64, C.c_int, _vp, _sz, _vp]),
+        "rmge_refine_uniform_batched": (C.c_int, [_i64, _i64, _i64, _vp, _i64, _i64, _vp, _i64, _i64, _vp, _i64, _vp,
+                                                  _i64, _i64, _vp, _i64, _i64, C.c_int, C.c_int32, C.c_double, _vp,
+                                                  _vp, _vp, _sz, _vp]),
+        "rmge_solve_backward_uniform_batched": (C.c_int, [_i64, _i64, _i64, _vp, _i64, _i64, _vp, _i64, _i64, _vp,
+                                                          _i64, _vp, _i64, _i64, _vp, _i64, _i64, _vp, _i64, _i64,
+                                                          _vp, _i64, _i64, C.c_int, C.c_int32, C.c_double, _vp, _vp,
+                                                          _vp, _sz, _vp]),
         "rmge_solve_batched": (C.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u64, C.c_int32,
                                          C.c_double, _i64, C.c_int32, C.c_int32, _vp, _sz, _vp]),
         "rmge_solve_batched_ex": (C.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u64, C.c_int32,
@@ -291,6 +307,116 @@ def apply_multiplier_ex(kind, A, G, prec, opts, M=None, ws=None) -> torch.Tensor
                                                                   _prec(prec), C.byref(opts), _p(ws), ws.numel(),
                                                                   _stream()))
     return M
+
+
+def uniform_workspace(count, n, prec, device="cuda") -> torch.Tensor:
+    """Scratch for rmge_apply_multiplier_batched / rmge_factor_batched (count systems of order n)."""
+    nb = int(load_library().rmge_batched_uniform_workspace_size(int(count), int(n), _prec(prec)))
+    if nb == 0:
+        raise ValueError("invalid uniform-batch workspace request")
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def _need3(t, name):
+    if t.device.type != "cuda" or t.dtype != torch.float64 or t.dim() != 3 or t.stride(2) != 1:
+        raise ValueError(f"{name} must be a (count, n, n) row-major float64 CUDA tensor")
+
+
+def apply_multiplier_batched(A, G, prec="f64x", opts=None, M=None, ws=None) -> torch.Tensor:
+    """rmge_apply_multiplier_batched: M[i] = A[i] G[i] for (count, n, n) tensors, one launch per kernel."""
+    L = _cuda_lib()
+    _need3(A, "A")
+    _need3(G, "G")
+    count, n, _ = A.shape
+    if M is None:
+        M = torch.empty(count, n, n, dtype=torch.float64, device=A.device)
+    _need3(M, "M")
+    if ws is None:
+        ws = uniform_workspace(count, n, prec)
+    o = options() if opts is None else opts
+    _check("rmge_apply_multiplier_batched", L.rmge_apply_multiplier_batched(
+        count, n, _p(A), A.stride(1), A.stride(0), _p(G), G.stride(0), _p(M), M.stride(1), M.stride(0), _prec(prec),
+        C.byref(o), _p(ws), ws.numel(), _stream()))
+    return M
+
+
+def factor_batched(M, prec="f64x", ws=None):
+    """rmge_factor_batched: in-place GENP of every M[i]; returns (info, growth) device tensors of count entries."""
+    L = _cuda_lib()
+    _need3(M, "M")
+    count, n, _ = M.shape
+    info = torch.empty(count, dtype=torch.int32, device=M.device)
+    growth = torch.empty(count, dtype=torch.float64, device=M.device)
+    if ws is None:
+        ws = uniform_workspace(count, n, prec)
+    _check("rmge_factor_batched", L.rmge_factor_batched(count, n, _p(M), M.stride(1), M.stride(0), _prec(prec),
+                                                        _p(info), _p(growth), _p(ws), ws.numel(), _stream()))
+    return info, growth
+
+
+def uniform_solve_workspace(count, n, nrhs, prec, device="cuda") -> torch.Tensor:
+    nb = int(load_library().rmge_uniform_solve_workspace_size(int(count), int(n), int(nrhs), _prec(prec)))
+    if nb == 0:
+        raise ValueError("invalid uniform-batch solve workspace request")
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def _b3(t, name):
+    if t.device.type != "cuda" or t.dtype != torch.float64 or t.dim() != 3 or t.stride(2) != 1:
+        raise ValueError(f"{name} must be a (count, rows, cols) row-major float64 CUDA tensor")
+    return t.stride(1), t.stride(0)
+
+
+def solve_uniform_batched(LU, G, B, prec="f64x", X=None, ws=None) -> torch.Tensor:
+    """rmge_solve_uniform_batched: X[i] = G[i] U_i^{-1} L_i^{-1} B[i] for (count, n, .) tensors."""
+    L = _cuda_lib()
+    count, n, k = B.shape
+    if X is None:
+        X = torch.empty(count, n, k, dtype=torch.float64, device=B.device)
+    (ldlu, slu), (_, sg), (ldb, sb), (ldx, sx) = _b3(LU, "LU"), _b3(G, "G"), _b3(B, "B"), _b3(X, "X")
+    if ws is None:
+        ws = uniform_solve_workspace(count, n, k, prec)
+    _check("rmge_solve_uniform_batched", L.rmge_solve_uniform_batched(
+        count, n, k, _p(LU), ldlu, slu, _p(G), sg, _p(B), ldb, sb, _p(X), ldx, sx, _prec(prec), _p(ws), ws.numel(),
+        _stream()))
+    return X
+
+
+def refine_uniform_batched(A, LU, G, B, X, prec="f64x", max_iters=10, be_tol=1e-13, ws=None):
+    """rmge_refine_uniform_batched: in-place refinement of every X[i]; returns (berr (count, max_iters + 1),
+    iters (count,))."""
+    L = _cuda_lib()
+    count, n, k = B.shape
+    (lda, sa), (ldlu, slu), (_, sg), (ldb, sb), (ldx, sx) = (_b3(A, "A"), _b3(LU, "LU"), _b3(G, "G"), _b3(B, "B"),
+                                                            _b3(X, "X"))
+    berr = torch.empty(count, max_iters + 1, dtype=torch.float64, device=B.device)
+    iters = torch.empty(count, dtype=torch.int32, device=B.device)
+    if ws is None:
+        ws = uniform_solve_workspace(count, n, k, prec)
+    _check("rmge_refine_uniform_batched", L.rmge_refine_uniform_batched(
+        count, n, k, _p(A), lda, sa, _p(LU), ldlu, slu, _p(G), sg, _p(B), ldb, sb, _p(X), ldx, sx, _prec(prec),
+        int(max_iters), float(be_tol), _p(berr), _p(iters), _p(ws), ws.numel(), _stream()))
+    return berr, iters
+
+
+def solve_backward_uniform_batched(A, LU, G, X, dX, prec="f64x", want_dA=True, max_iters=0, be_tol=1e-13, ws=None):
+    """rmge_solve_backward_uniform_batched: (dB, dA, berr, iters) for every system (dA None without want_dA)."""
+    L = _cuda_lib()
+    count, n, k = dX.shape
+    dB = torch.empty(count, n, k, dtype=torch.float64, device=dX.device)
+    dA = torch.empty(count, n, n, dtype=torch.float64, device=dX.device) if want_dA else None
+    (lda, sa), (ldlu, slu), (_, sg), (ldx, sx), (lddx, sdx), (lddb, sdb) = (
+        _b3(A, "A"), _b3(LU, "LU"), _b3(G, "G"), _b3(X, "X"), _b3(dX, "dX"), _b3(dB, "dB"))
+    ldda, sda = _b3(dA, "dA") if dA is not None else (n, n * n)
+    berr = torch.empty(count, max_iters + 1, dtype=torch.float64, device=dX.device)
+    iters = torch.zeros(count, dtype=torch.int32, device=dX.device)
+    if ws is None:
+        ws = uniform_solve_workspace(count, n, k, prec)
+    _check("rmge_solve_backward_uniform_batched", L.rmge_solve_backward_uniform_batched(
+        count, n, k, _p(A), lda, sa, _p(LU), ldlu, slu, _p(G), sg, _p(X), ldx, sx, _p(dX), lddx, sdx, _p(dB), lddb,
+        sdb, _p(dA), ldda, sda, _prec(prec), int(max_iters), float(be_tol), _p(berr) if max_iters > 0 else None,
+        _p(iters) if max_iters > 0 else None, _p(ws), ws.numel(), _stream()))
+    return dB, dA, berr, iters
 
 
 def factor_ex(M, prec, opts, ws=None):

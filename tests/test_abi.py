@@ -113,3 +113,17 @@ def test_options_defaults_and_validation(lib):
                                      1 << 20, None) == INVALID
     assert lib.rmge_status_string(9) == b"non-finite values in the result"
     assert lib.rmge_status_string(3) == b"growth above threshold"
+
+
+def test_uniform_batch_sizes_and_argument_checks(lib):
+    INVALID, WORKSPACE, UNSUPPORTED = 1, 7, 8
+    assert lib.rmge_batched_uniform_workspace_size(64, 2048, 6) > 2 * 64 * 7 * 2048 * 2048 * 2
+    assert lib.rmge_batched_uniform_workspace_size(64, 2048, 0) == 0  # emulated FP64 only
+    assert lib.rmge_batched_uniform_workspace_size(0, 2048, 6) == 0
+    assert lib.rmge_batched_uniform_workspace_size(70000, 64, 6) == 0
+    p = C.c_void_p(256)
+    # overlapping systems (stride below (n - 1) ld + n) are refused before any GPU work
+    assert lib.rmge_factor_batched(2, 8, p, 8, 10, 6, p, None, p, 1 << 20, None) == INVALID
+    assert lib.rmge_factor_batched(2, 8, p, 8, 64, 0, p, None, p, 1 << 20, None) == UNSUPPORTED
+    assert lib.rmge_factor_batched(2, 8, p, 8, 64, 6, p, None, p, 16, None) == WORKSPACE
+    assert lib.rmge_apply_multiplier_batched(2, 8, p, 8, 64, p, 64, p, 8, 63, 6, None, p, 1 << 20, None) == INVALID
