@@ -111,6 +111,10 @@ typedef enum {
  *   and column maxima per term.  Refinement with FP64 residuals wins that back while kappa(A G) times
  *   that error stays well below 1 (a sweep more for each factor of about 1e4 lost); the factorization
  *   itself is unchanged.
+ * - factor_digits (default 7, from 4 to 7): the same for GENP's Schur updates in rmge_factor_ex with
+ *   RMGE_F64X_TC (d (d + 1) / 2 digit-pair products per update).  Fewer digits give factors of about
+ *   8 d - 1 bits: the growth g of GENP multiplies their error, so refinement to FP64 accuracy needs
+ *   kappa(A G) g 2^(-8 d) well below 1, and then takes a sweep for each factor of that product lost.
  * - status (device int32, may be NULL): receives the call's outcome, RMGE_OK or the first of
  *   RMGE_ERR_TIMEOUT, RMGE_ERR_BREAKDOWN, RMGE_ERR_NONFINITE, then RMGE_ERR_GROWTH (factor) or
  *   RMGE_ERR_NOT_CONVERGED (refine) that applies; valid once the stream is synchronised.
@@ -124,6 +128,7 @@ typedef struct rmge_options {
     int32_t gmres_m;
     int32_t apply_digits;
     int32_t sync;
+    int32_t factor_digits;
 } rmge_options;
 
 void rmge_options_init(rmge_options* opts);

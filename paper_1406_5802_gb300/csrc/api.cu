@@ -58,7 +58,8 @@ struct Opts {
     int gm_m = kGmresM;
     bool sync = false;
     int32_t* status = nullptr;
-    int digits = kOzSlices;  // balanced base-256 digits of the emulated A G
+    int digits = kOzSlices;   // balanced base-256 digits of the emulated A G
+    int fdigits = kOzSlices;  // ... of the emulated Schur updates
     bool report() const { return sync || status != nullptr; }
 };
 
@@ -66,9 +67,10 @@ bool opts_of(const rmge_options* o, Opts* out) {
     *out = Opts{};
     if (o == nullptr) return true;
     if (!(o->growth_tol >= 0.0) || o->spin_limit < 0 || o->gmres_m < 1 || o->gmres_m > kMaxGmresM ||
-        o->apply_digits < 1 || o->apply_digits > kOzSlices)
+        o->apply_digits < 1 || o->apply_digits > kOzSlices || o->factor_digits < 4 || o->factor_digits > kOzSlices)
         return false;
     out->digits = o->apply_digits;
+    out->fdigits = o->factor_digits;
     out->growth_tol = o->growth_tol;
     out->spin = o->spin_limit;
     out->gm_m = o->gmres_m;
@@ -500,6 +502,7 @@ void rmge_options_init(rmge_options* opts) {
     opts->spin_limit = d.spin;
     opts->gmres_m = d.gm_m;
     opts->apply_digits = d.digits;
+    opts->factor_digits = d.fdigits;
     opts->sync = 0;
     opts->status = nullptr;
 }
@@ -609,7 +612,7 @@ rmge_status rmge_factor_ex(int64_t n, void* M, int64_t ldm, rmge_prec prec, int3
         const OzUpdate oz = oz_buffers(w, n);
         RMGE_TRY(state_init(w.st, w.flags, 0, reinterpret_cast<double*>(oz.kmax), (int)oz_kmax_slots(n), nullptr, 0, s,
                             w.spin));
-        RMGE_TRY(genp_factor_oz(n, static_cast<double*>(M), ldm, w.st, oz, s));
+        RMGE_TRY(genp_factor_oz(n, static_cast<double*>(M), ldm, w.st, oz, s, 1, 0, o.fdigits));
     }
     else if (prec == RMGE_F32)
         RMGE_TRY(genp_factor<float>(n, static_cast<float*>(M), ldm, w.st, s));

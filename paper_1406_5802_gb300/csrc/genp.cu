@@ -273,7 +273,7 @@ rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const
 // The update launch of step k also factors the pivot block of step k + 1 (CTA 0 takes the tile holding it
 // alone), so only the first pivot block has a launch of its own.
 rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s,
-                           int count, int64_t sM) {
+                           int count, int64_t sM, int digits) {
     constexpr int PT = 16;
     const unsigned nz = (unsigned)count;
     const int64_t steps = (n + NB - 1) / NB;
@@ -309,7 +309,7 @@ rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, cons
         bt.sA = bt.sB = bt.sC = sM;
         bt.sK = 128 * steps;
         bt.sFlag = kStateInt;
-        RMGE_TRY(oz_gemm(rest, rest, b, kOzSlices, -1.0, L21, ldm, U12, ldm, 1.0, E, ldm, oz.planesA, oz.planesB,
+        RMGE_TRY(oz_gemm(rest, rest, b, digits, -1.0, L21, ldm, U12, ldm, 1.0, E, ldm, oz.planesA, oz.planesB,
                          oz.ea, oz.eb, kmA, kmA + 64, &st->error, &st->halt, s, &next, bt));
     }
     {

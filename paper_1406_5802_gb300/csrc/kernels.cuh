@@ -131,9 +131,10 @@ rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const
 // tensor cores (oz_gemm); pivot blocks and panels on the FP64 pipe.
 // count > 1: a batch of count equal-size systems, matrices sM elements apart, control blocks st[0..count),
 // per-system blocks of digit planes, exponents and per-k maxima in oz (OzBatch); one launch per kernel
-// and step covers every system.
+// and step covers every system.  digits (4 .. kOzSlices): balanced base-256 digits per operand of the
+// emulated updates (digits (digits + 1) / 2 digit-pair products; kOzSlices reproduces FP64 rounding).
 rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s,
-                           int count = 1, int64_t sM = 0);
+                           int count = 1, int64_t sM = 0, int digits = kOzSlices);
 // growth = max|U| / max|M| and info from the DevState (writes the caller's outputs); count consecutive
 // control blocks to count outputs.
 rmge_status genp_finish(DevState* st, int32_t* info, double* growth, cudaStream_t s, int count = 1);

@@ -101,26 +101,18 @@ __device__ __forceinline__ void tile_of(int t, int tm, int tn, int& m, int& n) {
 // -> FP64 conversion and the scaling are kept off it.  Results that would be subnormal or overflow
 // take the FP64 route.
 __device__ __forceinline__ double fixed_to_double(long long a, int E) {
-    if (a == 0) return 0.0;
-    const unsigned long long sgn = a < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long sgn = (unsigned long long)a & 0x8000000000000000ull;
     const unsigned long long m = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
-    int p = 63 - __clzll((long long)m);  // position of the leading bit
-    unsigned long long q;
-    if (p > 52) {
-        const int r = p - 52;
-        q = m >> r;
-        const unsigned long long rem = m & ((1ull << r) - 1ull), half = 1ull << (r - 1);
-        if (rem > half || (rem == half && (q & 1ull))) ++q;
-        if (q >> 53) {  // the rounding carried into a new leading bit
-            q >>= 1;
-            ++p;
-        }
-    } else {
-        q = m << (52 - p);
-    }
-    const int ex = p + E + 1023;
-    if (ex <= 0 || ex >= 2047) return ldexp((double)a, E);
-    return __longlong_as_double((long long)(sgn | ((unsigned long long)ex << 52) | (q & ((1ull << 52) - 1ull))));
+    if (m == 0) return 0.0;
+    // normalise the leading bit to bit 63, keep 53 bits and round the 11 below them to nearest even
+    const int lz = __clzll((long long)m);
+    const unsigned long long mn = m << lz;
+    const unsigned long long keep = mn >> 11, rest = mn & 0x7FFull;
+    const unsigned long long q = keep + (unsigned long long)((rest > 0x400ull) | ((rest == 0x400ull) & (keep & 1ull)));
+    const int ex = 63 - lz + E + 1023;  // biased exponent before a rounding carry
+    if (ex <= 0 || ex >= 2046) return ldexp((double)a, E);
+    // q in [2^52, 2^53]: its leading bit adds one to (ex - 1), and a carry to 2^53 one more
+    return __longlong_as_double((long long)(sgn | (((unsigned long long)(ex - 1) << 52) + q)));
 }
 
 __global__ void __launch_bounds__(OTHREADS, 1)
@@ -332,12 +324,13 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
 
 // ---------------------------------------------------------------------------------------------
 // Products with K <= 64 (GENP's Schur updates: one 64-deep K block).  A persistent CTA walks its
-// share of 128 x 64 output tiles in row-major order, so the 7 A digit planes of a row block (112 KB)
-// are loaded once and stay in shared memory; the B digit planes of each tile stream through a 4-stage
-// ring.  The 28 digit pairs run in two passes, diagonals d = 0-3 then 4-6, each diagonal in
-// its own 64-column TMEM accumulator; the two passes use the two halves of TMEM, so one pass's MMAs
-// overlap the drain of the other and the tile's final store.  Per tile the TMA moves 11 B planes (88 KB)
-// instead of 28 A and 28 B tiles.  (d + 1) 2^14 64 < 2^24 keeps every accumulator exact.
+// share of 128 x 64 output tiles in row-major order, so the ND A digit planes of a row block (7 planes:
+// 112 KB) are loaded once and stay in shared memory; the B digit planes of each tile stream through a
+// 4-stage ring.  With the full ND = 7 digits the 28 digit pairs run in two passes, diagonals d = 0-3 then
+// 4-6, each diagonal in its own 64-column TMEM accumulator; the two passes use the two halves of TMEM, so
+// one pass's MMAs overlap the drain of the other and the tile's final store.  Per tile the TMA moves 11 B
+// planes (88 KB) instead of 28 A and 28 B tiles.  Fewer digits (ND = 4 .. 6) drop the low diagonals:
+// ND (ND + 1) / 2 pairs, operands of 8 ND - 1 bits.  (d + 1) 2^14 64 < 2^24 keeps every accumulator exact.
 // ---------------------------------------------------------------------------------------------
 constexpr int UBM = 128, UBN = 64;
 constexpr int UA_PLANE = UBM * OBK * 2;  // 16 KB
@@ -352,6 +345,14 @@ static_assert(kUpdSmem <= 232448, "update kernel shared memory");
 // a compile-time constant here: the epilogue's shifts and scalings are then immediates (the epilogue is
 // ALU-bound).
 constexpr int kUpdF = 56;
+
+// A drained diagonal d (K <= 64): an integer-valued float with |v| <= (d + 1) 2^20.  For d <= 3 that is at
+// most 2^22: adding 1.5 2^23 lands in the binade whose unit is 1 (up to 2^24 inclusive), where the bit
+// pattern grows by exactly one per unit, so the pattern minus that of 1.5 2^23 is v.  One FADD and one
+// integer subtraction replace the conversion; larger diagonals keep the conversion.
+__device__ __forceinline__ int diag_to_int(float v, int d) {
+    return d <= 3 ? __float_as_int(v + 12582912.0f) - 0x4B400000 : __float2int_rn(v);
+}
 
 struct UpdParams {
     int M, N;            // output rows, columns
@@ -385,23 +386,29 @@ struct EpiSync {
     __device__ void operator()() const { asm volatile("bar.sync 1, %0;" ::"r"(OEPI * 32) : "memory"); }
 };
 
-// Pass P streams B planes q = 0 .. upd_nq(P)-1 and pairs each with the A planes p in [upd_p0, upd_p1],
-// so that p + q covers the diagonals 4P .. 4P + upd_nd(P) - 1 (0-3, then 4-6); q = 0 opens every diagonal
-// of the pass.
-constexpr int kDiagLast = kOzSlices - 1;  // the last kept diagonal, 6
-__device__ __forceinline__ constexpr int upd_nd(int P) { return P == 0 ? 4 : kOzSlices - 4; }
-__device__ __forceinline__ int upd_nq(int P) { return P == 0 ? 4 : kOzSlices; }
-__device__ __forceinline__ int upd_p0(int P, int q) { return P == 0 ? 0 : (q < 4 ? 4 - q : 0); }
-__device__ __forceinline__ int upd_p1(int P, int q) { return P == 0 ? 3 - q : kDiagLast - q; }
+// Pass P streams B planes q = 0 .. nq(P)-1 and pairs each with the A planes p in [p0, p1], so that p + q
+// covers the diagonals 4P .. 4P + nd(P) - 1 (0-3, then 4 .. ND-1); q = 0 opens every diagonal of the pass.
+// ND digits per operand keep the diagonals 0 .. ND-1 (ND (ND + 1) / 2 pairs); ND = 4 runs one pass.
+template <int ND>
+struct UpdDiag {
+    static_assert(ND >= 4 && ND <= kOzSlices, "update digits");
+    static constexpr int kPasses = ND > 4 ? 2 : 1;
+    static __device__ __forceinline__ constexpr int nd(int P) { return P == 0 ? 4 : ND - 4; }
+    static __device__ __forceinline__ constexpr int nq(int P) { return P == 0 ? 4 : ND; }
+    static __device__ __forceinline__ constexpr int p0(int P, int q) { return P == 0 ? 0 : (q < 4 ? 4 - q : 0); }
+    static __device__ __forceinline__ constexpr int p1(int P, int q) { return P == 0 ? 3 - q : ND - 1 - q; }
+};
 
+template <int ND>
 __global__ void __launch_bounds__(OTHREADS, 1)
 oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, UpdParams p,
                  uint32_t idesc) {
+    using Dg = UpdDiag<ND>;
     if (p.halt != nullptr && *(volatile const int*)p.halt != 0) return;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = base;
-    uint8_t* sB = sA + kOzSlices * UA_PLANE;
+    uint8_t* sB = sA + ND * UA_PLANE;
     double* stg = reinterpret_cast<double*>(sB + URING * UB_PLANE);  // 128 x 64, columns XOR-swizzled by row
     uint64_t* fullA = reinterpret_cast<uint64_t*>(stg + UBM * UBN);
     uint64_t* doneA = fullA + 1;   // the MMAs reading the resident A planes have completed
@@ -470,21 +477,21 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(fullA, kOzSlices * UA_PLANE);
-                    for (int pl = 0; pl < kOzSlices; ++pl)
-                        tma_load_2d(sA + pl * UA_PLANE, &tA, 0, (z * kOzSlices + pl) * p.Mp + mbz * UBM, fullA);
+                    mbar_expect_tx(fullA, ND * UA_PLANE);
+                    for (int pl = 0; pl < ND; ++pl)
+                        tma_load_2d(sA + pl * UA_PLANE, &tA, 0, (z * ND + pl) * p.Mp + mbz * UBM, fullA);
                     ++na;
                     cur = mb;
                 }
-                for (int P = 0; P < 2 && ok; ++P)
-                    for (int q = 0; q < upd_nq(P); ++q, ++it) {
+                for (int P = 0; P < Dg::kPasses && ok; ++P)
+                    for (int q = 0; q < Dg::nq(P); ++q, ++it) {
                         const int st = it % URING;
                         if (!mbar_wait_idle(emptyB + st, (uint32_t)(((it / URING) & 1) ^ 1), deadline)) {
                             ok = false;
                             break;
                         }
                         mbar_expect_tx(fullB + st, UB_PLANE);
-                        tma_load_2d(sB + st * UB_PLANE, &tB, 0, (z * kOzSlices + q) * p.Np + nb * UBN, fullB + st);
+                        tma_load_2d(sB + st * UB_PLANE, &tB, 0, (z * ND + q) * p.Np + nb * UBN, fullB + st);
                     }
             }
             if (!ok) atomicExch(&aborted, 1);
@@ -508,14 +515,14 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
                     ++na;
                     cur = mb;
                 }
-                for (int P = 0; P < 2 && ok; ++P, ++u) {
+                for (int P = 0; P < Dg::kPasses && ok; ++P, ++u) {
                     const int bank = u & 1;
                     if (!mbar_wait(tempty + bank, (uint32_t)(((u >> 1) & 1) ^ 1), deadline)) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    for (int q = 0; q < upd_nq(P); ++q, ++it) {
+                    for (int q = 0; q < Dg::nq(P); ++q, ++it) {
                         const int st = it % URING;
                         if (!mbar_wait(fullB + st, (uint32_t)((it / URING) & 1), deadline)) {
                             ok = false;
@@ -523,7 +530,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint64_t bd = smem_desc(smem_u32(sB + st * UB_PLANE));
-                        for (int pa = upd_p0(P, q); pa <= upd_p1(P, q); ++pa) {
+                        for (int pa = Dg::p0(P, q); pa <= Dg::p1(P, q); ++pa) {
                             const uint64_t ad = smem_desc(smem_u32(sA + pa * UA_PLANE));
                             const uint32_t dcol = tmem + (uint32_t)(bank * 256 + (pa + q - 4 * P) * UBN);
 #pragma unroll
@@ -553,11 +560,18 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
             double* const C = p.C + (int64_t)z * p.sC;
             const int* const ea = p.ea + (int64_t)z * p.Mp;
             const int* const eb = p.eb + (int64_t)z * p.Np;
+            if (p.mode != 0 && p.beta != 0.0) {
+                // the tile's rows of C into L2 while its MMAs run (one 128-byte line per thread), so that the
+                // read-modify-write after the drains waits on L2 rather than on HBM
+                const int row = mb * UBM + (threadIdx.x >> 2), col = nb * UBN + (threadIdx.x & 3) * 16;
+                if (row < p.M && col < p.N)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(C + (int64_t)row * p.ldc + col));
+            }
             long long acc[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) acc[j] = 0;
 #pragma unroll  // P compile-time: the epilogue shifts become immediates
-            for (int P = 0; P < 2; ++P, ++u) {
+            for (int P = 0; P < Dg::kPasses; ++P, ++u) {
                 const int bank = u & 1;
                 if (!mbar_wait_idle(tfull + bank, (uint32_t)((u >> 1) & 1), deadline)) {
                     atomicExch(&aborted, 1);
@@ -566,15 +580,34 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (ok) {
+                    const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(bank * 256 + cg * 16);
+                    // Diagonals two at a time: v_a 2^8 + v_b is an exact int32 (|v_a| <= 5 2^20 for the first
+                    // diagonal of a pair, |v_b| <= 7 2^20), so one 64-bit shift-add serves both.  A diagonal
+                    // whose weight is below the fixed point's last bit (sh < 0: diagonal 6) goes alone, rounded.
 #pragma unroll
-                    for (int sl = 0; sl < upd_nd(P); ++sl) {
-                        const int sh = kUpdF - 8 * (4 * P + sl) - 14;  // compile-time: constant shifts
-                        const float rscale = __int_as_float((127 + (sh < 0 ? sh : 0)) << 23);
-                        const int lsh = sh > 0 ? sh : 0;
-                        float v[16];
-                        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(bank * 256 + sl * UBN + cg * 16), v);
+                    for (int sl = 0; sl < Dg::nd(P); sl += 2) {
+                        const int d = 4 * P + sl;  // compile-time after unrolling: constant shifts
+                        const int sha = kUpdF - 8 * d - 14, shb = sha - 8;
+                        if (sl + 1 < Dg::nd(P) && shb >= 0) {
+                            float va[16], vb[16];
+                            tmem_ld16x2(tq + sl * UBN, tq + (sl + 1) * UBN, va, vb);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) acc[j] += (long long)__float2int_rn(v[j] * rscale) << lsh;
+                            for (int j = 0; j < 16; ++j)
+                                acc[j] += (long long)(diag_to_int(va[j], d) * 256 + diag_to_int(vb[j], d + 1)) << shb;
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                if (sl + e >= Dg::nd(P)) break;
+                                const int sh = sha - 8 * e;
+                                const float rscale = __int_as_float((127 + (sh < 0 ? sh : 0)) << 23);
+                                const int lsh = sh > 0 ? sh : 0;
+                                float v[16];
+                                tmem_ld16(tq + (sl + e) * UBN, v);
+#pragma unroll
+                                for (int j = 0; j < 16; ++j)
+                                    acc[j] += (long long)__float2int_rn(v[j] * rscale) << lsh;
+                            }
+                        }
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -934,6 +967,19 @@ size_t oz_plane_bytes(int64_t rows, int64_t k, int s) {
     return (size_t)s * (size_t)rp * (size_t)kp * 2;
 }
 
+template <int ND>
+rmge_status launch_update(const CUtensorMap& ta, const CUtensorMap& tb, const UpdParams& u, uint32_t idesc, int grid,
+                          cudaStream_t st) {
+    if (cudaFuncSetAttribute(oz_update_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpdSmem) !=
+        cudaSuccess) {
+        (void)cudaGetLastError();
+        return RMGE_ERR_CUDA;
+    }
+    oz_update_kernel<ND><<<grid, OTHREADS, kUpdSmem, st>>>(ta, tb, u, idesc);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
 rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* planesA, void* planesB,
                     int* ea, int* eb, const unsigned long long* kmaxA, const unsigned long long* kmaxB, int* err,
@@ -945,7 +991,7 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
         return RMGE_ERR_INVALID_ARG;
     const int64_t Mp = (M + 127) / 128 * 128, Np = (N + 127) / 128 * 128, Kp = (K + 63) / 64 * 64;
     // the fused pivot block needs the persistent update kernel and must lie in its first tile
-    if (fuse != nullptr && (Kp != OBK || s != kOzSlices || fuse->D == nullptr || fuse->b < 1 || fuse->b > UBN ||
+    if (fuse != nullptr && (Kp != OBK || s < 4 || fuse->D == nullptr || fuse->b < 1 || fuse->b > UBN ||
                             fuse->b > M || fuse->b > N || fuse->info == nullptr || fuse->halt == nullptr))
         return RMGE_ERR_INVALID_ARG;
     __nv_bfloat16* pa = static_cast<__nv_bfloat16*>(planesA);
@@ -977,7 +1023,7 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
     const long long alpha_sign = (mode < 2 && alpha < 0.0) ? -1 : 1;
     const double alpha_g = (mode < 2) ? 1.0 : alpha;
 
-    if (Kp == OBK && s == kOzSlices) {  // one K block: the persistent update kernel
+    if (Kp == OBK && s >= 4) {  // one K block: the persistent update kernel
         CUtensorMap ta, tb;
         if (!tc_make_map(&ta, pa, true, (int64_t)bt.count * s * Mp, Kp, Kp, UBM) ||
             !tc_make_map(&tb, pb, true, (int64_t)bt.count * s * Np, Kp, Kp, UBN))
@@ -1014,16 +1060,14 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
         // idesc: FP32 accumulate, BF16 A and B, both K-major, N = 64, M = 128
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UBN >> 3) << 17) |
                                ((uint32_t)(UBM >> 4) << 24);
-        if (cudaFuncSetAttribute(oz_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpdSmem) !=
-            cudaSuccess) {
-            (void)cudaGetLastError();
-            return RMGE_ERR_CUDA;
-        }
         const int64_t all = (int64_t)u.tiles * bt.count;
         const int grid = all < sm_count() ? (int)all : sm_count();
-        oz_update_kernel<<<grid, OTHREADS, kUpdSmem, st>>>(ta, tb, u, idesc);
-        RMGE_LAUNCH_CHECK();
-        return RMGE_OK;
+        switch (s) {
+            case 4: return launch_update<4>(ta, tb, u, idesc, grid, st);
+            case 5: return launch_update<5>(ta, tb, u, idesc, grid, st);
+            case 6: return launch_update<6>(ta, tb, u, idesc, grid, st);
+            default: return launch_update<7>(ta, tb, u, idesc, grid, st);
+        }
     }
 
     // |acc| < (chunks on diagonal 0 + 1) 2^(F + 10) must stay below 2^62

@@ -44,7 +44,7 @@ EXPORTED = ["rmge_multiplier_bytes", "rmge_workspace_size", "rmge_make_multiplie
 class Options(C.Structure):
     """rmge_options (include/rmge.h)."""
     _fields_ = [("growth_tol", C.c_double), ("spin_limit", C.c_int64), ("status", C.c_void_p), ("gmres_m", C.c_int32),
-                ("apply_digits", C.c_int32), ("sync", C.c_int32)]
+                ("apply_digits", C.c_int32), ("sync", C.c_int32), ("factor_digits", C.c_int32)]
 
 
 class RmgeError(RuntimeError):
@@ -257,7 +257,8 @@ def solve(kind, LU, G, B, prec="f64", X=None, ws=None) -> torch.Tensor:
     return X
 
 
-def options(growth_tol=0.0, spin_limit=None, gmres_m=None, sync=False, status=None, apply_digits=None) -> Options:
+def options(growth_tol=0.0, spin_limit=None, gmres_m=None, sync=False, status=None, apply_digits=None,
+            factor_digits=None) -> Options:
     """rmge_options with the library's defaults (rmge_options_init) and the given fields replaced; status is
     a device int32 tensor or None."""
     o = Options()
@@ -269,6 +270,8 @@ def options(growth_tol=0.0, spin_limit=None, gmres_m=None, sync=False, status=No
         o.gmres_m = int(gmres_m)
     if apply_digits is not None:
         o.apply_digits = int(apply_digits)
+    if factor_digits is not None:
+        o.factor_digits = int(factor_digits)
     o.sync = 1 if sync else 0
     o.status = None if status is None else status.data_ptr()
     return o

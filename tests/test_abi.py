@@ -90,7 +90,10 @@ def test_options_defaults_and_validation(lib):
     INVALID = 1
     o = rmge.options()
     assert o.growth_tol == 0.0 and o.gmres_m == 16 and o.spin_limit == 1 << 22 and o.sync == 0 and not o.status
-    assert o.apply_digits == 7
+    assert o.apply_digits == 7 and o.factor_digits == 7
+    assert rmge.workspace_size_ex(64, 1, "gaussian", "f64x", rmge.options(factor_digits=3)) == 0
+    assert rmge.workspace_size_ex(64, 1, "gaussian", "f64x", rmge.options(factor_digits=8)) == 0
+    assert rmge.workspace_size_ex(64, 1, "gaussian", "f64x", rmge.options(factor_digits=4)) > 0
     assert rmge.workspace_size_ex(64, 1, "gaussian", "f64x", rmge.options(apply_digits=0)) == 0
     assert rmge.workspace_size_ex(64, 1, "gaussian", "f64x", rmge.options(apply_digits=8)) == 0
     # the FGMRES basis grows with the restart length; out-of-range options make every size request invalid

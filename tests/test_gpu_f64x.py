@@ -187,3 +187,49 @@ def test_fewer_digit_product_is_won_back_by_refinement(orc, digits):
     it = int(host(iters)[0])
     assert it <= 6, it
     assert orc.backward_error(A, host(X), B) <= 1e-13
+
+
+@pytest.mark.parametrize("digits", [4, 5, 6, 7])
+def test_factor_digits_exact_on_integer_factors(orc, digits):
+    """M = L U with small-integer L (unit lower) and U (unit-modulus diagonal): GENP's multipliers, panels and
+    Schur complements are all integers of a few bits, which any digit count represents exactly, so the
+    factors come back exactly (the fixed-point sums, the per-k balancing and the digit split lose nothing)."""
+    n = 320
+    r = W.rng(4000 + digits)
+    L = np.tril(r.integers(-2, 3, (n, n)), -1).astype(np.float64) + np.eye(n)
+    U = np.triu(r.integers(-2, 3, (n, n)), 1).astype(np.float64) + np.diag(r.choice([-1.0, 1.0], n))
+    M0 = L @ U
+    assert np.max(np.abs(M0)) < 2.0**20
+    M = dev(M0)
+    info, growth, _ = rmge.factor_ex(M, "f64x", rmge.options(factor_digits=digits))
+    LU = host(M)
+    assert int(host(info)[0]) == 0
+    assert np.array_equal(np.tril(LU, -1), np.tril(L, -1))
+    assert np.array_equal(np.triu(LU), U)
+
+
+@pytest.mark.parametrize("digits", [5, 6])
+def test_fewer_factor_digits_are_won_back_by_refinement(orc, digits):
+    """Schur updates from 5 or 6 digits (factors of about 39 or 47 bits), A G from the same digits: the FP64
+    refinement still takes the precision workload's matrices (sigma down to 1e-4) to the FP64 target."""
+    n, k = 2048, 8
+    A, B = W.orthogonal_factor_system(n, k, 1e-4, seed=2148 + digits)
+    Ad, Bd = dev(A), dev(B)
+    opts = rmge.options(apply_digits=digits, factor_digits=digits)
+    ws = rmge.workspace_ex(n, k, "gaussian", "f64x", opts)
+    G = rmge.make_multiplier("gaussian", n, seed=33, subsequence=1, prec="f64x")
+    M7 = rmge.apply_multiplier("gaussian", Ad, G, "f64x")
+    _, g7 = rmge.factor(M7, "f64x")
+    M = rmge.apply_multiplier_ex("gaussian", Ad, G, "f64x", opts, ws=ws)
+    info, growth, _ = rmge.factor_ex(M, "f64x", opts, ws=ws)
+    assert int(host(info)[0]) == 0
+    g = float(host(growth)[0])
+    # the factors really are those of fewer digits (GENP without pivoting amplifies the difference by the
+    # conditioning of the leading blocks: the factors move far more than their backward error)
+    d = np.max(np.abs(host(M) - host(M7))) / np.max(np.abs(host(M7)))
+    assert d >= 2.0**(-8 * digits - 16), (d, g, float(host(g7)[0]))
+    X = rmge.solve("gaussian", M, G, Bd, "f64x", ws=ws)
+    berr, iters, _ = rmge.refine_ex("gaussian", Ad, M, G, Bd, X, "f64x", 10, 1e-13, opts, ws=ws)
+    it = int(host(iters)[0])
+    assert it <= 8, it
+    assert orc.backward_error(A, host(X), B) <= 1e-13
