@@ -34,16 +34,21 @@ N3, K3, SIGMA3 = 16384, 8, 1e-4       # the precision workload (headline)
 N2, K2, SIGMA2 = 4096, 16, 1e-6       # the FP64 workload with its multiplier forms
 BE_TOL, MAX_ITERS = 1e-13, 10
 HEADLINE = ("gaussian", "f64x")       # multiplier kind, precision of the headline form
+# Balanced base-256 digits of the headline's emulated products: A G from 4 (31 bits, 10 digit-pair MMAs), the
+# Schur updates from 6 (47 bits, 21 pairs); FP64 refinement wins the rest back.  Its sweep count follows the
+# draw's growth (2 to 8 sweeps seen at n = 16384), hence the larger sweep limit of the mixed forms.
+HEADLINE_DIGITS = (4, 6)
+MAX_ITERS_MIXED = 20
 # FP64 on GB300 runs on the DFMA pipe: 2 DFMA per clock per SM; at the 2070 MHz maximum SM clock that is
 # 152 SMs x 2 DFMA x 2 flop x 2.070 GHz = 1.2586 TFLOP/s.  The measured FP64 GEMM rate (cuBLAS DGEMM) is
 # taken live by dgemm_peak_tflops() and reported beside it (profiles/fp64_peak_cublas_dgemm_n8192.md).
 FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) per launch of the two A G kernels from ncu captures, per n^3 (the tiled
-# products re-read their panels, so the traffic scales with n^3 once the panels exceed L2); None until
-# captured for the kernel as built.  Sources: profiles/gemm_kernel_fp64_AG_n4096.md and
-# profiles/oz_gemm_kernel_f64x_AG_n8192.md.
+# products re-read their panels, so the traffic scales with n^3 once the panels exceed L2); the emulated
+# kernel's by apply digits.  A kernel changed since its capture has no entry (traffic null).  Sources:
+# profiles/gemm_kernel_fp64_AG_n4096.md and profiles/oz_gemm_kernel_f64x_AG_n8192.md.
 AG_TRAFFIC_PER_N3 = (3.730475e9 + 0.134292e9) / 4096**3
-OZ_AG_TRAFFIC_PER_N3 = (14.101759e9 + 0.810690e9) / 8192**3
+OZ_AG_TRAFFIC_PER_N3 = {}
 
 
 def flops_per_solve(n, k, sweeps):
@@ -157,11 +162,11 @@ class Form:
     """One form of the whole solve (multiplier kind, precision, options) on fixed device inputs, with its own
     buffers; step(i) runs the hot path once with the multiplier of step i."""
 
-    def __init__(self, rmge, A, B, kind, prec, digits=7, gmres_m=16, max_iters=MAX_ITERS):
+    def __init__(self, rmge, A, B, kind, prec, digits=7, fdigits=7, gmres_m=16, max_iters=MAX_ITERS):
         import torch
         self.rmge, self.A, self.B, self.kind, self.prec = rmge, A, B, kind, prec
         self.n, self.k = A.shape[0], B.shape[1]
-        self.opts = rmge.options(apply_digits=digits, gmres_m=gmres_m)
+        self.opts = rmge.options(apply_digits=digits, factor_digits=fdigits, gmres_m=gmres_m)
         self.max_iters = max_iters
         self.ws = rmge.workspace_ex(self.n, self.k, kind, prec, self.opts)
         self.G = rmge.empty_multiplier(kind, self.n, prec)
@@ -182,7 +187,7 @@ class Form:
         if record:
             e1.record()
             self.apply_events.append((e0, e1))
-        info, growth = r.factor(self.M, self.prec, ws=self.ws)
+        info, growth, _ = r.factor_ex(self.M, self.prec, self.opts, ws=self.ws)
         r.solve(self.kind, self.M, self.G, B, self.prec, X=self.X, ws=self.ws)
         berr, iters, _ = r.refine_ex(self.kind, A, self.M, self.G, B, self.X, self.prec, self.max_iters, BE_TOL,
                                      self.opts, ws=self.ws)
@@ -238,7 +243,7 @@ def oz_roofline(n, apply_ms, digits, peaks):
     return {"kernel": "oz_gemm_kernel (M = A G, FP64 emulated by BF16 digit-pair MMAs)", "bound": "tensor",
             "achieved": achieved, "peak": pk, "unit": "TFLOP/s (BF16 MMA)", "frac": achieved / pk,
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
-            "traffic": OZ_AG_TRAFFIC_PER_N3 * n**3 if OZ_AG_TRAFFIC_PER_N3 else None,
+            "traffic": OZ_AG_TRAFFIC_PER_N3[digits] * n**3 if digits in OZ_AG_TRAFFIC_PER_N3 else None,
             "algorithmic_bytes": 3 * n * n * 8,
             "digit_pairs": pairs,
             "algorithmic_fp64_tflops": (2 * n**3 - n**2) / (apply_ms / 1e3) / 1e12,
@@ -276,22 +281,26 @@ def fp64_roofline(n, apply_ms, dgemm_tflops=None):
             "apply_ms": apply_ms}
 
 
-# Other forms on the headline inputs: (name, kind, precision, apply digits, steps, gated, text)
+# Other forms on the headline inputs: (name, kind, precision, apply digits, factor digits, steps, text)
 FORMS3 = [
-    ("unitary_f64x", "circulant_unitary", "f64x", 7, 3,
-     "random unitary circulant G of Ex. 5.2 applied by 16384-point FFTs; Schur updates emulated on the BF16 tensor "
-     "cores; solves and refinement in FP64"),
-    ("f64x_digits6", "gaussian", "f64x", 6, 3,
-     "Gaussian G; A G from 6 balanced base-256 digits (21 digit-pair MMAs, 47 bits), won back by FP64 refinement; "
-     "Schur updates emulated with 7 digits"),
-    ("f64x_digits5", "gaussian", "f64x", 5, 3,
-     "Gaussian G; A G from 5 balanced base-256 digits (15 digit-pair MMAs, 39 bits), won back by FP64 refinement; "
-     "Schur updates emulated with 7 digits"),
-    ("bf16x3", "gaussian", "bf16x3", 7, 1, "Gaussian G; FP32 factors with three-pass BF16 tensor-core updates; FGMRES(16)"),
-    ("f16x3", "gaussian", "f16x3", 7, 1, "Gaussian G; FP32 factors with three-pass FP16 tensor-core updates; FGMRES(16)"),
-    ("unitary_bf16x3", "circulant_unitary", "bf16x3", 7, 1, "unitary circulant G; three-pass BF16 updates; FGMRES(16)"),
-    ("unitary_f16x3", "circulant_unitary", "f16x3", 7, 1, "unitary circulant G; three-pass FP16 updates; FGMRES(16)"),
-    ("unitary_f32", "circulant_unitary", "f32", 7, 1, "unitary circulant G; FP32 SIMT factors; FGMRES(16)"),
+    ("f64x_7_7", "gaussian", "f64x", 7, 7, 3,
+     "Gaussian G; A G and the Schur updates with all 7 balanced base-256 digits (28 digit-pair MMAs each, 55-bit "
+     "operands): FP64-equivalent emulation, FP64 refinement"),
+    ("f64x_5_6", "gaussian", "f64x", 5, 6, 3,
+     "Gaussian G; A G from 5 digits (15 digit-pair MMAs, 39 bits), Schur updates from 6 (21 MMAs, 47 bits); FP64 "
+     "refinement"),
+    ("unitary_f64x", "circulant_unitary", "f64x", 7, 6, 3,
+     "random unitary circulant G of Ex. 5.2 applied by 16384-point FFTs; Schur updates from 6 digits on the BF16 "
+     "tensor cores; solves and refinement in FP64"),
+    ("bf16x3", "gaussian", "bf16x3", 7, 7, 1, "Gaussian G; FP32 factors with three-pass BF16 tensor-core updates; "
+                                             "FGMRES(16)"),
+    ("f16x3", "gaussian", "f16x3", 7, 7, 1, "Gaussian G; FP32 factors with three-pass FP16 tensor-core updates; "
+                                           "FGMRES(16)"),
+    ("unitary_bf16x3", "circulant_unitary", "bf16x3", 7, 7, 1, "unitary circulant G; three-pass BF16 updates; "
+                                                              "FGMRES(16)"),
+    ("unitary_f16x3", "circulant_unitary", "f16x3", 7, 7, 1, "unitary circulant G; three-pass FP16 updates; "
+                                                            "FGMRES(16)"),
+    ("unitary_f32", "circulant_unitary", "f32", 7, 7, 1, "unitary circulant G; FP32 SIMT factors; FGMRES(16)"),
 ]
 # Forms on the n = 4096 FP64 workload: (name, kind, precision)
 FORMS2 = [("f64", "gaussian", "f64"), ("f64x", "gaussian", "f64x"), ("circ_f64", "circulant", "f64"),
@@ -512,7 +521,8 @@ def main():
     seed = ranks.system_seed(SEED_BASE + 3, rank)
     A, Bm = W.orthogonal_factor_system_torch(n, k, SIGMA3, seed=seed, device="cuda")
     kind, prec = HEADLINE
-    head = Form(rmge, A, Bm, kind, prec)
+    head = Form(rmge, A, Bm, kind, prec, digits=HEADLINE_DIGITS[0], fdigits=HEADLINE_DIGITS[1],
+                max_iters=MAX_ITERS_MIXED)
     stream = torch.cuda.current_stream()
 
     for i in range(args.warmup):
@@ -576,7 +586,7 @@ def main():
     A_h = A.cpu().pin_memory()
     B_h = Bm.cpu().pin_memory()
     X_h = torch.empty(n, k, dtype=torch.float64).pin_memory()
-    be_h = torch.empty(MAX_ITERS + 1, dtype=torch.float64).pin_memory()
+    be_h = torch.empty(head.max_iters + 1, dtype=torch.float64).pin_memory()
     A_d = torch.empty_like(A)
     B_d = torch.empty_like(Bm)
     barrier()
@@ -598,14 +608,15 @@ def main():
     # the other forms on the headline inputs
     forms3 = {}
     wanted = [f for f in args.forms.split(",") if f and f != "none"]
-    for name, fkind, fprec, digits, fsteps, text in FORMS3:
+    for name, fkind, fprec, digits, fdigits, fsteps, text in FORMS3:
         if name not in wanted:
             continue
         try:
-            f = Form(rmge, A, Bm, fkind, fprec, digits=digits)
+            f = Form(rmge, A, Bm, fkind, fprec, digits=digits, fdigits=fdigits,
+                     max_iters=MAX_ITERS_MIXED if fprec == "f64x" else MAX_ITERS)
             r = timed_form(f, fsteps, 1, seed + 200, barrier, world)
             r["form"] = text
-            r["apply_digits"] = digits if fprec == "f64x" else None
+            r["digits"] = {"apply": digits, "factor": fdigits} if fprec == "f64x" else None
             forms3[name] = r
             del f
             torch.cuda.empty_cache()
@@ -642,8 +653,8 @@ def main():
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         except Exception:
             pass
-        roof = oz_roofline(n, head_apply_ms, 7, peaks)
-        for name, fkind, fprec, digits, _, _ in FORMS3:
+        roof = oz_roofline(n, head_apply_ms, HEADLINE_DIGITS[0], peaks)
+        for name, fkind, fprec, digits, _, _, _ in FORMS3:
             f = forms3.get(name)
             if isinstance(f, dict) and "apply_ms" in f and fkind == "gaussian" and fprec == "f64x":
                 f["roofline"] = oz_roofline(n, f["apply_ms"], digits, peaks)
@@ -660,9 +671,12 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16 MMA (emulated f64) + f64", "data": "synthetic",
             "config": workload_config(n, k, SIGMA3, HEADLINE[0]),
-            "form": "mixed: Gaussian G; A G and GENP's Schur updates as FP64 products emulated on the BF16 tensor "
-                    "cores (7 balanced base-256 digits, 28 digit-pair MMAs with exact FP32 sums, 64-bit fixed "
-                    "point); pivot blocks, panels, triangular solves, residuals and refinement on the FP64 pipe",
+            "form": "mixed: Gaussian G; A G and GENP's Schur updates as products of balanced base-256 digit planes "
+                    "on the BF16 tensor cores (exact FP32 sums, 64-bit fixed point): A G from 4 digits (31-bit "
+                    "operands, 10 digit-pair MMAs), the updates from 6 (47 bits, 21 MMAs); pivot blocks, panels, "
+                    "triangular solves, residuals and refinement (up to 20 sweeps, each step gated at BE <= 1e-13) "
+                    "on the FP64 pipe",
+            "digits": {"apply": HEADLINE_DIGITS[0], "factor": HEADLINE_DIGITS[1]},
             "tflops": flops * value / 1e12,
             "accuracy": {"all_steps_be_le_1e-13": ok, "max_berr": max(bes), "mean_sweeps": mean_sweeps,
                          "infos": sorted(set(infos)), "oracle_berr_last": be_oracle,

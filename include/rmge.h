@@ -408,8 +408,9 @@ rmge_status rmge_solve_batched_ex(int64_t count, const int32_t* n, const int64_t
  * rmge_apply_multiplier_batched: M_i = A_i G_i; opts may be NULL (apply_digits applies as for
  * rmge_apply_multiplier_ex).
  * rmge_factor_batched: in-place GENP of every M_i, as rmge_factor; info[i] and growth[i] (device arrays of
- * count entries; growth may be NULL) as rmge_factor reports them.  A breakdown of one system does not stop
- * the others.
+ * count entries; growth may be NULL) as rmge_factor reports them; opts may be NULL (factor_digits and
+ * spin_limit apply as for rmge_factor_ex; growth_tol, status and sync are not used here: info and growth
+ * carry every system's outcome).  A breakdown of one system does not stop the others.
  */
 size_t rmge_batched_uniform_workspace_size(int64_t count, int64_t n, rmge_prec prec);
 rmge_status rmge_apply_multiplier_batched(int64_t count, int64_t n, const double* A, int64_t lda, int64_t strideA,
@@ -417,7 +418,8 @@ rmge_status rmge_apply_multiplier_batched(int64_t count, int64_t n, const double
                                           rmge_prec prec, const rmge_options* opts, void* ws, size_t ws_bytes,
                                           rmge_stream_t stream);
 rmge_status rmge_factor_batched(int64_t count, int64_t n, double* M, int64_t ldm, int64_t strideM, rmge_prec prec,
-                                int32_t* info, double* growth, void* ws, size_t ws_bytes, rmge_stream_t stream);
+                                int32_t* info, double* growth, const rmge_options* opts, void* ws, size_t ws_bytes,
+                                rmge_stream_t stream);
 
 /*
  * The rest of a uniform batch, with the FP64 factors that rmge_factor_batched leaves (RMGE_F64 or

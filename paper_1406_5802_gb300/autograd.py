@@ -66,7 +66,7 @@ class RmgeSolveUniform(torch.autograd.Function):
     rmge_solve_backward_uniform_batched)."""
 
     @staticmethod
-    def forward(ctx, A, B, seeds, prec, max_iters, be_tol, streams):
+    def forward(ctx, A, B, seeds, prec, max_iters, be_tol, streams, digits=(7, 7)):
         count, n, _ = A.shape
         A64 = A.detach().to(torch.float64).contiguous()
         B64 = B.detach().to(torch.float64).contiguous()
@@ -74,8 +74,9 @@ class RmgeSolveUniform(torch.autograd.Function):
         for i, s in enumerate(seeds):
             rmge.make_multiplier("gaussian", n, int(s), 1, prec, G=G[i])
         ws = rmge.uniform_workspace(count, n, prec)
-        M = rmge.apply_multiplier_batched(A64, G, prec, ws=ws)
-        info, _ = rmge.factor_batched(M, prec, ws=ws)
+        opts = rmge.options(apply_digits=digits[0], factor_digits=digits[1])
+        M = rmge.apply_multiplier_batched(A64, G, prec, opts=opts, ws=ws)
+        info, _ = rmge.factor_batched(M, prec, ws=ws, opts=opts)
         del ws
         # the solves and sweeps with FP64 factors are uniform batches too: one launch per kernel for all
         # systems, each system stopping its refinement on its own test
@@ -96,18 +97,20 @@ class RmgeSolveUniform(torch.autograd.Function):
                                                            max_iters=ctx.max_iters, be_tol=ctx.be_tol)
         gA = dA.to(dX.dtype) if dA is not None else None
         gB = dB.to(dX.dtype) if ctx.needs_input_grad[1] else None
-        return gA, gB, None, None, None, None, None
+        return gA, gB, None, None, None, None, None, None
 
 
 def rmge_solve_batched(As, Bs, seeds, kind: str = "gaussian", prec: str = "f32", streams: int = 8, **kw):
     """A list of independent differentiable solves.  Systems of one order with the emulated-FP64 precision
     ("f64x") and dense Gaussian multipliers go through the uniform batched path (one autograd node;
-    products and factorizations batched); otherwise each solve is its own node and the solves are spread
-    round-robin over CUDA streams so that small systems overlap on the GPU.  Returns the list of X."""
+    products, factorizations, solves, refinement and adjoint batched; digits=(apply, factor) sets the
+    balanced base-256 digits of the emulated products, default (7, 7)); otherwise each solve is its own
+    node and the solves are spread round-robin over CUDA streams so that small systems overlap on the GPU.
+    Returns the list of X."""
     if (prec == "f64x" and kind == "gaussian" and len(As) > 1 and len({tuple(a.shape) for a in As}) == 1
             and len({tuple(b.shape) for b in Bs}) == 1):
         X = RmgeSolveUniform.apply(torch.stack(As), torch.stack(Bs), list(seeds), prec, kw.get("max_iters", 10),
-                                   kw.get("be_tol", 1e-13), streams)
+                                   kw.get("be_tol", 1e-13), streams, tuple(kw.get("digits", (7, 7))))
         return list(X.unbind(0))
     pool = _stream_pool(max(1, streams), As[0].device.index if len(As) else None)
     cur = torch.cuda.current_stream()

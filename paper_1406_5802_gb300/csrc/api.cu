@@ -886,8 +886,10 @@ rmge_status rmge_apply_multiplier_batched(int64_t count, int64_t n, const double
 }
 
 rmge_status rmge_factor_batched(int64_t count, int64_t n, double* M, int64_t ldm, int64_t strideM, rmge_prec prec,
-                                int32_t* info, double* growth, void* ws, size_t ws_bytes, rmge_stream_t stream) {
-    if (!uni_args_ok(count, n) || !valid_prec(prec) || M == nullptr || info == nullptr ||
+                                int32_t* info, double* growth, const rmge_options* opts, void* ws, size_t ws_bytes,
+                                rmge_stream_t stream) {
+    Opts o;
+    if (!opts_of(opts, &o) || !uni_args_ok(count, n) || !valid_prec(prec) || M == nullptr || info == nullptr ||
         !uni_stride_ok(n, ldm, strideM))
         return RMGE_ERR_INVALID_ARG;
     if (prec != RMGE_F64X_TC) return RMGE_ERR_UNSUPPORTED;
@@ -903,7 +905,7 @@ rmge_status rmge_factor_batched(int64_t count, int64_t n, double* M, int64_t ldm
     oz.eb = reinterpret_cast<int*>(b + L.eb);
     oz.kmax = reinterpret_cast<unsigned long long*>(b + L.kmax);
     RMGE_TRY(states_init(st, (int)count, oz.kmax, 128 * L.steps * count, s));
-    RMGE_TRY(genp_factor_oz(n, M, ldm, st, oz, s, (int)count, strideM));
+    RMGE_TRY(genp_factor_oz(n, M, ldm, st, oz, s, (int)count, strideM, o.fdigits));
     return genp_finish(st, info, growth, s, (int)count);
 }
 

@@ -16,6 +16,7 @@
 //   FP32 Gaussian (multipliers of the reduced-precision paths): the same Box-Muller pair in FP32
 //   arithmetic on 24-bit uniforms: u1 = ((x0 >> 8) + 1) 2^-24, u2 = (x2 >> 8) 2^-24.
 #include "kernels.cuh"
+#include "box_muller_tables.cuh"
 
 namespace rmge {
 namespace {
@@ -46,16 +47,64 @@ __device__ __forceinline__ uint64_t join53(uint32_t hi, uint32_t lo) {
     return ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
 }
 
+// ln((m1 + 1) 2^-53) by the table-driven method of Tang (ACM TOMS 16(4), 1990), mostly in integer
+// operations: x = m1 + 1 = f 2^p with f in [1, 2); F_j = 1 + j/256 is the table point nearest f (j = 256,
+// that is F = 2, moves to the next binade as F = 1, so that u1 near 1 keeps its full relative accuracy);
+// g = f - F_j is exact, t = g / F_j, and ln(1 + t) for |t| <= 2^-9 is its Taylor series to t^6 (the first
+// term left out is below 2^-63).  (p - 53) ln 2 + ln F_j take the split constants of the table, whose
+// high parts add exactly.
+__device__ __forceinline__ double ln_uniform53(uint64_t m1, const double (*lt)[3]) {
+    const uint64_t x = m1 + 1;  // 1 .. 2^53
+    const int lz = __clzll((long long)x);
+    const uint64_t mant = ((x << lz) >> 11) & 0xFFFFFFFFFFFFFull;  // exact: x has at most 53 significant bits
+    uint64_t j = (mant + (1ull << 43)) >> 44;                       // nearest of the 256ths, 0 .. 256
+    const double f = __longlong_as_double((long long)((1023ull << 52) | mant));
+    double g = f - __longlong_as_double((long long)((1023ull << 52) + (j << 44)));  // exact (Sterbenz)
+    int e = 63 - lz - 53;
+    if (j == 256) {
+        g *= 0.5;
+        j = 0;
+        ++e;
+    }
+    const double t = g * lt[j][0];
+    const double q = fma(t, fma(t, fma(t, fma(t, -1.0 / 6, 0.2), -0.25), 1.0 / 3), -0.5);
+    const double poly = fma(t, t * q, t);  // t + t^2 (-1/2 + t/3 - t^2/4 + t^3/5 - t^4/6)
+    const double ed = (double)e;
+    return fma(ed, bm::kLn2Hi, lt[j][1]) + (fma(ed, bm::kLn2Lo, lt[j][2]) + poly);
+}
+
+// cos and sin of 2 pi m2 2^-53: k = the nearest 256th of the turn, phi = 2 pi (m2 2^-53 - k/256) with
+// |phi| <= pi / 256; cos phi = 1 - c2 and sin phi from their Taylor series (first terms left out below
+// 1e-17), then the addition theorems with the tabulated cos, sin of 2 pi k / 256.
+__device__ __forceinline__ void sincos_turn53(uint64_t m2, const double (*sc)[2], double* s, double* c) {
+    const uint64_t k = (m2 + (1ull << 44)) >> 45;  // 0 .. 256
+    const double phi = (double)((long long)m2 - (long long)(k << 45)) * bm::kTwoPi53;
+    const double z = phi * phi;
+    const double sp = fma(phi * z, fma(z, 1.0 / 120, -1.0 / 6), phi);
+    const double c2 = z * fma(z, fma(z, 1.0 / 720, -1.0 / 24), 0.5);
+    const double ck = sc[k & 255][0], sk = sc[k & 255][1];
+    *c = ck - fma(ck, c2, sk * sp);
+    *s = sk + fma(ck, sp, -sk * c2);
+}
+
 __global__ void gaussian_kernel(int64_t count, uint64_t seed, uint64_t subseq, double* __restrict__ out) {
+    __shared__ double lt[256][3];
+    __shared__ double sc[256][2];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        lt[i][0] = bm::kLogTable[i][0];
+        lt[i][1] = bm::kLogTable[i][1];
+        lt[i][2] = bm::kLogTable[i][2];
+        sc[i][0] = bm::kSinCosTable[i][0];
+        sc[i][1] = bm::kSinCosTable[i][1];
+    }
+    __syncthreads();
     const int64_t pairs = (count + 1) / 2;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < pairs;
          p += (int64_t)gridDim.x * blockDim.x) {
         const U4 x = block_for((uint64_t)p, seed, subseq);
-        const double u1 = (double)(join53(x.x, x.y) + 1) * 0x1p-53;
-        const double u2 = (double)join53(x.z, x.w) * 0x1p-53;
-        const double r = sqrt(-2.0 * log(u1));
+        const double r = sqrt(-2.0 * ln_uniform53(join53(x.x, x.y), lt));
         double sn, cs;
-        sincospi(2.0 * u2, &sn, &cs);
+        sincos_turn53(join53(x.z, x.w), sc, &sn, &cs);
         out[2 * p] = r * cs;
         if (2 * p + 1 < count) out[2 * p + 1] = r * sn;
     }

@@ -107,7 +107,7 @@ def load_library(path: str = LIB_PATH):
         "rmge_batched_uniform_workspace_size": (_sz, [_i64, _i64, C.c_int]),
         "rmge_apply_multiplier_batched": (C.c_int, [_i64, _i64, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _i64, C.c_int,
                                                     C.POINTER(Options), _vp, _sz, _vp]),
-        "rmge_factor_batched": (C.c_int, [_i64, _i64, _vp, _i64, _i64, C.c_int, _vp, _vp, _vp, _sz, _vp]),
+        "rmge_factor_batched": (C.c_int, [_i64, _i64, _vp, _i64, _i64, C.c_int, _vp, _vp, _vp, _vp, _sz, _vp]),
         "rmge_uniform_solve_workspace_size": (_sz, [_i64, _i64, _i64, C.c_int]),
         "rmge_solve_uniform_batched": (C.c_int, [_i64, _i64, _i64, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _i64, _vp,
                                                  _i64, _i64, C.c_int, _vp, _sz, _vp]),
@@ -343,7 +343,7 @@ def apply_multiplier_batched(A, G, prec="f64x", opts=None, M=None, ws=None) -> t
     return M
 
 
-def factor_batched(M, prec="f64x", ws=None):
+def factor_batched(M, prec="f64x", ws=None, opts=None):
     """rmge_factor_batched: in-place GENP of every M[i]; returns (info, growth) device tensors of count entries."""
     L = _cuda_lib()
     _need3(M, "M")
@@ -352,8 +352,10 @@ def factor_batched(M, prec="f64x", ws=None):
     growth = torch.empty(count, dtype=torch.float64, device=M.device)
     if ws is None:
         ws = uniform_workspace(count, n, prec)
+    o = options() if opts is None else opts
     _check("rmge_factor_batched", L.rmge_factor_batched(count, n, _p(M), M.stride(1), M.stride(0), _prec(prec),
-                                                        _p(info), _p(growth), _p(ws), ws.numel(), _stream()))
+                                                        _p(info), _p(growth), C.byref(o), _p(ws), ws.numel(),
+                                                        _stream()))
     return info, growth
 
 

@@ -126,7 +126,9 @@ def test_uniform_batch_sizes_and_argument_checks(lib):
     assert lib.rmge_batched_uniform_workspace_size(70000, 64, 6) == 0
     p = C.c_void_p(256)
     # overlapping systems (stride below (n - 1) ld + n) are refused before any GPU work
-    assert lib.rmge_factor_batched(2, 8, p, 8, 10, 6, p, None, p, 1 << 20, None) == INVALID
-    assert lib.rmge_factor_batched(2, 8, p, 8, 64, 0, p, None, p, 1 << 20, None) == UNSUPPORTED
-    assert lib.rmge_factor_batched(2, 8, p, 8, 64, 6, p, None, p, 16, None) == WORKSPACE
+    assert lib.rmge_factor_batched(2, 8, p, 8, 10, 6, p, None, None, p, 1 << 20, None) == INVALID
+    assert lib.rmge_factor_batched(2, 8, p, 8, 64, 0, p, None, None, p, 1 << 20, None) == UNSUPPORTED
+    assert lib.rmge_factor_batched(2, 8, p, 8, 64, 6, p, None, None, p, 16, None) == WORKSPACE
+    bad = rmge.options(factor_digits=3)
+    assert lib.rmge_factor_batched(2, 8, p, 8, 64, 6, p, None, C.byref(bad), p, 1 << 20, None) == INVALID
     assert lib.rmge_apply_multiplier_batched(2, 8, p, 8, 64, p, 64, p, 8, 63, 6, None, p, 1 << 20, None) == INVALID

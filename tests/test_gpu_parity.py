@@ -30,8 +30,11 @@ def _lib():
 
 # ----------------------------------------------------------------------------- multiplier draws
 
-@pytest.mark.parametrize("n", [1, 3, 64, 257])
+@pytest.mark.parametrize("n", [1, 3, 64, 257, 2048])
 def test_gaussian_multiplier_matches_oracle(orc, n):
+    """Philox + Box-Muller entries within a few ulps of the oracle's (libm log, cos, sin); n = 2048 draws
+    4.2 million entries, among them uniforms within 1e-6 of 1, where ln u1 needs its full relative
+    accuracy."""
     G = host(rmge.make_multiplier("gaussian", n, seed=W.SEED_BASE + 1, subsequence=1, prec="f64"))
     ref = orc.make_multiplier(orc.GAUSSIAN, n, seed=W.SEED_BASE + 1, subseq=1)
     assert np.max(np.abs(G - ref)) <= 8 * U64 * max(1.0, np.max(np.abs(ref)))
