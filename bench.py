@@ -46,9 +46,9 @@ FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) per launch of the two A G kernels from ncu captures, per n^3 (the tiled
 # products re-read their panels, so the traffic scales with n^3 once the panels exceed L2); the emulated
 # kernel's by apply digits.  A kernel changed since its capture has no entry (traffic null).  Sources:
-# profiles/gemm_kernel_fp64_AG_n4096.md and profiles/oz_gemm_kernel_f64x_AG_n8192.md.
+# profiles/gemm_kernel_fp64_AG_n4096.md and profiles/oz_gemm_kernel_AG_4digits_n8192.md.
 AG_TRAFFIC_PER_N3 = (3.730475e9 + 0.134292e9) / 4096**3
-OZ_AG_TRAFFIC_PER_N3 = {}
+OZ_AG_TRAFFIC_PER_N3 = {4: (6.474913e9 + 0.539855e9) / 8192**3}
 
 
 def flops_per_solve(n, k, sweeps):
