@@ -243,6 +243,8 @@ def oz_roofline(n, apply_ms, digits, peaks):
     return {"kernel": "oz_gemm_kernel (M = A G, FP64 emulated by BF16 digit-pair MMAs)", "bound": "tensor",
             "achieved": achieved, "peak": pk, "unit": "TFLOP/s (BF16 MMA)", "frac": achieved / pk,
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
+            "frac_of_sustained": achieved / peaks["bf16_tflops_sustained"] if peaks.get("bf16_tflops_sustained")
+            else None,
             "traffic": OZ_AG_TRAFFIC_PER_N3[digits] * n**3 if digits in OZ_AG_TRAFFIC_PER_N3 else None,
             "algorithmic_bytes": 3 * n * n * 8,
             "digit_pairs": pairs,
