@@ -131,7 +131,7 @@ OzUpdate oz_buffers(const Ws& w, int64_t n) {
 }
 
 // 128 per-k maxima slots per 64-wide pivot-block step of the emulated-update GENP.
-size_t oz_kmax_slots(int64_t n) { return 128 * (size_t)((n + kNb - 1) / kNb); }
+size_t oz_kmax_slots(int64_t n) { return (size_t)oz_kmax_per_system(n); }
 
 bool check_dims(int64_t n, int64_t nrhs) { return n >= 1 && n <= RMGE_MAX_N && nrhs >= 1 && nrhs <= RMGE_MAX_N; }
 
@@ -832,7 +832,7 @@ static UniLayout uni_layout(int64_t count, int64_t n) {
     L.states = off;
     off = align256(off + sizeof(DevState) * (size_t)count);
     L.kmax = off;
-    off = align256(off + sizeof(unsigned long long) * 128 * (size_t)L.steps * (size_t)count);
+    off = align256(off + sizeof(unsigned long long) * (size_t)oz_kmax_per_system(n) * (size_t)count);
     L.ea = off;
     off = align256(off + sizeof(int) * (size_t)L.Mp * (size_t)count);
     L.eb = off;
@@ -904,7 +904,7 @@ rmge_status rmge_factor_batched(int64_t count, int64_t n, double* M, int64_t ldm
     oz.ea = reinterpret_cast<int*>(b + L.ea);
     oz.eb = reinterpret_cast<int*>(b + L.eb);
     oz.kmax = reinterpret_cast<unsigned long long*>(b + L.kmax);
-    RMGE_TRY(states_init(st, (int)count, oz.kmax, 128 * L.steps * count, s));
+    RMGE_TRY(states_init(st, (int)count, oz.kmax, oz_kmax_per_system(n) * count, s));
     RMGE_TRY(genp_factor_oz(n, M, ldm, st, oz, s, (int)count, strideM, o.fdigits));
     return genp_finish(st, info, growth, s, (int)count);
 }

@@ -69,12 +69,13 @@ __global__ void __launch_bounds__(256) diag_factor_kernel(int64_t k, int b, T* _
 // PT rows (columns) per CTA, 16 lanes per row (column); the substitution of one row (column) is
 // sequential over the b pivot columns, held in registers and stepped by 16-lane shuffles.  With kmax != NULL the
 // kernel also leaves, for the balancing of the emulated Schur update, max_i |L21_ik| in kmax[k] and
-// max_j |U12_kj| in kmax[64 + k] (FP64 bit patterns of the finite maxima, merged by atomicMax into
+// max_j |U12_kj| in kmax[uoff + k] (FP64 bit patterns of the finite maxima, merged by atomicMax into
 // zeroed slots).
 template <typename T, int PT>
 __global__ void __launch_bounds__(256) panel_apply_kernel(int64_t k, int b, int64_t rest, int row_tiles,
                                                           T* __restrict__ M, int64_t ldm, const DevState* st,
-                                                          unsigned long long* kmax, int64_t sM, int64_t sK) {
+                                                          unsigned long long* kmax, int64_t sM, int64_t sK,
+                                                          int uoff) {
     static_assert(PT * 16 == 256, "16 lanes per row or column");
     __shared__ T dd[NB][LDS];
     __shared__ T tile[PT][LDS];  // row tile: tile[r][t]; column tile stored transposed: tile[c][t]
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(256) panel_apply_kernel(int64_t k, int b, int6
             const unsigned long long v = abs_bits((double)tile[r][tid]);
             if (v < 0x7ff0000000000000ull && v > m) m = v;  // finite entries only
         }
-        if (m != 0ull) atomicMax(kmax + (is_row ? 0 : 64) + tid, m);
+        if (m != 0ull) atomicMax(kmax + (is_row ? 0 : uoff) + tid, m);
     }
     if (is_row) {
         for (int e = tid; e < PT * NB; e += blockDim.x) {
@@ -219,7 +220,7 @@ rmge_status genp_factor(int64_t n, T* M, int64_t ldm, DevState* st, cudaStream_t
         const int64_t rest = n - k - b;
         if (rest <= 0) break;
         const int tiles = (int)((rest + PT - 1) / PT);
-        panel_apply_kernel<T, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, nullptr, 0, 0);
+        panel_apply_kernel<T, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, nullptr, 0, 0, 0);
         RMGE_LAUNCH_CHECK();
         RMGE_TRY(gemm_update_fused<T>(rest, rest, b, M + (k + b) * ldm + k, ldm, M + k * ldm + k + b, ldm,
                                       M + (k + b) * ldm + (k + b), ldm, &st->halt, (int)(rest < NB ? rest : NB),
@@ -244,7 +245,7 @@ rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const
         const int64_t rest = n - k - b;
         if (rest <= 0) break;
         const int tiles = (int)((rest + PT - 1) / PT);
-        panel_apply_kernel<float, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, nullptr, 0, 0);
+        panel_apply_kernel<float, PT><<<2 * tiles, 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, nullptr, 0, 0, 0);
         RMGE_LAUNCH_CHECK();
         const float* L21 = M + (k + b) * ldm + k;
         const float* U12 = M + k * ldm + k + b;
@@ -270,13 +271,23 @@ rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const
 // per-k maxima that the panel kernel leaves; without it the per-row scaling of L21 and per-column
 // scaling of U12 pair the large column of a small pivot with the large rows of other pivots and the
 // update loses most of its relative accuracy.
-// The update launch of step k also factors the pivot block of step k + 1 (CTA 0 takes the tile holding it
-// alone), so only the first pivot block has a launch of its own.
+//
+// Pivot steps go in pairs (k, k + 1), with one step of look-ahead (the Schur complements are the same for
+// any blocking, Sec. 3):
+//   1. the panel of step k (L21, U12 and their per-k maxima);
+//   2. step k's update of block column k + 1 only, whose launch also factors pivot block k + 1 (the CTA
+//      holding it takes that tile alone), and of block row k + 1 only;
+//   3. the panel of step k + 1;
+//   4. one 128-deep update of the rest by both steps, E -= [L21_k L21_k+1] [U12_k; U12_k+1], whose
+//      launch also factors pivot block k + 2.
+// The trailing matrix is read and written once per pair instead of once per step: the emulated update is
+// bound by that read-modify-write and the digit drains, not by its MMAs.  A last unpaired step takes one
+// 64-deep update that also factors the next pivot block.
 rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s,
                            int count, int64_t sM, int digits) {
     constexpr int PT = 16;
     const unsigned nz = (unsigned)count;
-    const int64_t steps = (n + NB - 1) / NB;
+    const int64_t sK = oz_kmax_per_system(n);
     constexpr int64_t kStateUll = sizeof(DevState) / sizeof(unsigned long long);
     constexpr int64_t kStateInt = sizeof(DevState) / sizeof(int);
     // growth numerator and denominator go to each system's control block
@@ -286,31 +297,55 @@ rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, cons
         maxabs_kernel<double><<<dim3((unsigned)g, nz), 256, 0, s>>>(n, n, M, ldm, false, &st->maxabs_m, sM, kStateUll);
         RMGE_LAUNCH_CHECK();
     }
+    OzBatch bt;
+    bt.count = count;
+    bt.sA = bt.sB = bt.sC = sM;
+    bt.sK = sK;
+    bt.sFlag = kStateInt;
+    // maxima of step j: L21 columns at kmax + 256 (j / 2) + 64 (j % 2), U12 rows 128 slots further
+    auto panel = [&](int64_t k, int b, int64_t rest, unsigned long long* kmL) -> rmge_status {
+        const int tiles = (int)((rest + PT - 1) / PT);
+        panel_apply_kernel<double, PT><<<dim3(2 * tiles, nz), 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, kmL, sM,
+                                                                           sK, 128);
+        RMGE_LAUNCH_CHECK();
+        return RMGE_OK;
+    };
+    diag_factor_kernel<double><<<dim3(1, nz), 256, 0, s>>>(0, (int)(n < NB ? n : NB), M, ldm, st, sM);
+    RMGE_LAUNCH_CHECK();
     int64_t step = 0;
-    for (int64_t k = 0; k < n; k += NB, ++step) {
+    for (int64_t k = 0; k < n;) {
         const int b = (int)((n - k) < NB ? (n - k) : NB);
-        if (k == 0) {  // every later pivot block is factored inside the previous step's update launch
-            diag_factor_kernel<double><<<dim3(1, nz), 256, 0, s>>>(k, b, M, ldm, st, sM);
-            RMGE_LAUNCH_CHECK();
-        }
         const int64_t rest = n - k - b;
         if (rest <= 0) break;
-        const int tiles = (int)((rest + PT - 1) / PT);
-        unsigned long long* kmA = oz.kmax + 128 * step;  // zeroed with the factorization's state
-        panel_apply_kernel<double, PT><<<dim3(2 * tiles, nz), 256, 0, s>>>(k, b, rest, tiles, M, ldm, st, kmA, sM,
-                                                                           128 * steps);
-        RMGE_LAUNCH_CHECK();
+        unsigned long long* kmL = oz.kmax + 256 * (step / 2) + 64 * (step % 2);  // zeroed with the state
+        RMGE_TRY(panel(k, b, rest, kmL));
         const double* L21 = M + (k + b) * ldm + k;
         const double* U12 = M + k * ldm + k + b;
         double* E = M + (k + b) * ldm + (k + b);
-        const OzFuse next{E, ldm, (int)(rest < NB ? rest : NB), k + b, &st->info, &st->halt};
-        OzBatch bt;
-        bt.count = count;
-        bt.sA = bt.sB = bt.sC = sM;
-        bt.sK = 128 * steps;
-        bt.sFlag = kStateInt;
-        RMGE_TRY(oz_gemm(rest, rest, b, digits, -1.0, L21, ldm, U12, ldm, 1.0, E, ldm, oz.planesA, oz.planesB,
-                         oz.ea, oz.eb, kmA, kmA + 64, &st->error, &st->halt, s, &next, bt));
+        if (step % 2 != 0 || rest <= NB) {  // an unpaired step: one 64-deep update, next pivot block fused
+            const OzFuse next{E, ldm, (int)(rest < NB ? rest : NB), k + b, &st->info, &st->halt};
+            RMGE_TRY(oz_gemm(rest, rest, b, digits, -1.0, L21, ldm, U12, ldm, 1.0, E, ldm, oz.planesA, oz.planesB,
+                             oz.ea, oz.eb, kmL, kmL + 128, &st->error, &st->halt, s, &next, bt));
+            k += b;
+            ++step;
+            continue;
+        }
+        // b == NB here.  Step k's update of block column k + 1 (factoring pivot block k + 1) and block row k + 1.
+        const OzFuse next{E, ldm, NB, k + b, &st->info, &st->halt};
+        RMGE_TRY(oz_gemm(rest, NB, b, digits, -1.0, L21, ldm, U12, ldm, 1.0, E, ldm, oz.planesA, oz.planesB, oz.ea,
+                         oz.eb, kmL, kmL + 128, &st->error, &st->halt, s, &next, bt));
+        RMGE_TRY(oz_gemm(NB, rest - NB, b, digits, -1.0, L21, ldm, U12 + NB, ldm, 1.0, E + NB, ldm, oz.planesA,
+                         oz.planesB, oz.ea, oz.eb, kmL, kmL + 128, &st->error, &st->halt, s, nullptr, bt));
+        // step k + 1's panel, then both steps' update of the rest in one 128-deep product
+        const int64_t k1 = k + NB, rest1 = rest - NB;
+        RMGE_TRY(panel(k1, NB, rest1, kmL + 64));
+        double* E2 = M + (k1 + NB) * ldm + k1 + NB;
+        const OzFuse next2{E2, ldm, (int)(rest1 < NB ? rest1 : NB), k1 + NB, &st->info, &st->halt};
+        RMGE_TRY(oz_update128(rest1, rest1, digits, M + (k1 + NB) * ldm + k, ldm, M + k * ldm + k1 + NB, ldm, E2, ldm,
+                              oz.planesA, oz.planesB, oz.ea, oz.eb, kmL, kmL + 128, &st->error, &st->halt, s, &next2,
+                              bt));
+        k += 2 * NB;
+        step += 2;
     }
     {
         int64_t g = (n * n + 255) / 256;

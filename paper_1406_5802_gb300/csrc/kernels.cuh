@@ -101,6 +101,21 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
                     const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* planesA, void* planesB,
                     int* ea, int* eb, const unsigned long long* kmaxA, const unsigned long long* kmaxB, int* err,
                     const int* halt, cudaStream_t st, const OzFuse* fuse = nullptr, const OzBatch& bt = OzBatch{});
+// E -= A B with K = 128 (two pivot blocks of GENP at once; A is M x 128, B is 128 x N), the digit planes
+// of A and B from s = 4 .. kOzSlices digits with the per-k balancing maxima kmaxA[0..128), kmaxB[0..128),
+// then the persistent 128-deep update kernel.  fuse and bt as for oz_gemm (the tile holding C's top-left
+// corner also factors the pivot block there).
+rmge_status oz_update128(int64_t M, int64_t N, int s, const double* A, int64_t lda, const double* B, int64_t ldb,
+                         double* C, int64_t ldc, void* planesA, void* planesB, int* ea, int* eb,
+                         const unsigned long long* kmaxA, const unsigned long long* kmaxB, int* err, const int* halt,
+                         cudaStream_t st, const OzFuse* fuse = nullptr, const OzBatch& bt = OzBatch{});
+// Slots of per-k maxima per system for the emulated factorization: for each pair of pivot steps, the
+// 64 + 64 column maxima of L21 and then the 64 + 64 row maxima of U12 (256 slots), so that the 128-deep
+// update of a pair finds both operands' maxima contiguous.
+inline int64_t oz_kmax_per_system(int64_t n) {
+    const int64_t steps = (n + kNb - 1) / kNb;
+    return 256 * ((steps + 1) / 2);
+}
 struct OzUpdate {
     void* planesA;
     void* planesB;

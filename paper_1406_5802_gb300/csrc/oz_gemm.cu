@@ -694,6 +694,299 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
 }
 
 // ---------------------------------------------------------------------------------------------
+// Products with K = 128: the Schur update of two pivot steps at once, E -= [L21_k L21_k+1] [U12_k; U12_k+1]
+// (GENP with one step of look-ahead).  A persistent CTA walks its share of 128 x 64 output tiles.  Per tile
+// it streams, for each A digit plane p (128 rows x 128 K, 32 KB, two 64-wide boxes), the B planes
+// q = 0 .. ND-1-p (64 columns x 128 K, 16 KB), so that every A plane crosses from L2 once per tile; each pair
+// adds into the 64-column TMEM accumulator of its diagonal p + q, all ND diagonals at once (ND x 64 <= 448
+// columns).  The epilogue drains the diagonals, releases TMEM to the next tile's MMAs, and then rounds
+// and adds the tile into E while those run.  (d + 1) 2^14 128 < 2^24 keeps every accumulator exact for
+// d <= 6; the fixed point has F = 55 fractional bits (the bound of the K = 64 kernel, doubled).
+// ---------------------------------------------------------------------------------------------
+constexpr int U2K = 128;                       // K of one launch (two pivot blocks)
+constexpr int U2A_SLOT = UBM * U2K * 2;        // 32 KB: one A plane of a row block
+constexpr int U2B_SLOT = UBN * U2K * 2;        // 16 KB: one B plane of a column block
+constexpr int U2A_RING = 2, U2B_RING = 6;
+constexpr int kUpd2F = 55;
+constexpr size_t kUpd2Smem =
+    1024 + (size_t)U2A_RING * U2A_SLOT + (size_t)U2B_RING * U2B_SLOT + (size_t)UBM * UBN * 8 + 256;
+static_assert(kUpd2Smem <= 232448, "128-deep update kernel shared memory");
+
+// |v| <= (d + 1) 2^14 128 for diagonal d of a 128-deep tile: the bit-pattern conversion holds for d <= 1.
+__device__ __forceinline__ int diag128_to_int(float v, int d) {
+    return d <= 1 ? __float_as_int(v + 12582912.0f) - 0x4B400000 : __float2int_rn(v);
+}
+
+template <int ND>
+__global__ void __launch_bounds__(OTHREADS, 1)
+oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, UpdParams p,
+                    uint32_t idesc) {
+    static_assert(ND >= 4 && ND <= kOzSlices, "update digits");
+    if (p.halt != nullptr && *(volatile const int*)p.halt != 0) return;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = base;
+    uint8_t* sB = sA + U2A_RING * U2A_SLOT;
+    double* stg = reinterpret_cast<double*>(sB + U2B_RING * U2B_SLOT);  // 128 x 64, columns XOR-swizzled
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(stg + UBM * UBN);      // [U2A_RING]
+    uint64_t* emptyA = fullA + U2A_RING;
+    uint64_t* fullB = emptyA + U2A_RING;  // [U2B_RING]
+    uint64_t* emptyB = fullB + U2B_RING;
+    uint64_t* tfull = emptyB + U2B_RING;  // the tile's MMAs have completed
+    uint64_t* tempty = tfull + 1;         // the epilogue has drained TMEM
+    uint64_t* mmaEnd = tempty + 1;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mmaEnd + 1);
+    __shared__ int aborted;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ double piv_rp;
+    // with a fused pivot block (one system), CTA 0 takes tile 0, which holds it, alone
+    const int tiles_all = p.tiles * p.count;
+    int t0, t1;
+    if (p.D != nullptr && gridDim.x > 1 && p.count == 1) {
+        t0 = (blockIdx.x == 0) ? 0 : 1 + (int)((long long)(blockIdx.x - 1) * (p.tiles - 1) / (gridDim.x - 1));
+        t1 = 1 + (int)((long long)blockIdx.x * (p.tiles - 1) / (gridDim.x - 1));
+    } else {
+        t0 = (int)((long long)blockIdx.x * tiles_all / gridDim.x);
+        t1 = (int)((long long)(blockIdx.x + 1) * tiles_all / gridDim.x);
+    }
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < U2A_RING; ++i) {
+            mbar_init(fullA + i, 1);
+            mbar_init(emptyA + i, 1);
+        }
+        for (int i = 0; i < U2B_RING; ++i) {
+            mbar_init(fullB + i, 1);
+            mbar_init(emptyB + i, 1);
+        }
+        mbar_init(tfull, 1);
+        mbar_init(tempty, OEPI);
+        mbar_init(mmaEnd, 1);
+        aborted = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_holder;
+    const unsigned long long deadline = now_ns() + kOzWaitNs;
+
+    if (warp == OEPI) {
+        if (lane == 0) {  // TMA producer: per tile, A plane p, then the B planes it pairs with
+            int ia = 0, ib = 0;
+            bool ok = true;
+            for (int t = t0; t < t1 && ok; ++t) {
+                const int z = t / p.tiles, tl = t - z * p.tiles;
+                const int mb = tl / p.tiles_n, nb = tl % p.tiles_n;
+                for (int pa = 0; pa < ND && ok; ++pa, ++ia) {
+                    const int sa = ia % U2A_RING;
+                    if (!mbar_wait_idle(emptyA + sa, (uint32_t)(((ia / U2A_RING) & 1) ^ 1), deadline)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(fullA + sa, U2A_SLOT);
+                    const int ya = (z * ND + pa) * p.Mp + mb * UBM;
+                    tma_load_2d(sA + sa * U2A_SLOT, &tA, 0, ya, fullA + sa);
+                    tma_load_2d(sA + sa * U2A_SLOT + U2A_SLOT / 2, &tA, OBK, ya, fullA + sa);
+                    for (int q = 0; q < ND - pa; ++q, ++ib) {
+                        const int sb = ib % U2B_RING;
+                        if (!mbar_wait_idle(emptyB + sb, (uint32_t)(((ib / U2B_RING) & 1) ^ 1), deadline)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(fullB + sb, U2B_SLOT);
+                        const int yb = (z * ND + q) * p.Np + nb * UBN;
+                        tma_load_2d(sB + sb * U2B_SLOT, &tB, 0, yb, fullB + sb);
+                        tma_load_2d(sB + sb * U2B_SLOT + U2B_SLOT / 2, &tB, OBK, yb, fullB + sb);
+                    }
+                }
+            }
+            if (!ok) atomicExch(&aborted, 1);
+            // the copies issued last must land before the CTA can leave
+            const unsigned long long d2 = now_ns() + kOzWaitNs;
+            for (int j = ia - U2A_RING < 0 ? 0 : ia - U2A_RING; j < ia; ++j)
+                (void)mbar_wait(fullA + j % U2A_RING, (uint32_t)((j / U2A_RING) & 1), d2);
+            for (int j = ib - U2B_RING < 0 ? 0 : ib - U2B_RING; j < ib; ++j)
+                (void)mbar_wait(fullB + j % U2B_RING, (uint32_t)((j / U2B_RING) & 1), d2);
+        }
+    } else if (warp == OEPI + 1) {
+        if (lane == 0) {  // MMA issuer
+            int ia = 0, ib = 0, u = 0;
+            bool ok = true;
+            for (int t = t0; t < t1 && ok; ++t, ++u) {
+                if (!mbar_wait(tempty, (uint32_t)((u & 1) ^ 1), deadline)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int pa = 0; pa < ND && ok; ++pa, ++ia) {
+                    const int sa = ia % U2A_RING;
+                    if (!mbar_wait(fullA + sa, (uint32_t)((ia / U2A_RING) & 1), deadline)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    for (int q = 0; q < ND - pa; ++q, ++ib) {
+                        const int sb = ib % U2B_RING;
+                        if (!mbar_wait(fullB + sb, (uint32_t)((ib / U2B_RING) & 1), deadline)) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t dcol = tmem + (uint32_t)((pa + q) * UBN);
+#pragma unroll
+                        for (int h = 0; h < U2K / OBK; ++h) {
+                            const uint64_t ad = smem_desc(smem_u32(sA + sa * U2A_SLOT + h * (U2A_SLOT / 2)));
+                            const uint64_t bd = smem_desc(smem_u32(sB + sb * U2B_SLOT + h * (U2B_SLOT / 2)));
+#pragma unroll
+                            for (int kk = 0; kk < OBK / 16; ++kk)
+                                mma_f16(dcol, ad + 2 * kk, bd + 2 * kk, idesc, (pa > 0 || h > 0 || kk > 0) ? 1u : 0u);
+                        }
+                        mma_commit(emptyB + sb);
+                    }
+                    mma_commit(emptyA + sa);
+                }
+                if (ok) mma_commit(tfull);
+            }
+            if (!ok) atomicExch(&aborted, 1);
+            mma_commit(mmaEnd);  // arrives once every MMA issued above has completed
+            (void)mbar_wait(mmaEnd, 0u, now_ns() + kOzWaitNs);
+        }
+    } else {
+        // epilogue warps 0-15: TMEM lane quadrant (tile rows) and group of 16 columns
+        const int quad = warp & 3, cg = warp >> 2;
+        const int r = quad * 32 + lane;
+        int u = 0;
+        bool ok = true;
+        for (int t = t0; t < t1; ++t, ++u) {
+            const int z = t / p.tiles, tl = t - z * p.tiles;
+            const int mb = tl / p.tiles_n, nb = tl % p.tiles_n;
+            double* const C = p.C + (int64_t)z * p.sC;
+            const int* const ea = p.ea + (int64_t)z * p.Mp;
+            const int* const eb = p.eb + (int64_t)z * p.Np;
+            if (p.mode != 0 && p.beta != 0.0) {
+                const int row = mb * UBM + (threadIdx.x >> 2), col = nb * UBN + (threadIdx.x & 3) * 16;
+                if (row < p.M && col < p.N)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(C + (int64_t)row * p.ldc + col));
+            }
+            long long acc[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = 0;
+            if (!mbar_wait_idle(tfull, (uint32_t)(u & 1), deadline)) {
+                atomicExch(&aborted, 1);
+                ok = false;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (ok) {
+                const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cg * 16);
+                // diagonals 0 and 1, then 2 and 3, two at a time (v_a 2^8 + v_b is exact in int32 while
+                // |v_a| <= 3 2^21), the others one at a time; diagonal 6's weight is below the last bit
+#pragma unroll
+                for (int d = 0; d < 4; d += 2) {
+                    float va[16], vb[16];
+                    tmem_ld16x2(tq + d * UBN, tq + (d + 1) * UBN, va, vb);
+                    const int shb = kUpd2F - 8 * (d + 1) - 14;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        acc[j] += (long long)(diag128_to_int(va[j], d) * 256 + diag128_to_int(vb[j], d + 1)) << shb;
+                }
+#pragma unroll
+                for (int d = 4; d < ND; ++d) {
+                    const int sh = kUpd2F - 8 * d - 14;
+                    const float rscale = __int_as_float((127 + (sh < 0 ? sh : 0)) << 23);
+                    const int lsh = sh > 0 ? sh : 0;
+                    float v[16];
+                    tmem_ld16(tq + d * UBN, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[j] += (long long)__float2int_rn(v[j] * rscale) << lsh;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty);  // the next tile's MMAs may start
+            if (ok) {
+                const int row = mb * UBM + r;
+                const int er = (row < p.M) ? ea[row] : 0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int c = cg * 16 + j, col = nb * UBN + c;
+                    const int ec = (col < p.N) ? eb[col] : 0;
+                    stg[r * UBN + (c ^ (r & 15))] = fixed_to_double(p.alpha_sign * acc[j], er + ec - kUpd2F);
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(OEPI * 32) : "memory");
+            if (!*(volatile int*)&aborted) {
+                constexpr int NR = UBM / OEPI, NG = 4, NH = UBN / 32;
+                const bool need_c = p.mode != 0 && p.beta != 0.0;
+#pragma unroll
+                for (int g0 = 0; g0 < NR; g0 += NG) {
+                    double cv[NG][NH];
+#pragma unroll
+                    for (int i = 0; i < NG; ++i)
+#pragma unroll
+                        for (int h = 0; h < NH; ++h) {
+                            const int row = mb * UBM + warp + OEPI * (g0 + i), col = nb * UBN + h * 32 + lane;
+                            cv[i][h] = (need_c && row < p.M && col < p.N) ? C[(int64_t)row * p.ldc + col] : 0.0;
+                        }
+#pragma unroll
+                    for (int i = 0; i < NG; ++i)
+#pragma unroll
+                        for (int h = 0; h < NH; ++h) {
+                            const int rr = warp + OEPI * (g0 + i), c = h * 32 + lane;
+                            const int row = mb * UBM + rr, col = nb * UBN + c;
+                            if (row < p.M && col < p.N) {
+                                const double v = stg[rr * UBN + (c ^ (rr & 15))];
+                                double out;
+                                if (p.mode == 0)
+                                    out = v;
+                                else if (p.mode == 1)
+                                    out = cv[i][h] + v;
+                                else
+                                    out = (p.beta == 0.0) ? p.alpha * v : fma(p.beta, cv[i][h], p.alpha * v);
+                                C[(int64_t)row * p.ldc + col] = out;
+                            }
+                        }
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(OEPI * 32) : "memory");  // the staging area is reused
+            if (p.D != nullptr && tl == 0) {
+                // tile 0 holds the next pivot block: factor it in the staging area (as the 64-deep kernel does)
+                double* a = stg;
+                double* const D = p.D + (int64_t)z * p.sC;
+                const int tid = threadIdx.x;
+                for (int i = tid >> 6; i < p.bd; i += (OEPI * 32) / 64)
+                    if ((tid & 63) < p.bd) a[i * kPivotLds + (tid & 63)] = D[i * p.ldd + (tid & 63)];
+                EpiSync{}();
+                const int broke = pivot_block_genp<double, OEPI * 32>(a, p.bd, &piv_rp, tid, EpiSync{});
+                if (broke != 0) {
+                    if (tid == 0) {
+                        atomicMin(p.dinfo + (int64_t)z * p.sFlag, (int)(p.dk + broke));
+                        atomicExch(p.dhalt + (int64_t)z * p.sFlag, 1);
+                    }
+                } else {
+                    for (int i = tid >> 6; i < p.bd; i += (OEPI * 32) / 64)
+                        if ((tid & 63) < p.bd) D[i * p.ldd + (tid & 63)] = a[i * kPivotLds + (tid & 63)];
+                }
+                EpiSync{}();
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (aborted && threadIdx.x == 0 && p.err != nullptr) atomicExch(p.err, (int)RMGE_ERR_TIMEOUT);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
+// ---------------------------------------------------------------------------------------------
 // Digit planes.  Row (trans = false) or column (trans = true) exponents of the source, then s BF16
 // planes of rows_p x kp (K-major, zero padded): plane[p][r][k].
 // ---------------------------------------------------------------------------------------------
@@ -860,41 +1153,48 @@ __global__ void col_digits_kernel(int64_t rows, int64_t cols, const double* __re
     }
 }
 
-// K <= 64 (one K block): the exponent and the digits of a row in one pass, one warp per padded row
-// (lanes hold k = lane and lane + 32).
-__device__ void row_prep64(int64_t bid, int64_t rows, int cols, const double* __restrict__ src, int64_t lds,
-                           const unsigned long long* __restrict__ kmaxA, const unsigned long long* __restrict__ kmaxB,
-                           int s, int64_t rows_p, int* __restrict__ e, __nv_bfloat16* __restrict__ planes) {
+// K <= KW (KW = 64: one K block; 128: two pivot blocks): the exponent and the digits of a row in one pass,
+// one warp per padded row (lane l holds k = l + 32 i).
+template <int KW>
+__device__ void row_prep(int64_t bid, int64_t rows, int cols, const double* __restrict__ src, int64_t lds,
+                         const unsigned long long* __restrict__ kmaxA, const unsigned long long* __restrict__ kmaxB,
+                         int s, int64_t rows_p, int* __restrict__ e, __nv_bfloat16* __restrict__ planes) {
+    constexpr int NV = KW / 32;
     const int lane = threadIdx.x & 31;
     const int64_t r = (bid * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (r >= rows_p) return;
     const bool live = r < rows;
-    const int k0 = lane, k1 = lane + 32;
-    const double v0 = (live && k0 < cols) ? src[r * lds + k0] : 0.0;
-    const double v1 = (live && k1 < cols) ? src[r * lds + k1] : 0.0;
-    const int t0 = (k0 < cols) ? bal_shift(kmaxA, kmaxB, k0) : 0;
-    const int t1 = (k1 < cols) ? bal_shift(kmaxA, kmaxB, k1) : 0;
-    int m = max(entry_exp(v0, t0), entry_exp(v1, t1));
+    double v[NV];
+    int t[NV];
+    int m = INT_MIN;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const int k = lane + 32 * i;
+        v[i] = (live && k < cols) ? src[r * lds + k] : 0.0;
+        t[i] = (k < cols) ? bal_shift(kmaxA, kmaxB, k) : 0;
+        m = max(m, entry_exp(v[i], t[i]));
+    }
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     const int er = (m == INT_MIN) ? 0 : m;
     if (lane == 0 && live) e[r] = er;
-    const int64_t total = rows_p * 64;
-    store_digits(v0, er - t0, s, planes + r * 64 + k0, total);
-    store_digits(v1, er - t1, s, planes + r * 64 + k1, total);
+    const int64_t total = rows_p * KW;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) store_digits(v[i], er - t[i], s, planes + r * KW + lane + 32 * i, total);
 }
 
-// K <= 64: the exponent and the (transposed) digits of 32 columns per block; 256 threads = 32 columns x
+// K <= KW: the exponent and the (transposed) digits of 32 columns per block; 256 threads = 32 columns x
 // 8 row groups for the exponent, then consecutive threads along k for the digit stores.
-__device__ void col_prep64(int64_t bid, int rows, int64_t cols, const double* __restrict__ src, int64_t lds,
-                           const unsigned long long* __restrict__ kmaxA, const unsigned long long* __restrict__ kmaxB,
-                           int s, int64_t cols_p, int* __restrict__ e, __nv_bfloat16* __restrict__ planes) {
-    __shared__ double t[64][33];
+template <int KW>
+__device__ void col_prep(int64_t bid, int rows, int64_t cols, const double* __restrict__ src, int64_t lds,
+                         const unsigned long long* __restrict__ kmaxA, const unsigned long long* __restrict__ kmaxB,
+                         int s, int64_t cols_p, int* __restrict__ e, __nv_bfloat16* __restrict__ planes) {
+    __shared__ double t[KW][33];
     __shared__ int part[8][32];
-    __shared__ int tk[64];
+    __shared__ int tk[KW];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int64_t c0 = bid * 32, c = c0 + tx;
-    if (threadIdx.x < 64) tk[threadIdx.x] = ((int)threadIdx.x < rows) ? bal_shift(kmaxA, kmaxB, threadIdx.x) : 0;
-    for (int i = ty; i < 64; i += 8) t[i][tx] = (i < rows && c < cols) ? src[(int64_t)i * lds + c] : 0.0;
+    for (int i = threadIdx.x; i < KW; i += 256) tk[i] = (i < rows) ? bal_shift(kmaxA, kmaxB, i) : 0;
+    for (int i = ty; i < KW; i += 8) t[i][tx] = (i < rows && c < cols) ? src[(int64_t)i * lds + c] : 0.0;
     __syncthreads();
     int m = INT_MIN;
     for (int i = ty; i < rows; i += 8) m = max(m, entry_exp(t[i][tx], -tk[i]));
@@ -907,23 +1207,24 @@ __device__ void col_prep64(int64_t bid, int rows, int64_t cols, const double* __
         if (c < cols) e[c] = part[0][tx];
     }
     __syncthreads();
-    const int64_t total = cols_p * 64;
-    for (int idx = threadIdx.x; idx < 32 * 64; idx += 256) {
-        const int cl = idx >> 6, k = idx & 63;
+    const int64_t total = cols_p * KW;
+    for (int idx = threadIdx.x; idx < 32 * KW; idx += 256) {
+        const int cl = idx / KW, k = idx % KW;
         if (c0 + cl < cols_p)
             store_digits(t[k][cl], (c0 + cl < cols && k < rows) ? part[0][cl] + tk[k] : 0, s,
-                         planes + (c0 + cl) * 64 + k, total);
+                         planes + (c0 + cl) * KW + k, total);
     }
 }
 
-// Both operands of a K <= 64 product in one launch: blocks [0, row_blocks) prepare the rows of A, the
-// rest the columns of B (one launch less per GENP step).
-__global__ void prep64_kernel(int64_t row_blocks, int64_t M, int64_t N, int K, const double* __restrict__ A,
-                              int64_t lda, const double* __restrict__ B, int64_t ldb,
-                              const unsigned long long* __restrict__ kmaxA,
-                              const unsigned long long* __restrict__ kmaxB, int s, int64_t Mp, int64_t Np,
-                              int* __restrict__ ea, int* __restrict__ eb, __nv_bfloat16* __restrict__ pa,
-                              __nv_bfloat16* __restrict__ pb, BatchOff boA, BatchOff boB) {
+// Both operands of a K <= KW product in one launch: blocks [0, row_blocks) prepare the rows of A, the
+// rest the columns of B (one launch instead of four per GENP step).
+template <int KW>
+__global__ void prep_kernel(int64_t row_blocks, int64_t M, int64_t N, int K, const double* __restrict__ A,
+                            int64_t lda, const double* __restrict__ B, int64_t ldb,
+                            const unsigned long long* __restrict__ kmaxA,
+                            const unsigned long long* __restrict__ kmaxB, int s, int64_t Mp, int64_t Np,
+                            int* __restrict__ ea, int* __restrict__ eb, __nv_bfloat16* __restrict__ pa,
+                            __nv_bfloat16* __restrict__ pb, BatchOff boA, BatchOff boB) {
     const int64_t z = blockIdx.y;
     A += z * boA.src;
     B += z * boB.src;
@@ -936,9 +1237,9 @@ __global__ void prep64_kernel(int64_t row_blocks, int64_t M, int64_t N, int K, c
         kmaxB += z * boA.kmax;
     }
     if ((int64_t)blockIdx.x < row_blocks)
-        row_prep64(blockIdx.x, M, K, A, lda, kmaxA, kmaxB, s, Mp, ea, pa);
+        row_prep<KW>(blockIdx.x, M, K, A, lda, kmaxA, kmaxB, s, Mp, ea, pa);
     else
-        col_prep64((int64_t)blockIdx.x - row_blocks, K, N, B, ldb, kmaxA, kmaxB, s, Np, eb, pb);
+        col_prep<KW>((int64_t)blockIdx.x - row_blocks, K, N, B, ldb, kmaxA, kmaxB, s, Np, eb, pb);
 }
 
 unsigned grid_for(int64_t work) {
@@ -980,6 +1281,19 @@ rmge_status launch_update(const CUtensorMap& ta, const CUtensorMap& tb, const Up
     return RMGE_OK;
 }
 
+template <int ND>
+rmge_status launch_update128(const CUtensorMap& ta, const CUtensorMap& tb, const UpdParams& u, uint32_t idesc,
+                             int grid, cudaStream_t st) {
+    if (cudaFuncSetAttribute(oz_update128_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpd2Smem) !=
+        cudaSuccess) {
+        (void)cudaGetLastError();
+        return RMGE_ERR_CUDA;
+    }
+    oz_update128_kernel<ND><<<grid, OTHREADS, kUpd2Smem, st>>>(ta, tb, u, idesc);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
 rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* planesA, void* planesB,
                     int* ea, int* eb, const unsigned long long* kmaxA, const unsigned long long* kmaxB, int* err,
@@ -1001,7 +1315,7 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
     const BatchOff boA{bt.sA, bt.sK, Mp, (int64_t)s * Mp * Kp}, boB{bt.sB, bt.sK, Np, (int64_t)s * Np * Kp};
     if (Kp == OBK) {
         const int64_t row_blocks = (Mp * 32 + 255) / 256, col_blocks = Np / 32;
-        prep64_kernel<<<dim3((unsigned)(row_blocks + col_blocks), nz), 256, 0, st>>>(
+        prep_kernel<64><<<dim3((unsigned)(row_blocks + col_blocks), nz), 256, 0, st>>>(
             row_blocks, M, N, (int)K, A, lda, B, ldb, kmaxA, kmaxB, s, Mp, Np, ea, eb, pa, pb, boA, boB);
         RMGE_LAUNCH_CHECK();
     } else {
@@ -1106,6 +1420,75 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
     oz_gemm_kernel<<<dim3((unsigned)((Np / OBN) * (Mp / OBM)), nz), OTHREADS, kOzSmem, st>>>(ta, tb, prm, idesc);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
+}
+
+rmge_status oz_update128(int64_t M, int64_t N, int s, const double* A, int64_t lda, const double* B, int64_t ldb,
+                         double* C, int64_t ldc, void* planesA, void* planesB, int* ea, int* eb,
+                         const unsigned long long* kmaxA, const unsigned long long* kmaxB, int* err, const int* halt,
+                         cudaStream_t st, const OzFuse* fuse, const OzBatch& bt) {
+    if (bt.count < 1 || bt.count > 65535 || s < 4 || s > kOzSlices || (kmaxA == nullptr) != (kmaxB == nullptr))
+        return RMGE_ERR_INVALID_ARG;
+    if (fuse != nullptr && (fuse->D == nullptr || fuse->b < 1 || fuse->b > UBN || fuse->b > M || fuse->b > N ||
+                            fuse->info == nullptr || fuse->halt == nullptr))
+        return RMGE_ERR_INVALID_ARG;
+    if (M <= 0 || N <= 0) return RMGE_OK;
+    if (M > INT32_MAX / 16 || N > INT32_MAX / 16) return RMGE_ERR_INVALID_ARG;
+    constexpr int64_t K = U2K, Kp = U2K;
+    const int64_t Mp = (M + 127) / 128 * 128, Np = (N + 127) / 128 * 128;
+    __nv_bfloat16* pa = static_cast<__nv_bfloat16*>(planesA);
+    __nv_bfloat16* pb = static_cast<__nv_bfloat16*>(planesB);
+    const unsigned nz = (unsigned)bt.count;
+    const BatchOff boA{bt.sA, bt.sK, Mp, (int64_t)s * Mp * Kp}, boB{bt.sB, bt.sK, Np, (int64_t)s * Np * Kp};
+    {
+        const int64_t row_blocks = (Mp * 32 + 255) / 256, col_blocks = Np / 32;
+        prep_kernel<U2K><<<dim3((unsigned)(row_blocks + col_blocks), nz), 256, 0, st>>>(
+            row_blocks, M, N, (int)K, A, lda, B, ldb, kmaxA, kmaxB, s, Mp, Np, ea, eb, pa, pb, boA, boB);
+        RMGE_LAUNCH_CHECK();
+    }
+    CUtensorMap ta, tb;
+    if (!tc_make_map(&ta, pa, true, (int64_t)bt.count * s * Mp, Kp, Kp, UBM) ||
+        !tc_make_map(&tb, pb, true, (int64_t)bt.count * s * Np, Kp, Kp, UBN))
+        return RMGE_ERR_CUDA;
+    UpdParams u{};
+    u.M = (int)M;
+    u.N = (int)N;
+    u.count = bt.count;
+    u.sC = bt.sC;
+    u.sFlag = bt.sFlag;
+    u.F = kUpd2F;
+    u.Mp = (int)Mp;
+    u.Np = (int)Np;
+    u.tiles_n = (int)((N + UBN - 1) / UBN);
+    u.tiles = (int)((M + UBM - 1) / UBM) * u.tiles_n;
+    u.ea = ea;
+    u.eb = eb;
+    u.alpha_sign = -1;  // E - A B: mode 1 (alpha = -1, beta = 1)
+    u.mode = 1;
+    u.alpha = 1.0;
+    u.beta = 1.0;
+    u.C = C;
+    u.ldc = ldc;
+    u.err = err;
+    u.halt = bt.count == 1 ? halt : nullptr;
+    if (fuse != nullptr) {
+        u.D = fuse->D;
+        u.ldd = fuse->ldd;
+        u.bd = fuse->b;
+        u.dk = fuse->k;
+        u.dinfo = fuse->info;
+        u.dhalt = fuse->halt;
+    }
+    // idesc: FP32 accumulate, BF16 A and B, both K-major, N = 64, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UBN >> 3) << 17) |
+                           ((uint32_t)(UBM >> 4) << 24);
+    const int64_t all = (int64_t)u.tiles * bt.count;
+    const int grid = all < sm_count() ? (int)all : sm_count();
+    switch (s) {
+        case 4: return launch_update128<4>(ta, tb, u, idesc, grid, st);
+        case 5: return launch_update128<5>(ta, tb, u, idesc, grid, st);
+        case 6: return launch_update128<6>(ta, tb, u, idesc, grid, st);
+        default: return launch_update128<7>(ta, tb, u, idesc, grid, st);
+    }
 }
 
 }  // namespace rmge

@@ -71,7 +71,15 @@ def test_emulated_factor_backward_error(orc, n):
     assert be <= 1e-13, be
     ref, _ = orc.genp(M)
     g = orc.growth(M, ref)
-    assert abs(float(host(growth)[0]) - g) <= 1e-6 * g
+    # blocked factorizations differ from the unblocked oracle by rounding amplified by growth (Sec. 3: the
+    # same Schur complements in exact arithmetic only); the native FP64 blocked factorization of the same
+    # M sets that scale
+    Md64 = dev(M)
+    rmge.factor(Md64, "f64")
+    e64 = np.max(np.abs(host(Md64) - ref)) / np.max(np.abs(ref))
+    err = np.max(np.abs(LU - ref)) / np.max(np.abs(ref))
+    assert err <= 64 * e64 + 1e-15, (err, e64)
+    assert abs(float(host(growth)[0]) - g) <= 2 * err * np.max(np.abs(ref)) / np.max(np.abs(M)) + 1e-12 * g
 
 
 def test_emulated_factor_matches_oracle_at_bench_size(orc):
