@@ -695,22 +695,31 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__
 
 // ---------------------------------------------------------------------------------------------
 // Products with K = 128: the Schur update of two pivot steps at once, E -= [L21_k L21_k+1] [U12_k; U12_k+1]
-// (GENP with one step of look-ahead).  A persistent CTA walks its share of 128 x 64 output tiles.  Per tile
-// it streams, for each A digit plane p (128 rows x 128 K, 32 KB, two 64-wide boxes), the B planes
-// q = 0 .. ND-1-p (64 columns x 128 K, 16 KB), so that every A plane crosses from L2 once per tile; each pair
-// adds into the 64-column TMEM accumulator of its diagonal p + q, all ND diagonals at once (ND x 64 <= 448
-// columns).  The epilogue drains the diagonals, releases TMEM to the next tile's MMAs, and then rounds
-// and adds the tile into E while those run.  (d + 1) 2^14 128 < 2^24 keeps every accumulator exact for
-// d <= 6; the fixed point has F = 55 fractional bits (the bound of the K = 64 kernel, doubled).
+// (GENP with one step of look-ahead).  A persistent CTA walks its share of 128 x 64 output tiles.
+// - The ND B digit planes of a tile (64 columns x 128 K, 16 KB each) sit in ND slots, one per plane; the A
+//   planes (128 rows x 128 K, 32 KB) stream through a ring.  Per tile that is ND + ND loads (288 KB at
+//   ND = 6) instead of one B load per digit pair.
+// - Pairs run A plane by A plane, p = 0 .. ND-1, and within one in descending q, so B plane q is last
+//   read by pair (ND-1-q, q): B planes ND-1, ND-2, ... are refilled for the next tile while this one is
+//   still multiplying, and the next tile starts with the planes refilled first.
+// - Each pair adds into the 64-column TMEM accumulator of its diagonal p + q (ND x 64 <= 448 columns).  The
+//   epilogue drains the diagonals, releases TMEM to the next tile's MMAs, then rounds and adds the tile
+//   into E while those run, through a half-tile staging area in two rounds.
+// (d + 1) 2^14 128 < 2^24 keeps every accumulator exact for d <= 6; the fixed point has F = 55 fractional
+// bits (the bound of the K = 64 kernel, doubled).
 // ---------------------------------------------------------------------------------------------
 constexpr int U2K = 128;                       // K of one launch (two pivot blocks)
 constexpr int U2A_SLOT = UBM * U2K * 2;        // 32 KB: one A plane of a row block
 constexpr int U2B_SLOT = UBN * U2K * 2;        // 16 KB: one B plane of a column block
-constexpr int U2A_RING = 2, U2B_RING = 6;
+constexpr int U2STG = 64 * kPivotLds * 8 > UBM * 32 * 8 ? 64 * kPivotLds * 8 : UBM * 32 * 8;  // half tile, or pivot
 constexpr int kUpd2F = 55;
-constexpr size_t kUpd2Smem =
-    1024 + (size_t)U2A_RING * U2A_SLOT + (size_t)U2B_RING * U2B_SLOT + (size_t)UBM * UBN * 8 + 256;
-static_assert(kUpd2Smem <= 232448, "128-deep update kernel shared memory");
+template <int ND>
+struct Upd2Cfg {
+    static constexpr int kARing = ND == 7 ? 2 : 3;
+    static constexpr size_t kSmem =
+        1024 + (size_t)kARing * U2A_SLOT + (size_t)ND * U2B_SLOT + (size_t)U2STG + 256;
+    static_assert(kSmem <= 232448, "128-deep update kernel shared memory");
+};
 
 // |v| <= (d + 1) 2^14 128 for diagonal d of a 128-deep tile: the bit-pattern conversion holds for d <= 1.
 __device__ __forceinline__ int diag128_to_int(float v, int d) {
@@ -722,24 +731,25 @@ __global__ void __launch_bounds__(OTHREADS, 1)
 oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, UpdParams p,
                     uint32_t idesc) {
     static_assert(ND >= 4 && ND <= kOzSlices, "update digits");
+    constexpr int AR = Upd2Cfg<ND>::kARing;
     if (p.halt != nullptr && *(volatile const int*)p.halt != 0) return;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = base;
-    uint8_t* sB = sA + U2A_RING * U2A_SLOT;
-    double* stg = reinterpret_cast<double*>(sB + U2B_RING * U2B_SLOT);  // 128 x 64, columns XOR-swizzled
-    uint64_t* fullA = reinterpret_cast<uint64_t*>(stg + UBM * UBN);      // [U2A_RING]
-    uint64_t* emptyA = fullA + U2A_RING;
-    uint64_t* fullB = emptyA + U2A_RING;  // [U2B_RING]
-    uint64_t* emptyB = fullB + U2B_RING;
-    uint64_t* tfull = emptyB + U2B_RING;  // the tile's MMAs have completed
-    uint64_t* tempty = tfull + 1;         // the epilogue has drained TMEM
+    uint8_t* sB = sA + AR * U2A_SLOT;
+    double* stg = reinterpret_cast<double*>(sB + ND * U2B_SLOT);  // 128 x 32, columns XOR-swizzled by row
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(stg) + U2STG);  // [AR]
+    uint64_t* emptyA = fullA + AR;
+    uint64_t* fullB = emptyA + AR;  // [ND]
+    uint64_t* emptyB = fullB + ND;
+    uint64_t* tfull = emptyB + ND;  // the tile's MMAs have completed
+    uint64_t* tempty = tfull + 1;   // the epilogue has drained TMEM
     uint64_t* mmaEnd = tempty + 1;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mmaEnd + 1);
     __shared__ int aborted;
+    __shared__ double piv_rp;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ double piv_rp;
     // with a fused pivot block (one system), CTA 0 takes tile 0, which holds it, alone
     const int tiles_all = p.tiles * p.count;
     int t0, t1;
@@ -752,11 +762,11 @@ oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constan
     }
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < U2A_RING; ++i) {
+        for (int i = 0; i < AR; ++i) {
             mbar_init(fullA + i, 1);
             mbar_init(emptyA + i, 1);
         }
-        for (int i = 0; i < U2B_RING; ++i) {
+        for (int i = 0; i < ND; ++i) {
             mbar_init(fullB + i, 1);
             mbar_init(emptyB + i, 1);
         }
@@ -779,15 +789,15 @@ oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constan
     const unsigned long long deadline = now_ns() + kOzWaitNs;
 
     if (warp == OEPI) {
-        if (lane == 0) {  // TMA producer: per tile, A plane p, then the B planes it pairs with
-            int ia = 0, ib = 0;
+        if (lane == 0) {  // TMA producer, in the MMA warp's order: A_0, B_ND-1 .. B_0, then A_1 .. A_ND-1
+            int ia = 0, u = 0;
             bool ok = true;
-            for (int t = t0; t < t1 && ok; ++t) {
+            for (int t = t0; t < t1 && ok; ++t, ++u) {
                 const int z = t / p.tiles, tl = t - z * p.tiles;
                 const int mb = tl / p.tiles_n, nb = tl % p.tiles_n;
                 for (int pa = 0; pa < ND && ok; ++pa, ++ia) {
-                    const int sa = ia % U2A_RING;
-                    if (!mbar_wait_idle(emptyA + sa, (uint32_t)(((ia / U2A_RING) & 1) ^ 1), deadline)) {
+                    const int sa = ia % AR;
+                    if (!mbar_wait_idle(emptyA + sa, (uint32_t)(((ia / AR) & 1) ^ 1), deadline)) {
                         ok = false;
                         break;
                     }
@@ -795,30 +805,30 @@ oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constan
                     const int ya = (z * ND + pa) * p.Mp + mb * UBM;
                     tma_load_2d(sA + sa * U2A_SLOT, &tA, 0, ya, fullA + sa);
                     tma_load_2d(sA + sa * U2A_SLOT + U2A_SLOT / 2, &tA, OBK, ya, fullA + sa);
-                    for (int q = 0; q < ND - pa; ++q, ++ib) {
-                        const int sb = ib % U2B_RING;
-                        if (!mbar_wait_idle(emptyB + sb, (uint32_t)(((ib / U2B_RING) & 1) ^ 1), deadline)) {
-                            ok = false;
-                            break;
+                    if (pa == 0)
+                        for (int q = ND - 1; q >= 0; --q) {
+                            if (!mbar_wait_idle(emptyB + q, (uint32_t)((u & 1) ^ 1), deadline)) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_expect_tx(fullB + q, U2B_SLOT);
+                            const int yb = (z * ND + q) * p.Np + nb * UBN;
+                            tma_load_2d(sB + q * U2B_SLOT, &tB, 0, yb, fullB + q);
+                            tma_load_2d(sB + q * U2B_SLOT + U2B_SLOT / 2, &tB, OBK, yb, fullB + q);
                         }
-                        mbar_expect_tx(fullB + sb, U2B_SLOT);
-                        const int yb = (z * ND + q) * p.Np + nb * UBN;
-                        tma_load_2d(sB + sb * U2B_SLOT, &tB, 0, yb, fullB + sb);
-                        tma_load_2d(sB + sb * U2B_SLOT + U2B_SLOT / 2, &tB, OBK, yb, fullB + sb);
-                    }
                 }
             }
             if (!ok) atomicExch(&aborted, 1);
             // the copies issued last must land before the CTA can leave
             const unsigned long long d2 = now_ns() + kOzWaitNs;
-            for (int j = ia - U2A_RING < 0 ? 0 : ia - U2A_RING; j < ia; ++j)
-                (void)mbar_wait(fullA + j % U2A_RING, (uint32_t)((j / U2A_RING) & 1), d2);
-            for (int j = ib - U2B_RING < 0 ? 0 : ib - U2B_RING; j < ib; ++j)
-                (void)mbar_wait(fullB + j % U2B_RING, (uint32_t)((j / U2B_RING) & 1), d2);
+            for (int j = ia - AR < 0 ? 0 : ia - AR; j < ia; ++j)
+                (void)mbar_wait(fullA + j % AR, (uint32_t)((j / AR) & 1), d2);
+            if (u > 0)
+                for (int q = 0; q < ND; ++q) (void)mbar_wait(fullB + q, (uint32_t)((u - 1) & 1), d2);
         }
     } else if (warp == OEPI + 1) {
         if (lane == 0) {  // MMA issuer
-            int ia = 0, ib = 0, u = 0;
+            int ia = 0, u = 0;
             bool ok = true;
             for (int t = t0; t < t1 && ok; ++t, ++u) {
                 if (!mbar_wait(tempty, (uint32_t)((u & 1) ^ 1), deadline)) {
@@ -827,29 +837,30 @@ oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constan
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int pa = 0; pa < ND && ok; ++pa, ++ia) {
-                    const int sa = ia % U2A_RING;
-                    if (!mbar_wait(fullA + sa, (uint32_t)((ia / U2A_RING) & 1), deadline)) {
+                    const int sa = ia % AR;
+                    if (!mbar_wait(fullA + sa, (uint32_t)((ia / AR) & 1), deadline)) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    for (int q = 0; q < ND - pa; ++q, ++ib) {
-                        const int sb = ib % U2B_RING;
-                        if (!mbar_wait(fullB + sb, (uint32_t)((ib / U2B_RING) & 1), deadline)) {
-                            ok = false;
-                            break;
+                    for (int q = ND - 1 - pa; q >= 0; --q) {
+                        if (pa == 0) {  // the tile's first use of B plane q
+                            if (!mbar_wait(fullB + q, (uint32_t)(u & 1), deadline)) {
+                                ok = false;
+                                break;
+                            }
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         }
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint32_t dcol = tmem + (uint32_t)((pa + q) * UBN);
 #pragma unroll
                         for (int h = 0; h < U2K / OBK; ++h) {
                             const uint64_t ad = smem_desc(smem_u32(sA + sa * U2A_SLOT + h * (U2A_SLOT / 2)));
-                            const uint64_t bd = smem_desc(smem_u32(sB + sb * U2B_SLOT + h * (U2B_SLOT / 2)));
+                            const uint64_t bd = smem_desc(smem_u32(sB + q * U2B_SLOT + h * (U2B_SLOT / 2)));
 #pragma unroll
                             for (int kk = 0; kk < OBK / 16; ++kk)
                                 mma_f16(dcol, ad + 2 * kk, bd + 2 * kk, idesc, (pa > 0 || h > 0 || kk > 0) ? 1u : 0u);
                         }
-                        mma_commit(emptyB + sb);
+                        if (pa == ND - 1 - q) mma_commit(emptyB + q);  // its last use in this tile
                     }
                     mma_commit(emptyA + sa);
                 }
@@ -871,7 +882,8 @@ oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constan
             double* const C = p.C + (int64_t)z * p.sC;
             const int* const ea = p.ea + (int64_t)z * p.Mp;
             const int* const eb = p.eb + (int64_t)z * p.Np;
-            if (p.mode != 0 && p.beta != 0.0) {
+            const bool need_c = p.mode != 0 && p.beta != 0.0;
+            if (need_c) {
                 const int row = mb * UBM + (threadIdx.x >> 2), col = nb * UBN + (threadIdx.x & 3) * 16;
                 if (row < p.M && col < p.N)
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(C + (int64_t)row * p.ldc + col));
@@ -912,51 +924,58 @@ oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constan
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty);  // the next tile's MMAs may start
-            if (ok) {
+            double dv[16];
+            {
                 const int row = mb * UBM + r;
                 const int er = (row < p.M) ? ea[row] : 0;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int c = cg * 16 + j, col = nb * UBN + c;
+                    const int col = nb * UBN + cg * 16 + j;
                     const int ec = (col < p.N) ? eb[col] : 0;
-                    stg[r * UBN + (c ^ (r & 15))] = fixed_to_double(p.alpha_sign * acc[j], er + ec - kUpd2F);
+                    dv[j] = fixed_to_double(p.alpha_sign * acc[j], er + ec - kUpd2F);
                 }
             }
-            asm volatile("bar.sync 1, %0;" ::"r"(OEPI * 32) : "memory");
-            if (!*(volatile int*)&aborted) {
-                constexpr int NR = UBM / OEPI, NG = 4, NH = UBN / 32;
-                const bool need_c = p.mode != 0 && p.beta != 0.0;
+            // two rounds of 32 columns through the half-tile staging area
 #pragma unroll
-                for (int g0 = 0; g0 < NR; g0 += NG) {
-                    double cv[NG][NH];
+            for (int half = 0; half < 2; ++half) {
+                if (ok && (cg >> 1) == half)
 #pragma unroll
-                    for (int i = 0; i < NG; ++i)
+                    for (int j = 0; j < 16; ++j) {
+                        const int c = (cg & 1) * 16 + j;
+                        stg[r * 32 + (c ^ (r & 15))] = dv[j];
+                    }
+                asm volatile("bar.sync 1, %0;" ::"r"(OEPI * 32) : "memory");
+                if (!*(volatile int*)&aborted) {
+                    constexpr int NR = UBM / OEPI, NG = 4;
+                    const int col = nb * UBN + half * 32 + lane;
 #pragma unroll
-                        for (int h = 0; h < NH; ++h) {
-                            const int row = mb * UBM + warp + OEPI * (g0 + i), col = nb * UBN + h * 32 + lane;
-                            cv[i][h] = (need_c && row < p.M && col < p.N) ? C[(int64_t)row * p.ldc + col] : 0.0;
+                    for (int g0 = 0; g0 < NR; g0 += NG) {
+                        double cv[NG];
+#pragma unroll
+                        for (int i = 0; i < NG; ++i) {
+                            const int row = mb * UBM + warp + OEPI * (g0 + i);
+                            cv[i] = (need_c && row < p.M && col < p.N) ? C[(int64_t)row * p.ldc + col] : 0.0;
                         }
 #pragma unroll
-                    for (int i = 0; i < NG; ++i)
-#pragma unroll
-                        for (int h = 0; h < NH; ++h) {
-                            const int rr = warp + OEPI * (g0 + i), c = h * 32 + lane;
-                            const int row = mb * UBM + rr, col = nb * UBN + c;
+                        for (int i = 0; i < NG; ++i) {
+                            const int rr = warp + OEPI * (g0 + i);
+                            const int row = mb * UBM + rr;
                             if (row < p.M && col < p.N) {
-                                const double v = stg[rr * UBN + (c ^ (rr & 15))];
+                                const double v = stg[rr * 32 + (lane ^ (rr & 15))];
                                 double out;
                                 if (p.mode == 0)
                                     out = v;
                                 else if (p.mode == 1)
-                                    out = cv[i][h] + v;
+                                    out = cv[i] + v;
                                 else
-                                    out = (p.beta == 0.0) ? p.alpha * v : fma(p.beta, cv[i][h], p.alpha * v);
+                                    out = (p.beta == 0.0) ? p.alpha * v : fma(p.beta, cv[i], p.alpha * v);
                                 C[(int64_t)row * p.ldc + col] = out;
                             }
                         }
+                    }
                 }
+                asm volatile("bar.sync 1, %0;" ::"r"(OEPI * 32) : "memory");  // the staging area is reused
             }
-            asm volatile("bar.sync 1, %0;" ::"r"(OEPI * 32) : "memory");  // the staging area is reused
             if (p.D != nullptr && tl == 0) {
                 // tile 0 holds the next pivot block: factor it in the staging area (as the 64-deep kernel does)
                 double* a = stg;
@@ -1284,12 +1303,13 @@ rmge_status launch_update(const CUtensorMap& ta, const CUtensorMap& tb, const Up
 template <int ND>
 rmge_status launch_update128(const CUtensorMap& ta, const CUtensorMap& tb, const UpdParams& u, uint32_t idesc,
                              int grid, cudaStream_t st) {
-    if (cudaFuncSetAttribute(oz_update128_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpd2Smem) !=
+    constexpr size_t smem = Upd2Cfg<ND>::kSmem;
+    if (cudaFuncSetAttribute(oz_update128_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
         (void)cudaGetLastError();
         return RMGE_ERR_CUDA;
     }
-    oz_update128_kernel<ND><<<grid, OTHREADS, kUpd2Smem, st>>>(ta, tb, u, idesc);
+    oz_update128_kernel<ND><<<grid, OTHREADS, smem, st>>>(ta, tb, u, idesc);
     RMGE_LAUNCH_CHECK();
     return RMGE_OK;
 }
