@@ -281,8 +281,8 @@ rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const
 //   4. one 128-deep update of the rest by both steps, E -= [L21_k L21_k+1] [U12_k; U12_k+1], whose
 //      launch also factors pivot block k + 2.
 // The trailing matrix is read and written once per pair instead of once per step: the emulated update is
-// bound by that read-modify-write and the digit drains, not by its MMAs.  A last unpaired step takes one
-// 64-deep update that also factors the next pivot block.
+// bound by that read-modify-write and the digit drains, not by its MMAs.  Steps whose trailing matrix is
+// small (below) go unpaired: one 64-deep update that also factors the next pivot block.
 rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s,
                            int count, int64_t sM, int digits) {
     constexpr int PT = 16;
@@ -322,7 +322,11 @@ rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, cons
         const double* L21 = M + (k + b) * ldm + k;
         const double* U12 = M + k * ldm + k + b;
         double* E = M + (k + b) * ldm + (k + b);
-        if (step % 2 != 0 || rest <= NB) {  // an unpaired step: one 64-deep update, next pivot block fused
+        // Pairing exposes the factorization of pivot block k + 1 (about 70 us on one SM) in the thin strip update,
+        // and saves about a third of the Schur updates' time (128 x 64 tiles of 2 steps in 12 us instead of
+        // 2 x 9.3 us): it pays once all systems together have more than about 2^24 trailing entries.
+        const bool big = (double)count * (double)rest * (double)rest >= 16777216.0;
+        if (step % 2 != 0 || rest <= NB || !big) {  // an unpaired step: one 64-deep update, next pivot fused
             const OzFuse next{E, ldm, (int)(rest < NB ? rest : NB), k + b, &st->info, &st->halt};
             RMGE_TRY(oz_gemm(rest, rest, b, digits, -1.0, L21, ldm, U12, ldm, 1.0, E, ldm, oz.planesA, oz.planesB,
                              oz.ea, oz.eb, kmL, kmL + 128, &st->error, &st->halt, s, &next, bt));
