@@ -423,11 +423,14 @@ def extra_workloads(W, rmge, peaks, which=("batch", "grad", "lowrank")):
         Ws = [torch.randn(n, k, generator=g, device="cuda") for _ in range(count)]
         res = {"workload": "64 systems, n=2048, 4 RHS, FP32, A = 4I + N(0,1)/sqrt(n), loss = sum(X*W), "
                            "forward + adjoint backward"}
-        for prec, iters in (("f32", 3), ("f64x", 4)):
+        # the mixed form takes A G from 5 digits (39 bits) and the factors from 7: these matrices are well
+        # conditioned, so two sweeps at most win A G's error back, forward and adjoint
+        for prec, iters, digits in (("f32", 3, None), ("f64x", 4, (5, 7))):
             def step():
                 for t in As + Bs:
                     t.grad = None
-                Xs = rmge_solve_batched(As, Bs, seeds=list(range(count)), prec=prec, streams=16, max_iters=iters)
+                kw = {"digits": digits} if digits else {}
+                Xs = rmge_solve_batched(As, Bs, seeds=list(range(count)), prec=prec, streams=16, max_iters=iters, **kw)
                 loss = sum((X * Wt).sum() for X, Wt in zip(Xs, Ws))
                 loss.backward()
                 return loss
@@ -440,7 +443,8 @@ def extra_workloads(W, rmge, peaks, which=("batch", "grad", "lowrank")):
             t1.record()
             torch.cuda.synchronize()
             ms = t0.elapsed_time(t1)
-            res[prec] = {"ms_per_batch": ms, "systems_per_s": count / (ms / 1e3), "max_iters": iters}
+            res[prec] = {"ms_per_batch": ms, "systems_per_s": count / (ms / 1e3), "max_iters": iters,
+                         "digits": {"apply": digits[0], "factor": digits[1]} if digits else None}
             # The same step captured once in a CUDA graph and replayed, as a training loop with fixed
             # shapes would run it: the eager step pays a host launch per kernel (hundreds per system).
             try:

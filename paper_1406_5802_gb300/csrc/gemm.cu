@@ -232,6 +232,66 @@ __global__ void __launch_bounds__(256) gemv_kernel(int64_t M, int64_t K, T alpha
         }
 }
 
+// The same products with op(A) = A^T (the adjoint's G^T dX and A^T dB): column m of A is row m of op(A),
+// so a lane takes one column (consecutive lanes on consecutive columns: coalesced rows of A) and the 8
+// warps of a block split the rows of A, their partial sums reduced in shared memory.
+template <typename T, typename SA, typename SB, int NC>
+__global__ void __launch_bounds__(256) gemv_t_kernel(int64_t M, int64_t K, T alpha, const SA* __restrict__ A,
+                                                     int64_t lda, const SB* __restrict__ B, int64_t ldb, T beta,
+                                                     T* __restrict__ C, int64_t ldc, const int* halt, Zb zb) {
+    __shared__ T part[8][NC][32];
+    halt = zws(halt, zb.ws);
+    if (halt != nullptr && *(volatile const int*)halt != 0) return;
+    A = zmat(A, zb.m0);
+    B = zmat(B, zb.m1);
+    C = zmat(C, zb.m2);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t m = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t k0 = K * w / 8, k1 = K * (w + 1) / 8;
+    T acc[NC], acc2[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[j] = acc2[j] = T(0);
+    if (m < M) {
+        int64_t k = k0;
+#pragma unroll 4
+        for (; k + 1 < k1; k += 2) {
+            const T a0 = (T)A[k * lda + m], a1 = (T)A[(k + 1) * lda + m];
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                acc[j] = fma(a0, (T)B[k * ldb + j], acc[j]);
+                acc2[j] = fma(a1, (T)B[(k + 1) * ldb + j], acc2[j]);
+            }
+        }
+        if (k < k1) {
+            const T a0 = (T)A[k * lda + m];
+#pragma unroll
+            for (int j = 0; j < NC; ++j) acc[j] = fma(a0, (T)B[k * ldb + j], acc[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NC; ++j) part[w][j][lane] = acc[j] + acc2[j];
+    __syncthreads();
+    if (w < NC && m < M) {
+        const int j = w;
+        T v = part[0][j][lane];
+#pragma unroll
+        for (int g = 1; g < 8; ++g) v += part[g][j][lane];
+        T* c = C + m * ldc + j;
+        const T av = alpha * v;
+        *c = (beta == T(0)) ? av : fma(beta, *c, av);
+    }
+}
+
+template <typename T, typename SA, typename SB, int NC>
+rmge_status launch_gemv_t(int64_t M, int64_t K, T alpha, const SA* A, int64_t lda, const SB* B, int64_t ldb, T beta,
+                          T* C, int64_t ldc, const int* halt, cudaStream_t s, const Zb& zb) {
+    const int64_t blocks = (M + 31) / 32;
+    gemv_t_kernel<T, SA, SB, NC><<<dim3((unsigned)blocks, 1, zb.count), 256, 0, s>>>(M, K, alpha, A, lda, B, ldb,
+                                                                                    beta, C, ldc, halt, zb);
+    RMGE_LAUNCH_CHECK();
+    return RMGE_OK;
+}
+
 template <typename T, typename SA, typename SB, int NC>
 rmge_status launch_gemv(int64_t M, int64_t K, T alpha, const SA* A, int64_t lda, const SB* B, int64_t ldb, T beta,
                         T* C, int64_t ldc, const int* halt, cudaStream_t s, const Zb& zb) {
@@ -263,6 +323,14 @@ template <typename T, typename SA, typename SB>
 rmge_status gemm_any(bool trans_a, int64_t M, int64_t N, int64_t K, T alpha, const SA* A, int64_t lda, const SB* B,
                      int64_t ldb, T beta, T* C, int64_t ldc, const int* halt, cudaStream_t s, const Zb& zb = Zb{}) {
     if (M <= 0 || N <= 0) return RMGE_OK;
+    if (trans_a && N <= 4) {
+        switch (N) {
+            case 1: return launch_gemv_t<T, SA, SB, 1>(M, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s, zb);
+            case 2: return launch_gemv_t<T, SA, SB, 2>(M, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s, zb);
+            case 3: return launch_gemv_t<T, SA, SB, 3>(M, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s, zb);
+            default: return launch_gemv_t<T, SA, SB, 4>(M, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s, zb);
+        }
+    }
     if (!trans_a && N <= 4) {
         switch (N) {
             case 1: return launch_gemv<T, SA, SB, 1>(M, K, alpha, A, lda, B, ldb, beta, C, ldc, halt, s, zb);

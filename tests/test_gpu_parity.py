@@ -210,8 +210,10 @@ def test_dft_like_input_fails_without_gaussian_multiplier(orc):
 # ----------------------------------------------------------------------------- adjoint
 
 @pytest.mark.parametrize("kind", ["gaussian", "circulant"])
-@pytest.mark.parametrize("n,k", [(16, 4), (64, 1), (256, 9)])
+@pytest.mark.parametrize("n,k", [(16, 4), (64, 1), (256, 9), (300, 2), (129, 3)])
 def test_adjoint_matches_oracle_gradient(orc, kind, n, k):
+    if kind == "circulant" and n & (n - 1):
+        pytest.skip("the FFT multipliers take power-of-two orders")
     A, B, Wt = W.grad_system(n, k, seed=W.SEED_BASE + 5 + n)
     out = rmge.gesv(kind, dev(A), dev(B), seed=3, prec="f64")
     X = out["X"]

@@ -88,14 +88,16 @@ def test_batched_factors_solve_to_fp64_target(orc):
         assert orc.backward_error(a, host(X), b) <= 1e-13
 
 
-def test_uniform_autograd_matches_oracle_gradient(orc):
-    """The gradient workload's matrices through the uniform batched autograd node (emulated FP64): X and
-    the gradients of sum(X * W) against the oracle's GEPP solution and GEPP-based adjoint."""
+@pytest.mark.parametrize("digits", [(7, 7), (5, 7)])
+def test_uniform_autograd_matches_oracle_gradient(orc, digits):
+    """The gradient workload's matrices through the uniform batched autograd node (emulated products, all 7
+    digits or A G from 5): X and the gradients of sum(X * W) against the oracle's GEPP solution and
+    GEPP-based adjoint."""
     n, k, count = 256, 4, 5
     systems = [W.grad_system(n, k, seed=800 + i) for i in range(count)]
     As = [torch.tensor(a, dtype=torch.float64, device="cuda", requires_grad=True) for a, _, _ in systems]
     Bs = [torch.tensor(b, dtype=torch.float64, device="cuda", requires_grad=True) for _, b, _ in systems]
-    Xs = rmge_solve_batched(As, Bs, seeds=list(range(count)), prec="f64x", streams=3, max_iters=4)
+    Xs = rmge_solve_batched(As, Bs, seeds=list(range(count)), prec="f64x", streams=3, max_iters=4, digits=digits)
     loss = sum((X * torch.tensor(w, device="cuda")).sum() for X, (_, _, w) in zip(Xs, systems))
     loss.backward()
     torch.cuda.synchronize()
