@@ -602,7 +602,7 @@ def main():
     for i in range(args.steps):
         A_d.copy_(A_h, non_blocking=True)
         B_d.copy_(B_h, non_blocking=True)
-        info, berr, iters, _ = head.step(seed + i, A=A_d, B=B_d)
+        info, berr, iters, _ = head.step(seed + args.warmup + i, A=A_d, B=B_d)  # the timed steps' draws
         X_h.copy_(head.X, non_blocking=True)
         be_h.copy_(berr, non_blocking=True)
         torch.cuda.synchronize()
