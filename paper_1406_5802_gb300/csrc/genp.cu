@@ -282,10 +282,11 @@ rmge_status genp_factor_tc(int64_t n, float* M, int64_t ldm, DevState* st, const
 //      launch also factors pivot block k + 2.
 // The trailing matrix is read and written once per pair instead of once per step: the emulated update is
 // bound by that read-modify-write and the digit drains, not by its MMAs.  Steps whose trailing matrix is
-// small (below) go unpaired: one 64-deep update that also factors the next pivot block.
+// smaller than 4096 rows go unpaired: one 64-deep update that also factors the next pivot block.
 rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, const OzUpdate& oz, cudaStream_t s,
                            int count, int64_t sM, int digits) {
     constexpr int PT = 16;
+    constexpr int64_t kPairRest = 4096;
     const unsigned nz = (unsigned)count;
     const int64_t sK = oz_kmax_per_system(n);
     constexpr int64_t kStateUll = sizeof(DevState) / sizeof(unsigned long long);
@@ -324,9 +325,9 @@ rmge_status genp_factor_oz(int64_t n, double* M, int64_t ldm, DevState* st, cons
         double* E = M + (k + b) * ldm + (k + b);
         // Pairing exposes the factorization of pivot block k + 1 (about 70 us on one SM) in the thin strip update,
         // and saves about a third of the Schur updates' time (128 x 64 tiles of 2 steps in 12 us instead of
-        // 2 x 9.3 us): it pays once all systems together have more than about 2^24 trailing entries.
-        const bool big = (double)count * (double)rest * (double)rest >= 16777216.0;
-        if (step % 2 != 0 || rest <= NB || !big) {  // an unpaired step: one 64-deep update, next pivot fused
+        // 2 x 9.3 us): it pays once the trailing matrix has more than about 2^24 entries.  The test looks at one
+        // system only, so that a system of a batch is factored exactly as it is alone.
+        if (step % 2 != 0 || rest < kPairRest) {  // an unpaired step: one 64-deep update, next pivot fused
             const OzFuse next{E, ldm, (int)(rest < NB ? rest : NB), k + b, &st->info, &st->halt};
             RMGE_TRY(oz_gemm(rest, rest, b, digits, -1.0, L21, ldm, U12, ldm, 1.0, E, ldm, oz.planesA, oz.planesB,
                              oz.ea, oz.eb, kmL, kmL + 128, &st->error, &st->halt, s, &next, bt));

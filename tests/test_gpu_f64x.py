@@ -113,6 +113,59 @@ def test_emulated_factor_matches_oracle_at_bench_size(orc):
     assert be <= 1e-13, be
 
 
+def test_paired_pivot_steps_match_oracle(orc):
+    """n = 4352: the first pivot steps go in pairs (a thin update of the next block column and row that
+    factors the next pivot block, the next panel, then one 128-deep update of the rest by both steps),
+    the rest one by one (the trailing matrix falls below 4096 rows).  Against the oracle's unblocked GENP,
+    on the native FP64 yardstick as at the bench size, and a single system of a uniform batch gets the same
+    bits as the system alone."""
+    orc.set_threads(os.cpu_count() or 1)
+    n = 4352
+    A, _ = W.gaussian_system(n, 1, seed=4352 + 90)
+    G = W.gaussian_multiplier(n, 4352 + 91)
+    M = orc.matmul(A, G)
+    Md = dev(M)
+    info, growth = rmge.factor(Md, "f64x")
+    LU = host(Md)
+    ref, rinfo = orc.genp(M.copy())
+    assert int(host(info)[0]) == rinfo == 0
+    Md64 = dev(M)
+    rmge.factor(Md64, "f64")
+    e64 = np.max(np.abs(host(Md64) - ref)) / np.max(np.abs(ref))
+    err = np.max(np.abs(LU - ref)) / np.max(np.abs(ref))
+    assert err <= 64 * e64 + 1e-15, (err, e64)
+    L = np.tril(LU, -1) + np.eye(n)
+    U = np.triu(LU)
+    be = np.max(np.abs(L @ U - M)) / np.max(np.abs(L) @ np.abs(U))
+    assert be <= 1e-13, be
+    Mb = torch.stack([dev(M), dev(M)])
+    infob, _ = rmge.factor_batched(Mb, "f64x")
+    assert np.all(host(infob) == 0)
+    assert np.array_equal(host(Mb)[1], LU)
+
+
+@pytest.mark.parametrize("digits", [4, 7])
+def test_paired_pivot_steps_exact_on_integer_factors(orc, digits):
+    """Integer L and U of a few bits at n = 4224, so that the paired 128-deep updates run: every intermediate
+    is an integer the digits hold exactly, so the factors come back bit for bit."""
+    n = 4224
+    r = W.rng(5000 + digits)
+    L = np.tril(r.integers(-1, 2, (n, n)), -1).astype(np.float64) + np.eye(n)
+    L[:, :] *= (np.abs(np.arange(n)[:, None] - np.arange(n)[None, :]) < 24)  # banded: small integers
+    L[np.diag_indices(n)] = 1.0
+    U = np.triu(r.integers(-1, 2, (n, n)), 1).astype(np.float64)
+    U *= (np.abs(np.arange(n)[:, None] - np.arange(n)[None, :]) < 24)
+    U += np.diag(r.choice([-1.0, 1.0], n))
+    M0 = L @ U
+    assert np.max(np.abs(M0)) < 2.0**20
+    M = dev(M0)
+    info, _, _ = rmge.factor_ex(M, "f64x", rmge.options(factor_digits=digits))
+    LU = host(M)
+    assert int(host(info)[0]) == 0
+    assert np.array_equal(np.tril(LU, -1), np.tril(L, -1))
+    assert np.array_equal(np.triu(LU), U)
+
+
 def _coupled(n, i):
     """Identity with a 2 x 2 block of ones at rows / columns i, i + 1: pivot i + 1 (1-based) is 1 and the
     Schur update leaves exactly 1 - 1 = 0 at step i + 2."""
