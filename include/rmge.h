@@ -84,7 +84,9 @@ typedef enum {
                            updates are FP64 products emulated on the BF16 tensor cores (7 balanced base-256
                            digits per entry, 28 digit-pair products in exact FP32 chunks, 64-bit fixed-point
                            sums; the updates first balance column k of L21 against row k of U12 by a power
-                           of two); pivot blocks, panels, solves and residuals run on the FP64 pipe */
+                           of two; while 4096 or more rows remain, pivot steps go in pairs with one step of
+                           look-ahead, one 128-deep update per pair); pivot blocks, panels, solves and
+                           residuals run on the FP64 pipe */
 } rmge_prec;
 
 /*
