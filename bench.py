@@ -173,6 +173,7 @@ class Form:
         self.M = torch.empty(self.n, self.n, dtype=rmge.factor_dtype(prec), device="cuda")
         self.X = torch.empty(self.n, self.k, dtype=torch.float64, device="cuda")
         self.apply_events = []
+        self.factor_events = []
 
     def step(self, seed, record=False, A=None, B=None):
         import torch
@@ -188,6 +189,10 @@ class Form:
             e1.record()
             self.apply_events.append((e0, e1))
         info, growth, _ = r.factor_ex(self.M, self.prec, self.opts, ws=self.ws)
+        if record:
+            e2 = torch.cuda.Event(enable_timing=True)
+            e2.record()
+            self.factor_events.append((e1, e2))
         r.solve(self.kind, self.M, self.G, B, self.prec, X=self.X, ws=self.ws)
         berr, iters, _ = r.refine_ex(self.kind, A, self.M, self.G, B, self.X, self.prec, self.max_iters, BE_TOL,
                                      self.opts, ws=self.ws)
@@ -195,6 +200,9 @@ class Form:
 
     def apply_ms(self):
         return sum(a.elapsed_time(b) for a, b in self.apply_events) / max(1, len(self.apply_events))
+
+    def factor_ms(self):
+        return sum(a.elapsed_time(b) for a, b in self.factor_events) / max(1, len(self.factor_events))
 
 
 def outcomes(results):
@@ -251,6 +259,25 @@ def oz_roofline(n, apply_ms, digits, peaks):
             "algorithmic_fp64_tflops": (2 * n**3 - n**2) / (apply_ms / 1e3) / 1e12,
             "apply_ms": apply_ms,
             "note": "apply_ms brackets the apply call: the digit-plane kernels and oz_gemm_kernel"}
+
+
+def factor_roofline(n, factor_ms, digits, peaks):
+    """GENP's emulated Schur updates (oz_update128_kernel, oz_update_kernel), the top kernels of the mixed
+    solve by time: their BF16 MMA work is d (d + 1) / 2 digit pairs of 2 rest^2 64 flops per pivot step.
+    CUDA events can only bracket the whole rmge_factor_ex call (the updates are launched inside it), so
+    the rate is over the factorization's time, panels and pivot blocks included: a lower bound of the
+    update kernels' own rate."""
+    pairs = digits * (digits + 1) // 2
+    flops = sum(pairs * 2.0 * rest * rest * 64 for rest in range(n - 64, 0, -64))
+    achieved = flops / (factor_ms / 1e3) / 1e12
+    pk = peaks.get("bf16_tflops", 1910.7)
+    return {"kernel": "oz_update128_kernel + oz_update_kernel (GENP's Schur updates, emulated by BF16 digit-pair "
+                      "MMAs), timed over the whole factorization call", "bound": "tensor", "achieved": achieved,
+            "peak": pk, "unit": "TFLOP/s (BF16 MMA)", "frac": achieved / pk,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured", "traffic": None,
+            "digit_pairs": pairs, "factor_ms": factor_ms,
+            "note": "bound by the epilogue (TMEM drains, fixed-point rounding, the FP64 add into E), not by the "
+                    "MMAs: profiles/oz_update128_kernel_schur_6digits_n8192.md"}
 
 
 def dgemm_peak_tflops(n=8192, reps=5):
@@ -660,6 +687,7 @@ def main():
         except Exception:
             pass
         roof = oz_roofline(n, head_apply_ms, HEADLINE_DIGITS[0], peaks)
+        roof_factor = factor_roofline(n, head.factor_ms(), HEADLINE_DIGITS[1], peaks)
         for name, fkind, fprec, digits, _, _, _ in FORMS3:
             f = forms3.get(name)
             if isinstance(f, dict) and "apply_ms" in f and fkind == "gaussian" and fprec == "f64x":
@@ -688,6 +716,7 @@ def main():
                          "infos": sorted(set(infos)), "oracle_berr_last": be_oracle,
                          "growth_last": float(results[-1][3].item())},
             "roofline": roof,
+            "roofline_factor": roof_factor,
             "fp64": fp64,
             "speedup_vs_fp64": (value / fp64["value_ungated"]) if isinstance(fp64, dict) and fp64.get("value_ungated")
             else None,
