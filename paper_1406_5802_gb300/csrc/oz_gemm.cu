@@ -761,6 +761,19 @@ oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constan
         t1 = (int)((long long)(blockIdx.x + 1) * tiles_all / gridDim.x);
     }
 
+    // tiles run down each column block (system z, row block mb, column block nb), so that consecutive tiles
+    // of a CTA share their B planes, which then load once per column block
+    const int tiles_m = p.tiles / p.tiles_n;
+    auto tile_at = [&](int t, int& z, int& mb, int& nb) {
+        z = t / p.tiles;
+        const int tl = t - z * p.tiles;
+        nb = tl / tiles_m;
+        mb = tl - nb * tiles_m;
+    };
+    auto bkey = [&](int t) {
+        const int z = t / p.tiles;
+        return z * p.tiles_n + (t - z * p.tiles) / tiles_m;
+    };
     if (threadIdx.x == 0) {
         for (int i = 0; i < AR; ++i) {
             mbar_init(fullA + i, 1);
@@ -790,11 +803,12 @@ oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constan
 
     if (warp == OEPI) {
         if (lane == 0) {  // TMA producer, in the MMA warp's order: A_0, B_ND-1 .. B_0, then A_1 .. A_ND-1
-            int ia = 0, u = 0;
+            int ia = 0, g = 0;  // A loads; B fills (one per run of tiles in one column block)
             bool ok = true;
-            for (int t = t0; t < t1 && ok; ++t, ++u) {
-                const int z = t / p.tiles, tl = t - z * p.tiles;
-                const int mb = tl / p.tiles_n, nb = tl % p.tiles_n;
+            for (int t = t0; t < t1 && ok; ++t) {
+                int z, mb, nb;
+                tile_at(t, z, mb, nb);
+                const bool newB = (t == t0) || bkey(t) != bkey(t - 1);
                 for (int pa = 0; pa < ND && ok; ++pa, ++ia) {
                     const int sa = ia % AR;
                     if (!mbar_wait_idle(emptyA + sa, (uint32_t)(((ia / AR) & 1) ^ 1), deadline)) {
@@ -805,9 +819,9 @@ oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constan
                     const int ya = (z * ND + pa) * p.Mp + mb * UBM;
                     tma_load_2d(sA + sa * U2A_SLOT, &tA, 0, ya, fullA + sa);
                     tma_load_2d(sA + sa * U2A_SLOT + U2A_SLOT / 2, &tA, OBK, ya, fullA + sa);
-                    if (pa == 0)
+                    if (pa == 0 && newB)
                         for (int q = ND - 1; q >= 0; --q) {
-                            if (!mbar_wait_idle(emptyB + q, (uint32_t)((u & 1) ^ 1), deadline)) {
+                            if (!mbar_wait_idle(emptyB + q, (uint32_t)((g & 1) ^ 1), deadline)) {
                                 ok = false;
                                 break;
                             }
@@ -816,6 +830,7 @@ oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constan
                             tma_load_2d(sB + q * U2B_SLOT, &tB, 0, yb, fullB + q);
                             tma_load_2d(sB + q * U2B_SLOT + U2B_SLOT / 2, &tB, OBK, yb, fullB + q);
                         }
+                    if (pa == 0 && newB) ++g;
                 }
             }
             if (!ok) atomicExch(&aborted, 1);
@@ -823,14 +838,17 @@ oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constan
             const unsigned long long d2 = now_ns() + kOzWaitNs;
             for (int j = ia - AR < 0 ? 0 : ia - AR; j < ia; ++j)
                 (void)mbar_wait(fullA + j % AR, (uint32_t)((j / AR) & 1), d2);
-            if (u > 0)
-                for (int q = 0; q < ND; ++q) (void)mbar_wait(fullB + q, (uint32_t)((u - 1) & 1), d2);
+            if (g > 0)
+                for (int q = 0; q < ND; ++q) (void)mbar_wait(fullB + q, (uint32_t)((g - 1) & 1), d2);
         }
     } else if (warp == OEPI + 1) {
         if (lane == 0) {  // MMA issuer
-            int ia = 0, u = 0;
+            int ia = 0, u = 0, g = 0;
             bool ok = true;
             for (int t = t0; t < t1 && ok; ++t, ++u) {
+                const bool newB = (t == t0) || bkey(t) != bkey(t - 1);
+                const bool lastB = (t + 1 == t1) || bkey(t + 1) != bkey(t);
+                if (newB) ++g;  // B fill g - 1 serves this tile
                 if (!mbar_wait(tempty, (uint32_t)((u & 1) ^ 1), deadline)) {
                     ok = false;
                     break;
@@ -844,8 +862,8 @@ oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constan
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     for (int q = ND - 1 - pa; q >= 0; --q) {
-                        if (pa == 0) {  // the tile's first use of B plane q
-                            if (!mbar_wait(fullB + q, (uint32_t)(u & 1), deadline)) {
+                        if (pa == 0 && newB) {  // the first use of this fill of B plane q
+                            if (!mbar_wait(fullB + q, (uint32_t)((g - 1) & 1), deadline)) {
                                 ok = false;
                                 break;
                             }
@@ -860,7 +878,7 @@ oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constan
                             for (int kk = 0; kk < OBK / 16; ++kk)
                                 mma_f16(dcol, ad + 2 * kk, bd + 2 * kk, idesc, (pa > 0 || h > 0 || kk > 0) ? 1u : 0u);
                         }
-                        if (pa == ND - 1 - q) mma_commit(emptyB + q);  // its last use in this tile
+                        if (lastB && pa == ND - 1 - q) mma_commit(emptyB + q);  // its last use in this fill
                     }
                     mma_commit(emptyA + sa);
                 }
@@ -877,8 +895,9 @@ oz_update128_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constan
         int u = 0;
         bool ok = true;
         for (int t = t0; t < t1; ++t, ++u) {
-            const int z = t / p.tiles, tl = t - z * p.tiles;
-            const int mb = tl / p.tiles_n, nb = tl % p.tiles_n;
+            int z, mb, nb;
+            tile_at(t, z, mb, nb);
+            const int tl = t - z * p.tiles;
             double* const C = p.C + (int64_t)z * p.sC;
             const int* const ea = p.ea + (int64_t)z * p.Mp;
             const int* const eb = p.eb + (int64_t)z * p.Np;
