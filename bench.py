@@ -622,18 +622,26 @@ def main():
     be_h = torch.empty(head.max_iters + 1, dtype=torch.float64).pin_memory()
     A_d = torch.empty_like(A)
     B_d = torch.empty_like(Bm)
+
+    def e2e_step(s):
+        A_d.copy_(A_h, non_blocking=True)
+        B_d.copy_(B_h, non_blocking=True)
+        info, berr, iters, _ = head.step(s, A=A_d, B=B_d)
+        X_h.copy_(head.X, non_blocking=True)
+        be_h.copy_(berr, non_blocking=True)
+        torch.cuda.synchronize()
+        return int(info.item()) == 0 and float(be_h[int(iters.item())]) <= BE_TOL
+
+    e2e_step(seed)  # one untimed pass: the first touch of the new device buffers
     barrier()
     torch.cuda.synchronize()
     te = time.perf_counter()
     e2e_ok = True
+    e2e_steps_ms = []
     for i in range(args.steps):
-        A_d.copy_(A_h, non_blocking=True)
-        B_d.copy_(B_h, non_blocking=True)
-        info, berr, iters, _ = head.step(seed + args.warmup + i, A=A_d, B=B_d)  # the timed steps' draws
-        X_h.copy_(head.X, non_blocking=True)
-        be_h.copy_(berr, non_blocking=True)
-        torch.cuda.synchronize()
-        e2e_ok = e2e_ok and int(info.item()) == 0 and float(be_h[int(iters.item())]) <= BE_TOL
+        t_i = time.perf_counter()
+        e2e_ok = e2e_step(seed + args.warmup + i) and e2e_ok  # the timed steps' draws
+        e2e_steps_ms.append((time.perf_counter() - t_i) * 1e3)
     e2e_s = time.perf_counter() - te
     e2e_value = ranks.whole_job_rate(args.steps, world, ranks.max_over_ranks(e2e_s, world, 'cuda'))
     del A_d, B_d
@@ -724,6 +732,7 @@ def main():
                     "h2d_bytes_per_step": (A.numel() + Bm.numel()) * 8,
                     "d2h_bytes_per_step": (head.X.numel() + MAX_ITERS + 1) * 8},
             "e2e_all_steps_be_le_1e-13": e2e_ok,
+            "e2e_step_ms": [round(x, 1) for x in e2e_steps_ms],
             "gpu_launches": launches,
             "clocks": clocks_summary(clk),
             "cpu_baseline": cpu,
