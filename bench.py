@@ -49,6 +49,9 @@ FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # profiles/gemm_kernel_fp64_AG_n4096.md and profiles/oz_gemm_kernel_AG_4digits_n8192.md.
 AG_TRAFFIC_PER_N3 = (3.730475e9 + 0.134292e9) / 4096**3
 OZ_AG_TRAFFIC_PER_N3 = {4: (6.474913e9 + 0.539855e9) / 8192**3}
+# DRAM bytes (read + write) of one 128-deep update launch per element of its trailing matrix (M N): E is read
+# and written once per launch, so the traffic scales with M N.  None: no capture of the kernel as it stands.
+UPD128_TRAFFIC_PER_MN = None
 
 
 def flops_per_solve(n, k, sweeps):
@@ -259,6 +262,39 @@ def oz_roofline(n, apply_ms, digits, peaks):
             "algorithmic_fp64_tflops": (2 * n**3 - n**2) / (apply_ms / 1e3) / 1e12,
             "apply_ms": apply_ms,
             "note": "apply_ms brackets the apply call: the digit-plane kernels and oz_gemm_kernel"}
+
+
+def update_roofline(timing, steps, step_ms, digits, peaks):
+    """The dominant kernel of the mixed solve, oz_update128_kernel: the 128-deep Schur update of two paired pivot
+    steps (Sec. 3), E -= [L21_k L21_k+1] [U12_k; U12_k+1] on the trailing M x N matrix.  Its BF16 MMA work is
+    d (d + 1) / 2 digit pairs of 2 M N 128 flops per launch, and its algorithmic HBM bytes are those of E, read
+    and written once in FP64 (16 M N; the digit planes of L21 and U12 add 2 d 128 (M + N)).  The library times
+    every launch with a CUDA event pair on the launching stream over the timed region (rmge_launch_timing)."""
+    launches, ms, mma = timing["update128"]
+    if launches == 0 or ms <= 0.0:
+        return None
+    pairs = digits * (digits + 1) // 2
+    mn = mma / (pairs * 2.0 * 128 * launches)          # mean M N of a launch
+    achieved = mma / (ms / 1e3) / 1e12
+    pk = peaks.get("bf16_tflops", 1910.7)
+    n64, ms64, mma64 = timing["update"]
+    return {"kernel": "oz_update128_kernel (two paired pivot steps' Schur update, FP64 emulated by BF16 digit-pair "
+                      "MMAs)", "bound": "tensor",
+            "achieved": achieved, "peak": pk, "unit": "TFLOP/s (BF16 MMA)", "frac": achieved / pk,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; the SM clock stayed at its maximum), of measured",
+            "frac_of_sustained": achieved / peaks["bf16_tflops_sustained"] if peaks.get("bf16_tflops_sustained")
+            else None,
+            "traffic": UPD128_TRAFFIC_PER_MN * mn if UPD128_TRAFFIC_PER_MN else None,
+            "algorithmic_bytes_per_launch": 16.0 * mn,
+            "hbm_gbs": 16.0 * mn * launches / (ms / 1e3) / 1e9,
+            "digit_pairs": pairs, "launches_per_step": launches / steps, "ms_per_launch": ms / launches,
+            "share_of_step": ms / steps / step_ms,
+            "algorithmic_fp64_tflops": mma / pairs / (ms / 1e3) / 1e12,
+            "other_updates": {"kernel": "oz_update_kernel (64-deep updates: unpaired steps and the strips of paired "
+                                        "ones)", "launches_per_step": n64 / steps,
+                              "ms_per_step": ms64 / steps,
+                              "achieved": mma64 / (ms64 / 1e3) / 1e12 if ms64 > 0 else None,
+                              "share_of_step": ms64 / steps / step_ms}}
 
 
 def factor_roofline(n, factor_ms, digits, peaks):
@@ -573,6 +609,7 @@ def main():
     t0.record(stream)
     results = []
     launches0 = rmge.kernel_launches()
+    rmge.launch_timing(True)  # event pairs around the Schur-update launches (a host-side switch)
     torch.cuda.nvtx.range_push("headline_timed")  # lets a profiler select the timed region's launches
     for i in range(args.steps):
         results.append(head.step(seed + args.warmup + i, record=True))
@@ -585,6 +622,9 @@ def main():
     barrier()
     ms = t0.elapsed_time(t1)
     ms_max = ranks.max_over_ranks(ms, world, "cuda")  # the whole job lasts as long as its slowest rank
+    upd_timing = {"update128": rmge.launch_timing_read(rmge.TIMED_UPDATE128),
+                  "update": rmge.launch_timing_read(rmge.TIMED_UPDATE)}
+    rmge.launch_timing(False)
 
     # every timed solve must have met the accuracy target, or the line carries no value
     ok, infos, sweeps, bes = outcomes(results)
@@ -714,7 +754,8 @@ def main():
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         except Exception:
             pass
-        roof = oz_roofline(n, head_apply_ms, HEADLINE_DIGITS[0], peaks)
+        roof_apply = oz_roofline(n, head_apply_ms, HEADLINE_DIGITS[0], peaks)
+        roof = update_roofline(upd_timing, args.steps, ms / args.steps, HEADLINE_DIGITS[1], peaks) or roof_apply
         roof_factor = factor_roofline(n, head.factor_ms(), HEADLINE_DIGITS[1], peaks)
         for name, fkind, fprec, digits, _, _, _ in FORMS3:
             f = forms3.get(name)
@@ -744,6 +785,7 @@ def main():
                          "infos": sorted(set(infos)), "oracle_berr_last": be_oracle,
                          "growth_last": float(results[-1][3].item())},
             "roofline": roof,
+            "roofline_apply": roof_apply,
             "roofline_factor": roof_factor,
             "fp64": fp64,
             "speedup_vs_fp64": (value / fp64["value_ungated"]) if isinstance(fp64, dict) and fp64.get("value_ungated")

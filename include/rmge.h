@@ -458,6 +458,25 @@ rmge_status rmge_solve_backward_uniform_batched(int64_t count, int64_t n, int64_
  * counter; lets a caller count the kernels of a timed region). */
 unsigned long long rmge_kernel_launches(void);
 
+/* Launch timing of GENP's emulated Schur updates (Sec. 3's E -= L21 U12 on the BF16 tensor cores), a
+ * measurement aid.  These launches happen inside rmge_factor*, out of the caller's reach, and they take
+ * the largest share of the RMGE_F64X_TC solve's time.
+ *   RMGE_TIMED_UPDATE128  the 128-deep update of two paired pivot steps (oz_update128_kernel);
+ *   RMGE_TIMED_UPDATE     the 64-deep update of one step, and the two thin strips of a paired step
+ *                         (oz_update_kernel).
+ * rmge_launch_timing(1) clears the records and starts recording: each later launch of these kernels
+ * records a CUDA event pair around itself on its own stream, with its BF16 MMA work, digit pairs
+ * s(s+1)/2 x 2 M N K per system.  rmge_launch_timing(0) stops recording.  Launches on a stream that is
+ * being captured into a CUDA graph are not recorded, and neither are launches beyond the 65536th.
+ * Returns RMGE_OK, or RMGE_ERR_INVALID_ARG for `enable` other than 0 or 1.
+ * rmge_launch_timing_read waits for the recorded launches of `kernel` to finish.  It writes their count,
+ * their summed device time in ms and their summed MMA flops.  Returns RMGE_ERR_INVALID_ARG for an unknown
+ * kernel or a null pointer, and RMGE_ERR_CUDA if an event fails.  Both calls take a lock; factorizations
+ * in several host threads at once interleave their records. */
+typedef enum { RMGE_TIMED_UPDATE128 = 0, RMGE_TIMED_UPDATE = 1 } rmge_timed_kernel;
+rmge_status rmge_launch_timing(int32_t enable);
+rmge_status rmge_launch_timing_read(int32_t kernel, int64_t* launches, double* ms, double* mma_flops);
+
 /* Human-readable name of a status code (static string). */
 const char* rmge_status_string(rmge_status s);
 

@@ -109,6 +109,11 @@ rmge_status oz_update128(int64_t M, int64_t N, int s, const double* A, int64_t l
                          double* C, int64_t ldc, void* planesA, void* planesB, int* ea, int* eb,
                          const unsigned long long* kmaxA, const unsigned long long* kmaxB, int* err, const int* halt,
                          cudaStream_t st, const OzFuse* fuse = nullptr, const OzBatch& bt = OzBatch{});
+// launch_timing.cu: CUDA event pairs around the emulated Schur-update launches while rmge_launch_timing(1) is
+// on.  timing_begin records the first event of launch class `kernel` (rmge_timed_kernel) with its MMA flops
+// and returns a token for timing_end; a negative token means nothing was recorded.
+int64_t timing_begin(int kernel, cudaStream_t s, double mma_flops);
+void timing_end(int64_t token, cudaStream_t s);
 // Slots of per-k maxima per system for the emulated factorization: for each pair of pivot steps, the
 // 64 + 64 column maxima of L21 and then the 64 + 64 row maxima of U12 (256 slots), so that the 128-deep
 // update of a pair finds both operands' maxima contiguous.

@@ -1415,12 +1415,20 @@ rmge_status oz_gemm(int64_t M, int64_t N, int64_t K, int s, double alpha, const 
                                ((uint32_t)(UBM >> 4) << 24);
         const int64_t all = (int64_t)u.tiles * bt.count;
         const int grid = all < sm_count() ? (int)all : sm_count();
+        // GENP's balanced updates (per-k maxima given) are the ones rmge_launch_timing records
+        const int64_t tk = kmaxA == nullptr ? -1
+                                            : timing_begin(RMGE_TIMED_UPDATE, st, (double)(s * (s + 1) / 2) * 2.0 *
+                                                                                      (double)M * (double)N * (double)K *
+                                                                                      (double)bt.count);
+        rmge_status rc;
         switch (s) {
-            case 4: return launch_update<4>(ta, tb, u, idesc, grid, st);
-            case 5: return launch_update<5>(ta, tb, u, idesc, grid, st);
-            case 6: return launch_update<6>(ta, tb, u, idesc, grid, st);
-            default: return launch_update<7>(ta, tb, u, idesc, grid, st);
+            case 4: rc = launch_update<4>(ta, tb, u, idesc, grid, st); break;
+            case 5: rc = launch_update<5>(ta, tb, u, idesc, grid, st); break;
+            case 6: rc = launch_update<6>(ta, tb, u, idesc, grid, st); break;
+            default: rc = launch_update<7>(ta, tb, u, idesc, grid, st); break;
         }
+        timing_end(tk, st);
+        return rc;
     }
 
     // |acc| < (chunks on diagonal 0 + 1) 2^(F + 10) must stay below 2^62
@@ -1522,12 +1530,17 @@ rmge_status oz_update128(int64_t M, int64_t N, int s, const double* A, int64_t l
                            ((uint32_t)(UBM >> 4) << 24);
     const int64_t all = (int64_t)u.tiles * bt.count;
     const int grid = all < sm_count() ? (int)all : sm_count();
+    const int64_t tk = timing_begin(RMGE_TIMED_UPDATE128, st, (double)(s * (s + 1) / 2) * 2.0 * (double)M *
+                                                                  (double)N * (double)K * (double)bt.count);
+    rmge_status rc;
     switch (s) {
-        case 4: return launch_update128<4>(ta, tb, u, idesc, grid, st);
-        case 5: return launch_update128<5>(ta, tb, u, idesc, grid, st);
-        case 6: return launch_update128<6>(ta, tb, u, idesc, grid, st);
-        default: return launch_update128<7>(ta, tb, u, idesc, grid, st);
+        case 4: rc = launch_update128<4>(ta, tb, u, idesc, grid, st); break;
+        case 5: rc = launch_update128<5>(ta, tb, u, idesc, grid, st); break;
+        case 6: rc = launch_update128<6>(ta, tb, u, idesc, grid, st); break;
+        default: rc = launch_update128<7>(ta, tb, u, idesc, grid, st); break;
     }
+    timing_end(tk, st);
+    return rc;
 }
 
 }  // namespace rmge

@@ -38,7 +38,8 @@ EXPORTED = ["rmge_multiplier_bytes", "rmge_workspace_size", "rmge_make_multiplie
             "rmge_apply_multiplier_ex", "rmge_batched_uniform_workspace_size", "rmge_apply_multiplier_batched",
             "rmge_factor_batched", "rmge_uniform_solve_workspace_size", "rmge_solve_uniform_batched",
             "rmge_refine_uniform_batched", "rmge_solve_backward_uniform_batched",
-            "rmge_solve_batched", "rmge_solve_batched_ex", "rmge_batched_workspace_size"]
+            "rmge_solve_batched", "rmge_solve_batched_ex", "rmge_batched_workspace_size", "rmge_launch_timing",
+            "rmge_launch_timing_read"]
 
 
 class Options(C.Structure):
@@ -78,6 +79,9 @@ def load_library(path: str = LIB_PATH):
                                           _i64, _vp, _i64, C.c_int, C.c_int32, C.c_double, _vp, _vp, _vp, _sz, _vp]),
         "rmge_status_string": (C.c_char_p, [C.c_int]),
         "rmge_kernel_launches": (C.c_ulonglong, []),
+        "rmge_launch_timing": (C.c_int, [C.c_int32]),
+        "rmge_launch_timing_read": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                              C.POINTER(C.c_double)]),
         "rmge_solve_workspace_size": (_sz, [_i64, _i64, C.c_int, C.c_int]),
         "rmge_solve_noalloc": (C.c_int, [C.c_int, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, C.c_int, _vp]),
         "rmge_noalloc_capacity": (_sz, []),
@@ -175,6 +179,24 @@ def _need(t, dtype, name):
 def kernel_launches() -> int:
     """Kernel launches enqueued through the library by this process so far."""
     return int(load_library().rmge_kernel_launches())
+
+
+# launch classes of rmge_launch_timing (rmge_timed_kernel)
+TIMED_UPDATE128, TIMED_UPDATE = 0, 1
+
+
+def launch_timing(enable: bool) -> None:
+    """rmge_launch_timing: True clears the records and starts recording event pairs around the emulated Schur
+    updates (no CUDA call until a launch is recorded); False stops recording."""
+    _check("rmge_launch_timing", load_library().rmge_launch_timing(1 if enable else 0))
+
+
+def launch_timing_read(kernel: int):
+    """rmge_launch_timing_read: (launches, summed device ms, summed BF16 MMA flops) of one launch class."""
+    n, ms, fl = C.c_int64(0), C.c_double(0.0), C.c_double(0.0)
+    _check("rmge_launch_timing_read",
+           load_library().rmge_launch_timing_read(int(kernel), C.byref(n), C.byref(ms), C.byref(fl)))
+    return int(n.value), float(ms.value), float(fl.value)
 
 
 def factor_dtype(prec) -> torch.dtype:

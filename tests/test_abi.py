@@ -132,3 +132,18 @@ def test_uniform_batch_sizes_and_argument_checks(lib):
     bad = rmge.options(factor_digits=3)
     assert lib.rmge_factor_batched(2, 8, p, 8, 64, 6, p, None, C.byref(bad), p, 1 << 20, None) == INVALID
     assert lib.rmge_apply_multiplier_batched(2, 8, p, 8, 64, p, 64, p, 8, 63, 6, None, p, 1 << 20, None) == INVALID
+
+
+def test_launch_timing_arguments_and_empty_records(lib):
+    """rmge_launch_timing rejects flags other than 0 and 1, rmge_launch_timing_read unknown launch classes
+    and null outputs; with nothing launched the records are empty (no CUDA call is made)."""
+    INVALID = rmge.CODES["RMGE_ERR_INVALID_ARG"]
+    assert lib.rmge_launch_timing(2) == INVALID
+    n, ms, fl = C.c_int64(-1), C.c_double(-1.0), C.c_double(-1.0)
+    assert lib.rmge_launch_timing_read(2, C.byref(n), C.byref(ms), C.byref(fl)) == INVALID
+    assert lib.rmge_launch_timing_read(-1, C.byref(n), C.byref(ms), C.byref(fl)) == INVALID
+    assert lib.rmge_launch_timing_read(0, None, C.byref(ms), C.byref(fl)) == INVALID
+    rmge.launch_timing(True)
+    assert rmge.launch_timing_read(rmge.TIMED_UPDATE128) == (0, 0.0, 0.0)
+    assert rmge.launch_timing_read(rmge.TIMED_UPDATE) == (0, 0.0, 0.0)
+    rmge.launch_timing(False)

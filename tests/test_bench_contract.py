@@ -55,7 +55,8 @@ def test_main_line_keys():
     assert MAIN_KEYS <= _keys(line)
     assert E2E_KEYS <= _keys(_sub(line, "e2e"))
     assert CPU_KEYS <= _keys(_dict_assigned(fns["main"], "cpu"))
-    # the roofline object is built by oz_roofline (the headline's dominant kernel)
+    # the roofline object is built by update_roofline (the headline's dominant kernel), or by oz_roofline (A G)
+    assert ROOFLINE_KEYS <= _keys(_returned_dict(fns["update_roofline"]))
     assert ROOFLINE_KEYS <= _keys(_returned_dict(fns["oz_roofline"]))
     assert ROOFLINE_KEYS <= _keys(_returned_dict(fns["fp64_roofline"]))
     assert "workload" in _keys(_returned_dict(fns["workload_config"]))

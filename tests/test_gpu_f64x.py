@@ -294,3 +294,60 @@ def test_fewer_factor_digits_are_won_back_by_refinement(orc, digits):
     it = int(host(iters)[0])
     assert it <= 8, it
     assert orc.backward_error(A, host(X), B) <= 1e-13
+
+
+def _update_launches(n):
+    """(M, N, K) of each emulated Schur-update launch of an n x n factorization, by launch class: pivot blocks
+    of 64 (Sec. 3), steps paired while the trailing matrix has at least 4096 rows (two thin strips of 64-deep
+    updates, then one 128-deep update of the rest), the others one 64-deep update each."""
+    u128, u64 = [], []
+    k, step = 0, 0
+    while k < n:
+        b = min(64, n - k)
+        rest = n - k - b
+        if rest <= 0:
+            break
+        if step % 2 != 0 or rest < 4096:
+            u64.append((rest, rest, b))
+            k, step = k + b, step + 1
+            continue
+        u64 += [(rest, 64, b), (64, rest - 64, b)]
+        u128.append((rest - 64, rest - 64, 128))
+        k, step = k + 128, step + 2
+    return u128, u64
+
+
+def test_launch_timing_records_the_schur_updates():
+    """rmge_launch_timing: one event pair per update launch, with its digit-pair MMA work; nothing once
+    stopped, nothing from a launch captured into a CUDA graph."""
+    n, d = 4352, 6
+    A, _ = W.gaussian_system(n, 1, seed=4352 + 92)
+    opts = rmge.options(factor_digits=d)
+    rmge.launch_timing(True)
+    info, _, _ = rmge.factor_ex(dev(A), "f64x", opts)
+    n128, ms128, fl128 = rmge.launch_timing_read(rmge.TIMED_UPDATE128)
+    n64, ms64, fl64 = rmge.launch_timing_read(rmge.TIMED_UPDATE)
+    assert int(host(info)[0]) == 0
+    u128, u64 = _update_launches(n)
+    pairs = d * (d + 1) // 2
+    assert (n128, n64) == (len(u128), len(u64)) == (2, 67)
+    assert fl128 == sum(pairs * 2.0 * m * nn * kk for m, nn, kk in u128)
+    assert fl64 == sum(pairs * 2.0 * m * nn * kk for m, nn, kk in u64)
+    assert ms128 > 0 and ms64 > 0
+    rmge.launch_timing(False)
+    rmge.factor_ex(dev(A), "f64x", opts)
+    assert rmge.launch_timing_read(rmge.TIMED_UPDATE128) == (n128, ms128, fl128)
+    # a launch on a stream under graph capture records nothing
+    Mc = dev(A)
+    ws = rmge.workspace_ex(n, 1, "gaussian", "f64x", opts)
+    rmge.factor_ex(Mc, "f64x", opts, ws=ws)
+    torch.cuda.synchronize()
+    rmge.launch_timing(True)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rmge.factor_ex(Mc, "f64x", opts, ws=ws)
+    g.replay()
+    torch.cuda.synchronize()
+    assert rmge.launch_timing_read(rmge.TIMED_UPDATE128)[0] == 0
+    assert rmge.launch_timing_read(rmge.TIMED_UPDATE)[0] == 0
+    rmge.launch_timing(False)
