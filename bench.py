@@ -50,8 +50,9 @@ FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 AG_TRAFFIC_PER_N3 = (3.730475e9 + 0.134292e9) / 4096**3
 OZ_AG_TRAFFIC_PER_N3 = {4: (6.474913e9 + 0.539855e9) / 8192**3}
 # DRAM bytes (read + write) of one 128-deep update launch per element of its trailing matrix (M N): E is read
-# and written once per launch, so the traffic scales with M N.  None: no capture of the kernel as it stands.
-UPD128_TRAFFIC_PER_MN = None
+# and written once per launch, so the traffic scales with M N.  Source: profiles/oz_update128_kernel_schur_6digits_
+# n8192.md (M = N = 7936).
+UPD128_TRAFFIC_PER_MN = (0.540766464e9 + 0.448927744e9) / 7936**2
 
 
 def flops_per_solve(n, k, sweeps):
