@@ -39,6 +39,7 @@ HEADLINE = ("gaussian", "f64x")       # multiplier kind, precision of the headli
 # draw's growth (2 to 8 sweeps seen at n = 16384), hence the larger sweep limit of the mixed forms.
 HEADLINE_DIGITS = (4, 6)
 MAX_ITERS_MIXED = 20
+BATCH_CPU_SAMPLE = 1024               # systems of the uneven batch in the oracle's cpu_baseline sample
 # FP64 on GB300 runs on the DFMA pipe: 2 DFMA per clock per SM; at the 2070 MHz maximum SM clock that is
 # 152 SMs x 2 DFMA x 2 flop x 2.070 GHz = 1.2586 TFLOP/s.  The measured FP64 GEMM rate (cuBLAS DGEMM) is
 # taken live by dgemm_peak_tflops() and reported beside it (profiles/fp64_peak_cublas_dgemm_n8192.md).
@@ -114,6 +115,50 @@ def oracle_rate(A, G, rows, threads, k):
     n = A.shape[0]
     t_solve = dt * flops_per_solve(n, k, 1) / fl
     return 1.0 / t_solve, dt
+
+
+def batch_flops(n):
+    """Flops of one randomized GENP solve of order n with one right-hand side: A G and GENP (2n^3 + 2n^3/3)."""
+    return 2.0 * n**3 + 2.0 * n**3 / 3
+
+
+def oracle_batch_baseline(systems, sizes, seed, threads):
+    """The CPU oracle on a bounded sample of the uneven batch: its whole solve (the Gaussian G of each system
+    from its own Philox stream, A G, unblocked GENP, solves, FP64 refinement to 1e-13) of the given leading
+    systems, extrapolated to all `sizes` by batch_flops."""
+    from oracle import oracle as orc
+    orc.set_threads(threads)
+    t0 = time.perf_counter()
+    worst = 0.0
+    for i, (A, b) in enumerate(systems):
+        G = orc.make_multiplier(orc.GAUSSIAN, A.shape[0], seed, i + 1)
+        r = orc.rmge_solve(orc.GAUSSIAN, A, G, b, 10, 1e-13)
+        worst = max(worst, r["berr"][-1] if r["berr"] else float("inf"))
+    dt = time.perf_counter() - t0
+    sample = sum(batch_flops(A.shape[0]) for A, _ in systems)
+    ms = dt * sum(batch_flops(int(n)) for n in sizes) / sample * 1e3
+    return {"value": len(sizes) / (ms / 1e3), "unit": "systems/s", "ms_per_batch": ms, "cores": threads,
+            "kind": "oracle", "max_berr_sample": worst,
+            "sample": f"the oracle's whole solve of the first {len(systems)} of {len(sizes)} systems ({dt:.1f} s), "
+                      f"extrapolated to the batch by the flops of A G and GENP"}
+
+
+def oracle_grad_baseline(A, B, Wbar, count, seed, threads):
+    """The CPU oracle on a bounded sample of the gradient batch: one system's forward solve (its randomized
+    GENP solve with FP64 refinement) and its adjoint (dB = A^-T Wbar, dA = -dB X^T, by GEPP of A^T), times
+    `count` systems."""
+    from oracle import oracle as orc
+    orc.set_threads(threads)
+    t0 = time.perf_counter()
+    G = orc.make_multiplier(orc.GAUSSIAN, A.shape[0], seed, 1)
+    r = orc.rmge_solve(orc.GAUSSIAN, A, G, B, 10, 1e-13)
+    orc.solve_adjoint_gepp(A, r["X"], Wbar)
+    dt = time.perf_counter() - t0
+    ms = dt * count * 1e3
+    return {"value": count / (ms / 1e3), "unit": "systems/s", "ms_per_batch": ms, "cores": threads,
+            "kind": "oracle",
+            "sample": f"the oracle's forward solve and adjoint of one of the {count} systems ({dt:.1f} s), times "
+                      f"{count}"}
 
 
 def reference_inputs(n, k):
@@ -374,7 +419,7 @@ FORMS2 = [("f64", "gaussian", "f64"), ("f64x", "gaussian", "f64x"), ("circ_f64",
           ("toeplitz_f64x", "toeplitz", "f64x")]
 
 
-def extra_workloads(W, rmge, peaks, which=("batch", "grad", "lowrank")):
+def extra_workloads(W, rmge, peaks, which=("batch", "grad", "lowrank"), cpu_baselines=True):
     """The other measured workloads (one JSON object each, added to the main line): the batch of 4096 uneven
     systems in one persistent graph-captured launch, the differentiable batch of 64 systems, and Algorithm
     6.1's low-rank approximation."""
@@ -393,6 +438,7 @@ def extra_workloads(W, rmge, peaks, which=("batch", "grad", "lowrank")):
         from paper_1406_5802_gb300.batch import BatchedSolver
         sizes = W.batch_sizes(4096, 32, 512, W.SEED_BASE + 4)
         bs = BatchedSolver.synthetic(sizes, seed=W.SEED_BASE + 4, max_sweeps=40, be_tol=1e-13)
+        sample = [tuple(t.cpu().numpy() for t in bs.system(i)) for i in range(BATCH_CPU_SAMPLE)]
         tune = bs.tune(reps=1)
         bs.capture()
         bs.run()
@@ -416,6 +462,12 @@ def extra_workloads(W, rmge, peaks, which=("batch", "grad", "lowrank")):
                              "all_info_zero": bool(np.all(info == 0)),
                              "systems_be_le_1e-13": int(np.sum(berr <= 1e-13)), "max_berr": float(np.max(berr)),
                              "tuned": {"config": tune["config"], "ctas": tune["ctas"]}}
+        if cpu_baselines:
+            try:
+                out["batch_4096"]["cpu_baseline"] = oracle_batch_baseline(
+                    [(A, b.reshape(-1, 1)) for A, b in sample], sizes, W.SEED_BASE + 4, os.cpu_count() or 1)
+            except Exception as e:
+                out["batch_4096"]["cpu_baseline"] = {"error": repr(e)[:200]}
     except Exception as e:
         out["batch_4096"] = {"error": repr(e)}
 
@@ -535,6 +587,13 @@ def extra_workloads(W, rmge, peaks, which=("batch", "grad", "lowrank")):
                 del graph
             except Exception as e:  # report, keep the eager number
                 res[prec]["graph_error"] = repr(e)[:200]
+        if cpu_baselines:
+            try:
+                res["cpu_baseline"] = oracle_grad_baseline(
+                    As[0].detach().double().cpu().numpy(), Bs[0].detach().double().cpu().numpy(),
+                    Ws[0].double().cpu().numpy(), count, W.SEED_BASE + 5, os.cpu_count() or 1)
+            except Exception as e:
+                res["cpu_baseline"] = {"error": repr(e)[:200]}
         out["grad_64x2048"] = res
     except Exception as e:
         out["grad_64x2048"] = {"error": repr(e)}
@@ -807,7 +866,8 @@ def main():
         }
         if not args.no_extras:
             sel = tuple(x for x in args.extras.split(",") if x)
-            line["extras"] = {k: v for k, v in extra_workloads(W, rmge, peaks, sel).items()
+            line["extras"] = {k: v for k, v in extra_workloads(W, rmge, peaks, sel,
+                                                               not args.no_cpu_baseline).items()
                               if not (isinstance(v, dict) and v.get("error") == repr(LookupError("not selected")))}
         print(json.dumps(line), flush=True)
     if world > 1:

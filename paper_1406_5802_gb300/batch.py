@@ -178,6 +178,11 @@ class BatchedSolver:
         else:
             self.launch()
 
+    def system(self, i: int):
+        """(A_i, b_i) of system i: views of the packed device arrays (A_i row-major, n_i x n_i)."""
+        n = int(self.sizes[i])
+        return self.A[self.offA[i]:self.offA[i] + n * n].view(n, n), self.b[self.offv[i]:self.offv[i] + n]
+
     def solution(self, i: int) -> torch.Tensor:
         n = int(self.sizes[i])
         return self.x[self.offv[i]:self.offv[i] + n]
