@@ -39,7 +39,8 @@ HEADLINE = ("gaussian", "f64x")       # multiplier kind, precision of the headli
 # draw's growth (2 to 8 sweeps seen at n = 16384), hence the larger sweep limit of the mixed forms.
 HEADLINE_DIGITS = (4, 6)
 MAX_ITERS_MIXED = 20
-BATCH_CPU_SAMPLE = 1024               # systems of the uneven batch in the oracle's cpu_baseline sample
+BATCH_CPU_SAMPLE = 2048               # systems of the uneven batch in the oracle's cpu_baseline sample
+GRAD_CPU_SAMPLE = 16                  # systems of the gradient batch in the oracle's cpu_baseline sample
 # FP64 on GB300 runs on the DFMA pipe: 2 DFMA per clock per SM; at the 2070 MHz maximum SM clock that is
 # 152 SMs x 2 DFMA x 2 flop x 2.070 GHz = 1.2586 TFLOP/s.  The measured FP64 GEMM rate (cuBLAS DGEMM) is
 # taken live by dgemm_peak_tflops() and reported beside it (profiles/fp64_peak_cublas_dgemm_n8192.md).
@@ -143,22 +144,23 @@ def oracle_batch_baseline(systems, sizes, seed, threads):
                       f"extrapolated to the batch by the flops of A G and GENP"}
 
 
-def oracle_grad_baseline(A, B, Wbar, count, seed, threads):
-    """The CPU oracle on a bounded sample of the gradient batch: one system's forward solve (its randomized
-    GENP solve with FP64 refinement) and its adjoint (dB = A^-T Wbar, dA = -dB X^T, by GEPP of A^T), times
-    `count` systems."""
+def oracle_grad_baseline(systems, count, seed, threads):
+    """The CPU oracle on a bounded sample of the gradient batch: for each given system (A, B, Wbar), its
+    forward solve (the randomized GENP solve with FP64 refinement) and its adjoint (dB = A^-T Wbar,
+    dA = -dB X^T, by GEPP of A^T); the time is scaled to `count` systems."""
     from oracle import oracle as orc
     orc.set_threads(threads)
     t0 = time.perf_counter()
-    G = orc.make_multiplier(orc.GAUSSIAN, A.shape[0], seed, 1)
-    r = orc.rmge_solve(orc.GAUSSIAN, A, G, B, 10, 1e-13)
-    orc.solve_adjoint_gepp(A, r["X"], Wbar)
+    for i, (A, B, Wbar) in enumerate(systems):
+        G = orc.make_multiplier(orc.GAUSSIAN, A.shape[0], seed, i + 1)
+        r = orc.rmge_solve(orc.GAUSSIAN, A, G, B, 10, 1e-13)
+        orc.solve_adjoint_gepp(A, r["X"], Wbar)
     dt = time.perf_counter() - t0
-    ms = dt * count * 1e3
+    ms = dt * count / len(systems) * 1e3
     return {"value": count / (ms / 1e3), "unit": "systems/s", "ms_per_batch": ms, "cores": threads,
             "kind": "oracle",
-            "sample": f"the oracle's forward solve and adjoint of one of the {count} systems ({dt:.1f} s), times "
-                      f"{count}"}
+            "sample": f"the oracle's forward solve and adjoint of {len(systems)} of the {count} systems "
+                      f"({dt:.1f} s), scaled to {count}"}
 
 
 def reference_inputs(n, k):
@@ -419,10 +421,10 @@ FORMS2 = [("f64", "gaussian", "f64"), ("f64x", "gaussian", "f64x"), ("circ_f64",
           ("toeplitz_f64x", "toeplitz", "f64x")]
 
 
-def extra_workloads(W, rmge, peaks, which=("batch", "grad", "lowrank"), cpu_baselines=True):
-    """The other measured workloads (one JSON object each, added to the main line): the batch of 4096 uneven
-    systems in one persistent graph-captured launch, the differentiable batch of 64 systems, and Algorithm
-    6.1's low-rank approximation."""
+def extra_workloads(W, rmge, peaks, which=("latency", "batch", "grad", "lowrank"), cpu_baselines=True):
+    """The other measured workloads (one JSON object each, added to the main line): the latency of one small
+    solve, the batch of 4096 uneven systems in one persistent graph-captured launch, the differentiable batch
+    of 64 systems, and Algorithm 6.1's low-rank approximation."""
     import numpy as np
     import torch
 
@@ -430,6 +432,54 @@ def extra_workloads(W, rmge, peaks, which=("batch", "grad", "lowrank"), cpu_base
 
     def ev():
         return torch.cuda.Event(enable_timing=True)
+
+    # -- latency: one FP64 solve of order 256 whose leading pivot is zero, one solve after another ---------
+    try:
+        if "latency" not in which:
+            raise LookupError("not selected")
+        n1 = 256
+        A1, B1 = W.gaussian_system(n1, 1, seed=W.SEED_BASE + 1, zero_leading_pivot=True)
+        A1d, B1d = torch.as_tensor(A1, device="cuda"), torch.as_tensor(B1, device="cuda")
+        info0, _ = rmge.factor(A1d.clone(), "f64")  # unmultiplied GENP breaks down at step 1 (Cor. 3.1)
+        form = Form(rmge, A1d, B1d, "gaussian", "f64")
+        for i in range(3):
+            form.step(W.SEED_BASE + 1 + i)
+        torch.cuda.synchronize()
+        reps = 50
+        t0, t1 = ev(), ev()
+        t0.record()
+        results = [form.step(W.SEED_BASE + 11 + i) for i in range(reps)]
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / reps
+        ok, infos, sweeps, bes = outcomes(results)
+        out["latency_n256"] = {"workload": "n=256, A i.i.d. N(0,1) with A[0,0] = 0, 1 RHS, Gaussian G, FP64, "
+                                           "50 solves back to back on one stream",
+                               "us_per_solve": ms * 1e3, "solves_per_s": 1e3 / ms, "all_steps_be_le_1e-13": ok,
+                               "max_berr": max(bes), "mean_sweeps": sum(sweeps) / len(sweeps),
+                               "unmultiplied_genp_info": int(info0.item())}
+        del form
+        try:  # the same system as a batch of one: the whole solve in one persistent launch, replayed as a graph
+            from paper_1406_5802_gb300.batch import BatchedSolver
+            one = BatchedSolver([A1], [B1], seed=W.SEED_BASE + 1, max_sweeps=40, be_tol=1e-13)
+            one.capture()
+            one.run()
+            torch.cuda.synchronize()
+            t0, t1 = ev(), ev()
+            t0.record()
+            for _ in range(reps):
+                one.run()
+            t1.record()
+            torch.cuda.synchronize()
+            ms1 = t0.elapsed_time(t1) / reps
+            out["latency_n256"]["batched_kernel"] = {
+                "form": "FP32 GENP of A G and FP64 refinement in one persistent launch (batch of one)",
+                "us_per_solve": ms1 * 1e3, "solves_per_s": 1e3 / ms1, "info": int(one.info[0].item()),
+                "berr": float(one.berr[0].item())}
+        except Exception as e:
+            out["latency_n256"]["batched_kernel"] = {"error": repr(e)[:200]}
+    except Exception as e:
+        out["latency_n256"] = {"error": repr(e)}
 
     # -- batching: 4096 systems, n ~ U{32..512}, one persistent CUDA-graph launch -----------------------
     try:
@@ -590,8 +640,9 @@ def extra_workloads(W, rmge, peaks, which=("batch", "grad", "lowrank"), cpu_base
         if cpu_baselines:
             try:
                 res["cpu_baseline"] = oracle_grad_baseline(
-                    As[0].detach().double().cpu().numpy(), Bs[0].detach().double().cpu().numpy(),
-                    Ws[0].double().cpu().numpy(), count, W.SEED_BASE + 5, os.cpu_count() or 1)
+                    [(As[i].detach().double().cpu().numpy(), Bs[i].detach().double().cpu().numpy(),
+                      Ws[i].double().cpu().numpy()) for i in range(GRAD_CPU_SAMPLE)],
+                    count, W.SEED_BASE + 5, os.cpu_count() or 1)
             except Exception as e:
                 res["cpu_baseline"] = {"error": repr(e)[:200]}
         out["grad_64x2048"] = res
@@ -612,7 +663,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 form at the headline size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other measured workloads")
-    ap.add_argument("--extras", default="batch,grad,lowrank", help="comma list of the other workloads")
+    ap.add_argument("--extras", default="latency,batch,grad,lowrank", help="comma list of the other workloads")
     ap.add_argument("--forms", default=",".join(f[0] for f in FORMS3),
                     help="comma list of the other forms on the headline inputs ('none' for none)")
     ap.add_argument("--forms4096", default=",".join(f[0] for f in FORMS2),

@@ -21,7 +21,7 @@ def test_batch_baseline_extrapolates_by_flops(orc):
 
 
 def test_grad_baseline_runs_forward_and_adjoint(orc):
-    A, B, Wbar = W.grad_system(48, 4, seed=5)
-    out = bench.oracle_grad_baseline(A, B, Wbar, count=64, seed=5, threads=1)
+    systems = [W.grad_system(48, 4, seed=5), W.grad_system(40, 4, seed=6)]
+    out = bench.oracle_grad_baseline(systems, count=64, seed=5, threads=1)
     assert CPU_KEYS <= set(out) and out["unit"] == "systems/s"
     assert out["value"] > 0 and abs(out["value"] * out["ms_per_batch"] / 1e3 - 64) < 1e-9
