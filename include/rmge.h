@@ -472,7 +472,9 @@ unsigned long long rmge_kernel_launches(void);
  * rmge_launch_timing_read waits for the recorded launches of `kernel` to finish.  It writes their count,
  * their summed device time in ms and their summed MMA flops.  Returns RMGE_ERR_INVALID_ARG for an unknown
  * kernel or a null pointer, and RMGE_ERR_CUDA if an event fails.  Both calls take a lock; factorizations
- * in several host threads at once interleave their records. */
+ * in several host threads at once interleave their records.  Each event is created on the device current
+ * at the time and reused until the next rmge_launch_timing(1), which destroys them: a process that moves
+ * to another device calls it again there, or launches on that device go unrecorded. */
 typedef enum { RMGE_TIMED_UPDATE128 = 0, RMGE_TIMED_UPDATE = 1 } rmge_timed_kernel;
 rmge_status rmge_launch_timing(int32_t enable);
 rmge_status rmge_launch_timing_read(int32_t kernel, int64_t* launches, double* ms, double* mma_flops);

@@ -91,11 +91,15 @@ rmge_status rmge_launch_timing(int32_t enable) {
     if (enable != 0 && enable != 1) return RMGE_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
     if (enable) {
+        // destroyed rather than kept: the next events are created on the device current now
         for (const Record& r : g_records) {
-            give_back(r.begin);
-            give_back(r.end);
+            (void)cudaEventDestroy(r.begin);
+            (void)cudaEventDestroy(r.end);
         }
+        for (cudaEvent_t e : g_spare) (void)cudaEventDestroy(e);
+        if (!g_records.empty() || !g_spare.empty()) (void)cudaGetLastError();
         g_records.clear();
+        g_spare.clear();
         ++g_generation;
     }
     g_on = enable != 0;
