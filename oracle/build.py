@@ -14,15 +14,21 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liborc.so")
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile one C source of the oracle into the shared library `out`, with the flags above."""
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-o", out, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Build the oracle library if it is missing or older than its source."""
     os.makedirs(OUT_DIR, exist_ok=True)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", "-Wall", "-o", tmp, SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    compile_source(SRC, tmp)
     os.replace(tmp, LIB)
     return LIB
 

@@ -31,7 +31,9 @@ TOEPLITZ_UNIFORM = 5
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # RMGE_ORACLE_LIB names another build of the same source: the planted-mistake tests load a copy
+        # with one deliberate error there, to show that the pins catch it
+        path = os.environ.get("RMGE_ORACLE_LIB") or _build.build()
         L = C.CDLL(path)
         sig = {
             "orc_set_threads": (None, [C.c_int]),

@@ -109,6 +109,24 @@ def test_backward_error_definition_and_invariance(orc):
     assert np.max(np.sum(np.abs(dA), 1)) <= eta * an * (1 + 1e-9)
 
 
+def test_relative_residual_definition(orc):
+    """Sec. 7.1's relative residual ||A x - b||_2 / ||b||_2, the largest over the columns: closed forms
+    with a residual of known length, and invariance under scaling of the whole system."""
+    A = np.diag([2.0, 4.0, 1.0])
+    X = np.array([[1.0, 0.0], [1.0, 0.0], [1.0, 0.0]])
+    B = np.array([[2.0, 3.0], [7.0, 0.0], [1.0, 4.0]])  # residuals (0, 3, 0) and (3, 0, 4); ||b|| 7.348.., 5
+    assert orc.relative_residual(A, X, B) == pytest.approx(1.0, rel=1e-15)  # column 2: ||(3, 0, 4)|| / 5
+    assert orc.relative_residual(A, X[:, :1], B[:, :1]) == pytest.approx(3.0 / np.sqrt(54.0), rel=1e-15)
+    r = W.rng(9)
+    A = r.standard_normal((12, 12))
+    X = r.standard_normal((12, 2))
+    B = A @ X + 1e-6 * r.standard_normal((12, 2))
+    e = orc.relative_residual(A, X, B)
+    assert orc.relative_residual(3.0 * A, X, 3.0 * B) == pytest.approx(e, rel=1e-12)
+    ref = max(np.linalg.norm(A @ X[:, c] - B[:, c]) / np.linalg.norm(B[:, c]) for c in range(2))
+    assert e == pytest.approx(ref, rel=1e-6)
+
+
 def test_backward_error_flags_nonfinite(orc):
     A = np.eye(3)
     X = np.array([[1.0], [np.nan], [0.0]])
