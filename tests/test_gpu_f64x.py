@@ -113,16 +113,17 @@ def test_emulated_factor_matches_oracle_at_bench_size(orc):
     assert be <= 1e-13, be
 
 
-def test_paired_pivot_steps_match_oracle(orc):
+@pytest.mark.parametrize("n", [4352, 4200])
+def test_paired_pivot_steps_match_oracle(orc, n):
     """n = 4352: the first pivot steps go in pairs (a thin update of the next block column and row that
     factors the next pivot block, the next panel, then one 128-deep update of the rest by both steps),
-    the rest one by one (the trailing matrix falls below 4096 rows).  Against the oracle's unblocked GENP,
-    on the native FP64 yardstick as at the bench size, and a single system of a uniform batch gets the same
-    bits as the system alone."""
+    the rest one by one (the trailing matrix falls below 4096 rows).  n = 4200: one pair, whose 128-deep
+    update covers a 4072 x 4072 trailing matrix, a ragged edge of 104 rows and 40 columns in its last
+    tiles.  Against the oracle's unblocked GENP, on the native FP64 yardstick as at the bench size, and a
+    single system of a uniform batch gets the same bits as the system alone."""
     orc.set_threads(os.cpu_count() or 1)
-    n = 4352
-    A, _ = W.gaussian_system(n, 1, seed=4352 + 90)
-    G = W.gaussian_multiplier(n, 4352 + 91)
+    A, _ = W.gaussian_system(n, 1, seed=n + 90)
+    G = W.gaussian_multiplier(n, n + 91)
     M = orc.matmul(A, G)
     Md = dev(M)
     info, growth = rmge.factor(Md, "f64x")
@@ -144,11 +145,11 @@ def test_paired_pivot_steps_match_oracle(orc):
     assert np.array_equal(host(Mb)[1], LU)
 
 
-@pytest.mark.parametrize("digits", [4, 7])
-def test_paired_pivot_steps_exact_on_integer_factors(orc, digits):
-    """Integer L and U of a few bits at n = 4224, so that the paired 128-deep updates run: every intermediate
-    is an integer the digits hold exactly, so the factors come back bit for bit."""
-    n = 4224
+@pytest.mark.parametrize("n,digits", [(4224, 4), (4224, 7), (4200, 6)])
+def test_paired_pivot_steps_exact_on_integer_factors(orc, n, digits):
+    """Integer L and U of a few bits at n = 4224 and 4200 (a ragged 4072 x 4072 paired update), so that the
+    paired 128-deep updates run: every intermediate is an integer the digits hold exactly, so the factors
+    come back bit for bit."""
     r = W.rng(5000 + digits)
     L = np.tril(r.integers(-1, 2, (n, n)), -1).astype(np.float64) + np.eye(n)
     L[:, :] *= (np.abs(np.arange(n)[:, None] - np.arange(n)[None, :]) < 24)  # banded: small integers
